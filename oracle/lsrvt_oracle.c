@@ -1,0 +1,936 @@
+/*
+ * lsrvt_oracle.c -- plain, slow, single-threaded CPU oracle of the LSRVT hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code, header,
+ * table or constant generator with the CUDA library, and the CUDA library never
+ * calls it.
+ *
+ * Method: Neuroth et al., "Level Set Restricted Voronoi Tessellation for Large
+ * scale Spatial Statistical Analysis", arXiv 2208.06970.  Every function cites the
+ * section / equation / algorithm it follows.  Where the paper is silent, garbled or
+ * ambiguous the reading taken is stated beside the code (the same readings are
+ * listed in the design notes of the repository).
+ *
+ * Conventions: volume dims (nx, ny, nz), linear index i = x + nx*(y + ny*z), x fastest.
+ * All integer results are exact.  Floating point follows IEEE-754 single or double
+ * precision with round-to-nearest and no contraction (build with -ffp-contract=off).
+ *
+ * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fPIC -shared -o liboracle.so lsrvt_oracle.c -lm
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* return codes (oracle-private numbering) */
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOTSORTED -2
+#define ORC_ECAPACITY -3
+#define ORC_ENOMEM -4
+#define ORC_EOVERFLOW -5
+#define ORC_ENONFINITE -6
+
+#define INVALID_BAND 0xFF
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------------- */
+/* Isoband classification.  Sec. 3.1 "Level Sets, Isobands, and Connected    */
+/* Components": B_{a,b} = { v : a < f(v) <= b }.                             */
+/* Reading: isovalues t_1 < ... < t_K split the line into K+1 bands; band    */
+/* index = #{ i : t_i < f(v) }, so band 0 = (-inf, t_1] and band K = (t_K,   */
+/* inf).  NaN voxels are not graph nodes (the `node` bit of Sec. 3.2) and get */
+/* band 0xFF.                                                                 */
+/* ------------------------------------------------------------------------- */
+int orc_classify(const float *field, int64_t n, const float *iso, int32_t n_iso, uint8_t *band)
+{
+    if (n < 0 || n_iso < 0 || n_iso > 254) return ORC_EINVAL;
+    for (int32_t i = 0; i < n_iso; ++i)
+        if (isnan(iso[i])) return ORC_ENOTSORTED;
+    for (int32_t i = 1; i < n_iso; ++i)
+        if (!(iso[i - 1] < iso[i])) return ORC_ENOTSORTED;
+    for (int64_t v = 0; v < n; ++v) {
+        float f = field[v];
+        if (isnan(f)) { band[v] = INVALID_BAND; continue; }
+        int b = 0;
+        for (int32_t i = 0; i < n_iso; ++i)
+            if (iso[i] < f) ++b;
+        band[v] = (uint8_t)b;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Connected components of each isoband.  Sec. 3.1: an isoband is the union   */
+/* of components C^k such that no voxel of one is adjacent to a voxel of      */
+/* another.  Reading: 6-adjacency.  The paper fixes no labelling, so ids are  */
+/* made canonical: ordered by (band, smallest linear index in the component). */
+/* Algorithm: breadth-first flood fill started from voxels in linear order.   */
+/* ------------------------------------------------------------------------- */
+int orc_label_components(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+                         int32_t *comp, uint8_t *comp_band, int64_t *comp_size,
+                         int32_t *comp_first, int32_t max_comp, int32_t *n_comp_out)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0) return ORC_EINVAL;
+    int64_t n = (int64_t)nx * ny * nz;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *raw_first = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!queue || !raw_first) { free(queue); free(raw_first); return ORC_ENOMEM; }
+    for (int64_t v = 0; v < n; ++v) comp[v] = -1;
+    int32_t n_raw = 0;
+    /* pass 1: raw ids in order of discovery = order of smallest linear index */
+    for (int64_t s = 0; s < n; ++s) {
+        if (band[s] == INVALID_BAND || comp[s] >= 0) continue;
+        int32_t id = n_raw++;
+        raw_first[id] = (int32_t)s;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = (int32_t)s;
+        comp[s] = id;
+        while (head < tail) {
+            int32_t v = queue[head++];
+            int32_t x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+            int32_t nb[6]; int k = 0;
+            if (x > 0) nb[k++] = v - 1;
+            if (x < nx - 1) nb[k++] = v + 1;
+            if (y > 0) nb[k++] = v - nx;
+            if (y < ny - 1) nb[k++] = v + nx;
+            if (z > 0) nb[k++] = v - nx * ny;
+            if (z < nz - 1) nb[k++] = v + nx * ny;
+            for (int i = 0; i < k; ++i) {
+                int32_t u = nb[i];
+                if (comp[u] < 0 && band[u] == band[s]) { comp[u] = id; queue[tail++] = u; }
+            }
+        }
+    }
+    /* pass 2: stable re-numbering by band */
+    int64_t band_count[256];
+    memset(band_count, 0, sizeof(band_count));
+    for (int32_t r = 0; r < n_raw; ++r) band_count[band[raw_first[r]]]++;
+    int64_t band_off[256];
+    int64_t acc = 0;
+    for (int b = 0; b < 256; ++b) { band_off[b] = acc; acc += band_count[b]; }
+    int32_t *remap = queue; /* reuse */
+    for (int32_t r = 0; r < n_raw; ++r) remap[r] = (int32_t)(band_off[band[raw_first[r]]]++);
+    *n_comp_out = n_raw;
+    int over = n_raw > max_comp;
+    for (int64_t v = 0; v < n; ++v)
+        if (comp[v] >= 0) comp[v] = remap[comp[v]];
+    if (!over) {
+        for (int32_t r = 0; r < n_raw; ++r) {
+            int32_t c = remap[r];
+            comp_band[c] = band[raw_first[r]];
+            comp_first[c] = raw_first[r];
+            comp_size[c] = 0;
+        }
+        for (int64_t v = 0; v < n; ++v)
+            if (comp[v] >= 0) comp_size[comp[v]]++;
+    }
+    free(queue); free(raw_first);
+    return over ? ORC_ECAPACITY : ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Saliency weights m_v.  Sec. 3.1 "Centroids" (m_v, the weighting function)  */
+/* and Sec. 3.3 "Role and Choice of Parameters" (the second field, attraction */
+/* gamma).  The paper gives no formula; reading: m_v = |grad f|^gamma with    */
+/* central differences (one-sided half differences at the faces), evaluated   */
+/* in float in the order written below, then quantised to 16-bit integers     */
+/* q = max(1, rint(g^gamma * 65535/gmax)).  gamma must be an integer 0..4.    */
+/* ------------------------------------------------------------------------- */
+int orc_saliency(const float *f, int32_t nx, int32_t ny, int32_t nz, int32_t gamma, uint16_t *q)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || gamma < 0 || gamma > 4) return ORC_EINVAL;
+    int64_t n = (int64_t)nx * ny * nz;
+    if (gamma == 0) { for (int64_t v = 0; v < n; ++v) q[v] = 1; return ORC_OK; }
+    float *gp = (float *)malloc(sizeof(float) * (size_t)n);
+    if (!gp) return ORC_ENOMEM;
+    float gmax = 0.0f;
+    for (int32_t z = 0; z < nz; ++z)
+        for (int32_t y = 0; y < ny; ++y)
+            for (int32_t x = 0; x < nx; ++x) {
+                int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+                int32_t xm = x > 0 ? x - 1 : 0, xp = x < nx - 1 ? x + 1 : nx - 1;
+                int32_t ym = y > 0 ? y - 1 : 0, yp = y < ny - 1 ? y + 1 : ny - 1;
+                int32_t zm = z > 0 ? z - 1 : 0, zp = z < nz - 1 ? z + 1 : nz - 1;
+                float fxp = f[xp + (int64_t)nx * (y + (int64_t)ny * z)];
+                float fxm = f[xm + (int64_t)nx * (y + (int64_t)ny * z)];
+                float fyp = f[x + (int64_t)nx * (yp + (int64_t)ny * z)];
+                float fym = f[x + (int64_t)nx * (ym + (int64_t)ny * z)];
+                float fzp = f[x + (int64_t)nx * (y + (int64_t)ny * zp)];
+                float fzm = f[x + (int64_t)nx * (y + (int64_t)ny * zm)];
+                float dx = 0.5f * (fxp - fxm);
+                float dy = 0.5f * (fyp - fym);
+                float dz = 0.5f * (fzp - fzm);
+                float s = dx * dx;
+                s = s + dy * dy;
+                s = s + dz * dz;
+                float g = sqrtf(s);
+                float p = g;
+                for (int32_t k = 1; k < gamma; ++k) p = p * g;
+                gp[v] = p;
+                if (isfinite(p) && p > gmax) gmax = p;
+            }
+    float scale = gmax > 0.0f ? 65535.0f / gmax : 0.0f;
+    for (int64_t v = 0; v < n; ++v) {
+        float p = gp[v];
+        float t = p * scale;
+        uint16_t w = 1;
+        if (isfinite(p) && t >= 0.5f) {
+            float r = rintf(t); /* round half to even */
+            if (r > 65535.0f) r = 65535.0f;
+            w = (uint16_t)r;
+            if (w < 1) w = 1;
+        }
+        q[v] = w;
+    }
+    free(gp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number       */
+/* generators", OOPSLA 2014): one step of the generator whose state advances  */
+/* by the golden gamma 0x9e3779b97f4a7c15, i.e. the output for state x.       */
+/* ------------------------------------------------------------------------- */
+uint64_t orc_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+typedef struct { int32_t comp; int32_t block; int64_t k; uint64_t m; int64_t nb; } orc_stratum;
+
+static int stratum_cmp(const void *a, const void *b)
+{
+    const orc_stratum *p = (const orc_stratum *)a, *r = (const orc_stratum *)b;
+    if (p->comp != r->comp) return p->comp < r->comp ? -1 : 1;
+    if (p->block != r->block) return p->block < r->block ? -1 : 1;
+    return 0;
+}
+
+/* Apportion n sites over the strata st[0..ns) of one component.  Sec. 3.2     */
+/* "Stratified Random Initial Site Distribution": first floor(n m_b / m_C) per */
+/* stratum, then the remainder to the most under-represented strata.  The      */
+/* printed ur(b) is garbled (it equals 1 for every stratum after the first    */
+/* pass); reading: largest remainder (Hamilton) -- the remaining sites go one */
+/* each to the strata with the largest (n m_b) mod m_C, ties to the lower     */
+/* stratum position.  A stratum never receives more sites than voxels: if a   */
+/* stratum exceeds its voxel count it is capped and the surplus is             */
+/* re-apportioned by the same rule over the strata not yet capped.             */
+static void apportion(orc_stratum *st, int64_t ns, int64_t n)
+{
+    uint8_t *capped = (uint8_t *)calloc((size_t)ns, 1);
+    u128 *rem = (u128 *)malloc(sizeof(u128) * (size_t)ns);
+    uint8_t *chosen = (uint8_t *)calloc((size_t)ns, 1);
+    for (int64_t i = 0; i < ns; ++i) st[i].nb = 0;
+    for (;;) {
+        int64_t assigned = 0;
+        for (int64_t i = 0; i < ns; ++i) assigned += st[i].nb;
+        int64_t remaining = n - assigned;
+        if (remaining <= 0) break;
+        u128 mA = 0;
+        for (int64_t i = 0; i < ns; ++i) if (!capped[i]) mA += st[i].m;
+        if (mA == 0) break; /* cannot happen: q >= 1 */
+        int64_t given = 0;
+        for (int64_t i = 0; i < ns; ++i) {
+            chosen[i] = 0;
+            if (capped[i]) continue;
+            u128 prod = (u128)(uint64_t)remaining * st[i].m;
+            int64_t fl = (int64_t)(prod / mA);
+            rem[i] = prod % mA;
+            st[i].nb += fl;
+            given += fl;
+        }
+        int64_t left = remaining - given;
+        /* hand out `left` single sites by (remainder desc, position asc) */
+        for (int64_t t = 0; t < left; ++t) {
+            int64_t best = -1;
+            for (int64_t i = 0; i < ns; ++i) {
+                if (capped[i] || chosen[i]) continue;
+                if (best < 0 || rem[i] > rem[best]) best = i;
+            }
+            if (best < 0) break;
+            chosen[best] = 1;
+            st[best].nb += 1;
+        }
+        int any = 0;
+        for (int64_t i = 0; i < ns; ++i)
+            if (!capped[i] && st[i].nb > st[i].k) { st[i].nb = st[i].k; capped[i] = 1; any = 1; }
+        if (!any) break;
+    }
+    free(capped); free(rem); free(chosen);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initial sites.  Sec. 3.2 "Stratified Random Initial Site Distribution",    */
+/* Eq. (nc), Algorithm 1 (StratifiedRandomSiteDistribution).                  */
+/* Eq. (nc) as printed reduces to ceil(alpha); reading (alpha = ratio of      */
+/* sites to voxels, Sec. 3.3): n_c = max(ceil(|V| m(C) / (P m(V))), 1),        */
+/* capped at |C|, with P = 1/alpha voxels per site, |V| the valid voxels and  */
+/* m(.) the sum of the weights q.  Strata = component x cubic block of side   */
+/* `sb` aligned to the origin; block index = linear index of the block.       */
+/* Placement (the paper only says "random"): the stratum's k voxels in linear */
+/* order are split into n_b contiguous rank ranges [floor(jk/n), floor((j+1)k */
+/* /n)); site j takes rank lo_j + h_j mod (hi_j - lo_j) with                  */
+/* h_j = splitmix64((seed ^ splitmix64(block)) + j).                           */
+/* Site ids are ordered by (component, block, j).                             */
+/* ------------------------------------------------------------------------- */
+int orc_seed(const int32_t *comp, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+             int32_t n_comp, int64_t voxels_per_site, int32_t sb, uint64_t seed,
+             int32_t *site_pos, int32_t *site_comp, int32_t *comp_site_off,
+             int32_t max_sites, int32_t *n_sites_out, int64_t *n_site_comp /* nullable, n_c per comp */)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || voxels_per_site < 1 || sb < 1 || n_comp < 0) return ORC_EINVAL;
+    int64_t n = (int64_t)nx * ny * nz;
+    int64_t *csize = (int64_t *)calloc((size_t)(n_comp + 1), sizeof(int64_t));
+    uint64_t *cmass = (uint64_t *)calloc((size_t)(n_comp + 1), sizeof(uint64_t));
+    int64_t *nc = (int64_t *)calloc((size_t)(n_comp + 1), sizeof(int64_t));
+    if (!csize || !cmass || !nc) { free(csize); free(cmass); free(nc); return ORC_ENOMEM; }
+    int64_t nV = 0; uint64_t mV = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t c = comp[v];
+        if (c < 0) continue;
+        if (c >= n_comp) { free(csize); free(cmass); free(nc); return ORC_EINVAL; }
+        uint64_t w = q ? q[v] : 1;
+        nV++; mV += w; csize[c]++; cmass[c] += w;
+    }
+    for (int32_t c = 0; c < n_comp; ++c) {
+        u128 num = (u128)(uint64_t)nV * cmass[c];
+        u128 den = (u128)(uint64_t)voxels_per_site * mV;
+        int64_t k = den ? (int64_t)((num + den - 1) / den) : 1;
+        if (k < 1) k = 1;
+        if (k > csize[c]) k = csize[c];
+        nc[c] = k;
+        if (n_site_comp) n_site_comp[c] = k;
+    }
+    /* enumerate strata block by block */
+    int32_t nbx = (nx + sb - 1) / sb, nby = (ny + sb - 1) / sb, nbz = (nz + sb - 1) / sb;
+    int64_t cap = 1024, ns = 0;
+    orc_stratum *st = (orc_stratum *)malloc(sizeof(orc_stratum) * (size_t)cap);
+    for (int32_t bz = 0; bz < nbz; ++bz)
+        for (int32_t by = 0; by < nby; ++by)
+            for (int32_t bx = 0; bx < nbx; ++bx) {
+                int32_t b = bx + nbx * (by + nby * bz);
+                int64_t first = ns;
+                for (int32_t z = bz * sb; z < nz && z < (bz + 1) * sb; ++z)
+                    for (int32_t y = by * sb; y < ny && y < (by + 1) * sb; ++y)
+                        for (int32_t x = bx * sb; x < nx && x < (bx + 1) * sb; ++x) {
+                            int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+                            int32_t c = comp[v];
+                            if (c < 0) continue;
+                            int64_t i;
+                            for (i = first; i < ns; ++i) if (st[i].comp == c) break;
+                            if (i == ns) {
+                                if (ns == cap) { cap *= 2; st = (orc_stratum *)realloc(st, sizeof(orc_stratum) * (size_t)cap); }
+                                st[ns].comp = c; st[ns].block = b; st[ns].k = 0; st[ns].m = 0; st[ns].nb = 0;
+                                ++ns;
+                            }
+                            st[i].k++;
+                            st[i].m += q ? q[v] : 1;
+                        }
+            }
+    qsort(st, (size_t)ns, sizeof(orc_stratum), stratum_cmp);
+    /* apportion per component */
+    int64_t i0 = 0;
+    while (i0 < ns) {
+        int64_t i1 = i0;
+        while (i1 < ns && st[i1].comp == st[i0].comp) ++i1;
+        apportion(st + i0, i1 - i0, nc[st[i0].comp]);
+        i0 = i1;
+    }
+    int64_t total = 0;
+    for (int64_t i = 0; i < ns; ++i) total += st[i].nb;
+    *n_sites_out = (int32_t)(total > 0x7fffffff ? 0x7fffffff : total);
+    if (total > max_sites) { free(st); free(csize); free(cmass); free(nc); return ORC_ECAPACITY; }
+    /* comp_site_off */
+    {
+        int64_t acc = 0;
+        int64_t j = 0;
+        for (int32_t c = 0; c < n_comp; ++c) {
+            comp_site_off[c] = (int32_t)acc;
+            while (j < ns && st[j].comp == c) { acc += st[j].nb; ++j; }
+        }
+        comp_site_off[n_comp] = (int32_t)acc;
+    }
+    /* placement */
+    int32_t *vox = (int32_t *)malloc(sizeof(int32_t) * (size_t)sb * sb * sb);
+    int64_t sid = 0;
+    for (int64_t i = 0; i < ns; ++i) {
+        int32_t b = st[i].block, c = st[i].comp;
+        int32_t bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+        int64_t k = 0;
+        for (int32_t z = bz * sb; z < nz && z < (bz + 1) * sb; ++z)
+            for (int32_t y = by * sb; y < ny && y < (by + 1) * sb; ++y)
+                for (int32_t x = bx * sb; x < nx && x < (bx + 1) * sb; ++x) {
+                    int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    if (comp[v] == c) vox[k++] = (int32_t)v;
+                }
+        uint64_t hb = seed ^ orc_splitmix64((uint64_t)b);
+        int64_t nb = st[i].nb;
+        for (int64_t j = 0; j < nb; ++j) {
+            uint64_t lo = (uint64_t)j * (uint64_t)k / (uint64_t)nb;
+            uint64_t hi = (uint64_t)(j + 1) * (uint64_t)k / (uint64_t)nb;
+            uint64_t h = orc_splitmix64(hb + (uint64_t)j);
+            uint64_t r = lo + h % (hi - lo);
+            site_pos[sid] = vox[r];
+            site_comp[sid] = c;
+            ++sid;
+        }
+    }
+    free(vox); free(st); free(csize); free(cmass); free(nc);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Restricted graph.  Eq. 1 and Sec. 3.2 "Discrete Restricted Geodesic        */
+/* Voronoi Tessellation": voxels are nodes and no edge crosses a boundary.    */
+/* Reading: an edge joins 26-neighbours u, v when every voxel of the          */
+/* axis-aligned box spanned by u and v has the band of v (so no edge cuts a   */
+/* level set, and the edge graph's components are the 6-connected ones).     */
+/* Edge lengths are the Euclidean lengths in 16.16 fixed point, rounded up.   */
+/* ------------------------------------------------------------------------- */
+#define W_FACE 65536u
+#define W_EDGE 92682u
+#define W_CORNER 113512u
+
+static uint32_t edge_weight(int dx, int dy, int dz)
+{
+    int k = (dx != 0) + (dy != 0) + (dz != 0);
+    return k == 1 ? W_FACE : (k == 2 ? W_EDGE : W_CORNER);
+}
+
+/* does the edge v -> v+(dx,dy,dz) exist?  (x,y,z) = coords of v */
+static int has_edge(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+                    int32_t x, int32_t y, int32_t z, int dx, int dy, int dz)
+{
+    int32_t ux = x + dx, uy = y + dy, uz = z + dz;
+    if (ux < 0 || ux >= nx || uy < 0 || uy >= ny || uz < 0 || uz >= nz) return 0;
+    uint8_t b = band[x + (int64_t)nx * (y + (int64_t)ny * z)];
+    if (b == INVALID_BAND) return 0;
+    for (int az = 0; az <= (dz != 0); ++az)
+        for (int ay = 0; ay <= (dy != 0); ++ay)
+            for (int ax = 0; ax <= (dx != 0); ++ax) {
+                int32_t px = x + ax * dx, py = y + ay * dy, pz = z + az * dz;
+                if (band[px + (int64_t)nx * (py + (int64_t)ny * pz)] != b) return 0;
+            }
+    return 1;
+}
+
+/* binary heap of (dist, site, voxel), lexicographic */
+typedef struct { uint64_t d; int32_t s; int32_t v; } hent;
+typedef struct { hent *a; int64_t n, cap; } heap;
+
+static int hless(const hent *p, const hent *q)
+{
+    if (p->d != q->d) return p->d < q->d;
+    if (p->s != q->s) return p->s < q->s;
+    return p->v < q->v;
+}
+
+static int hpush(heap *h, hent e)
+{
+    if (h->n == h->cap) {
+        int64_t nc = h->cap ? h->cap * 2 : 1024;
+        hent *na = (hent *)realloc(h->a, sizeof(hent) * (size_t)nc);
+        if (!na) return ORC_ENOMEM;
+        h->a = na; h->cap = nc;
+    }
+    int64_t i = h->n++;
+    h->a[i] = e;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!hless(&h->a[i], &h->a[p])) break;
+        hent t = h->a[i]; h->a[i] = h->a[p]; h->a[p] = t;
+        i = p;
+    }
+    return ORC_OK;
+}
+
+static hent hpop(heap *h)
+{
+    hent top = h->a[0];
+    h->a[0] = h->a[--h->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < h->n && hless(&h->a[l], &h->a[m])) m = l;
+        if (r < h->n && hless(&h->a[r], &h->a[m])) m = r;
+        if (m == i) break;
+        hent t = h->a[i]; h->a[i] = h->a[m]; h->a[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Restricted geodesic Voronoi assignment, Eq. 1: each voxel v of component C */
+/* belongs to the site of S_C with the smallest graph-geodesic distance.      */
+/* Ties (equal distance) go to the lowest site id, so the label is the        */
+/* lexicographic minimum of (gd, site).  Multi-source Dijkstra on             */
+/* (distance, site).  Unreached / invalid voxels: cell -1, dist 0xFFFFFFFF.   */
+/* Distances are 16.16 fixed point and must stay below 2^32.                  */
+/* ------------------------------------------------------------------------- */
+int orc_assign(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+               const int32_t *site_pos, int32_t n_sites, int32_t *cell, uint32_t *dist)
+{
+    int64_t n = (int64_t)nx * ny * nz;
+    uint64_t *kd = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    if (!kd) return ORC_ENOMEM;
+    for (int64_t v = 0; v < n; ++v) { kd[v] = UINT64_MAX; cell[v] = -1; }
+    heap h = {0, 0, 0};
+    int rc = ORC_OK;
+    for (int32_t s = 0; s < n_sites; ++s) {
+        int32_t p = site_pos[s];
+        if (p < 0 || p >= n || band[p] == INVALID_BAND) { rc = ORC_EINVAL; goto done; }
+        if (kd[p] == 0 && cell[p] <= s) continue; /* lower id already there */
+        kd[p] = 0; cell[p] = s;
+        hent e = {0, s, p};
+        if (hpush(&h, e)) { rc = ORC_ENOMEM; goto done; }
+    }
+    while (h.n > 0) {
+        hent e = hpop(&h);
+        if (e.d != kd[e.v] || e.s != cell[e.v]) continue; /* stale */
+        int32_t v = e.v, x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!dx && !dy && !dz) continue;
+                    if (!has_edge(band, nx, ny, nz, x, y, z, dx, dy, dz)) continue;
+                    int64_t u = (x + dx) + (int64_t)nx * ((y + dy) + (int64_t)ny * (z + dz));
+                    uint64_t nd = e.d + edge_weight(dx, dy, dz);
+                    if (nd > 0xFFFFFFFFull) { rc = ORC_EOVERFLOW; goto done; }
+                    if (nd < kd[u] || (nd == kd[u] && e.s < cell[u])) {
+                        kd[u] = nd; cell[u] = e.s;
+                        hent f = {nd, e.s, (int32_t)u};
+                        if (hpush(&h, f)) { rc = ORC_ENOMEM; goto done; }
+                    }
+                }
+    }
+    for (int64_t v = 0; v < n; ++v) dist[v] = kd[v] == UINT64_MAX ? 0xFFFFFFFFu : (uint32_t)kd[v];
+done:
+    free(h.a); free(kd);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Discrete line of sight.  Eq. 2 (los(v, s)) and Sec. 3.2 "Geodesically      */
+/* Weighted Voronoi Site Update" (ray cast toward the centroid).  Reading:    */
+/* the 6-connected voxel traversal of Amanatides & Woo (1987) of the segment  */
+/* joining the centres of voxels a and b, walked from a toward b.  The k-th   */
+/* crossing on axis i happens at t = (2k-1) / (2|d_i|); the next axis to step */
+/* is the one with the earliest crossing, compared exactly by cross-          */
+/* multiplication; simultaneous crossings step x, then y, then z.             */
+/* walk_traversal returns the number of steps taken before the first voxel   */
+/* whose band differs from `b` (all steps if none), and the reached voxel.    */
+/* ------------------------------------------------------------------------- */
+static int64_t walk_traversal(const uint8_t *band, int32_t nx, int32_t ny,
+                              int32_t ax0, int32_t ay0, int32_t az0,
+                              int32_t bx, int32_t by, int32_t bz, uint8_t b,
+                              int32_t *ex, int32_t *ey, int32_t *ez)
+{
+    int64_t d[3] = {bx - ax0, by - ay0, bz - az0};
+    int64_t A[3], S[3], k[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) { A[i] = d[i] < 0 ? -d[i] : d[i]; S[i] = d[i] < 0 ? -1 : 1; }
+    int32_t p[3] = {ax0, ay0, az0};
+    int64_t steps = 0;
+    for (;;) {
+        int best = -1;
+        for (int i = 0; i < 3; ++i) {
+            if (k[i] >= A[i]) continue;
+            if (best < 0) { best = i; continue; }
+            /* t_i = (2k_i+1)/(2A_i) < t_best = (2k_b+1)/(2A_b) ? (strictly earlier wins; ties keep lower axis) */
+            if ((2 * k[i] + 1) * A[best] < (2 * k[best] + 1) * A[i]) best = i;
+        }
+        if (best < 0) break;
+        int32_t np[3] = {p[0], p[1], p[2]};
+        np[best] += (int32_t)S[best];
+        if (band[np[0] + (int64_t)nx * (np[1] + (int64_t)ny * np[2])] != b) break;
+        p[0] = np[0]; p[1] = np[1]; p[2] = np[2];
+        k[best]++;
+        steps++;
+    }
+    *ex = p[0]; *ey = p[1]; *ez = p[2];
+    return steps;
+}
+
+int orc_los(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+            int32_t v, int32_t s)
+{
+    (void)nz;
+    int32_t vx = v % nx, vy = (v / nx) % ny, vz = v / (nx * ny);
+    int32_t sx = s % nx, sy = (s / nx) % ny, sz = s / (nx * ny);
+    int32_t ex, ey, ez;
+    int64_t need = (int64_t)abs(sx - vx) + abs(sy - vy) + abs(sz - vz);
+    int64_t got = walk_traversal(band, nx, ny, vx, vy, vz, sx, sy, sz, band[v], &ex, &ey, &ez);
+    return got == need;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geodesically weighted site update, Eq. 2 and Sec. 3.2 "Geodesically        */
+/* Weighted Voronoi Site Update".                                             */
+/*  parent(v) (the src map of Sec. 3.2): reading -- the first 26-neighbour u  */
+/*   in offset order (dz,dy,dx) = (-1,-1,-1) ... (1,1,1) with an edge to v,    */
+/*   the same site, and D(u) + w(u,v) = D(v); a site voxel is its own parent. */
+/*  phi(v) = v if los(v, site(v)) else phi(parent(v))            (Eq. 2)     */
+/*  x'_c = sum_v m_v x_phi(v) / sum_v m_v   (integer sums, exact)  (Eq. 2)     */
+/*  target = per-axis floor((2 S + M) / (2 M))  (round half up)               */
+/*  move: walk the traversal from the site toward the target and stop at the */
+/*   last voxel of the site's band (move only as far as possible before      */
+/*   crossing the boundary).  Cells with M = 0 do not move.                   */
+/* stats[0] = sites moved, stats[1] = sum of squared displacements.           */
+/* parent_out / los_out / phi_out / sums_out are optional (NULL) diagnostics. */
+/* ------------------------------------------------------------------------- */
+int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+               const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
+               int32_t *new_pos, int64_t *stats,
+               int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
+{
+    int64_t n = (int64_t)nx * ny * nz;
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int8_t *los = (int8_t *)malloc((size_t)n);
+    int32_t *phi = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *S = (int64_t *)calloc((size_t)n_sites * 4 + 1, sizeof(int64_t));
+    if (!parent || !los || !phi || !S) { free(parent); free(los); free(phi); free(S); return ORC_ENOMEM; }
+    int rc = ORC_OK;
+    for (int64_t v = 0; v < n; ++v) {
+        parent[v] = -1; los[v] = 0; phi[v] = -1;
+        int32_t s = cell[v];
+        if (s < 0) continue;
+        int32_t x = (int32_t)(v % nx), y = (int32_t)((v / nx) % ny), z = (int32_t)(v / ((int64_t)nx * ny));
+        if (dist[v] == 0) { parent[v] = (int32_t)v; }
+        else {
+            for (int dz = -1; dz <= 1 && parent[v] < 0; ++dz)
+                for (int dy = -1; dy <= 1 && parent[v] < 0; ++dy)
+                    for (int dx = -1; dx <= 1 && parent[v] < 0; ++dx) {
+                        if (!dx && !dy && !dz) continue;
+                        if (!has_edge(band, nx, ny, nz, x, y, z, dx, dy, dz)) continue;
+                        int64_t u = (x + dx) + (int64_t)nx * ((y + dy) + (int64_t)ny * (z + dz));
+                        if (cell[u] != s) continue;
+                        if ((uint64_t)dist[u] + edge_weight(dx, dy, dz) == (uint64_t)dist[v]) parent[v] = (int32_t)u;
+                    }
+            if (parent[v] < 0) { rc = ORC_EINVAL; goto done; } /* not a shortest-path labelling */
+        }
+        los[v] = (int8_t)orc_los(band, nx, ny, nz, (int32_t)v, site_pos[s]);
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        if (cell[v] < 0) continue;
+        int64_t u = v;
+        int64_t guard = 0;
+        while (!los[u]) {
+            u = parent[u];
+            if (++guard > n) { rc = ORC_EINVAL; goto done; }
+        }
+        phi[v] = (int32_t)u;
+        int64_t w = q ? q[v] : 1;
+        int32_t s = cell[v];
+        int64_t px = u % nx, py = (u / nx) % ny, pz = u / ((int64_t)nx * ny);
+        S[4 * s + 0] += w * px;
+        S[4 * s + 1] += w * py;
+        S[4 * s + 2] += w * pz;
+        S[4 * s + 3] += w;
+    }
+    int64_t moved = 0, sumsq = 0;
+    for (int32_t s = 0; s < n_sites; ++s) {
+        int32_t p = site_pos[s];
+        int32_t x = p % nx, y = (p / nx) % ny, z = p / (nx * ny);
+        int64_t M = S[4 * s + 3];
+        int32_t nxp = x, nyp = y, nzp = z;
+        if (M > 0) {
+            int32_t tx = (int32_t)((2 * S[4 * s + 0] + M) / (2 * M));
+            int32_t ty = (int32_t)((2 * S[4 * s + 1] + M) / (2 * M));
+            int32_t tz = (int32_t)((2 * S[4 * s + 2] + M) / (2 * M));
+            walk_traversal(band, nx, ny, x, y, z, tx, ty, tz, band[p], &nxp, &nyp, &nzp);
+        }
+        new_pos[s] = nxp + nx * (nyp + ny * nzp);
+        if (new_pos[s] != p) {
+            moved++;
+            int64_t ddx = nxp - x, ddy = nyp - y, ddz = nzp - z;
+            sumsq += ddx * ddx + ddy * ddy + ddz * ddz;
+        }
+    }
+    stats[0] = moved; stats[1] = sumsq;
+    if (parent_out) memcpy(parent_out, parent, sizeof(int32_t) * (size_t)n);
+    if (los_out) for (int64_t v = 0; v < n; ++v) los_out[v] = (uint8_t)los[v];
+    if (phi_out) memcpy(phi_out, phi, sizeof(int32_t) * (size_t)n);
+    if (sums_out) memcpy(sums_out, S, sizeof(int64_t) * (size_t)n_sites * 4);
+done:
+    free(parent); free(los); free(phi); free(S);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 1 (LRCVT) after seeding: n_iters x (restricted geodesic VT,      */
+/* geodesically weighted update), then a final VT.  The paper loops until    */
+/* converged (mean d_s below a tolerance, Fig. "scaling"/Table 1); here the  */
+/* count is given.  trace[2*it] = sites moved, trace[2*it+1] = sum |dx|^2.    */
+/* ------------------------------------------------------------------------- */
+int orc_cvt_iterate(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+                    int32_t *site_pos, int32_t n_sites, int32_t n_iters,
+                    int32_t *cell, uint32_t *dist, int64_t *trace)
+{
+    int32_t *np = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_sites > 0 ? n_sites : 1));
+    if (!np) return ORC_ENOMEM;
+    int rc = ORC_OK;
+    for (int32_t it = 0; it < n_iters; ++it) {
+        rc = orc_assign(band, nx, ny, nz, site_pos, n_sites, cell, dist);
+        if (rc) goto done;
+        int64_t st[2];
+        rc = orc_update(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, np, st, 0, 0, 0, 0);
+        if (rc) goto done;
+        memcpy(site_pos, np, sizeof(int32_t) * (size_t)n_sites);
+        if (trace) { trace[2 * it] = st[0]; trace[2 * it + 1] = st[1]; }
+    }
+    rc = orc_assign(band, nx, ny, nz, site_pos, n_sites, cell, dist);
+done:
+    free(np);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-variable value range over valid voxels (cell >= 0), used as the        */
+/* default histogram range, and the float bin scale B / (hi - lo).            */
+/* ------------------------------------------------------------------------- */
+int orc_aux_range(const int32_t *cell, const float *aux, int32_t m, int64_t n, int32_t n_bins,
+                  float *lo, float *hi, float *scale)
+{
+    for (int32_t j = 0; j < m; ++j) {
+        float a = INFINITY, b = -INFINITY;
+        const float *x = aux + (int64_t)j * n;
+        for (int64_t v = 0; v < n; ++v) {
+            if (cell[v] < 0) continue;
+            if (!isfinite(x[v])) return ORC_ENONFINITE;
+            if (x[v] < a) a = x[v];
+            if (x[v] > b) b = x[v];
+        }
+        if (a > b) { a = 0.0f; b = 0.0f; }
+        lo[j] = a; hi[j] = b;
+        float w = b - a;
+        scale[j] = (w > 0.0f) ? (float)n_bins / w : 0.0f;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Statistical aggregation per Voronoi cell.  Sec. 3.3 "Aggregation" and the  */
+/* introduction (statistics aggregated within segments, e.g. histograms and  */
+/* Gaussians).  Per cell s and variable j: count, mean, M2 = sum (x-mean)^2   */
+/* (population variance = M2 / n), min, max, an n_bins histogram on          */
+/* [lo_j, lo_j + n_bins/scale_j] with bin = (int)((x - lo) * scale) clamped,  */
+/* and optionally the co-moment sums C_ij = sum (x_i-mean_i)(x_j-mean_j)      */
+/* (upper triangle, row-major).  Two passes, FP64: the textbook definition.  */
+/* Empty cells: count 0, mean 0, M2 0, min +inf, max -inf.                    */
+/* ------------------------------------------------------------------------- */
+int orc_aggregate(const int32_t *cell, const float *aux, int32_t m, int64_t n, int32_t n_cells,
+                  const float *lo, const float *scale, int32_t n_bins, int32_t want_cov,
+                  int64_t *count, double *mean, double *m2, float *vmin, float *vmax,
+                  uint32_t *hist, double *comom)
+{
+    int32_t T = m * (m + 1) / 2;
+    for (int32_t s = 0; s < n_cells; ++s) {
+        count[s] = 0;
+        for (int32_t j = 0; j < m; ++j) {
+            mean[(int64_t)s * m + j] = 0.0; m2[(int64_t)s * m + j] = 0.0;
+            vmin[(int64_t)s * m + j] = INFINITY; vmax[(int64_t)s * m + j] = -INFINITY;
+            for (int32_t b = 0; b < n_bins; ++b) hist[((int64_t)s * m + j) * n_bins + b] = 0;
+        }
+        if (want_cov) for (int32_t t = 0; t < T; ++t) comom[(int64_t)s * T + t] = 0.0;
+    }
+    double *sum = (double *)calloc((size_t)n_cells * (size_t)(m > 0 ? m : 1), sizeof(double));
+    if (!sum) return ORC_ENOMEM;
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t s = cell[v];
+        if (s < 0) continue;
+        if (s >= n_cells) { free(sum); return ORC_EINVAL; }
+        count[s]++;
+        for (int32_t j = 0; j < m; ++j) {
+            float x = aux[(int64_t)j * n + v];
+            if (!isfinite(x)) { free(sum); return ORC_ENONFINITE; }
+            int64_t k = (int64_t)s * m + j;
+            sum[k] += (double)x;
+            if (x < vmin[k]) vmin[k] = x;
+            if (x > vmax[k]) vmax[k] = x;
+            if (n_bins > 0) {
+                float t = (x - lo[j]) * scale[j];
+                int32_t bin;
+                if (!(t > 0.0f)) bin = 0;
+                else if (t >= (float)n_bins) bin = n_bins - 1;
+                else bin = (int32_t)t;
+                hist[k * n_bins + bin]++;
+            }
+        }
+    }
+    for (int32_t s = 0; s < n_cells; ++s)
+        for (int32_t j = 0; j < m; ++j)
+            if (count[s] > 0) mean[(int64_t)s * m + j] = sum[(int64_t)s * m + j] / (double)count[s];
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t s = cell[v];
+        if (s < 0) continue;
+        int32_t t = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            double di = (double)aux[(int64_t)i * n + v] - mean[(int64_t)s * m + i];
+            m2[(int64_t)s * m + i] += di * di;
+            if (want_cov)
+                for (int32_t j = i; j < m; ++j) {
+                    double dj = (double)aux[(int64_t)j * n + v] - mean[(int64_t)s * m + j];
+                    comom[(int64_t)s * T + t] += di * dj;
+                    ++t;
+                }
+        }
+    }
+    free(sum);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Merging statistics up the hierarchy cell -> component -> isoband ->        */
+/* volume (introduction: aggregations may be merged over cells, components   */
+/* and isobands).  Pairwise update of Chan, Golub & LeVeque (1979) in FP64,   */
+/* merging children in increasing id order:                                   */
+/*   n = na + nb, d = mean_b - mean_a, mean = mean_a + d nb / n,              */
+/*   M2 = M2a + M2b + d^2 na nb / n, C_ij = Ca + Cb + d_i d_j na nb / n.       */
+/* Counts, histograms, min and max combine exactly.  `parent` maps each of    */
+/* the n_child records to its parent record in [0, n_parent).                  */
+/* ------------------------------------------------------------------------- */
+int orc_merge(int32_t n_child, const int32_t *parent, int32_t n_parent, int32_t m, int32_t n_bins, int32_t want_cov,
+              const int64_t *c_count, const double *c_mean, const double *c_m2, const float *c_min,
+              const float *c_max, const uint32_t *c_hist, const double *c_comom,
+              int64_t *p_count, double *p_mean, double *p_m2, float *p_min, float *p_max,
+              uint32_t *p_hist, double *p_comom)
+{
+    int32_t T = m * (m + 1) / 2;
+    for (int32_t p = 0; p < n_parent; ++p) {
+        p_count[p] = 0;
+        for (int32_t j = 0; j < m; ++j) {
+            p_mean[(int64_t)p * m + j] = 0.0; p_m2[(int64_t)p * m + j] = 0.0;
+            p_min[(int64_t)p * m + j] = INFINITY; p_max[(int64_t)p * m + j] = -INFINITY;
+            for (int32_t b = 0; b < n_bins; ++b) p_hist[((int64_t)p * m + j) * n_bins + b] = 0;
+        }
+        if (want_cov) for (int32_t t = 0; t < T; ++t) p_comom[(int64_t)p * T + t] = 0.0;
+    }
+    double *d = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    if (!d) return ORC_ENOMEM;
+    for (int32_t c = 0; c < n_child; ++c) {
+        int32_t p = parent[c];
+        if (p < 0 || p >= n_parent) { free(d); return ORC_EINVAL; }
+        int64_t nb = c_count[c];
+        if (nb == 0) continue;
+        int64_t na = p_count[p];
+        for (int32_t j = 0; j < m; ++j) {
+            int64_t kp = (int64_t)p * m + j, kc = (int64_t)c * m + j;
+            if (c_min[kc] < p_min[kp]) p_min[kp] = c_min[kc];
+            if (c_max[kc] > p_max[kp]) p_max[kp] = c_max[kc];
+            for (int32_t b = 0; b < n_bins; ++b) p_hist[kp * n_bins + b] += c_hist[kc * n_bins + b];
+        }
+        if (na == 0) {
+            for (int32_t j = 0; j < m; ++j) {
+                p_mean[(int64_t)p * m + j] = c_mean[(int64_t)c * m + j];
+                p_m2[(int64_t)p * m + j] = c_m2[(int64_t)c * m + j];
+            }
+            if (want_cov) for (int32_t t = 0; t < T; ++t) p_comom[(int64_t)p * T + t] = c_comom[(int64_t)c * T + t];
+            p_count[p] = nb;
+            continue;
+        }
+        double nn = (double)(na + nb);
+        double f = (double)na * (double)nb / nn;
+        for (int32_t j = 0; j < m; ++j) d[j] = c_mean[(int64_t)c * m + j] - p_mean[(int64_t)p * m + j];
+        if (want_cov) {
+            int32_t t = 0;
+            for (int32_t i = 0; i < m; ++i)
+                for (int32_t j = i; j < m; ++j) {
+                    p_comom[(int64_t)p * T + t] = p_comom[(int64_t)p * T + t] + c_comom[(int64_t)c * T + t] + d[i] * d[j] * f;
+                    ++t;
+                }
+        }
+        for (int32_t j = 0; j < m; ++j) {
+            int64_t kp = (int64_t)p * m + j, kc = (int64_t)c * m + j;
+            p_m2[kp] = p_m2[kp] + c_m2[kc] + d[j] * d[j] * f;
+            p_mean[kp] = p_mean[kp] + d[j] * ((double)nb / nn);
+        }
+        p_count[p] = na + nb;
+    }
+    free(d);
+    return ORC_OK;
+}
+
+/* ========================================================================= */
+/* Checkers used by the tests (not part of the method).                      */
+/* ========================================================================= */
+
+/* Bellman certificate of an assignment: with positive edge weights the      */
+/* lexicographic key K(v) = min_s (D_s(v), s) is the unique solution of       */
+/*   K(v) = min( (0, s) for sites s at v,  min_edges (K(u).d + w, K(u).s) ),  */
+/* so checking this equation at every voxel certifies (cell, dist) exactly.  */
+/* Returns the number of voxels that violate it (0 = certified).             */
+int64_t orc_certify(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+                    const int32_t *site_pos, int32_t n_sites, const int32_t *cell, const uint32_t *dist)
+{
+    int64_t n = (int64_t)nx * ny * nz;
+    int32_t *own = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!own) return -1;
+    for (int64_t v = 0; v < n; ++v) own[v] = -1;
+    for (int32_t s = n_sites - 1; s >= 0; --s) {
+        int32_t p = site_pos[s];
+        if (p < 0 || p >= n) { free(own); return -1; }
+        own[p] = s; /* lowest id wins */
+    }
+    int64_t bad = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t x = (int32_t)(v % nx), y = (int32_t)((v / nx) % ny), z = (int32_t)(v / ((int64_t)nx * ny));
+        uint64_t bd = UINT64_MAX; int64_t bs = INT64_MAX;
+        if (band[v] != INVALID_BAND) {
+            if (own[v] >= 0) { bd = 0; bs = own[v]; }
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (!dx && !dy && !dz) continue;
+                        if (!has_edge(band, nx, ny, nz, x, y, z, dx, dy, dz)) continue;
+                        int64_t u = (x + dx) + (int64_t)nx * ((y + dy) + (int64_t)ny * (z + dz));
+                        if (cell[u] < 0) continue;
+                        uint64_t cd = (uint64_t)dist[u] + edge_weight(dx, dy, dz);
+                        if (cd < bd || (cd == bd && cell[u] < bs)) { bd = cd; bs = cell[u]; }
+                    }
+        }
+        int ok;
+        if (bd == UINT64_MAX) ok = (cell[v] == -1);
+        else ok = (cell[v] == bs && (uint64_t)dist[v] == bd);
+        if (!ok) ++bad;
+    }
+    free(own);
+    return bad;
+}
+
+/* Single-source Dijkstra (distances only), used by the brute-force check    */
+/* "per-seed shortest paths, then lexicographic minimum".                     */
+int orc_sssp(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz, int32_t src, uint64_t *d)
+{
+    int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
+    heap h = {0, 0, 0};
+    d[src] = 0;
+    hent e0 = {0, 0, src};
+    if (hpush(&h, e0)) return ORC_ENOMEM;
+    while (h.n > 0) {
+        hent e = hpop(&h);
+        if (e.d != d[e.v]) continue;
+        int32_t v = e.v, x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!dx && !dy && !dz) continue;
+                    if (!has_edge(band, nx, ny, nz, x, y, z, dx, dy, dz)) continue;
+                    int64_t u = (x + dx) + (int64_t)nx * ((y + dy) + (int64_t)ny * (z + dz));
+                    uint64_t nd = e.d + edge_weight(dx, dy, dz);
+                    if (nd < d[u]) {
+                        d[u] = nd;
+                        hent f = {nd, 0, (int32_t)u};
+                        if (hpush(&h, f)) { free(h.a); return ORC_ENOMEM; }
+                    }
+                }
+    }
+    free(h.a);
+    return ORC_OK;
+}
