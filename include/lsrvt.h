@@ -1,0 +1,221 @@
+/*
+ * lsrvt.h -- C ABI of the B300 (sm_103a) Level Set Restricted Voronoi Tessellation
+ * hot path.
+ *
+ * Method: Neuroth et al., "Level Set Restricted Voronoi Tessellation for Large scale
+ * Spatial Statistical Analysis" (arXiv 2208.06970).  Each entry point below cites the
+ * section / equation / algorithm of the paper that defines the operation.
+ *
+ * Conventions shared by every entry point
+ *  - Volumes are dense 3D grids (nx, ny, nz), linear index i = x + nx*(y + ny*z), x
+ *    fastest, N = nx*ny*nz < 2^31 voxels.
+ *  - Arrays named *_host are host memory.  Every other array is device memory owned
+ *    by the caller; the library never allocates, frees or retains device memory.
+ *    Scratch memory comes from a caller workspace `ws` of at least
+ *    lsrvt_workspace_bytes(step, ...) bytes, 256-byte aligned.  A workspace may be
+ *    reused by later calls on the same stream once they are ordered after this one.
+ *  - All calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL =
+ *    the legacy default stream).  Argument errors (bad dims, NULL pointers, isovalues
+ *    not strictly increasing, too small a workspace) return synchronously and launch
+ *    nothing.  Errors that depend on the data (capacity exceeded, distance overflow,
+ *    non-finite statistics input, relaxation round limit) are written to the caller's
+ *    device status word `status_dev` (int32, first error wins; 0 = OK); the caller
+ *    clears it and reads it after synchronising.  LSRVT_ERR_CUDA reports a failed
+ *    kernel launch (cudaGetLastError) on return.
+ *  - Integer results (bands, components, sites, cells, distances, counts, min, max,
+ *    histograms) are deterministic and bit-identical from run to run.
+ *  - Voxels whose field value is NaN are not graph nodes: band 0xFF, component -1,
+ *    cell -1.
+ */
+#ifndef LSRVT_H
+#define LSRVT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSRVT_OK = 0,
+    LSRVT_ERR_INVALID_ARG = 1, /* bad dims / NULL pointer / parameter out of range       */
+    LSRVT_ERR_NOT_SORTED = 2,  /* isovalues not strictly increasing (or NaN)             */
+    LSRVT_ERR_CAPACITY = 3,    /* more components / sites / strata than the capacity     */
+    LSRVT_ERR_NONFINITE = 4,   /* a statistics input is NaN or infinite                  */
+    LSRVT_ERR_TIMEOUT = 5,     /* a bounded device loop hit its limit                    */
+    LSRVT_ERR_OVERFLOW = 6,    /* a geodesic distance reached 2^32 (65536 voxel widths)  */
+    LSRVT_ERR_CUDA = 7,        /* a CUDA launch failed                                   */
+    LSRVT_ERR_WORKSPACE = 8    /* workspace NULL, misaligned or too small                */
+} lsrvt_status;
+
+typedef struct {
+    int32_t nx, ny, nz;
+} lsrvt_dims;
+
+/* Steps, for lsrvt_workspace_bytes. */
+typedef enum {
+    LSRVT_STEP_CLASSIFY = 0,
+    LSRVT_STEP_LABEL = 1,
+    LSRVT_STEP_SALIENCY = 2,
+    LSRVT_STEP_SEED = 3,
+    LSRVT_STEP_CVT = 4,
+    LSRVT_STEP_AGGREGATE = 5,
+    LSRVT_STEP_MERGE = 6
+} lsrvt_step;
+
+/* Seeding parameters (Sec. 3.2 "Stratified Random Initial Site Distribution", Eq. nc;
+ * Sec. 3.3 "Role and Choice of Parameters"). */
+typedef struct {
+    int64_t voxels_per_site; /* P = 1/alpha, the site density parameter as voxels per site (>= 1) */
+    int32_t strat_block;     /* side of the cubic stratification blocks, 1..16 (default 16); part
+                                of the result, not a tuning knob */
+    int32_t max_strata;      /* capacity of the (component x block) stratum table; 0 = default   */
+    uint64_t rng_seed;       /* seed of the SplitMix64 placement hash                            */
+} lsrvt_seed_params;
+
+/* Statistics records (Sec. 3.3 "Aggregation"): one row per cell / component / band.
+ * All arrays are device memory with `rows` rows; m = number of variables, B = bins.
+ *   count[rows]            int64  voxels
+ *   mean[rows][m]          double mean
+ *   m2[rows][m]            double sum of squared deviations (population variance = m2/count)
+ *   vmin, vmax[rows][m]    float  exact min / max (+inf / -inf for empty rows)
+ *   hist[rows][m][B]       uint32 histogram (may be NULL when B = 0)
+ *   comom[rows][m(m+1)/2]  double co-moment sums C_ij = sum (x_i-mean_i)(x_j-mean_j),
+ *                          upper triangle row-major (NULL unless LSRVT_STATS_COV)   */
+typedef struct {
+    int64_t *count;
+    double *mean;
+    double *m2;
+    float *vmin;
+    float *vmax;
+    uint32_t *hist;
+    double *comom;
+} lsrvt_stats;
+
+#define LSRVT_STATS_HIST 1u
+#define LSRVT_STATS_COV 2u
+
+/* Human-readable name of a status code (static string). */
+const char *lsrvt_status_string(lsrvt_status s);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int32_t lsrvt_version(void);
+
+/* Workspace bytes needed by `step` for a volume of dims `d` with the given capacities
+ * (max_comp components, max_sites sites, n_aux statistics variables; pass 0 where the
+ * step does not use a capacity).  Returns 0 for invalid dims. */
+size_t lsrvt_workspace_bytes(lsrvt_step step, lsrvt_dims d, int32_t max_comp, int32_t max_sites,
+                             int32_t n_aux);
+
+/* Isoband classification.  Sec. 3.1 "Level Sets, Isobands, and Connected Components":
+ * B_{a,b} = { v : a < f(v) <= b }.  With strictly increasing isovalues t_1 < ... < t_K
+ * (0 <= K <= 254, host array) the band of a voxel is #{ i : t_i < f(v) }: band 0 is
+ * (-inf, t_1] and band K is (t_K, inf).  NaN -> 0xFF.  -0 and +0 compare equal.
+ *   field [N] float (in), band [N] uint8 (out).
+ * Errors: INVALID_ARG (dims, NULL, K > 254), NOT_SORTED. */
+lsrvt_status lsrvt_classify(const float *field, lsrvt_dims d, const float *iso_host, int32_t n_iso,
+                            uint8_t *band, void *stream);
+
+/* Connected components of each isoband.  Sec. 3.1: an isoband is split into components
+ * C^k with no voxel of one adjacent to a voxel of another; 6-adjacency.  Component ids
+ * are dense and canonical: ordered by (band, smallest linear index).
+ *   band [N] uint8 (in); comp [N] int32 (out, -1 for NaN voxels);
+ *   comp_band [max_comp] uint8, comp_size [max_comp] int64, comp_first [max_comp] int32
+ *   (out: band, voxel count, smallest linear index of each component);
+ *   n_comp_dev [1] int32 (out: number of components, also when it exceeds max_comp).
+ * If the count exceeds max_comp, CAPACITY is written to status_dev and the tables hold
+ * only the first max_comp entries; comp[] is complete. */
+lsrvt_status lsrvt_label_components(const uint8_t *band, lsrvt_dims d, int32_t *comp, uint8_t *comp_band,
+                                    int64_t *comp_size, int32_t *comp_first, int32_t max_comp,
+                                    int32_t *n_comp_dev, void *ws, size_t ws_bytes, int32_t *status_dev,
+                                    void *stream);
+
+/* Saliency weights m_v (Sec. 3.1 "Centroids or Centers of Mass": m_v; Sec. 3.3: the
+ * second field and the attraction gamma).  q = max(1, rint(g^gamma * 65535 / gmax)),
+ * g = |grad f| by central differences (one-sided half differences at the faces),
+ * evaluated in IEEE float in a fixed order; gmax = largest finite g^gamma.  gamma is an
+ * integer 0..4 (0 gives q = 1 everywhere).
+ *   field [N] float (in), q [N] uint16 (out). */
+lsrvt_status lsrvt_saliency_grad(const float *field, lsrvt_dims d, int32_t gamma, uint16_t *q, void *ws,
+                                 size_t ws_bytes, void *stream);
+
+/* Stratified random initial sites.  Sec. 3.2 "Stratified Random Initial Site
+ * Distribution", Eq. (nc), Algorithm 1 (StratifiedRandomSiteDistribution).
+ *   n_c = max(ceil(|V| m(C) / (P m(V))), 1) capped at |C|   (m = sum of q; q NULL = 1)
+ * apportioned to strata (component x cubic block) by largest remainder with capacity
+ * caps; inside a stratum the k voxels in linear order are split into n_b rank ranges
+ * and site j takes rank lo_j + splitmix64((seed ^ splitmix64(block)) + j) mod width.
+ * Site ids are ordered by (component, block, j).
+ *   comp [N] int32 (in, from lsrvt_label_components); n_comp_dev (in);
+ *   site_pos [max_sites] int32 (out, linear voxel index), site_comp [max_sites] int32
+ *   (out), comp_site_off [max_comp+1] int32 (out: sites of component c are
+ *   [off[c], off[c+1])), n_sites_dev [1] int32 (out).
+ * CAPACITY (status_dev) if sites > max_sites or strata > the stratum capacity. */
+lsrvt_status lsrvt_seed(const int32_t *comp, const uint16_t *q, lsrvt_dims d, const int32_t *n_comp_dev,
+                        int32_t max_comp, lsrvt_seed_params p, int32_t *site_pos, int32_t *site_comp,
+                        int32_t *comp_site_off, int32_t max_sites, int32_t *n_sites_dev, void *ws,
+                        size_t ws_bytes, int32_t *status_dev, void *stream);
+
+/* Lloyd iterations of the level set restricted CVT.  Algorithm 1 (LRCVT) after
+ * seeding: n_iters x (restricted geodesic Voronoi tessellation, Eq. 1; geodesically
+ * weighted update, Eq. 2) followed by a final tessellation.
+ *  Tessellation: cell(v) = the site s of v's component minimising (gd(v, s), s)
+ *   lexicographically, gd = shortest path on the graph of 26-neighbour edges whose
+ *   spanned box lies in one band, edge lengths 65536, 92682, 113512 (16.16 fixed
+ *   point Euclidean lengths rounded up).
+ *  Update: phi(v) = v if the voxel traversal v -> site stays in the band, else
+ *   phi(parent(v)); target = round-half-up(sum q_v x_phi(v) / sum q_v) per axis; the
+ *   site walks the traversal toward the target and stops before leaving its band.
+ *   band [N] uint8, q [N] uint16 or NULL (uniform weight) (in);
+ *   site_pos [max_sites] int32 (in/out), n_sites_dev (in);
+ *   cell [N] int32 (out, site id, -1 for NaN voxels); dist [N] uint32 (out, optional:
+ *   16.16 geodesic distance to the site, 0xFFFFFFFF for NaN voxels);
+ *   iter_trace [n_iters][2] int64 (out, optional: sites moved, sum of squared moves).
+ * OVERFLOW if a distance reaches 2^32; TIMEOUT if the relaxation exceeds its round limit. */
+lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q, lsrvt_dims d, int32_t *site_pos,
+                               const int32_t *n_sites_dev, int32_t max_sites, int32_t n_iters, int32_t *cell,
+                               uint32_t *dist, int64_t *iter_trace, void *ws, size_t ws_bytes,
+                               int32_t *status_dev, void *stream);
+
+/* Per-variable histogram range: lo_j = min, scale_j = float(n_bins) / (max - min) (0 if
+ * max == min) over voxels with cell >= 0 (Sec. 3.3 "Aggregation": histograms).
+ *   cell [N] int32; aux_host[n_aux] = device pointers to [N] float; lo_dev, scale_dev
+ *   [n_aux] float (out).  NONFINITE if an input value is NaN or infinite. */
+lsrvt_status lsrvt_aux_range(const int32_t *cell, const float *const *aux_host, int32_t n_aux, lsrvt_dims d,
+                             int32_t n_bins, float *lo_dev, float *scale_dev, int32_t *status_dev, void *stream);
+
+/* Per-cell statistics of n_aux variables (Sec. 3.3 "Aggregation"; introduction:
+ * statistics aggregated within segments).  count, mean, m2, min, max always; an n_bins
+ * histogram with bin = clamp((int)((x - lo_j) * scale_j), 0, n_bins-1) in IEEE float if
+ * flags & LSRVT_STATS_HIST; co-moments if flags & LSRVT_STATS_COV.  Sums are
+ * accumulated in float-float (about 44 significant bits) per brick and combined in
+ * FP64; co-moments use BF16 split products on tensor cores with FP32 accumulation.
+ *   cell [N] int32 (in); aux_host[n_aux] device pointers to [N] float (in);
+ *   lo_dev, scale_dev [n_aux] float (in, device; e.g. from lsrvt_aux_range);
+ *   out: rows = max_sites.  NONFINITE if a value is NaN or infinite. */
+lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const *aux_host, int32_t n_aux, lsrvt_dims d,
+                             const float *lo_dev, const float *scale_dev, int32_t n_bins, uint32_t flags,
+                             const int32_t *site_pos, const int32_t *n_sites_dev, int32_t max_sites,
+                             lsrvt_stats out, void *ws, size_t ws_bytes, int32_t *status_dev, void *stream);
+
+/* Merge statistics up the hierarchy cell -> component -> band -> volume (introduction
+ * and Sec. 3.2 "Data Reduction and Structured Data Layout": aggregates merged over
+ * cells, components and isobands).  Counts, histograms, min, max combine exactly;
+ * means, m2 and co-moments combine in FP64 by the pairwise formulas of Chan, Golub &
+ * LeVeque (1979) evaluated as sum n_i mean_i / n and sum (m2_i + n_i (mean_i-mean)^2).
+ *   cells (rows max_sites, n_sites_dev valid); comp_site_off [n_comp+1] (from
+ *   lsrvt_seed); comp_band [n_comp]; n_bands = number of isovalues + 1;
+ *   comps (rows max_comp), bands (rows n_bands), volume (1 row) (out). */
+lsrvt_status lsrvt_merge_hierarchy(lsrvt_stats cells, const int32_t *n_sites_dev, int32_t max_sites,
+                                   int32_t n_aux, int32_t n_bins, uint32_t flags,
+                                   const int32_t *comp_site_off, const uint8_t *comp_band,
+                                   const int32_t *n_comp_dev, int32_t max_comp, int32_t n_bands,
+                                   lsrvt_stats comps, lsrvt_stats bands, lsrvt_stats volume, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSRVT_H */

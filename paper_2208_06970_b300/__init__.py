@@ -1,0 +1,353 @@
+"""B300-native Level Set Restricted Voronoi Tessellation (LSRVT) hot path.
+
+Thin Python binding of the C ABI in ``include/lsrvt.h`` (``liblsrvt.so``, hand-written
+CUDA for sm_103a).  Every step runs in the library's kernels; this module only
+allocates device tensors with PyTorch, passes their pointers and the current CUDA stream,
+and reads the device status word.  There is no CPU fallback: without the built library
+or without a CUDA device the calls raise.
+
+Method: Neuroth et al., "Level Set Restricted Voronoi Tessellation for Large scale
+Spatial Statistical Analysis" (arXiv 2208.06970).
+
+The functions keep the C names without the ``lsrvt_`` prefix:
+    classify, label_components, saliency_grad, seed, cvt_iterate, aux_range,
+    aggregate, merge_hierarchy
+and ``decompose`` chains them (Algorithm 1 plus statistics) on one stream.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblsrvt.so")
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "isovalues not strictly increasing", 3: "capacity exceeded",
+          4: "non-finite input value", 5: "device loop limit reached", 6: "geodesic distance overflow",
+          7: "CUDA launch failure", 8: "workspace missing, misaligned or too small"}
+STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6)
+STATS_HIST = 1
+STATS_COV = 2
+
+
+class LsrvtError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s: %s (%d)" % (where, STATUS.get(code, "?"), code))
+        self.code = code
+
+
+class Dims(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+class SeedParams(C.Structure):
+    _fields_ = [("voxels_per_site", C.c_int64), ("strat_block", C.c_int32), ("max_strata", C.c_int32),
+                ("rng_seed", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("count", C.c_void_p), ("mean", C.c_void_p), ("m2", C.c_void_p), ("vmin", C.c_void_p),
+                ("vmax", C.c_void_p), ("hist", C.c_void_p), ("comom", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblsrvt.so (built in-tree by build.py); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblsrvt.so is not built; run paper_2208_06970_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        P, i32, i64, u32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_size_t
+        L.lsrvt_status_string.argtypes = [C.c_int]
+        L.lsrvt_status_string.restype = C.c_char_p
+        L.lsrvt_version.restype = i32
+        L.lsrvt_workspace_bytes.argtypes = [C.c_int, Dims, i32, i32, i32]
+        L.lsrvt_workspace_bytes.restype = sz
+        L.lsrvt_classify.argtypes = [P, Dims, P, i32, P, P]
+        L.lsrvt_label_components.argtypes = [P, Dims, P, P, P, P, i32, P, P, sz, P, P]
+        L.lsrvt_saliency_grad.argtypes = [P, Dims, i32, P, P, sz, P]
+        L.lsrvt_seed.argtypes = [P, P, Dims, P, i32, SeedParams, P, P, P, i32, P, P, sz, P, P]
+        L.lsrvt_cvt_iterate.argtypes = [P, P, Dims, P, P, i32, i32, P, P, P, P, sz, P, P]
+        L.lsrvt_aux_range.argtypes = [P, P, i32, Dims, i32, P, P, P, P]
+        L.lsrvt_aggregate.argtypes = [P, P, i32, Dims, P, P, i32, u32, P, P, i32, Stats, P, sz, P, P]
+        L.lsrvt_merge_hierarchy.argtypes = [Stats, P, i32, i32, i32, u32, P, P, P, i32, i32, Stats, Stats, Stats, P,
+                                            sz, P]
+        for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_saliency_grad", "lsrvt_seed",
+                     "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
+            "lsrvt_label_components", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
+            "lsrvt_aggregate", "lsrvt_merge_hierarchy"]
+
+
+# --------------------------------------------------------------------------- helpers
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dims(t):
+    nz, ny, nx = t.shape[-3:]
+    return Dims(int(nx), int(ny), int(nz))
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise LsrvtError(rc, where)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("device tensors must be contiguous CUDA tensors")
+
+
+def default_max_comp(n):
+    """Default component capacity: every voxel for small volumes, N/16 (at least 2^20) otherwise."""
+    return int(min(n, max(1 << 20, n // 16)))
+
+
+def workspace_bytes(step, dims, max_comp=0, max_sites=0, n_aux=0):
+    d = dims if isinstance(dims, Dims) else Dims(*[int(v) for v in dims])
+    return int(lib().lsrvt_workspace_bytes(STEP[step], d, int(max_comp), int(max_sites), int(n_aux)))
+
+
+class Workspace:
+    """A growing device scratch buffer (256-byte aligned) reused across calls on one stream."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes):
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def new_status(device="cuda"):
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def check_status(status, where="device"):
+    """Synchronise and raise on a data-dependent error recorded by the kernels."""
+    code = int(status.item())
+    if code != 0:
+        raise LsrvtError(code, where)
+
+
+# --------------------------------------------------------------------------- steps
+def classify(field, iso, band=None):
+    """Isoband index per voxel (Sec. 3.1): band = #{i : iso[i] < f}; NaN -> 255."""
+    _require_cuda(field)
+    iso = np.ascontiguousarray(iso, dtype=np.float32)
+    if band is None:
+        band = torch.empty(field.shape, dtype=torch.uint8, device=field.device)
+    _check(lib().lsrvt_classify(_ptr(field), _dims(field), iso.ctypes.data_as(C.c_void_p), len(iso), _ptr(band),
+                                _stream()), "lsrvt_classify")
+    return band
+
+
+def label_components(band, max_comp=None, ws=None, status=None):
+    """6-connected components of each isoband, ids ordered by (band, min index).
+
+    Returns (comp, comp_band, comp_size, comp_first, n_comp_dev)."""
+    _require_cuda(band)
+    dev = band.device
+    n = band.numel()
+    max_comp = default_max_comp(n) if max_comp is None else int(max_comp)
+    comp = torch.empty(band.shape, dtype=torch.int32, device=dev)
+    cb = torch.empty(max(max_comp, 1), dtype=torch.uint8, device=dev)
+    cs = torch.empty(max(max_comp, 1), dtype=torch.int64, device=dev)
+    cf = torch.empty(max(max_comp, 1), dtype=torch.int32, device=dev)
+    nc = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ws or Workspace(dev)
+    status = new_status(dev) if status is None else status
+    wb = workspace_bytes("label", _dims(band))
+    buf = ws.get(wb)
+    _check(lib().lsrvt_label_components(_ptr(band), _dims(band), _ptr(comp), _ptr(cb), _ptr(cs), _ptr(cf), max_comp,
+                                        _ptr(nc), _ptr(buf), buf.numel(), _ptr(status), _stream()),
+           "lsrvt_label_components")
+    return comp, cb, cs, cf, nc
+
+
+def saliency_grad(field, gamma=1, ws=None):
+    """Weights q = max(1, rint(|grad f|^gamma * 65535 / max)) (uint16)."""
+    _require_cuda(field)
+    q = torch.empty(field.shape, dtype=torch.int16, device=field.device)
+    ws = ws or Workspace(field.device)
+    buf = ws.get(workspace_bytes("saliency", _dims(field)))
+    _check(lib().lsrvt_saliency_grad(_ptr(field), _dims(field), int(gamma), _ptr(q), _ptr(buf), buf.numel(),
+                                     _stream()), "lsrvt_saliency_grad")
+    return q
+
+
+def seed(comp, q, n_comp_dev, max_comp, voxels_per_site, strat_block=16, rng_seed=0, max_sites=None,
+         max_strata=0, ws=None, status=None):
+    """Stratified initial sites (Sec. 3.2, Eq. nc).  q is an int16 view of uint16 weights or None.
+
+    Returns (site_pos, site_comp, comp_site_off, n_sites_dev)."""
+    _require_cuda(comp, q)
+    dev = comp.device
+    n = comp.numel()
+    if max_sites is None:
+        max_sites = int(min(n, n // max(int(voxels_per_site), 1) + int(max_comp) + 1024))
+    sp = torch.empty(max(max_sites, 1), dtype=torch.int32, device=dev)
+    sc = torch.empty(max(max_sites, 1), dtype=torch.int32, device=dev)
+    off = torch.empty(int(max_comp) + 1, dtype=torch.int32, device=dev)
+    ns = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ws or Workspace(dev)
+    status = new_status(dev) if status is None else status
+    params = SeedParams(int(voxels_per_site), int(strat_block), int(max_strata), int(rng_seed) & (2 ** 64 - 1))
+    buf = ws.get(workspace_bytes("seed", _dims(comp), max_comp=max_comp) if not max_strata else
+                 max(workspace_bytes("seed", _dims(comp), max_comp=max_comp), 64 * int(max_strata) + (1 << 24)))
+    _check(lib().lsrvt_seed(_ptr(comp), _ptr(q), _dims(comp), _ptr(n_comp_dev), int(max_comp), params, _ptr(sp),
+                            _ptr(sc), _ptr(off), int(max_sites), _ptr(ns), _ptr(buf), buf.numel(), _ptr(status),
+                            _stream()), "lsrvt_seed")
+    return sp, sc, off, ns
+
+
+def cvt_iterate(band, q, site_pos, n_sites_dev, n_iters, want_dist=True, want_trace=True, ws=None, status=None,
+                cell=None, dist=None):
+    """Algorithm 1 after seeding: n_iters x (Eq. 1 assignment, Eq. 2 update) + final assignment.
+
+    site_pos is updated in place.  Returns (cell, dist or None, trace[n_iters, 2] or None)."""
+    _require_cuda(band, q, site_pos)
+    dev = band.device
+    max_sites = site_pos.numel()
+    if cell is None:
+        cell = torch.empty(band.shape, dtype=torch.int32, device=dev)
+    if want_dist and dist is None:
+        dist = torch.empty(band.shape, dtype=torch.int32, device=dev)
+    trace = torch.zeros((max(n_iters, 1), 2), dtype=torch.int64, device=dev) if want_trace else None
+    ws = ws or Workspace(dev)
+    status = new_status(dev) if status is None else status
+    buf = ws.get(workspace_bytes("cvt", _dims(band), max_sites=max_sites))
+    _check(lib().lsrvt_cvt_iterate(_ptr(band), _ptr(q), _dims(band), _ptr(site_pos), _ptr(n_sites_dev), max_sites,
+                                   int(n_iters), _ptr(cell), _ptr(dist if want_dist else None),
+                                   _ptr(trace), _ptr(buf), buf.numel(), _ptr(status), _stream()),
+           "lsrvt_cvt_iterate")
+    return cell, (dist if want_dist else None), (trace[:n_iters] if want_trace else None)
+
+
+def _aux_ptrs(aux):
+    ptrs = (C.c_void_p * max(len(aux), 1))(*[t.data_ptr() for t in aux])
+    return ptrs
+
+
+def aux_range(cell, aux, n_bins, status=None):
+    """Per-variable histogram range over valid voxels: (lo, scale) float32 device tensors."""
+    aux = [a.contiguous() for a in aux]
+    _require_cuda(cell, *aux)
+    dev = cell.device
+    m = len(aux)
+    lo = torch.empty(max(m, 1), dtype=torch.float32, device=dev)
+    sc = torch.empty(max(m, 1), dtype=torch.float32, device=dev)
+    status = new_status(dev) if status is None else status
+    ptrs = _aux_ptrs(aux)
+    _check(lib().lsrvt_aux_range(_ptr(cell), C.cast(ptrs, C.c_void_p), m, _dims(cell), int(n_bins), _ptr(lo),
+                                 _ptr(sc), _ptr(status), _stream()), "lsrvt_aux_range")
+    return lo, sc
+
+
+def alloc_stats(rows, m, n_bins, cov, device="cuda"):
+    T = m * (m + 1) // 2
+    return dict(count=torch.empty(max(rows, 1), dtype=torch.int64, device=device),
+                mean=torch.empty((max(rows, 1), m), dtype=torch.float64, device=device),
+                m2=torch.empty((max(rows, 1), m), dtype=torch.float64, device=device),
+                min=torch.empty((max(rows, 1), m), dtype=torch.float32, device=device),
+                max=torch.empty((max(rows, 1), m), dtype=torch.float32, device=device),
+                hist=torch.empty((max(rows, 1), m, n_bins), dtype=torch.int32, device=device) if n_bins else None,
+                comom=torch.empty((max(rows, 1), T), dtype=torch.float64, device=device) if cov else None)
+
+
+def _stats_struct(st):
+    return Stats(st["count"].data_ptr(), st["mean"].data_ptr(), st["m2"].data_ptr(), st["min"].data_ptr(),
+                 st["max"].data_ptr(), st["hist"].data_ptr() if st.get("hist") is not None else None,
+                 st["comom"].data_ptr() if st.get("comom") is not None else None)
+
+
+def aggregate(cell, aux, site_pos, n_sites_dev, lo=None, scale=None, n_bins=32, cov=False, ws=None, status=None,
+              out=None):
+    """Per-cell statistics (Sec. 3.3).  Rows = site_pos.numel().  Returns a dict of device tensors."""
+    aux = [a.contiguous() for a in aux]
+    _require_cuda(cell, site_pos, *aux)
+    dev = cell.device
+    m = len(aux)
+    max_sites = site_pos.numel()
+    status = new_status(dev) if status is None else status
+    if n_bins and m and (lo is None or scale is None):
+        lo, scale = aux_range(cell, aux, n_bins, status)
+    out = out or alloc_stats(max_sites, m, n_bins, cov, dev)
+    ws = ws or Workspace(dev)
+    buf = ws.get(workspace_bytes("aggregate", _dims(cell), max_sites=max_sites, n_aux=m))
+    flags = (STATS_HIST if n_bins else 0) | (STATS_COV if cov else 0)
+    ptrs = _aux_ptrs(aux)
+    _check(lib().lsrvt_aggregate(_ptr(cell), C.cast(ptrs, C.c_void_p), m, _dims(cell), _ptr(lo), _ptr(scale),
+                                 int(n_bins), flags, _ptr(site_pos), _ptr(n_sites_dev), max_sites,
+                                 _stats_struct(out), _ptr(buf), buf.numel(), _ptr(status), _stream()),
+           "lsrvt_aggregate")
+    return out
+
+
+def merge_hierarchy(cells, n_sites_dev, comp_site_off, comp_band, n_comp_dev, max_comp, n_bands, n_bins=32,
+                    cov=False, ws=None):
+    """cell -> component -> band -> volume statistics.  Returns (comps, bands, volume)."""
+    dev = cells["count"].device
+    m = cells["mean"].shape[1]
+    max_sites = cells["count"].numel()
+    comps = alloc_stats(max_comp, m, n_bins, cov, dev)
+    bands = alloc_stats(n_bands, m, n_bins, cov, dev)
+    vol = alloc_stats(1, m, n_bins, cov, dev)
+    ws = ws or Workspace(dev)
+    buf = ws.get(workspace_bytes("merge", _dims_of_nothing(), max_comp=max_comp, max_sites=max_sites, n_aux=m))
+    flags = (STATS_HIST if n_bins else 0) | (STATS_COV if cov else 0)
+    _check(lib().lsrvt_merge_hierarchy(_stats_struct(cells), _ptr(n_sites_dev), max_sites, m, int(n_bins), flags,
+                                       _ptr(comp_site_off), _ptr(comp_band), _ptr(n_comp_dev), int(max_comp),
+                                       int(n_bands), _stats_struct(comps), _stats_struct(bands), _stats_struct(vol),
+                                       _ptr(buf), buf.numel(), _stream()), "lsrvt_merge_hierarchy")
+    return comps, bands, vol
+
+
+def _dims_of_nothing():
+    return Dims(1, 1, 1)
+
+
+# --------------------------------------------------------------------------- pipeline
+def decompose(field, iso, voxels_per_site, n_iters, aux=(), gamma=0, strat_block=16, rng_seed=0, n_bins=32,
+              cov=False, max_comp=None, ws=None, check=True):
+    """The whole hot path on the current stream: classify -> CCL -> [saliency] -> seed ->
+    Lloyd iterations -> per-cell statistics -> hierarchy merge.  Returns a dict of tensors."""
+    dev = field.device
+    ws = ws or Workspace(dev)
+    status = new_status(dev)
+    band = classify(field, iso)
+    n = field.numel()
+    if max_comp is None:
+        max_comp = default_max_comp(n)
+    comp, cb, cs, cf, nc = label_components(band, max_comp, ws, status)
+    q = saliency_grad(field, gamma, ws) if gamma else None
+    sp, sc, off, ns = seed(comp, q, nc, max_comp, voxels_per_site, strat_block, rng_seed, ws=ws, status=status)
+    cell, dist, trace = cvt_iterate(band, q, sp, ns, n_iters, ws=ws, status=status)
+    out = dict(band=band, comp=comp, comp_band=cb, comp_size=cs, comp_first=cf, n_comp=nc, q=q, site_pos=sp,
+               site_comp=sc, comp_site_off=off, n_sites=ns, cell=cell, dist=dist, trace=trace, status=status)
+    if len(aux):
+        cells = aggregate(cell, list(aux), sp, ns, n_bins=n_bins, cov=cov, ws=ws, status=status)
+        comps, bands, vol = merge_hierarchy(cells, ns, off, cb, nc, max_comp, len(iso) + 1, n_bins, cov, ws)
+        out.update(cells=cells, comps=comps, bands=bands, volume=vol)
+    if check:
+        check_status(status, "decompose")
+    return out

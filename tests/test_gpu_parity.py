@@ -1,0 +1,239 @@
+"""GPU parity: every step of the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs.  Integer results must match bit for bit; moments within
+|got - ref| <= 1e-6 max(|ref|, 1e-6 <x^2>_cell) (mean and population variance).
+Sizes span several bricks / tiles and ragged edges."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_06970_b300 as pkg
+    from paper_2208_06970_b300 import build
+    build.build()
+    return pkg
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+def blob_case(side, seed=1):
+    w = workloads.blobs_workload(side=side, seed=seed)
+    return w
+
+
+RAGGED = [(37, 29, 23), (64, 64, 64), (70, 9, 33), (1, 1, 300), (17, 1, 1)]
+
+
+@pytest.mark.parametrize("dims", RAGGED)
+def test_classify_parity(pk, dims):
+    f = workloads.blob_field(dims, 5, "cpu", n_blobs=6).numpy()
+    f.ravel()[::97] = np.nan
+    for iso in ([0.3], [0.2, 0.4, 0.6, 0.8], list(np.linspace(0.05, 0.95, 8)), list(np.linspace(-1, 2, 254))):
+        iso = np.array(iso, np.float32)
+        ref = oracle.classify(f, iso)
+        got = cpu(pk.classify(torch.from_numpy(f).cuda(), iso))
+        assert np.array_equal(got, ref)
+    # unaligned but contiguous input: scalar path
+    n = f.size
+    base = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+    view = base[1:].view(f.shape)
+    view.copy_(torch.from_numpy(f))
+    iso = np.array([0.2, 0.4, 0.6, 0.8], np.float32)
+    assert np.array_equal(cpu(pk.classify(view, iso)), oracle.classify(f, iso))
+
+
+def test_classify_errors(pk):
+    f = torch.zeros((4, 4, 4), device="cuda")
+    with pytest.raises(pk.LsrvtError) as e:
+        pk.classify(f, np.array([0.5, 0.5], np.float32))
+    assert e.value.code == 2
+
+
+def _ccl_compare(pk, band):
+    comp, cb, cs, cf = oracle.label_components(band)
+    g = pk.label_components(torch.from_numpy(band).cuda(), max_comp=band.size)
+    nc = int(g[4].item())
+    assert nc == len(cb)
+    assert np.array_equal(cpu(g[0]), comp)
+    assert np.array_equal(cpu(g[1])[:nc], cb)
+    assert np.array_equal(cpu(g[2])[:nc], cs)
+    assert np.array_equal(cpu(g[3])[:nc], cf)
+
+
+@pytest.mark.parametrize("dims,nb,seed", [((37, 29, 23), 3, 0), ((70, 9, 33), 2, 1), ((64, 64, 64), 4, 2),
+                                          ((1, 1, 300), 2, 3), ((100, 3, 2), 5, 4)])
+def test_ccl_parity_random(pk, dims, nb, seed):
+    rng = np.random.default_rng(seed)
+    shape = dims[::-1]
+    band = rng.integers(0, nb, size=shape).astype(np.uint8)
+    band[rng.random(shape) < 0.05] = 255
+    _ccl_compare(pk, band)
+
+
+def test_ccl_parity_blobs_and_checkerboard(pk):
+    w = blob_case(64)
+    _ccl_compare(pk, oracle.classify(w["field"].numpy(), w["iso"]))
+    z, y, x = np.indices((20, 21, 22))
+    _ccl_compare(pk, ((x + y + z) % 2).astype(np.uint8))
+    _ccl_compare(pk, np.zeros((40, 50, 70), np.uint8))  # one component spanning every brick
+
+
+def test_ccl_capacity_status(pk):
+    z, y, x = np.indices((8, 8, 8))
+    band = torch.from_numpy(((x + y + z) % 2).astype(np.uint8)).cuda()
+    st = pk.new_status()
+    g = pk.label_components(band, max_comp=100, status=st)
+    assert int(g[4].item()) == 512 and int(st.item()) == 3
+
+
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_saliency_parity(pk, gamma):
+    for dims, seed in (((37, 29, 23), 3), ((64, 64, 64), 4)):
+        f = workloads.blob_field(dims, seed, "cpu").numpy()
+        ref = oracle.saliency(f, gamma)
+        got = cpu(pk.saliency_grad(torch.from_numpy(f).cuda(), gamma)).view(np.uint16)
+        assert np.array_equal(got, ref)
+    f, u = workloads.flame_field((48, 40, 36), 2, "cpu")
+    f = f.numpy()
+    assert np.array_equal(cpu(pk.saliency_grad(torch.from_numpy(f).cuda(), gamma)).view(np.uint16),
+                          oracle.saliency(f, gamma))
+
+
+def _seed_compare(pk, f, iso, P, sb, rs, gamma):
+    band = oracle.classify(f, iso)
+    comp, cb, cs, cf = oracle.label_components(band)
+    q = oracle.saliency(f, gamma) if gamma else None
+    sp, sc, off, nc = oracle.seed(comp, q, len(cb), P, sb, rs)
+    gb = pk.classify(torch.from_numpy(f).cuda(), iso)
+    gc = pk.label_components(gb, max_comp=f.size)
+    gq = pk.saliency_grad(torch.from_numpy(f).cuda(), gamma) if gamma else None
+    gs = pk.seed(gc[0], gq, gc[4], f.size, P, sb, rs)
+    ns = int(gs[3].item())
+    assert ns == len(sp)
+    assert np.array_equal(cpu(gs[0])[:ns], sp)
+    assert np.array_equal(cpu(gs[1])[:ns], sc)
+    assert np.array_equal(cpu(gs[2])[:len(cb) + 1], off)
+    return sp
+
+
+@pytest.mark.parametrize("P,sb,gamma", [(512, 16, 0), (64, 8, 0), (200, 5, 1), (37, 16, 2), (1, 4, 0)])
+def test_seed_parity(pk, P, sb, gamma):
+    w = blob_case(48, seed=3)
+    _seed_compare(pk, w["field"].numpy(), w["iso"], P, sb, 1234, gamma)
+
+
+def test_seed_parity_ragged(pk):
+    f = workloads.blob_field((37, 29, 23), 9, "cpu").numpy()
+    _seed_compare(pk, f, np.array([0.25, 0.5], np.float32), 100, 16, 7, 1)
+
+
+def _cvt_compare(pk, f, iso, P, gamma, n_iters, rs=1):
+    band = oracle.classify(f, iso)
+    comp, cb, cs, cf = oracle.label_components(band)
+    q = oracle.saliency(f, gamma) if gamma else None
+    sp, sc, off, nc = oracle.seed(comp, q, len(cb), P, 16, rs)
+    sp_ref, cell_ref, dist_ref, tr_ref = oracle.cvt_iterate(band, q, sp, n_iters)
+    gband = torch.from_numpy(band).cuda()
+    gq = torch.from_numpy(q.view(np.int16)).cuda() if q is not None else None
+    gsp = torch.from_numpy(sp).cuda()
+    ns = torch.tensor([len(sp)], dtype=torch.int32, device="cuda")
+    st = pk.new_status()
+    cell, dist, tr = pk.cvt_iterate(gband, gq, gsp, ns, n_iters, status=st)
+    pk.check_status(st)
+    assert np.array_equal(cpu(gsp), sp_ref)
+    assert np.array_equal(cpu(cell), cell_ref)
+    assert np.array_equal(cpu(dist).view(np.uint32), dist_ref)
+    assert np.array_equal(cpu(tr), tr_ref)
+
+
+@pytest.mark.parametrize("n_iters", [0, 1, 3])
+def test_cvt_parity_blobs(pk, n_iters):
+    w = blob_case(64)
+    _cvt_compare(pk, w["field"].numpy(), w["iso"], 512, 0, n_iters)
+
+
+def test_cvt_parity_weighted_ragged(pk):
+    f = workloads.blob_field((45, 38, 27), 11, "cpu").numpy()
+    _cvt_compare(pk, f, np.array([0.2, 0.45, 0.7], np.float32), 150, 1, 2, rs=3)
+
+
+def test_cvt_parity_flame(pk):
+    f, u = workloads.flame_field((40, 36, 32), 2, "cpu")
+    _cvt_compare(pk, f.numpy(), (np.arange(1, 9, dtype=np.float32) / np.float32(9)), 300, 1, 2)
+
+
+def test_cvt_config1_full(pk):
+    w = blob_case(64)
+    _cvt_compare(pk, w["field"].numpy(), w["iso"], 512, 0, 10)
+
+
+def _moment_ok(got_mean, got_m2, ref_mean, ref_m2, count):
+    n = np.maximum(count, 1)[:, None].astype(np.float64)
+    var_r, var_g = ref_m2 / n, got_m2 / n
+    msq = var_r + ref_mean ** 2
+    floor = 1e-6 * msq
+    assert np.all(np.abs(got_mean - ref_mean) <= 1e-6 * np.maximum(np.abs(ref_mean), floor) + 1e-300)
+    assert np.all(np.abs(var_g - var_r) <= 1e-6 * np.maximum(np.abs(var_r), floor) + 1e-300)
+
+
+def test_aggregate_and_merge_parity(pk):
+    w = blob_case(64)
+    f = w["field"].numpy()
+    band = oracle.classify(f, w["iso"])
+    comp, cb, cs, cf = oracle.label_components(band)
+    sp, sc, off, nc = oracle.seed(comp, None, len(cb), 512, 16, 1)
+    sp2, cell, dist, tr = oracle.cvt_iterate(band, None, sp, 2)
+    aux = w["aux"].numpy()
+    aux[2] += np.float32(50.0)  # far from zero: exercises the per-cell shift
+    lo, hi, scale = oracle.aux_range(cell, aux, 32)
+    ref = oracle.aggregate(cell, aux, len(sp2), lo, scale, 32)
+    gcell = torch.from_numpy(cell).cuda()
+    gaux = [torch.from_numpy(a).cuda() for a in aux]
+    gsp = torch.from_numpy(sp2).cuda()
+    ns = torch.tensor([len(sp2)], dtype=torch.int32, device="cuda")
+    st = pk.new_status()
+    glo, gsc = pk.aux_range(gcell, gaux, 32, st)
+    assert np.array_equal(cpu(glo), lo) and np.array_equal(cpu(gsc), scale)
+    got = pk.aggregate(gcell, gaux, gsp, ns, glo, gsc, 32, status=st)
+    pk.check_status(st)
+    assert np.array_equal(cpu(got["count"]), ref["count"])
+    assert np.array_equal(cpu(got["min"]), ref["min"])
+    assert np.array_equal(cpu(got["max"]), ref["max"])
+    assert np.array_equal(cpu(got["hist"]).view(np.uint32), ref["hist"])
+    _moment_ok(cpu(got["mean"]), cpu(got["m2"]), ref["mean"], ref["m2"], ref["count"])
+    # hierarchy
+    rc, rb, rv = oracle.merge_hierarchy(ref, sc, cb, len(w["iso"]) + 1)
+    gc, gb, gv = pk.merge_hierarchy(got, ns, torch.from_numpy(off).cuda(), torch.from_numpy(cb).cuda(),
+                                    torch.tensor([len(cb)], dtype=torch.int32, device="cuda"), len(cb),
+                                    len(w["iso"]) + 1)
+    for g, r in ((gc, rc), (gb, rb), (gv, rv)):
+        assert np.array_equal(cpu(g["count"]), r["count"])
+        assert np.array_equal(cpu(g["min"]), r["min"]) and np.array_equal(cpu(g["max"]), r["max"])
+        assert np.array_equal(cpu(g["hist"]).view(np.uint32), r["hist"])
+        _moment_ok(cpu(g["mean"]), cpu(g["m2"]), r["mean"], r["m2"], r["count"])
+
+
+def test_decompose_pipeline_config1(pk):
+    w = blob_case(64)
+    f = w["field"]
+    out = pk.decompose(f.cuda(), w["iso"], 512, 10, aux=[a.cuda() for a in w["aux"]], gamma=0, rng_seed=1)
+    band = oracle.classify(f.numpy(), w["iso"])
+    comp, cb, cs, cf = oracle.label_components(band)
+    sp, sc, off, nc = oracle.seed(comp, None, len(cb), 512, 16, 1)
+    sp2, cell, dist, tr = oracle.cvt_iterate(band, None, sp, 10)
+    ns = int(out["n_sites"].item())
+    assert np.array_equal(cpu(out["site_pos"])[:ns], sp2)
+    assert np.array_equal(cpu(out["cell"]), cell)
+    ref = oracle.aggregate(cell, w["aux"].numpy(), len(sp2), n_bins=32)
+    assert np.array_equal(cpu(out["cells"]["count"])[:ns], ref["count"])
+    assert np.array_equal(cpu(out["cells"]["hist"])[:ns].view(np.uint32), ref["hist"])
