@@ -22,6 +22,8 @@
 // and are resolved in a second pass by walking parents to the first LOS voxel (phi).  A
 // per-site pass rounds the centroid half up and walks the site toward it, stopping before
 // it would leave its band.
+#include <cstdio>
+
 #include "common.cuh"
 
 namespace lsrvt {
@@ -82,8 +84,9 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
     const uint8_t *__restrict__ band, Dims d, BrickGeom bg, unsigned long long *key, const int32_t *__restrict__ list_in,
     const int32_t *n_in, int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag, int32_t *work,
     int32_t *status) {
-    __shared__ uint32_t sd[HV];
-    __shared__ int32_t ss[HV];
+    // packed keys: one aligned 64-bit access per read/write, so a reader never pairs the
+    // distance of one update with the site of another
+    __shared__ unsigned long long sk[HV];
     __shared__ uint8_t sb[HV];
     __shared__ uint32_t changed[kRows];
     __shared__ uint32_t dirty[kRows];
@@ -111,8 +114,7 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
                 k = __ldcg(key + g);
             }
             sb[i] = b;
-            sd[i] = (uint32_t)(k >> 32);
-            ss[i] = (int32_t)(uint32_t)k;
+            sk[i] = k;
         }
         if (tid < kRows) {
             changed[tid] = 0;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
                 e = edges_from_same(S);
             }
             em[j] = e;
-            orig[j] = make_key(sd[h], ss[h]);
+            orig[j] = sk[h];
         }
         __syncthreads();
         // ---- relaxation steps
@@ -152,14 +154,15 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
                 if (!e || !((dirty[row] >> lx) & 1u)) continue;
                 int ly = row & (RY - 1), lz = row >> 3;
                 int h = (lx + 1) + HX * ((ly + 1) + HY * (lz + 1));
-                unsigned long long best = make_key(sd[h], ss[h]);
+                unsigned long long best = sk[h];
                 unsigned long long own = best;
 #pragma unroll
                 for (int o = 0; o < 27; ++o) {
                     if (o == 13) continue;
                     if (!((e >> o) & 1u)) continue;
                     int u = h + halo_off(o);
-                    uint32_t du = sd[u];
+                    unsigned long long ku = sk[u];
+                    uint32_t du = (uint32_t)(ku >> 32);
                     if (du == kInf32) continue;
                     unsigned long long cd = (unsigned long long)du + weight_of(o);
                     if (cd >= kInf32) {
@@ -167,12 +170,11 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
                         continue;
                     }
                     if ((cd << 32) > best) continue;  // distance alone already worse
-                    unsigned long long cand = (cd << 32) | (uint32_t)ss[u];
+                    unsigned long long cand = (cd << 32) | (ku & 0xFFFFFFFFull);
                     if (cand < best) best = cand;
                 }
                 if (best < own) {
-                    sd[h] = (uint32_t)(best >> 32);
-                    ss[h] = (int32_t)(uint32_t)best;
+                    sk[h] = best;
                     atomicOr(&changed[row], 1u << lx);
                     any = 1;
                 }
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
             int i = tid + kRelaxThreads * j;
             int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
             int h = (lx + 1) + HX * ((ly + 1) + HY * (lz + 1));
-            unsigned long long nk = make_key(sd[h], ss[h]);
+            unsigned long long nk = sk[h];
             if (nk == orig[j]) continue;
             int gx = ox + lx, gy = oy + ly, gz = oz + lz;
             key[gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)] = nk;
@@ -394,6 +396,10 @@ __global__ void update_nonlos_kernel(const uint16_t *__restrict__ q, Dims d, con
             if (++guard > n) { u = -1; break; }
         }
         if (u < 0) {
+#ifdef LSRVT_DEBUG
+            printf("nonlos fail v=%d par=%d key=%llx losbit=%u cnt=%d i=%d\n", v, par[v], key[v],
+                   (los_bits[v >> 5] >> (v & 31)) & 1u, cnt, i);
+#endif
             set_status(status, LSRVT_ERR_TIMEOUT);
             continue;
         }
