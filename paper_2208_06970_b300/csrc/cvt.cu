@@ -76,10 +76,6 @@ __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
     return e;
 }
 
-__device__ __forceinline__ unsigned long long make_key(uint32_t d, int32_t s) {
-    return ((unsigned long long)d << 32) | (uint32_t)s;
-}
-
 __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
     const uint8_t *__restrict__ band, Dims d, BrickGeom bg, unsigned long long *key, const int32_t *__restrict__ list_in,
     const int32_t *n_in, int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag, int32_t *work,
@@ -231,10 +227,73 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
     }
 }
 
-// sites: key of the site voxel = (0, lowest site id); queue the bricks that hold sites
-__global__ void place_sites_kernel(const int32_t *__restrict__ site_pos, const int32_t *n_sites_dev, int32_t max_sites,
-                                   Dims d, BrickGeom bg, unsigned long long *key, int32_t *list, int32_t *n_list,
-                                   uint32_t *flags, uint32_t tag, int32_t *status) {
+// ---------------------------------------------------------------- closed-form initialisation
+// Lower bound: the unconstrained 26-neighbour chamfer distance C(v, s) = (a-b) W1 +
+// (b-c) W2 + c W3 (a >= b >= c the sorted |v - s|) never exceeds the restricted geodesic
+// gd(v, s).  So min over the same-band sites of (C(v, s), s) is a lexicographic lower
+// bound of v's key; if one shortest chamfer path from v to that site s* stays in the band
+// (every edge box in band), gd(v, s*) = C(v, s*) is attained and the bound IS the key.
+// Sites are binned by brick; a CTA gathers the sites of the bricks within +-1 (x) / +-2
+// (y, z) bricks, so any site outside is at Chebyshev distance >= gap(v) and chamfer
+// distance >= gap(v) W1; the key is confirmed only when it is below that.  Unconfirmed
+// voxels start at +inf and their bricks are relaxed.
+constexpr int kSX = 1, kSY = 2, kSZ = 2;
+constexpr int kMaxCand = 1024;
+
+__device__ __forceinline__ unsigned long long chamfer(int dx, int dy, int dz) {
+    unsigned a = abs(dx), b = abs(dy), c = abs(dz), t;
+    if (a < b) { t = a; a = b; b = t; }
+    if (b < c) { t = b; b = c; c = t; }
+    if (a < b) { t = a; a = b; b = t; }
+    return (unsigned long long)(a - b) * kWFace + (unsigned long long)(b - c) * kWEdge +
+           (unsigned long long)c * kWCorner;
+}
+
+// One shortest chamfer path from v to s (26-connected digital line: the dominant axis
+// advances every step, the middle axis by rounded proportion, the smallest axis only on
+// middle-axis steps so that no corner move is split); true if every move's box is in band b.
+__device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, Dims d, int vx, int vy, int vz, int sx,
+                                     int sy, int sz, uint8_t b) {
+    int D[3] = {sx - vx, sy - vy, sz - vz};
+    int A[3] = {abs(D[0]), abs(D[1]), abs(D[2])};
+    int S[3] = {D[0] < 0 ? -1 : 1, D[1] < 0 ? -1 : 1, D[2] < 0 ? -1 : 1};
+    int i = 0, j = 1, k = 2, t;
+    if (A[i] < A[j]) { t = i; i = j; j = t; }
+    if (A[j] < A[k]) { t = j; j = k; k = t; }
+    if (A[i] < A[j]) { t = i; i = j; j = t; }
+    const int ai = A[i], aj = A[j], ak = A[k];
+    int p[3] = {vx, vy, vz};
+    int jc = 0, kc = 0;
+    const int64_t sxy = (int64_t)d.nx * d.ny;
+    for (int step = 1; step <= ai; ++step) {
+        int jt = (int)((2LL * step * aj + ai) / (2LL * ai));
+        bool mj = jt > jc;
+        bool mk = false;
+        if (mj) {
+            int kt = (int)((2LL * (jc + 1) * ak + aj) / (2LL * aj));
+            mk = kt > kc;
+        }
+        int m[3] = {0, 0, 0};
+        m[i] = S[i];
+        if (mj) m[j] = S[j];
+        if (mk) m[k] = S[k];
+        // every voxel of the box spanned by p and p + m, except p itself
+        for (int az = 0; az <= (m[2] != 0); ++az)
+            for (int ay = 0; ay <= (m[1] != 0); ++ay)
+                for (int ax = 0; ax <= (m[0] != 0); ++ax) {
+                    if (!ax && !ay && !az) continue;
+                    int64_t g = (p[0] + ax * m[0]) + (int64_t)d.nx * (p[1] + ay * m[1]) + sxy * (p[2] + az * m[2]);
+                    if (__ldg(band + g) != b) return false;
+                }
+        p[0] += m[0]; p[1] += m[1]; p[2] += m[2];
+        jc += mj;
+        kc += mk;
+    }
+    return true;
+}
+
+__global__ void site_bin_count_kernel(const int32_t *__restrict__ site_pos, const int32_t *n_sites_dev,
+                                      int32_t max_sites, Dims d, BrickGeom bg, int64_t *bin_cnt, int32_t *status) {
     int32_t ns = min(*n_sites_dev, max_sites);
     int64_t n = d.n();
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
@@ -243,13 +302,141 @@ __global__ void place_sites_kernel(const int32_t *__restrict__ site_pos, const i
             set_status(status, LSRVT_ERR_INVALID_ARG);
             continue;
         }
-        atomicMin(key + p, make_key(0u, s));
         int32_t x = p % d.nx, y = (p / d.nx) % d.ny, z = p / (d.nx * d.ny);
-        int nb = x / RX + bg.nbx * (y / RY + bg.nby * (z / RZ));
-        if (atomicExch(&flags[nb], tag) != tag) {
-            int pos = atomicAdd(n_list, 1);
-            list[pos] = nb;
+        atomicAdd((unsigned long long *)&bin_cnt[x / RX + bg.nbx * (y / RY + bg.nby * (z / RZ))], 1ULL);
+    }
+}
+
+__global__ void site_bin_fill_kernel(const int32_t *__restrict__ site_pos, const int32_t *n_sites_dev,
+                                     int32_t max_sites, const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
+                                     const int64_t *__restrict__ bin_off, int32_t *cursor, int4 *cand) {
+    int32_t ns = min(*n_sites_dev, max_sites);
+    int64_t n = d.n();
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
+        int32_t p = site_pos[s];
+        if (p < 0 || p >= n) continue;
+        int32_t x = p % d.nx, y = (p / d.nx) % d.ny, z = p / (d.nx * d.ny);
+        int b = x / RX + bg.nbx * (y / RY + bg.nby * (z / RZ));
+        int64_t pos = bin_off[b] + atomicAdd(&cursor[b], 1);
+        cand[pos] = make_int4(s, x, y, z | ((int)band[p] << 24));
+    }
+}
+
+__global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
+                                                            const int64_t *__restrict__ bin_off,
+                                                            const int4 *__restrict__ cand, unsigned long long *key,
+                                                            int32_t *list_out, int32_t *n_out, uint32_t *flags,
+                                                            uint32_t tag) {
+    __shared__ int4 cs[kMaxCand];
+    __shared__ unsigned long long ck[kMaxCand];
+    __shared__ int ncand_s, unknown_s;
+    const int tid = threadIdx.x;
+    const int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
+    for (int64_t brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+        const int bx = (int)(brick % bg.nbx), by = (int)((brick / bg.nbx) % bg.nby),
+                  bz = (int)(brick / ((int64_t)bg.nbx * bg.nby));
+        const int ox = bx * RX, oy = by * RY, oz = bz * RZ;
+        if (tid == 0) { ncand_s = 0; unknown_s = 0; }
+        __syncthreads();
+        // gather the sites of the neighbouring bins
+        constexpr int NBX = 2 * kSX + 1, NBY = 2 * kSY + 1, NBZ = 2 * kSZ + 1;
+        for (int q = tid; q < NBX * NBY * NBZ; q += blockDim.x) {
+            int cx = bx + q % NBX - kSX, cy = by + (q / NBX) % NBY - kSY, cz = bz + q / (NBX * NBY) - kSZ;
+            if (cx < 0 || cx >= bg.nbx || cy < 0 || cy >= bg.nby || cz < 0 || cz >= bg.nbz) continue;
+            int64_t bb = cx + (int64_t)bg.nbx * (cy + (int64_t)bg.nby * cz);
+            int64_t a0 = bin_off[bb], a1 = bin_off[bb + 1];
+            int cnt = (int)(a1 - a0);
+            if (cnt == 0) continue;
+            int at = atomicAdd(&ncand_s, cnt);
+            for (int r = 0; r < cnt && at + r < kMaxCand; ++r) cs[at + r] = cand[a0 + r];
         }
+        __syncthreads();
+        const int nc = ncand_s;
+        const bool overflow = nc > kMaxCand;
+        int npow2 = 1;
+        if (!overflow) {
+            while (npow2 < nc) npow2 <<= 1;
+            for (int i = tid; i < npow2; i += blockDim.x) {
+                unsigned long long e = ~0ULL;
+                if (i < nc) {
+                    int4 c = cs[i];
+                    int cz = c.w & 0xFFFFFF;
+                    int gx = max(max(ox - c.y, c.y - (ox + RX - 1)), 0);
+                    int gy = max(max(oy - c.z, c.z - (oy + RY - 1)), 0);
+                    int gz = max(max(oz - cz, cz - (oz + RZ - 1)), 0);
+                    unsigned long long lb = (unsigned long long)max(gx, max(gy, gz)) * kWFace;
+                    e = (lb << 32) | (unsigned)i;
+                }
+                ck[i] = e;
+            }
+            block_bitonic_sort(ck, npow2);
+        }
+        // search box in voxels and whether it reaches the volume faces
+        const int lox = (bx - kSX) * RX, hix = (bx + kSX + 1) * RX - 1;
+        const int loy = (by - kSY) * RY, hiy = (by + kSY + 1) * RY - 1;
+        const int loz = (bz - kSZ) * RZ, hiz = (bz + kSZ + 1) * RZ - 1;
+        int unknown = 0;
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j) {
+            int i = tid + kRelaxThreads * j;
+            int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
+            int x = ox + lx, y = oy + ly, z = oz + lz;
+            if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
+            int64_t g = x + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+            uint8_t b = band[g];
+            unsigned long long best = kInfKey;
+            int best_i = -1;
+            if (b != kInvalidBand && !overflow) {
+                for (int t = 0; t < nc; ++t) {
+                    unsigned long long e = ck[t];
+                    if ((e >> 32) > (best >> 32)) break;
+                    int4 c = cs[(unsigned)e];
+                    if ((uint8_t)(c.w >> 24) != b) continue;
+                    unsigned long long cd = chamfer(c.y - x, c.z - y, (c.w & 0xFFFFFF) - z);
+                    if (cd >= kInf32) continue;
+                    unsigned long long k2 = (cd << 32) | (unsigned)c.x;
+                    if (k2 < best) { best = k2; best_i = (int)(unsigned)e; }
+                }
+                if (best != kInfKey) {
+                    long long gap = 1LL << 40;
+                    if (lox > 0) gap = min(gap, (long long)(x - lox + 1));
+                    if (hix < d.nx - 1) gap = min(gap, (long long)(hix - x + 1));
+                    if (loy > 0) gap = min(gap, (long long)(y - loy + 1));
+                    if (hiy < d.ny - 1) gap = min(gap, (long long)(hiy - y + 1));
+                    if (loz > 0) gap = min(gap, (long long)(z - loz + 1));
+                    if (hiz < d.nz - 1) gap = min(gap, (long long)(hiz - z + 1));
+                    bool in_range = (best >> 32) < (unsigned long long)gap * kWFace;
+                    bool ok = false;
+                    if (in_range) {
+                        int4 c = cs[best_i];
+                        ok = chamfer_path_in_band(band, d, x, y, z, c.y, c.z, c.w & 0xFFFFFF, b);
+                    }
+                    if (!ok) best = kInfKey;
+                }
+                if (best == kInfKey) unknown = 1;
+            } else if (b != kInvalidBand) {
+                unknown = 1;  // candidate list overflowed: relax the whole brick
+            }
+            key[g] = best;
+        }
+        if (unknown) unknown_s = 1;
+        __syncthreads();
+        // the brick's own sites: distance 0, lowest id (needed where the candidate list overflowed)
+        {
+            int64_t a0 = bin_off[brick], a1 = bin_off[brick + 1];
+            for (int64_t r = a0 + tid; r < a1; r += blockDim.x) {
+                int4 c = cand[r];
+                int64_t g = c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * (c.w & 0xFFFFFF));
+                atomicMin(key + g, (unsigned long long)(uint32_t)c.x);
+            }
+        }
+        if (tid == 0 && unknown_s) {
+            if (atomicExch(&flags[brick], tag) != tag) {
+                int pos = atomicAdd(n_out, 1);
+                list_out[pos] = (int32_t)brick;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -461,6 +648,11 @@ struct CvtWs {
     unsigned long long *sums;
     uint32_t *flags;
     int32_t *list[2];
+    int64_t *bin_off;
+    int32_t *bin_cursor;
+    int4 *cand;
+    int64_t *bin_total;
+    void *scan;
 };
 
 CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need) {
@@ -478,6 +670,11 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.flags = c.take<uint32_t>(nbricks);
     w.list[0] = c.take<int32_t>(nbricks);
     w.list[1] = c.take<int32_t>(nbricks);
+    w.bin_off = c.take<int64_t>(nbricks + 1);
+    w.bin_cursor = c.take<int32_t>(nbricks);
+    w.cand = c.take<int4>((int64_t)max_sites + 1);
+    w.bin_total = c.take<int64_t>(1);
+    w.scan = c.take<char>(scan_temp_bytes(nbricks + 1));
     *need = c.used;
     return w;
 }
@@ -504,12 +701,31 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
                             int32_t max_sites, CvtWs &w, uint32_t &tag, int32_t *status, cudaStream_t s) {
     BrickGeom bg{(d.nx + RX - 1) / RX, (d.ny + RY - 1) / RY, (d.nz + RZ - 1) / RZ};
     int64_t n = d.n();
-    cudaMemsetAsync(w.key, 0xFF, sizeof(unsigned long long) * n, s);
+    int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
+    (void)n;
     cudaMemsetAsync(w.counters + 1, 0, sizeof(int32_t) * 4, s);
+    cudaMemsetAsync(w.bin_off, 0, sizeof(int64_t) * (nbricks + 1), s);
+    cudaMemsetAsync(w.bin_cursor, 0, sizeof(int32_t) * nbricks, s);
+    site_bin_count_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites, d, bg,
+                                                                            w.bin_off, status);
+    exclusive_scan_i64(w.bin_off, nbricks + 1, w.bin_total, w.scan, s);
+    site_bin_fill_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites, band, d,
+                                                                           bg, w.bin_off, w.bin_cursor, w.cand);
     ++tag;
-    place_sites_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites, d, bg, w.key,
-                                                                         w.list[0], w.counters + 1, w.flags, tag,
-                                                                         status);
+    int nb_cfi = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cfi, cfi_kernel, kRelaxThreads, 0);
+    if (nb_cfi < 1) nb_cfi = 1;
+    int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
+    cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, d, bg, w.bin_off, w.cand, w.key, w.list[0], w.counters + 1,
+                                               w.flags, tag);
+#ifdef LSRVT_DEBUG
+    {
+        int32_t q0 = 0;
+        cudaMemcpyAsync(&q0, w.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        fprintf(stderr, "cfi: %d of %lld bricks queued\n", q0, (long long)nbricks);
+    }
+#endif
     int nb_per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, relax_round_kernel, kRelaxThreads, 0);
     if (nb_per_sm < 1) nb_per_sm = 1;
@@ -522,6 +738,14 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
                                                            w.counters + 3 + cur, status);
         round_advance_kernel<<<1, 1, 0, s>>>(w.counters + 1 + cur, w.counters + 3 + cur);
         cur = 1 - cur;
+#ifdef LSRVT_DEBUG
+        {
+            int32_t pend = 0;
+            cudaMemcpyAsync(&pend, w.counters + 1 + cur, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            fprintf(stderr, "round %d next=%d\n", r, pend);
+        }
+#endif
         if ((r + 1) % kRoundsPerCheck == 0) {
             int32_t pending = 0;
             cudaMemcpyAsync(&pending, w.counters + 1 + cur, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -11,9 +11,10 @@ on the device they are given (CPU or CUDA) so large volumes are built quickly on
 Recipes (the five workloads):
   blobs   : sum of Gaussian blobs, centres U[0, side)^3, sigma U(3, 10), amplitude
             U(0.5, 1), plus N(0, 0.02) noise.  24 blobs per 64^3 of volume.
-  flame   : u = isotropic spectral field with amplitude ~ |k|^(-11/6) (E(k) ~ k^(-5/3)),
-            random phases, unit std; f = (1 + tanh((x - nx/2 + 24 u) / 4)) / 2, a
-            progress-variable-like front.
+  flame   : u = isotropic spectral field with amplitude ~ |k|^(-11/6) (E(k) ~ k^(-5/3))
+            and a dissipation-range cutoff exp(-2.6 k eta), eta = 2 voxels, random phases,
+            unit std; f = (1 + tanh((x - nx/2 + 24 u) / 8)) / 2, a progress-variable-like
+            front about 16 voxels thick.
   corr    : m correlated Gaussian variables x = mu + L z, L L^T = A A^T / m + 0.1 I.
 """
 import math
@@ -63,16 +64,23 @@ def blob_field(dims, seed, device="cpu", n_blobs=None, noise=0.02, window=True):
     return f
 
 
-def spectral_field(dims, seed, device="cpu", slope=-11.0 / 6.0):
-    """Isotropic Gaussian random field with spectral amplitude |k|^slope, unit std."""
+def spectral_field(dims, seed, device="cpu", slope=-11.0 / 6.0, eta=2.0):
+    """Isotropic Gaussian random field, unit std, spectral amplitude |k|^slope (inertial
+    range) times exp(-2.6 k eta) (the dissipation range of Pope's model spectrum,
+    exp(-5.2 k eta) in energy, with Kolmogorov scale eta in voxels), so that the field is
+    smooth at the grid scale like a resolved DNS.  eta = 0 disables the cutoff."""
     nx, ny, nz = dims
     g = _gen(seed, device)
     kz = torch.fft.fftfreq(nz, device=device).view(nz, 1, 1)
     ky = torch.fft.fftfreq(ny, device=device).view(1, ny, 1)
     kx = torch.fft.rfftfreq(nx, device=device).view(1, 1, nx // 2 + 1)
     k = torch.sqrt((kx * nx) ** 2 + (ky * ny) ** 2 + (kz * nz) ** 2)
+    kphys = 2.0 * math.pi * torch.sqrt(kx ** 2 + ky ** 2 + kz ** 2)  # radians per voxel
     k[0, 0, 0] = 1.0
     amp = k.pow(slope)
+    if eta > 0:
+        amp = amp * torch.exp(-2.6 * kphys * eta)
+    del kphys
     amp[0, 0, 0] = 0.0
     del k
     re = torch.randn(amp.shape, generator=g, device=device)
@@ -86,12 +94,13 @@ def spectral_field(dims, seed, device="cpu", slope=-11.0 / 6.0):
     return u.to(torch.float32).contiguous()
 
 
-def flame_field(dims, seed, device="cpu"):
-    """Progress-variable-like flame front wrinkled by spectral turbulence.  Returns (f, u)."""
+def flame_field(dims, seed, device="cpu", width=8.0):
+    """Progress-variable-like flame front wrinkled by spectral turbulence.  Returns (f, u).
+    The tanh width (8 voxels) makes the front about 16 voxels thick, resolved like a DNS flame."""
     nx, ny, nz = dims
     u = spectral_field(dims, seed, device)
     x = torch.arange(nx, dtype=torch.float32, device=device).view(1, 1, nx)
-    f = 0.5 * (1.0 + torch.tanh((x - nx / 2.0 + 24.0 * u) / 4.0))
+    f = 0.5 * (1.0 + torch.tanh((x - nx / 2.0 + 24.0 * u) / width))
     return f.to(torch.float32).contiguous(), u
 
 
