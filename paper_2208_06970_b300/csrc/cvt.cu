@@ -227,18 +227,110 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
     }
 }
 
+// ---------------------------------------------------------------- clearance field
+// c(v) = min(K, L-infinity distance from v to the nearest "boundary" voxel), a boundary
+// voxel being one with a 26-neighbour of another band or outside the volume.  Every voxel
+// within L-infinity distance c(v) of v then has band(v) (the (c-1)-ball holds no boundary
+// voxel, so it and its neighbours share one band), so c(v) path moves from v need no band
+// test.  The bands never change during the Lloyd iterations, so c is computed once per
+// call: S_0 = non-boundary voxels as a bit volume (32 voxels per word along x), S_k+1 =
+// S_k eroded by the 3x3x3 cube (shift-and of rows), c = number of sets holding v.
+constexpr int kClearLevels = 32;
+
+struct BitGeom {
+    int32_t W;  // words per x row
+    __host__ __device__ int64_t words(Dims d) const { return (int64_t)W * d.ny * d.nz; }
+};
+
+__global__ void clear_init_kernel(const uint8_t *__restrict__ band, Dims d, BitGeom bgm, uint32_t *S0) {
+    int64_t nw = bgm.words(d);
+    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nw;
+         wi += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int lane = threadIdx.x & 31;
+        int wx = (int)(wi % bgm.W);
+        int64_t row = wi / bgm.W;
+        int y = (int)(row % d.ny), z = (int)(row / d.ny);
+        int x = wx * 32 + lane;
+        bool ok = x >= 1 && x < d.nx - 1 && y >= 1 && y < d.ny - 1 && z >= 1 && z < d.nz - 1;
+        if (ok) {
+            int64_t g = x + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+            uint8_t b = band[g];
+            ok = b != kInvalidBand;
+            for (int dz = -1; dz <= 1 && ok; ++dz)
+                for (int dy = -1; dy <= 1 && ok; ++dy)
+                    for (int dx = -1; dx <= 1 && ok; ++dx)
+                        ok = band[g + dx + (int64_t)d.nx * (dy + (int64_t)d.ny * dz)] == b;
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) S0[wi] = bal;
+    }
+}
+
+// x-erosion of word wx of a row (bits outside the row count as 0)
+__device__ __forceinline__ uint32_t erode_x(const uint32_t *row, int wx, int W) {
+    uint32_t w = row[wx];
+    uint32_t lo = wx > 0 ? row[wx - 1] : 0u, hi = wx + 1 < W ? row[wx + 1] : 0u;
+    uint32_t left = (w << 1) | (lo >> 31);   // bit i <- bit i-1
+    uint32_t right = (w >> 1) | (hi << 31);  // bit i <- bit i+1
+    return w & left & right;
+}
+
+__global__ void clear_erode_kernel(const uint32_t *__restrict__ Sk, Dims d, BitGeom bgm, uint32_t *Sk1) {
+    int64_t nw = bgm.words(d);
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < nw; wi += (int64_t)gridDim.x * blockDim.x) {
+        int wx = (int)(wi % bgm.W);
+        int64_t row = wi / bgm.W;
+        int y = (int)(row % d.ny), z = (int)(row / d.ny);
+        uint32_t acc = 0xffffffffu;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy) {
+                int y2 = y + dy, z2 = z + dz;
+                if (y2 < 0 || y2 >= d.ny || z2 < 0 || z2 >= d.nz) { acc = 0; continue; }
+                acc &= erode_x(Sk + ((int64_t)y2 + (int64_t)d.ny * z2) * bgm.W, wx, bgm.W);
+            }
+        Sk1[wi] = acc;
+    }
+}
+
+__global__ void clear_count_kernel(const uint32_t *__restrict__ planes, Dims d, BitGeom bgm, int levels,
+                                   uint8_t *__restrict__ clr) {
+    int64_t n = d.n();
+    int64_t nw = bgm.words(d);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(v % d.nx);
+        int64_t row = v / d.nx;
+        int64_t wi = row * bgm.W + (x >> 5);
+        uint32_t bit = 1u << (x & 31);
+        int c = 0;
+        for (int k = 0; k < levels; ++k) {
+            if (!(planes[(int64_t)k * nw + wi] & bit)) break;
+            ++c;
+        }
+        clr[v] = (uint8_t)c;
+    }
+}
+
 // ---------------------------------------------------------------- closed-form initialisation
 // Lower bound: the unconstrained 26-neighbour chamfer distance C(v, s) = (a-b) W1 +
 // (b-c) W2 + c W3 (a >= b >= c the sorted |v - s|) never exceeds the restricted geodesic
 // gd(v, s).  So min over the same-band sites of (C(v, s), s) is a lexicographic lower
 // bound of v's key; if one shortest chamfer path from v to that site s* stays in the band
 // (every edge box in band), gd(v, s*) = C(v, s*) is attained and the bound IS the key.
-// Sites are binned by brick; a CTA gathers the sites of the bricks within +-1 (x) / +-2
-// (y, z) bricks, so any site outside is at Chebyshev distance >= gap(v) and chamfer
-// distance >= gap(v) W1; the key is confirmed only when it is below that.  Unconfirmed
-// voxels start at +inf and their bricks are relaxed.
-constexpr int kSX = 1, kSY = 2, kSZ = 2;
+// Candidates come in stages of growing boxes around the brick: first the bricks within
+// +-1 (x) / +-2 (y, z) bricks (fine bins), then shells of 32^3 coarse cells at Chebyshev
+// distance 1, 2, ... (coarse bins); only sites whose band occurs in the brick are taken.
+// A site outside the current box is at Chebyshev distance >= gap(v) and chamfer distance
+// >= gap(v) W1, so a voxel is settled once its best is below that.  Voxels not settled,
+// or whose path check fails, start at +inf and their bricks are relaxed.
 constexpr int kMaxCand = 1024;
+// largest chamfer distance from the brick centre (RX/2, RY/2, RZ/2) to a brick voxel: (8, 4, 4)
+constexpr unsigned long long kBrickChamferRadius = (RX / 2 - RY / 2) * 65536ull + (RY / 2) * 113512ull;
+constexpr int kCoarse = 32, kCoarseShift = 5;
+constexpr int kMaxRho = 12;
+
+struct CoarseGeom {
+    int32_t ncx, ncy, ncz;
+};
 
 __device__ __forceinline__ unsigned long long chamfer(int dx, int dy, int dz) {
     unsigned a = abs(dx), b = abs(dy), c = abs(dz), t;
@@ -249,51 +341,100 @@ __device__ __forceinline__ unsigned long long chamfer(int dx, int dy, int dz) {
            (unsigned long long)c * kWCorner;
 }
 
-// One shortest chamfer path from v to s (26-connected digital line: the dominant axis
-// advances every step, the middle axis by rounded proportion, the smallest axis only on
-// middle-axis steps so that no corner move is split); true if every move's box is in band b.
-__device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, Dims d, int vx, int vy, int vz, int sx,
-                                     int sy, int sz, uint8_t b) {
-    int D[3] = {sx - vx, sy - vy, sz - vz};
-    int A[3] = {abs(D[0]), abs(D[1]), abs(D[2])};
-    int S[3] = {D[0] < 0 ? -1 : 1, D[1] < 0 ? -1 : 1, D[2] < 0 ? -1 : 1};
-    int i = 0, j = 1, k = 2, t;
-    if (A[i] < A[j]) { t = i; i = j; j = t; }
-    if (A[j] < A[k]) { t = j; j = k; k = t; }
-    if (A[i] < A[j]) { t = i; i = j; j = t; }
-    const int ai = A[i], aj = A[j], ak = A[k];
-    int p[3] = {vx, vy, vz};
-    int jc = 0, kc = 0;
+// unsigned division, 32-bit when both operands fit (the common case for volumes <= 2048^3)
+__device__ __forceinline__ unsigned long long udiv(unsigned long long a, unsigned long long b) {
+    if (((a | b) >> 32) == 0) return (unsigned)a / (unsigned)b;
+    return a / b;
+}
+
+// One shortest chamfer path from v to s (26-connected digital line: the dominant axis i
+// advances every move, the middle axis j after move t has advanced round(t aj / ai)
+// times, the smallest axis k after m middle-axis advances round(m ak / aj) times, so it
+// only moves together with j and no corner move is split).  True if every move's box is
+// in band b.  From a voxel p with clearance c >= 1 the next c moves are in band and are
+// skipped without tests.  Single moves advance Bresenham error terms (no division).
+__device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d,
+                                     int vx, int vy, int vz, int sx, int sy, int sz, uint8_t b, int cs) {
+    const int D0 = sx - vx, D1 = sy - vy, D2 = sz - vz;
+    const int A0 = abs(D0), A1 = abs(D1), A2 = abs(D2);
+    // axes sorted by extent: i >= j >= k
+    int i = 0, j = 1, k = 2;
+    int Ai = A0, Aj = A1, Ak = A2;
+    if (Ai < Aj) { int t = i; i = j; j = t; t = Ai; Ai = Aj; Aj = t; }
+    if (Aj < Ak) { int t = j; j = k; k = t; t = Aj; Aj = Ak; Ak = t; }
+    if (Ai < Aj) { int t = i; i = j; j = t; t = Ai; Ai = Aj; Aj = t; }
+    if (Ai == 0) return true;
     const int64_t sxy = (int64_t)d.nx * d.ny;
-    for (int step = 1; step <= ai; ++step) {
-        int jt = (int)((2LL * step * aj + ai) / (2LL * ai));
-        bool mj = jt > jc;
+    // strides and signs along i, j, k in linear index space
+    const int64_t stride[3] = {1, d.nx, sxy};
+    const int sgn[3] = {D0 < 0 ? -1 : 1, D1 < 0 ? -1 : 1, D2 < 0 ? -1 : 1};
+    const int64_t si = stride[i] * sgn[i], sj = stride[j] * sgn[j], sk = stride[k] * sgn[k];
+    const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
+    const unsigned long long ai2 = 2ULL * Ai, aj2 = 2ULL * Aj;
+    int mv = 0, jc = 0, kc = 0;
+    // error terms: ej = 2 mv aj + ai - 2 ai jc in [0, 2ai); ek = 2 jc ak + aj - 2 aj kc in [0, 2aj)
+    long long ej = Ai, ek = Aj;
+    int64_t g = v0;
+    while (mv < Ai) {
+        // the rest of the path approaches s monotonically on every axis, so once within the
+        // site's own clearance ball it stays in band
+        int rem = max(Ai - mv, max(Aj - jc, Ak - kc));
+        if (rem <= cs) return true;
+        int c = __ldg(clr + g);
+        if (c >= 1) {
+            int mv2 = mv + c < Ai ? mv + c : Ai;
+            unsigned long long nj = 2ULL * mv2 * Aj + Ai;
+            jc = (int)udiv(nj, ai2);
+            ej = (long long)(nj - ai2 * jc);
+            if (Aj) {
+                unsigned long long nk = 2ULL * jc * Ak + Aj;
+                kc = (int)udiv(nk, aj2);
+                ek = (long long)(nk - aj2 * kc);
+            }
+            mv = mv2;
+            g = v0 + si * mv + sj * jc + sk * kc;
+            continue;
+        }
+        ej += 2LL * Aj;
+        bool mj = ej >= (long long)ai2;
+        if (mj) ej -= (long long)ai2;
         bool mk = false;
         if (mj) {
-            int kt = (int)((2LL * (jc + 1) * ak + aj) / (2LL * aj));
-            mk = kt > kc;
+            ek += 2LL * Ak;
+            mk = ek >= (long long)aj2;
+            if (mk) ek -= (long long)aj2;
         }
-        int m[3] = {0, 0, 0};
-        m[i] = S[i];
-        if (mj) m[j] = S[j];
-        if (mk) m[k] = S[k];
-        // every voxel of the box spanned by p and p + m, except p itself
-        for (int az = 0; az <= (m[2] != 0); ++az)
-            for (int ay = 0; ay <= (m[1] != 0); ++ay)
-                for (int ax = 0; ax <= (m[0] != 0); ++ax) {
-                    if (!ax && !ay && !az) continue;
-                    int64_t g = (p[0] + ax * m[0]) + (int64_t)d.nx * (p[1] + ay * m[1]) + sxy * (p[2] + az * m[2]);
-                    if (__ldg(band + g) != b) return false;
-                }
-        p[0] += m[0]; p[1] += m[1]; p[2] += m[2];
+        // box of the move g -> g + mi + (mj) + (mk), without g itself
+        const int64_t ci = si, cj = mj ? sj : 0, ck = mk ? sk : 0;
+        if (__ldg(band + g + ci) != b) return false;
+        if (mj) {
+            if (__ldg(band + g + cj) != b || __ldg(band + g + ci + cj) != b) return false;
+        }
+        if (mk) {
+            if (__ldg(band + g + ck) != b || __ldg(band + g + ci + ck) != b || __ldg(band + g + cj + ck) != b ||
+                __ldg(band + g + ci + cj + ck) != b)
+                return false;
+        }
+        g += ci + cj + ck;
+        ++mv;
         jc += mj;
         kc += mk;
     }
     return true;
 }
 
+// site bins: one pass counts, a scan gives offsets, a second pass fills entries
+// (site id, x, y, z | band << 24); the fine bins are the bricks, the coarse bins 32^3 cells
+__device__ __forceinline__ int64_t fine_bin(int x, int y, int z, BrickGeom bg) {
+    return x / RX + (int64_t)bg.nbx * (y / RY + (int64_t)bg.nby * (z / RZ));
+}
+__device__ __forceinline__ int64_t coarse_bin(int x, int y, int z, CoarseGeom cg) {
+    return (x >> kCoarseShift) + (int64_t)cg.ncx * ((y >> kCoarseShift) + (int64_t)cg.ncy * (z >> kCoarseShift));
+}
+
 __global__ void site_bin_count_kernel(const int32_t *__restrict__ site_pos, const int32_t *n_sites_dev,
-                                      int32_t max_sites, Dims d, BrickGeom bg, int64_t *bin_cnt, int32_t *status) {
+                                      int32_t max_sites, Dims d, BrickGeom bg, CoarseGeom cg, int64_t *fine_cnt,
+                                      int64_t *coarse_cnt, int32_t *status) {
     int32_t ns = min(*n_sites_dev, max_sites);
     int64_t n = d.n();
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
@@ -303,32 +444,233 @@ __global__ void site_bin_count_kernel(const int32_t *__restrict__ site_pos, cons
             continue;
         }
         int32_t x = p % d.nx, y = (p / d.nx) % d.ny, z = p / (d.nx * d.ny);
-        atomicAdd((unsigned long long *)&bin_cnt[x / RX + bg.nbx * (y / RY + bg.nby * (z / RZ))], 1ULL);
+        atomicAdd((unsigned long long *)&fine_cnt[fine_bin(x, y, z, bg)], 1ULL);
+        atomicAdd((unsigned long long *)&coarse_cnt[coarse_bin(x, y, z, cg)], 1ULL);
     }
 }
 
 __global__ void site_bin_fill_kernel(const int32_t *__restrict__ site_pos, const int32_t *n_sites_dev,
                                      int32_t max_sites, const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
-                                     const int64_t *__restrict__ bin_off, int32_t *cursor, int4 *cand) {
+                                     CoarseGeom cg, const int64_t *__restrict__ fine_off, int32_t *fine_cur,
+                                     int4 *fine_cand, const int64_t *__restrict__ coarse_off, int32_t *coarse_cur,
+                                     int4 *coarse_cand) {
     int32_t ns = min(*n_sites_dev, max_sites);
     int64_t n = d.n();
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
         int32_t p = site_pos[s];
         if (p < 0 || p >= n) continue;
         int32_t x = p % d.nx, y = (p / d.nx) % d.ny, z = p / (d.nx * d.ny);
-        int b = x / RX + bg.nbx * (y / RY + bg.nby * (z / RZ));
-        int64_t pos = bin_off[b] + atomicAdd(&cursor[b], 1);
-        cand[pos] = make_int4(s, x, y, z | ((int)band[p] << 24));
+        int4 e = make_int4(s, x, y, z | ((int)band[p] << 24));
+        int64_t fb = fine_bin(x, y, z, bg), cb = coarse_bin(x, y, z, cg);
+        fine_cand[fine_off[fb] + atomicAdd(&fine_cur[fb], 1)] = e;
+        coarse_cand[coarse_off[cb] + atomicAdd(&coarse_cur[cb], 1)] = e;
     }
 }
 
-__global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
-                                                            const int64_t *__restrict__ bin_off,
-                                                            const int4 *__restrict__ cand, unsigned long long *key,
+#ifdef LSRVT_DEBUG
+__device__ unsigned long long g_phase[12];
+#define PHASE_T0() long long _t0 = clock64()
+#define PHASE_ADD(i) do { if (threadIdx.x == 0) atomicAdd(&g_phase[i], (unsigned long long)(clock64() - _t0)); _t0 = clock64(); } while (0)
+#else
+#define PHASE_T0()
+#define PHASE_ADD(i)
+#endif
+
+// q-th cell of the Chebyshev shell of radius rho (count 2(2rho+1)^2 + 8 rho (2rho-1)):
+// the two z faces, then the square rings of the layers in between.
+__device__ __forceinline__ void shell_cell(int q, int rho, int &dx, int &dy, int &dz) {
+    const int side = 2 * rho + 1, face = side * side;
+    if (q < 2 * face) {
+        dz = q < face ? -rho : rho;
+        int r = q % face;
+        dx = r % side - rho;
+        dy = r / side - rho;
+        return;
+    }
+    q -= 2 * face;
+    const int ring = 8 * rho;
+    dz = -rho + 1 + q / ring;
+    int r = q % ring;
+    if (r < side) { dy = -rho; dx = -rho + r; return; }
+    r -= side;
+    if (r < side) { dy = rho; dx = -rho + r; return; }
+    r -= side;
+    const int inner = 2 * rho - 1;
+    dx = r < inner ? -rho : rho;
+    dy = -rho + 1 + (r % inner);
+}
+
+// ---------------------------------------------------------------- candidate lists per coarse cell
+// For a coarse cell Q (32^3 voxels) and a band b present in Q, let U_b = min over the band-b
+// sites s of Cmax(Q, s), the chamfer distance from s to the farthest voxel of Q (a corner:
+// the closed form grows with every |delta|).  Every band-b voxel of Q has a site within U_b,
+// so a site whose nearest possible distance Cmin(Q, s) (to the clamp of s into Q) exceeds
+// U_b can never be the minimum for a voxel of Q.  The list of Q keeps exactly the sites
+// with Cmin <= U_band(s); it is complete.  Sites are gathered ring by ring of coarse cells
+// (each ring's sites are at Chebyshev distance >= 32 (rho - 1) + 1 from Q) until every
+// band present has U_b below that bound; the buffer is pruned as U_b falls.
+constexpr int kCellGather = 4096;   // shared buffer while searching
+constexpr int kCellList = 2048;     // stored list per coarse cell
+constexpr int kCellThreads = 256;
+
+__device__ __forceinline__ unsigned long long chamfer_box_min(int sx, int sy, int sz, int lx, int ly, int lz, int hx,
+                                                              int hy, int hz) {
+    int cx = min(max(sx, lx), hx), cy = min(max(sy, ly), hy), cz = min(max(sz, lz), hz);
+    return chamfer(sx - cx, sy - cy, sz - cz);
+}
+__device__ __forceinline__ unsigned long long chamfer_box_max(int sx, int sy, int sz, int lx, int ly, int lz, int hx,
+                                                              int hy, int hz) {
+    return chamfer(max(abs(sx - lx), abs(sx - hx)), max(abs(sy - ly), abs(sy - hy)), max(abs(sz - lz), abs(sz - hz)));
+}
+
+__global__ void __launch_bounds__(kCellThreads) cell_bands_kernel(const uint8_t *__restrict__ band, Dims d,
+                                                                  CoarseGeom cg, uint32_t *cell_bands) {
+    __shared__ uint32_t m[8];
+    const int64_t ncell = (int64_t)cg.ncx * cg.ncy * cg.ncz;
+    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+        if (threadIdx.x < 8) m[threadIdx.x] = 0;
+        __syncthreads();
+        const int x0 = (int)(cell % cg.ncx) * kCoarse, y0 = (int)((cell / cg.ncx) % cg.ncy) * kCoarse,
+                  z0 = (int)(cell / ((int64_t)cg.ncx * cg.ncy)) * kCoarse;
+        for (int i = threadIdx.x; i < kCoarse * kCoarse * kCoarse; i += blockDim.x) {
+            int x = x0 + (i & 31), y = y0 + ((i >> 5) & 31), z = z0 + (i >> 10);
+            if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
+            uint8_t b = band[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)];
+            if (b != kInvalidBand) atomicOr(&m[b >> 5], 1u << (b & 31));
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) cell_bands[cell * 8 + threadIdx.x] = m[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kCellThreads) cell_list_kernel(Dims d, CoarseGeom cg, const uint32_t *cell_bands,
+                                                                 const int64_t *__restrict__ coarse_off,
+                                                                 const int4 *__restrict__ coarse_cand,
+                                                                 int4 *cell_list, int32_t *cell_count) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int4 *buf = (int4 *)smem_raw;                      // kCellGather
+    __shared__ unsigned long long U[256];
+    __shared__ uint32_t present[8];
+    __shared__ int nbuf_s, overflow_s, gscan[kCellThreads / 32], gstart[kCellThreads], gsrc[kCellThreads];
+    const int tid = threadIdx.x;
+    const int64_t ncell = (int64_t)cg.ncx * cg.ncy * cg.ncz;
+    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+        const int ccx = (int)(cell % cg.ncx), ccy = (int)((cell / cg.ncx) % cg.ncy),
+                  ccz = (int)(cell / ((int64_t)cg.ncx * cg.ncy));
+        const int lx = ccx * kCoarse, ly = ccy * kCoarse, lz = ccz * kCoarse;
+        const int hx = min(lx + kCoarse, d.nx) - 1, hy = min(ly + kCoarse, d.ny) - 1, hz = min(lz + kCoarse, d.nz) - 1;
+        if (tid < 8) present[tid] = cell_bands[cell * 8 + tid];
+        for (int b = tid; b < 256; b += blockDim.x) U[b] = ~0ULL;
+        if (tid == 0) { nbuf_s = 0; overflow_s = 0; }
+        __syncthreads();
+        bool any_band = false;
+        for (int k = 0; k < 8; ++k) any_band |= present[k] != 0;
+        for (int rho = 0; any_band && rho <= kMaxRho; ++rho) {
+            const int nshell = rho == 0 ? 1 : 2 * (2 * rho + 1) * (2 * rho + 1) + 8 * rho * (2 * rho - 1);
+            for (int base = 0; base < nshell; base += kCellThreads) {
+                const int q = base + tid;
+                int a0 = 0, cnt = 0;
+                if (q < nshell) {
+                    int dx = 0, dy = 0, dz = 0;
+                    if (rho > 0) shell_cell(q, rho, dx, dy, dz);
+                    int cx = ccx + dx, cy = ccy + dy, cz = ccz + dz;
+                    if (cx >= 0 && cx < cg.ncx && cy >= 0 && cy < cg.ncy && cz >= 0 && cz < cg.ncz) {
+                        int64_t cb = cx + (int64_t)cg.ncx * (cy + (int64_t)cg.ncy * cz);
+                        a0 = (int)coarse_off[cb];
+                        cnt = (int)(coarse_off[cb + 1] - a0);
+                    }
+                }
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t2 = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((tid & 31) >= o) incl += t2;
+                }
+                if ((tid & 31) == 31) gscan[tid >> 5] = incl;
+                __syncthreads();
+                int wbase = 0, total = 0;
+                for (int w2 = 0; w2 < kCellThreads / 32; ++w2) {
+                    if (w2 < (tid >> 5)) wbase += gscan[w2];
+                    total += gscan[w2];
+                }
+                gstart[tid] = wbase + incl - cnt;
+                gsrc[tid] = a0;
+                __syncthreads();
+                for (int e = tid; e < total; e += kCellThreads) {
+                    int lo2 = 0, hi2 = kCellThreads - 1;
+                    while (lo2 < hi2) {
+                        int mid = (lo2 + hi2 + 1) >> 1;
+                        if (gstart[mid] <= e) lo2 = mid; else hi2 = mid - 1;
+                    }
+                    int4 c = coarse_cand[gsrc[lo2] + (e - gstart[lo2])];
+                    int b = c.w >> 24, sz = c.w & 0xFFFFFF;
+                    if (!((present[b >> 5] >> (b & 31)) & 1u)) continue;
+                    if (chamfer_box_min(c.y, c.z, sz, lx, ly, lz, hx, hy, hz) > U[b]) continue;
+                    atomicMin(&U[b], chamfer_box_max(c.y, c.z, sz, lx, ly, lz, hx, hy, hz));
+                    int at = atomicAdd(&nbuf_s, 1);
+                    if (at < kCellGather) buf[at] = c;
+                    else overflow_s = 1;
+                }
+                __syncthreads();
+            }
+            if (overflow_s) break;
+            // prune the buffer with the current bounds (in place, order kept not needed)
+            {
+                int n0 = nbuf_s;
+                __syncthreads();
+                if (tid == 0) nbuf_s = 0;
+                __syncthreads();
+                for (int base = 0; base < n0; base += kCellThreads) {
+                    int i = base + tid;
+                    int4 c = make_int4(0, 0, 0, 0);
+                    bool keep = false;
+                    if (i < n0) {
+                        c = buf[i];
+                        int b = c.w >> 24;
+                        keep = chamfer_box_min(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz) <= U[b];
+                    }
+                    __syncthreads();
+                    if (keep) buf[atomicAdd(&nbuf_s, 1)] = c;
+                    __syncthreads();
+                }
+            }
+            // done when every present band has a site and the next ring cannot beat its bound
+            const unsigned long long next_min = (unsigned long long)(rho * kCoarse + 1) * kWFace;
+            int pending = 0;
+            for (int b = tid; b < 256; b += blockDim.x)
+                if (((present[b >> 5] >> (b & 31)) & 1u) && U[b] >= next_min) pending = 1;
+            bool covers = (ccx - rho) <= 0 && (ccx + rho) >= cg.ncx - 1 && (ccy - rho) <= 0 &&
+                          (ccy + rho) >= cg.ncy - 1 && (ccz - rho) <= 0 && (ccz + rho) >= cg.ncz - 1;
+            if (!__syncthreads_or(pending) || covers) break;
+        }
+        // store the list; bands without any site keep U = inf and their voxels are relaxed
+        const int n = nbuf_s;
+        const bool bad = overflow_s || n > kCellList;
+        for (int i = tid; i < n && !bad; i += blockDim.x) cell_list[cell * kCellList + i] = buf[i];
+        if (tid == 0) cell_count[cell] = bad ? -1 : n;
+        __syncthreads();
+    }
+}
+
+// Brick pass: the brick re-prunes its coarse cell's list with its own box (the same
+// argument at brick scale), sorts the survivors by (band, chamfer distance from the brick
+// centre), and every voxel scans its band's segment until C(centre, s) - R exceeds its
+// best (triangle inequality; R = the brick's chamfer radius).  Keys are exact where one
+// shortest chamfer path to the winner stays in band; elsewhere +inf and the brick is queued.
+__global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__restrict__ band,
+                                                            const uint8_t *__restrict__ clr, Dims d, BrickGeom bg,
+                                                            CoarseGeom cg, const int4 *__restrict__ cell_list,
+                                                            const int32_t *__restrict__ cell_count,
+                                                            const int64_t *__restrict__ fine_off,
+                                                            const int4 *__restrict__ fine_cand, unsigned long long *key,
                                                             int32_t *list_out, int32_t *n_out, uint32_t *flags,
                                                             uint32_t tag) {
     __shared__ int4 cs[kMaxCand];
     __shared__ unsigned long long ck[kMaxCand];
+    __shared__ unsigned long long Ub[256];
+    __shared__ uint32_t present[8];
+    __shared__ short band_start[257];
     __shared__ int ncand_s, unknown_s;
     const int tid = threadIdx.x;
     const int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
@@ -336,99 +678,115 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         const int bx = (int)(brick % bg.nbx), by = (int)((brick / bg.nbx) % bg.nby),
                   bz = (int)(brick / ((int64_t)bg.nbx * bg.nby));
         const int ox = bx * RX, oy = by * RY, oz = bz * RZ;
-        if (tid == 0) { ncand_s = 0; unknown_s = 0; }
+        const int lx = ox, ly = oy, lz = oz;
+        const int hx = min(ox + RX, d.nx) - 1, hy = min(oy + RY, d.ny) - 1, hz = min(oz + RZ, d.nz) - 1;
+        const int64_t cell = (ox >> kCoarseShift) + (int64_t)cg.ncx * ((oy >> kCoarseShift) + (int64_t)cg.ncy * (oz >> kCoarseShift));
+        PHASE_T0();
+        if (tid < 8) present[tid] = 0;
+        for (int b = tid; b < 256; b += blockDim.x) Ub[b] = ~0ULL;
+        if (tid == 0) { unknown_s = 0; ncand_s = 0; }
         __syncthreads();
-        // gather the sites of the neighbouring bins
-        constexpr int NBX = 2 * kSX + 1, NBY = 2 * kSY + 1, NBZ = 2 * kSZ + 1;
-        for (int q = tid; q < NBX * NBY * NBZ; q += blockDim.x) {
-            int cx = bx + q % NBX - kSX, cy = by + (q / NBX) % NBY - kSY, cz = bz + q / (NBX * NBY) - kSZ;
-            if (cx < 0 || cx >= bg.nbx || cy < 0 || cy >= bg.nby || cz < 0 || cz >= bg.nbz) continue;
-            int64_t bb = cx + (int64_t)bg.nbx * (cy + (int64_t)bg.nby * cz);
-            int64_t a0 = bin_off[bb], a1 = bin_off[bb + 1];
-            int cnt = (int)(a1 - a0);
-            if (cnt == 0) continue;
-            int at = atomicAdd(&ncand_s, cnt);
-            for (int r = 0; r < cnt && at + r < kMaxCand; ++r) cs[at + r] = cand[a0 + r];
+        uint8_t vb[kVPT];
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j) {
+            int i = tid + kRelaxThreads * j;
+            int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
+            uint8_t b = kInvalidBand;
+            if (x < d.nx && y < d.ny && z < d.nz) b = band[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)];
+            vb[j] = b;
+            if (b != kInvalidBand) atomicOr(&present[b >> 5], 1u << (b & 31));
         }
         __syncthreads();
+        const int nl = cell_count[cell];
+        const int4 *L = cell_list + cell * kCellList;
+        // brick-level bounds, then the survivors
+        for (int i = tid; i < nl; i += blockDim.x) {
+            int4 c = L[i];
+            int b = c.w >> 24;
+            if ((present[b >> 5] >> (b & 31)) & 1u)
+                atomicMin(&Ub[b], chamfer_box_max(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz));
+        }
+        __syncthreads();
+        for (int i = tid; i < nl; i += blockDim.x) {
+            int4 c = L[i];
+            int b = c.w >> 24;
+            if (!((present[b >> 5] >> (b & 31)) & 1u)) continue;
+            if (chamfer_box_min(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz) > Ub[b]) continue;
+            int at = atomicAdd(&ncand_s, 1);
+            if (at < kMaxCand) cs[at] = c;
+        }
+        __syncthreads();
+        PHASE_ADD(0);
         const int nc = ncand_s;
-        const bool overflow = nc > kMaxCand;
+        const bool ok_list = nl >= 0 && nc <= kMaxCand;
         int npow2 = 1;
-        if (!overflow) {
+        if (ok_list) {
             while (npow2 < nc) npow2 <<= 1;
             for (int i = tid; i < npow2; i += blockDim.x) {
                 unsigned long long e = ~0ULL;
                 if (i < nc) {
                     int4 c = cs[i];
-                    int cz = c.w & 0xFFFFFF;
-                    int gx = max(max(ox - c.y, c.y - (ox + RX - 1)), 0);
-                    int gy = max(max(oy - c.z, c.z - (oy + RY - 1)), 0);
-                    int gz = max(max(oz - cz, cz - (oz + RZ - 1)), 0);
-                    unsigned long long lb = (unsigned long long)max(gx, max(gy, gz)) * kWFace;
-                    e = (lb << 32) | (unsigned)i;
+                    unsigned long long cc = chamfer(c.y - (ox + RX / 2), c.z - (oy + RY / 2), (c.w & 0xFFFFFF) - (oz + RZ / 2));
+                    if (cc > (1ULL << 36) - 1) cc = (1ULL << 36) - 1;
+                    e = ((unsigned long long)(uint32_t)(c.w >> 24) << 56) | (cc << 12) | (unsigned)i;
                 }
                 ck[i] = e;
             }
-            block_bitonic_sort(ck, npow2);
+            if (npow2 > 1) block_bitonic_sort(ck, npow2);
+            for (int b2 = tid; b2 <= 256; b2 += blockDim.x) {
+                int lo2 = 0, hi2 = nc;
+                while (lo2 < hi2) {
+                    int mid = (lo2 + hi2) >> 1;
+                    if ((int)(ck[mid] >> 56) < b2) lo2 = mid + 1;
+                    else hi2 = mid;
+                }
+                band_start[b2] = (short)lo2;
+            }
         }
-        // search box in voxels and whether it reaches the volume faces
-        const int lox = (bx - kSX) * RX, hix = (bx + kSX + 1) * RX - 1;
-        const int loy = (by - kSY) * RY, hiy = (by + kSY + 1) * RY - 1;
-        const int loz = (bz - kSZ) * RZ, hiz = (bz + kSZ + 1) * RZ - 1;
+        __syncthreads();
+        PHASE_ADD(1);
         int unknown = 0;
 #pragma unroll
         for (int j = 0; j < kVPT; ++j) {
             int i = tid + kRelaxThreads * j;
-            int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
-            int x = ox + lx, y = oy + ly, z = oz + lz;
+            int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
             if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
-            int64_t g = x + (int64_t)d.nx * (y + (int64_t)d.ny * z);
-            uint8_t b = band[g];
             unsigned long long best = kInfKey;
-            int best_i = -1;
-            if (b != kInvalidBand && !overflow) {
-                for (int t = 0; t < nc; ++t) {
+            int4 bs = make_int4(0, 0, 0, 0);
+            if (vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL) {
+                const int t0 = band_start[vb[j]], t1 = band_start[vb[j] + 1];
+                for (int t = t0; t < t1; ++t) {
                     unsigned long long e = ck[t];
-                    if ((e >> 32) > (best >> 32)) break;
-                    int4 c = cs[(unsigned)e];
-                    if ((uint8_t)(c.w >> 24) != b) continue;
+                    if (((e >> 12) & ((1ULL << 36) - 1)) > (best >> 32) + kBrickChamferRadius) break;
+                    int4 c = cs[(unsigned)(e & 0xFFF)];
+#ifdef LSRVT_DEBUG
+                    atomicAdd(&g_phase[10], 1ULL);
+#endif
                     unsigned long long cd = chamfer(c.y - x, c.z - y, (c.w & 0xFFFFFF) - z);
                     if (cd >= kInf32) continue;
                     unsigned long long k2 = (cd << 32) | (unsigned)c.x;
-                    if (k2 < best) { best = k2; best_i = (int)(unsigned)e; }
+                    if (k2 < best) { best = k2; bs = c; }
                 }
-                if (best != kInfKey) {
-                    long long gap = 1LL << 40;
-                    if (lox > 0) gap = min(gap, (long long)(x - lox + 1));
-                    if (hix < d.nx - 1) gap = min(gap, (long long)(hix - x + 1));
-                    if (loy > 0) gap = min(gap, (long long)(y - loy + 1));
-                    if (hiy < d.ny - 1) gap = min(gap, (long long)(hiy - y + 1));
-                    if (loz > 0) gap = min(gap, (long long)(z - loz + 1));
-                    if (hiz < d.nz - 1) gap = min(gap, (long long)(hiz - z + 1));
-                    bool in_range = (best >> 32) < (unsigned long long)gap * kWFace;
-                    bool ok = false;
-                    if (in_range) {
-                        int4 c = cs[best_i];
-                        ok = chamfer_path_in_band(band, d, x, y, z, c.y, c.z, c.w & 0xFFFFFF, b);
-                    }
-                    if (!ok) best = kInfKey;
-                }
-                if (best == kInfKey) unknown = 1;
-            } else if (b != kInvalidBand) {
-                unknown = 1;  // candidate list overflowed: relax the whole brick
             }
-            key[g] = best;
+            unsigned long long k = kInfKey;
+            if (vb[j] != kInvalidBand) {
+                if (best != kInfKey &&
+                    chamfer_path_in_band(band, clr, d, x, y, z, bs.y, bs.z, bs.w & 0xFFFFFF, vb[j],
+                                         __ldg(clr + bs.y + (int64_t)d.nx * (bs.z + (int64_t)d.ny * (bs.w & 0xFFFFFF)))))
+                    k = best;
+                else
+                    unknown = 1;
+            }
+            key[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)] = k;
         }
         if (unknown) unknown_s = 1;
         __syncthreads();
-        // the brick's own sites: distance 0, lowest id (needed where the candidate list overflowed)
-        {
-            int64_t a0 = bin_off[brick], a1 = bin_off[brick + 1];
-            for (int64_t r = a0 + tid; r < a1; r += blockDim.x) {
-                int4 c = cand[r];
-                int64_t g = c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * (c.w & 0xFFFFFF));
-                atomicMin(key + g, (unsigned long long)(uint32_t)c.x);
-            }
+        PHASE_ADD(3);
+        // the brick's own sites: distance 0, lowest id (also where the list was unusable)
+        for (int64_t r = fine_off[brick] + tid; r < fine_off[brick + 1]; r += blockDim.x) {
+            int4 c = fine_cand[r];
+            int64_t g = c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * (c.w & 0xFFFFFF));
+            atomicMin(key + g, (unsigned long long)(uint32_t)c.x);
         }
         if (tid == 0 && unknown_s) {
             if (atomicExch(&flags[brick], tag) != tag) {
@@ -485,10 +843,69 @@ __device__ int walk(const uint8_t *__restrict__ band, Dims d, int ax, int ay, in
     return steps;
 }
 
+// Line of sight v -> s: the same traversal as walk(), but where the clearance c of the
+// current voxel is >= 2 it jumps to the state after the (k + c - 1)-th crossing of the
+// dominant axis (all crossings up to that time, ties included, exactly as the stepwise
+// walk takes them).  Over that interval each axis crosses at most c times, so every voxel
+// passed is within L-infinity distance c and in band: no tests are needed.
+__device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d, int vx, int vy,
+                          int vz, int sx, int sy, int sz, int cs) {
+    const int A0 = abs(sx - vx), A1 = abs(sy - vy), A2 = abs(sz - vz);
+    const int total = A0 + A1 + A2;
+    if (total == 0) return true;
+    const int64_t sxy = (int64_t)d.nx * d.ny;
+    const int64_t st0 = sx >= vx ? 1 : -1, st1 = sy >= vy ? d.nx : -(int64_t)d.nx, st2 = sz >= vz ? sxy : -sxy;
+    int m = 0, Am = A0;
+    if (A1 > Am) { m = 1; Am = A1; }
+    if (A2 > Am) { m = 2; Am = A2; }
+    const unsigned long long f0 = A0 ? A0 : 1, f1 = A1 ? A1 : 1, f2 = A2 ? A2 : 1;
+    const unsigned long long P0 = f1 * f2, P1 = f0 * f2, P2 = f0 * f1;
+    const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
+    const uint8_t b = band[v0];
+    const unsigned long long INF = ~0ULL;
+    int k0 = 0, k1 = 0, k2 = 0;
+    unsigned long long T0 = A0 ? P0 : INF, T1 = A1 ? P1 : INF, T2 = A2 ? P2 : INF;
+    int64_t g = v0;
+    int done = 0;
+    while (done < total) {
+        // inside the site's clearance ball the rest of the (monotone) traversal is in band
+        if (max(A0 - k0, max(A1 - k1, A2 - k2)) <= cs) return true;
+        int c = __ldg(clr + g);
+        int km = m == 0 ? k0 : (m == 1 ? k1 : k2);
+        if (c >= 2 && km < Am) {
+            long long mt = km + c - 1;
+            if (mt > Am) mt = Am;
+            unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
+            k0 = m == 0 ? (int)mt : (int)udiv(num * A0 + Am, den);
+            k1 = m == 1 ? (int)mt : (int)udiv(num * A1 + Am, den);
+            k2 = m == 2 ? (int)mt : (int)udiv(num * A2 + Am, den);
+            T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
+            T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
+            T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;
+            g = v0 + st0 * k0 + st1 * k1 + st2 * k2;
+            done = k0 + k1 + k2;
+            continue;
+        }
+        if (T0 <= T1 && T0 <= T2) {
+            g += st0;
+            T0 = ++k0 < A0 ? T0 + 2 * P0 : INF;
+        } else if (T1 <= T2) {
+            g += st1;
+            T1 = ++k1 < A1 ? T1 + 2 * P1 : INF;
+        } else {
+            g += st2;
+            T2 = ++k2 < A2 ? T2 + 2 * P2 : INF;
+        }
+        if (__ldg(band + g) != b) return false;
+        ++done;
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(256) update_voxels_kernel(
     const uint8_t *__restrict__ band, const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
-    const int32_t *__restrict__ site_pos, unsigned long long *sums, uint32_t *los_bits, int32_t *par,
-    int32_t *nonlos, int32_t *n_nonlos, bool small_coords) {
+    const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
+    uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, bool small_coords) {
     int64_t n = d.n();
     int64_t nw = (n + 31) >> 5;
     int lane = threadIdx.x & 31;
@@ -510,11 +927,15 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
                 if (dist == 0) {
                     los = true;
                 } else {
+#ifdef LSRVT_DEBUG
+                    long long _u0 = clock64();
+#endif
                     int32_t p = site_pos[s];
                     int px = p % d.nx, py = (p / d.nx) % d.ny, pz = p / (d.nx * d.ny);
-                    int ex, ey, ez;
-                    int need = abs(px - x) + abs(py - y) + abs(pz - z);
-                    los = walk(band, d, x, y, z, px, py, pz, band[v], &ex, &ey, &ez) == need;
+                    los = los_clear(band, clr, d, x, y, z, px, py, pz, __ldg(clr + p));
+#ifdef LSRVT_DEBUG
+                    atomicAdd(&g_phase[6], (unsigned long long)(clock64() - _u0));
+#endif
                 }
                 if (!los) {
                     // parent: first neighbour in (dz,dy,dx) order with an edge, same site and D(u)+w = D(v)
@@ -537,6 +958,9 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
                         if ((ku >> 32) + weight_of(o) == (k >> 32)) parent = (int32_t)u;
                     }
                     par[v] = parent;
+#ifdef LSRVT_DEBUG
+                    atomicAdd(&g_phase[7], 1ULL);
+#endif
                     int pos = atomicAdd(n_nonlos, 1);
                     nonlos[pos] = (int32_t)v;
                 }
@@ -648,10 +1072,15 @@ struct CvtWs {
     unsigned long long *sums;
     uint32_t *flags;
     int32_t *list[2];
-    int64_t *bin_off;
-    int32_t *bin_cursor;
-    int4 *cand;
+    int64_t *fine_off, *coarse_off;
+    int32_t *fine_cur, *coarse_cur;
+    int4 *fine_cand, *coarse_cand;
     int64_t *bin_total;
+    uint8_t *clr;
+    uint32_t *planes;
+    uint32_t *cell_bands;
+    int4 *cell_list;
+    int32_t *cell_count;
     void *scan;
 };
 
@@ -670,11 +1099,22 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.flags = c.take<uint32_t>(nbricks);
     w.list[0] = c.take<int32_t>(nbricks);
     w.list[1] = c.take<int32_t>(nbricks);
-    w.bin_off = c.take<int64_t>(nbricks + 1);
-    w.bin_cursor = c.take<int32_t>(nbricks);
-    w.cand = c.take<int4>((int64_t)max_sites + 1);
-    w.bin_total = c.take<int64_t>(1);
-    w.scan = c.take<char>(scan_temp_bytes(nbricks + 1));
+    CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
+    int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
+    w.fine_off = c.take<int64_t>(nbricks + 1);
+    w.coarse_off = c.take<int64_t>(ncoarse + 1);
+    w.fine_cur = c.take<int32_t>(nbricks);
+    w.coarse_cur = c.take<int32_t>(ncoarse);
+    w.fine_cand = c.take<int4>((int64_t)max_sites + 1);
+    w.coarse_cand = c.take<int4>((int64_t)max_sites + 1);
+    w.bin_total = c.take<int64_t>(2);
+    w.clr = c.take<uint8_t>(n);
+    BitGeom bgm{(d.nx + 31) / 32};
+    w.planes = c.take<uint32_t>(bgm.words(d) * kClearLevels);
+    w.cell_bands = c.take<uint32_t>(ncoarse * 8);
+    w.cell_list = c.take<int4>(ncoarse * kCellList);
+    w.cell_count = c.take<int32_t>(ncoarse);
+    w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
     *need = c.used;
     return w;
 }
@@ -703,21 +1143,34 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int64_t n = d.n();
     int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
     (void)n;
+    CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
+    int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
     cudaMemsetAsync(w.counters + 1, 0, sizeof(int32_t) * 4, s);
-    cudaMemsetAsync(w.bin_off, 0, sizeof(int64_t) * (nbricks + 1), s);
-    cudaMemsetAsync(w.bin_cursor, 0, sizeof(int32_t) * nbricks, s);
+    cudaMemsetAsync(w.fine_off, 0, sizeof(int64_t) * (nbricks + 1), s);
+    cudaMemsetAsync(w.coarse_off, 0, sizeof(int64_t) * (ncoarse + 1), s);
+    cudaMemsetAsync(w.fine_cur, 0, sizeof(int32_t) * nbricks, s);
+    cudaMemsetAsync(w.coarse_cur, 0, sizeof(int32_t) * ncoarse, s);
     site_bin_count_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites, d, bg,
-                                                                            w.bin_off, status);
-    exclusive_scan_i64(w.bin_off, nbricks + 1, w.bin_total, w.scan, s);
+                                                                            cg, w.fine_off, w.coarse_off, status);
+    exclusive_scan_i64(w.fine_off, nbricks + 1, w.bin_total, w.scan, s);
+    exclusive_scan_i64(w.coarse_off, ncoarse + 1, w.bin_total + 1, w.scan, s);
     site_bin_fill_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites, band, d,
-                                                                           bg, w.bin_off, w.bin_cursor, w.cand);
+                                                                           bg, cg, w.fine_off, w.fine_cur, w.fine_cand,
+                                                                           w.coarse_off, w.coarse_cur, w.coarse_cand);
+    {
+        size_t smem = kCellGather * sizeof(int4);
+        cudaFuncSetAttribute(cell_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int cgrid2 = (int)(ncoarse < (int64_t)kSMs * 4 ? ncoarse : (int64_t)kSMs * 4);
+        cell_list_kernel<<<cgrid2, kCellThreads, smem, s>>>(d, cg, w.cell_bands, w.coarse_off, w.coarse_cand,
+                                                            w.cell_list, w.cell_count);
+    }
     ++tag;
     int nb_cfi = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cfi, cfi_kernel, kRelaxThreads, 0);
     if (nb_cfi < 1) nb_cfi = 1;
     int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
-    cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, d, bg, w.bin_off, w.cand, w.key, w.list[0], w.counters + 1,
-                                               w.flags, tag);
+    cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
+                                               w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, tag);
 #ifdef LSRVT_DEBUG
     {
         int32_t q0 = 0;
@@ -775,6 +1228,19 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * nbricks, s);
     if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * 2 * n_iters, s);
     bool small = d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048;
+    {
+        BitGeom bgm{(d.nx + 31) / 32};
+        int64_t nw = bgm.words(d);
+        clear_init_kernel<<<grid_for(nw * 32, 256, kSMs * 16), 256, 0, s>>>(band, d, bgm, w.planes);
+        for (int k = 1; k < kClearLevels; ++k)
+            clear_erode_kernel<<<grid_for(nw, 256, kSMs * 16), 256, 0, s>>>(w.planes + (int64_t)(k - 1) * nw, d, bgm,
+                                                                          w.planes + (int64_t)k * nw);
+        clear_count_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.planes, d, bgm, kClearLevels, w.clr);
+        CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
+        int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
+        cell_bands_kernel<<<(int)(ncoarse < kSMs * 8 ? ncoarse : kSMs * 8), kCellThreads, 0, s>>>(band, d, cg,
+                                                                                                w.cell_bands);
+    }
     uint32_t tag = 0;
     int vgrid = grid_for((n + 31) / 32 * 32, 256, kSMs * 16);
     for (int32_t it = 0; it < n_iters; ++it) {
@@ -782,8 +1248,8 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         if (st != LSRVT_OK) return st;
         cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
-        update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.sums, w.los_bits, w.par, w.nonlos,
-                                                   w.counters, small);
+        update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
+                                                   w.nonlos, w.counters, small);
         update_nonlos_kernel<<<kSMs * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
@@ -793,5 +1259,17 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s);
     if (st != LSRVT_OK) return st;
     emit_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.key, n, cell, dist);
+#ifdef LSRVT_DEBUG
+    {
+        unsigned long long ph[12];
+        cudaMemcpyFromSymbol(ph, g_phase, sizeof(ph));
+        fprintf(stderr, "cand total %llu stage-visits %llu chamfer-evals %llu unsettled-voxel-stages %llu\n", ph[8], ph[9],
+                ph[10], ph[11]);
+        fprintf(stderr, "phases: gather %.3g sort %.3g voxels %.3g path %.3g stages %llu | los-cycles %.3g nonlos %llu\n",
+                (double)ph[0], (double)ph[1], (double)ph[2], (double)ph[3], ph[5], (double)ph[6], ph[7]);
+        unsigned long long z[12] = {0};
+        cudaMemcpyToSymbol(g_phase, z, sizeof(z));
+    }
+#endif
     return launch_status();
 }
