@@ -353,8 +353,13 @@ __device__ __forceinline__ unsigned long long udiv(unsigned long long a, unsigne
 // only moves together with j and no corner move is split).  True if every move's box is
 // in band b.  From a voxel p with clearance c >= 1 the next c moves are in band and are
 // skipped without tests.  Single moves advance Bresenham error terms (no division).
-__device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d,
-                                     int vx, int vy, int vz, int sx, int sy, int sz, uint8_t b, int cs) {
+// Returns 0 if a move leaves the band, 1 if the path is in band, 2 if it is in band with a
+// margin of 2: every jump anchor p covered only moves within L-infinity c(p) - 2 of p and
+// the walk ended at most c(s) - 2 from s.  The 6-connected traversal of the segment v-s
+// stays within L-infinity 2 of the digital path (per axis the rounding errors of the path
+// and of the segment's voxel add up to at most 2), so margin 2 also certifies line of sight.
+__device__ int chamfer_path_in_band(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d,
+                                    int vx, int vy, int vz, int sx, int sy, int sz, uint8_t b, int cs) {
     const int D0 = sx - vx, D1 = sy - vy, D2 = sz - vz;
     const int A0 = abs(D0), A1 = abs(D1), A2 = abs(D2);
     // axes sorted by extent: i >= j >= k
@@ -363,8 +368,9 @@ __device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, const uin
     if (Ai < Aj) { int t = i; i = j; j = t; t = Ai; Ai = Aj; Aj = t; }
     if (Aj < Ak) { int t = j; j = k; k = t; t = Aj; Aj = Ak; Ak = t; }
     if (Ai < Aj) { int t = i; i = j; j = t; t = Ai; Ai = Aj; Aj = t; }
-    if (Ai == 0) return true;
+    if (Ai == 0) return 2;
     const int64_t sxy = (int64_t)d.nx * d.ny;
+    bool margin = true;
     // strides and signs along i, j, k in linear index space
     const int64_t stride[3] = {1, d.nx, sxy};
     const int sgn[3] = {D0 < 0 ? -1 : 1, D1 < 0 ? -1 : 1, D2 < 0 ? -1 : 1};
@@ -379,10 +385,13 @@ __device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, const uin
         // the rest of the path approaches s monotonically on every axis, so once within the
         // site's own clearance ball it stays in band
         int rem = max(Ai - mv, max(Aj - jc, Ak - kc));
-        if (rem <= cs) return true;
+        if (rem <= cs) return (margin && rem <= cs - 2) ? 2 : 1;
         int c = __ldg(clr + g);
         if (c >= 1) {
-            int mv2 = mv + c < Ai ? mv + c : Ai;
+            int step = c;
+            if (c >= 3) step = c - 2;
+            else margin = false;
+            int mv2 = mv + step < Ai ? mv + step : Ai;
             unsigned long long nj = 2ULL * mv2 * Aj + Ai;
             jc = (int)udiv(nj, ai2);
             ej = (long long)(nj - ai2 * jc);
@@ -395,6 +404,7 @@ __device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, const uin
             g = v0 + si * mv + sj * jc + sk * kc;
             continue;
         }
+        margin = false;
         ej += 2LL * Aj;
         bool mj = ej >= (long long)ai2;
         if (mj) ej -= (long long)ai2;
@@ -406,21 +416,21 @@ __device__ bool chamfer_path_in_band(const uint8_t *__restrict__ band, const uin
         }
         // box of the move g -> g + mi + (mj) + (mk), without g itself
         const int64_t ci = si, cj = mj ? sj : 0, ck = mk ? sk : 0;
-        if (__ldg(band + g + ci) != b) return false;
+        if (__ldg(band + g + ci) != b) return 0;
         if (mj) {
-            if (__ldg(band + g + cj) != b || __ldg(band + g + ci + cj) != b) return false;
+            if (__ldg(band + g + cj) != b || __ldg(band + g + ci + cj) != b) return 0;
         }
         if (mk) {
             if (__ldg(band + g + ck) != b || __ldg(band + g + ci + ck) != b || __ldg(band + g + cj + ck) != b ||
                 __ldg(band + g + ci + cj + ck) != b)
-                return false;
+                return 0;
         }
         g += ci + cj + ck;
         ++mv;
         jc += mj;
         kc += mk;
     }
-    return true;
+    return margin ? 2 : 1;
 }
 
 // site bins: one pass counts, a scan gives offsets, a second pass fills entries
@@ -500,6 +510,65 @@ __device__ __forceinline__ void shell_cell(int q, int rho, int &dx, int &dy, int
     dy = -rho + 1 + (r % inner);
 }
 
+// Line of sight v -> s: the traversal of walk() below, but where the clearance c of the
+// current voxel is >= 2 it jumps to the state after the (k + c - 1)-th crossing of the
+// dominant axis (all crossings up to that time, ties included, exactly as the stepwise
+// walk takes them).  Over that interval each axis crosses at most c times, so every voxel
+// passed is within L-infinity distance c and in band: no tests are needed.
+__device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d, int vx, int vy,
+                          int vz, int sx, int sy, int sz, int cs) {
+    const int A0 = abs(sx - vx), A1 = abs(sy - vy), A2 = abs(sz - vz);
+    const int total = A0 + A1 + A2;
+    if (total == 0) return true;
+    const int64_t sxy = (int64_t)d.nx * d.ny;
+    const int64_t st0 = sx >= vx ? 1 : -1, st1 = sy >= vy ? d.nx : -(int64_t)d.nx, st2 = sz >= vz ? sxy : -sxy;
+    int m = 0, Am = A0;
+    if (A1 > Am) { m = 1; Am = A1; }
+    if (A2 > Am) { m = 2; Am = A2; }
+    const unsigned long long f0 = A0 ? A0 : 1, f1 = A1 ? A1 : 1, f2 = A2 ? A2 : 1;
+    const unsigned long long P0 = f1 * f2, P1 = f0 * f2, P2 = f0 * f1;
+    const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
+    const uint8_t b = band[v0];
+    const unsigned long long INF = ~0ULL;
+    int k0 = 0, k1 = 0, k2 = 0;
+    unsigned long long T0 = A0 ? P0 : INF, T1 = A1 ? P1 : INF, T2 = A2 ? P2 : INF;
+    int64_t g = v0;
+    int done = 0;
+    while (done < total) {
+        // inside the site's clearance ball the rest of the (monotone) traversal is in band
+        if (max(A0 - k0, max(A1 - k1, A2 - k2)) <= cs) return true;
+        int c = __ldg(clr + g);
+        int km = m == 0 ? k0 : (m == 1 ? k1 : k2);
+        if (c >= 2 && km < Am) {
+            long long mt = km + c - 1;
+            if (mt > Am) mt = Am;
+            unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
+            k0 = m == 0 ? (int)mt : (int)udiv(num * A0 + Am, den);
+            k1 = m == 1 ? (int)mt : (int)udiv(num * A1 + Am, den);
+            k2 = m == 2 ? (int)mt : (int)udiv(num * A2 + Am, den);
+            T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
+            T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
+            T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;
+            g = v0 + st0 * k0 + st1 * k1 + st2 * k2;
+            done = k0 + k1 + k2;
+            continue;
+        }
+        if (T0 <= T1 && T0 <= T2) {
+            g += st0;
+            T0 = ++k0 < A0 ? T0 + 2 * P0 : INF;
+        } else if (T1 <= T2) {
+            g += st1;
+            T1 = ++k1 < A1 ? T1 + 2 * P1 : INF;
+        } else {
+            g += st2;
+            T2 = ++k2 < A2 ? T2 + 2 * P2 : INF;
+        }
+        if (__ldg(band + g) != b) return false;
+        ++done;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- candidate lists per coarse cell
 // For a coarse cell Q (32^3 voxels) and a band b present in Q, let U_b = min over the band-b
 // sites s of Cmax(Q, s), the chamfer distance from s to the farthest voxel of Q (a corner:
@@ -509,6 +578,20 @@ __device__ __forceinline__ void shell_cell(int q, int rho, int &dx, int &dy, int
 // with Cmin <= U_band(s); it is complete.  Sites are gathered ring by ring of coarse cells
 // (each ring's sites are at Chebyshev distance >= 32 (rho - 1) + 1 from Q) until every
 // band present has U_b below that bound; the buffer is pruned as U_b falls.
+// Outputs of the geodesically weighted update (Eq. 2) filled while tessellating: integer
+// moment sums of line-of-sight voxels, the line-of-sight bit of every voxel, and the
+// "pending" bit of voxels whose update needs final neighbour keys (no line of sight, or
+// key not settled here).  enabled = false for the final tessellation.
+struct UpdateOut {
+    bool enabled;
+    bool small_coords;
+    const uint16_t *q;
+    const int32_t *site_pos;
+    unsigned long long *sums;
+    uint32_t *los_bits;
+    uint32_t *pending;
+};
+
 constexpr int kCellGather = 4096;   // shared buffer while searching
 constexpr int kCellList = 2048;     // stored list per coarse cell
 constexpr int kCellThreads = 256;
@@ -665,7 +748,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                                                             const int64_t *__restrict__ fine_off,
                                                             const int4 *__restrict__ fine_cand, unsigned long long *key,
                                                             int32_t *list_out, int32_t *n_out, uint32_t *flags,
-                                                            uint32_t tag) {
+                                                            uint32_t tag, UpdateOut up) {
     __shared__ int4 cs[kMaxCand];
     __shared__ unsigned long long ck[kMaxCand];
     __shared__ unsigned long long Ub[256];
@@ -750,10 +833,11 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         for (int j = 0; j < kVPT; ++j) {
             int i = tid + kRelaxThreads * j;
             int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
-            if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
+            const bool inb = x < d.nx && y < d.ny && z < d.nz;
+            const int64_t g = inb ? x + (int64_t)d.nx * (y + (int64_t)d.ny * z) : 0;
             unsigned long long best = kInfKey;
             int4 bs = make_int4(0, 0, 0, 0);
-            if (vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL) {
+            if (inb && vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL) {
                 const int t0 = band_start[vb[j]], t1 = band_start[vb[j] + 1];
                 for (int t = t0; t < t1; ++t) {
                     unsigned long long e = ck[t];
@@ -769,15 +853,65 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                 }
             }
             unsigned long long k = kInfKey;
-            if (vb[j] != kInvalidBand) {
-                if (best != kInfKey &&
-                    chamfer_path_in_band(band, clr, d, x, y, z, bs.y, bs.z, bs.w & 0xFFFFFF, vb[j],
-                                         __ldg(clr + bs.y + (int64_t)d.nx * (bs.z + (int64_t)d.ny * (bs.w & 0xFFFFFF)))))
+            bool los = false, pend = false;
+            if (inb && vb[j] != kInvalidBand) {
+                int status = 0;
+                int cs_site = 0;
+                const int bsz = bs.w & 0xFFFFFF;
+                if (best != kInfKey) {
+                    cs_site = __ldg(clr + bs.y + (int64_t)d.nx * (bs.z + (int64_t)d.ny * bsz));
+                    status = chamfer_path_in_band(band, clr, d, x, y, z, bs.y, bs.z, bsz, vb[j], cs_site);
+                }
+                if (status) {
                     k = best;
-                else
+                    if (up.enabled) {
+                        // O(1) line-of-sight certificates only; other voxels are walked in the pending pass
+                        los = (best >> 32) == 0 || status == 2;
+                        pend = !los;
+                    }
+                } else {
                     unknown = 1;
+                    pend = up.enabled;
+                }
+                key[g] = k;
+            } else if (inb) {
+                key[g] = k;
             }
-            key[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)] = k;
+            if (up.enabled) {
+                {
+                    // one atomic per distinct bit-array word in the warp
+                    const int64_t word = inb ? (g >> 5) : -1;
+                    const unsigned bit = inb ? (1u << (g & 31)) : 0u;
+                    unsigned mw = __match_any_sync(0xffffffffu, word);
+                    unsigned lb = __reduce_or_sync(mw, los ? bit : 0u);
+                    unsigned pb = __reduce_or_sync(mw, pend ? bit : 0u);
+                    if (inb && (mw & lanemask_lt()) == 0) {
+                        if (lb) atomicOr(&up.los_bits[word], lb);
+                        if (pb) atomicOr(&up.pending[word], pb);
+                    }
+                }
+                // warp-aggregated integer moment sums of the line-of-sight voxels (Eq. 2, phi(v) = v)
+                const int32_t sid = los ? bs.x : -1;
+                const unsigned w = los ? (up.q ? up.q[g] : 1u) : 0u;
+                if (up.small_coords) {
+                    unsigned m = __match_any_sync(0xffffffffu, sid);
+                    unsigned sx = __reduce_add_sync(m, w * (unsigned)x);
+                    unsigned sy = __reduce_add_sync(m, w * (unsigned)y);
+                    unsigned sz = __reduce_add_sync(m, w * (unsigned)z);
+                    unsigned sw = __reduce_add_sync(m, w);
+                    if (los && (m & lanemask_lt()) == 0) {
+                        atomicAdd(&up.sums[4 * (int64_t)sid + 0], (unsigned long long)sx);
+                        atomicAdd(&up.sums[4 * (int64_t)sid + 1], (unsigned long long)sy);
+                        atomicAdd(&up.sums[4 * (int64_t)sid + 2], (unsigned long long)sz);
+                        atomicAdd(&up.sums[4 * (int64_t)sid + 3], (unsigned long long)sw);
+                    }
+                } else if (los) {
+                    atomicAdd(&up.sums[4 * (int64_t)sid + 0], (unsigned long long)w * (unsigned)x);
+                    atomicAdd(&up.sums[4 * (int64_t)sid + 1], (unsigned long long)w * (unsigned)y);
+                    atomicAdd(&up.sums[4 * (int64_t)sid + 2], (unsigned long long)w * (unsigned)z);
+                    atomicAdd(&up.sums[4 * (int64_t)sid + 3], (unsigned long long)w);
+                }
+            }
         }
         if (unknown) unknown_s = 1;
         __syncthreads();
@@ -843,79 +977,23 @@ __device__ int walk(const uint8_t *__restrict__ band, Dims d, int ax, int ay, in
     return steps;
 }
 
-// Line of sight v -> s: the same traversal as walk(), but where the clearance c of the
-// current voxel is >= 2 it jumps to the state after the (k + c - 1)-th crossing of the
-// dominant axis (all crossings up to that time, ties included, exactly as the stepwise
-// walk takes them).  Over that interval each axis crosses at most c times, so every voxel
-// passed is within L-infinity distance c and in band: no tests are needed.
-__device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d, int vx, int vy,
-                          int vz, int sx, int sy, int sz, int cs) {
-    const int A0 = abs(sx - vx), A1 = abs(sy - vy), A2 = abs(sz - vz);
-    const int total = A0 + A1 + A2;
-    if (total == 0) return true;
-    const int64_t sxy = (int64_t)d.nx * d.ny;
-    const int64_t st0 = sx >= vx ? 1 : -1, st1 = sy >= vy ? d.nx : -(int64_t)d.nx, st2 = sz >= vz ? sxy : -sxy;
-    int m = 0, Am = A0;
-    if (A1 > Am) { m = 1; Am = A1; }
-    if (A2 > Am) { m = 2; Am = A2; }
-    const unsigned long long f0 = A0 ? A0 : 1, f1 = A1 ? A1 : 1, f2 = A2 ? A2 : 1;
-    const unsigned long long P0 = f1 * f2, P1 = f0 * f2, P2 = f0 * f1;
-    const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
-    const uint8_t b = band[v0];
-    const unsigned long long INF = ~0ULL;
-    int k0 = 0, k1 = 0, k2 = 0;
-    unsigned long long T0 = A0 ? P0 : INF, T1 = A1 ? P1 : INF, T2 = A2 ? P2 : INF;
-    int64_t g = v0;
-    int done = 0;
-    while (done < total) {
-        // inside the site's clearance ball the rest of the (monotone) traversal is in band
-        if (max(A0 - k0, max(A1 - k1, A2 - k2)) <= cs) return true;
-        int c = __ldg(clr + g);
-        int km = m == 0 ? k0 : (m == 1 ? k1 : k2);
-        if (c >= 2 && km < Am) {
-            long long mt = km + c - 1;
-            if (mt > Am) mt = Am;
-            unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
-            k0 = m == 0 ? (int)mt : (int)udiv(num * A0 + Am, den);
-            k1 = m == 1 ? (int)mt : (int)udiv(num * A1 + Am, den);
-            k2 = m == 2 ? (int)mt : (int)udiv(num * A2 + Am, den);
-            T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
-            T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
-            T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;
-            g = v0 + st0 * k0 + st1 * k1 + st2 * k2;
-            done = k0 + k1 + k2;
-            continue;
-        }
-        if (T0 <= T1 && T0 <= T2) {
-            g += st0;
-            T0 = ++k0 < A0 ? T0 + 2 * P0 : INF;
-        } else if (T1 <= T2) {
-            g += st1;
-            T1 = ++k1 < A1 ? T1 + 2 * P1 : INF;
-        } else {
-            g += st2;
-            T2 = ++k2 < A2 ? T2 + 2 * P2 : INF;
-        }
-        if (__ldg(band + g) != b) return false;
-        ++done;
-    }
-    return true;
-}
-
 __global__ void __launch_bounds__(256) update_voxels_kernel(
     const uint8_t *__restrict__ band, const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
     const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
-    uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, bool small_coords) {
+    uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const uint32_t *__restrict__ pending,
+    bool small_coords) {
     int64_t n = d.n();
     int64_t nw = (n + 31) >> 5;
     int lane = threadIdx.x & 31;
     for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv < nw;
          wv += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t pw = pending[wv];
+        if (pw == 0) continue;  // warp-uniform: nothing left to do for these 32 voxels
         int64_t v = wv * 32 + lane;
         bool los = false;
         int32_t s = -1;
         int x = 0, y = 0, z = 0;
-        if (v < n) {
+        if (v < n && ((pw >> lane) & 1u)) {
             unsigned long long k = key[v];
             if (k != kInfKey) {
                 s = (int32_t)(uint32_t)k;
@@ -967,7 +1045,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
             }
         }
         unsigned bal = __ballot_sync(0xffffffffu, los);
-        if (lane == 0 && wv < nw) los_bits[wv] = bal;
+        if (lane == 0 && bal) atomicOr(&los_bits[wv], bal);
         // warp-aggregated integer moment sums of the LOS voxels
         int32_t grp = los ? s : -1;
         unsigned m = __match_any_sync(0xffffffffu, grp);
@@ -1081,6 +1159,7 @@ struct CvtWs {
     uint32_t *cell_bands;
     int4 *cell_list;
     int32_t *cell_count;
+    uint32_t *pending;
     void *scan;
 };
 
@@ -1114,6 +1193,7 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.cell_bands = c.take<uint32_t>(ncoarse * 8);
     w.cell_list = c.take<int4>(ncoarse * kCellList);
     w.cell_count = c.take<int32_t>(ncoarse);
+    w.pending = c.take<uint32_t>((n + 31) / 32);
     w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
     *need = c.used;
     return w;
@@ -1138,7 +1218,8 @@ namespace {
 
 // One tessellation: keys <- restricted geodesic Voronoi assignment of the current sites.
 lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos, const int32_t *n_sites_dev,
-                            int32_t max_sites, CvtWs &w, uint32_t &tag, int32_t *status, cudaStream_t s) {
+                            int32_t max_sites, CvtWs &w, uint32_t &tag, int32_t *status, cudaStream_t s,
+                            UpdateOut up) {
     BrickGeom bg{(d.nx + RX - 1) / RX, (d.ny + RY - 1) / RY, (d.nz + RZ - 1) / RZ};
     int64_t n = d.n();
     int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
@@ -1170,7 +1251,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     if (nb_cfi < 1) nb_cfi = 1;
     int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
     cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
-                                               w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, tag);
+                                               w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, tag, up);
 #ifdef LSRVT_DEBUG
     {
         int32_t q0 = 0;
@@ -1243,20 +1324,25 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     }
     uint32_t tag = 0;
     int vgrid = grid_for((n + 31) / 32 * 32, 256, kSMs * 16);
+    UpdateOut up{true, small, q, site_pos, w.sums, w.los_bits, w.pending};
+    UpdateOut no_up{false, small, q, site_pos, nullptr, nullptr, nullptr};
+    const int64_t nwords = (n + 31) / 32;
     for (int32_t it = 0; it < n_iters; ++it) {
-        lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s);
-        if (st != LSRVT_OK) return st;
         cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
+        cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
+        cudaMemsetAsync(w.pending, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
+        lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, up);
+        if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
-                                                   w.nonlos, w.counters, small);
+                                                   w.nonlos, w.counters, w.pending, small);
         update_nonlos_kernel<<<kSMs * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
             band, d, site_pos, n_sites_dev, max_sites, w.sums,
             iter_trace ? (unsigned long long *)(iter_trace + 2 * it) : nullptr);
     }
-    lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s);
+    lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, no_up);
     if (st != LSRVT_OK) return st;
     emit_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.key, n, cell, dist);
 #ifdef LSRVT_DEBUG
