@@ -131,6 +131,25 @@ lsrvt_status lsrvt_label_components(const uint8_t *band, lsrvt_dims d, int32_t *
                                     int32_t *n_comp_dev, void *ws, size_t ws_bytes, int32_t *status_dev,
                                     void *stream);
 
+/* Allocation-free variant of lsrvt_label_components, for callers that cannot allocate
+ * device memory or pass a workspace (for example a simulation that embeds the library for
+ * in-situ analysis and owns all device memory through its own pool, or a host program that
+ * loads it as a plug-in without exposing its allocator).  The paper has no counterpart:
+ * this is a deployment form of the same labelling.  Same arguments and results as
+ * lsrvt_label_components without `ws`/`ws_bytes`.
+ *  - Scratch lives in a fixed device array inside the library (1.25 MiB, held by every
+ *    GPU that loads the library until the process exits); volumes of more than 2^18
+ *    voxels (64^3) are rejected with LSRVT_ERR_WORKSPACE and nothing is launched.
+ *  - The first call on a device looks up that array's device address (with the device
+ *    current); make that first call before any stream capture.
+ *  - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - Every call shares the one array: calls that may overlap on the GPU (different streams
+ *    without ordering, or several host threads) race and corrupt each other's results;
+ *    order them on one stream.  Each call overwrites what the previous call left. */
+lsrvt_status lsrvt_label_components_static(const uint8_t *band, lsrvt_dims d, int32_t *comp, uint8_t *comp_band,
+                                           int64_t *comp_size, int32_t *comp_first, int32_t max_comp,
+                                           int32_t *n_comp_dev, int32_t *status_dev, void *stream);
+
 /* Saliency weights m_v (Sec. 3.1 "Centroids or Centers of Mass": m_v; Sec. 3.3: the
  * second field and the attraction gamma).  q = max(1, rint(g^gamma * 65535 / gmax)),
  * g = |grad f| by central differences (one-sided half differences at the faces),

@@ -69,6 +69,7 @@ def lib():
         L.lsrvt_workspace_bytes.restype = sz
         L.lsrvt_classify.argtypes = [P, Dims, P, i32, P, P]
         L.lsrvt_label_components.argtypes = [P, Dims, P, P, P, P, i32, P, P, sz, P, P]
+        L.lsrvt_label_components_static.argtypes = [P, Dims, P, P, P, P, i32, P, P, P]
         L.lsrvt_saliency_grad.argtypes = [P, Dims, i32, P, P, sz, P]
         L.lsrvt_seed.argtypes = [P, P, Dims, P, i32, SeedParams, P, P, P, i32, P, P, sz, P, P]
         L.lsrvt_cvt_iterate.argtypes = [P, P, Dims, P, P, i32, i32, P, P, P, P, sz, P, P]
@@ -76,7 +77,8 @@ def lib():
         L.lsrvt_aggregate.argtypes = [P, P, i32, Dims, P, P, i32, u32, P, P, i32, Stats, P, sz, P, P]
         L.lsrvt_merge_hierarchy.argtypes = [Stats, P, i32, i32, i32, u32, P, P, P, i32, i32, Stats, Stats, Stats, P,
                                             sz, P]
-        for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_saliency_grad", "lsrvt_seed",
+        for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
+                     "lsrvt_saliency_grad", "lsrvt_seed",
                      "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -85,7 +87,7 @@ def lib():
 
 def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
-            "lsrvt_label_components", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
+            "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
             "lsrvt_aggregate", "lsrvt_merge_hierarchy"]
 
 
@@ -181,6 +183,25 @@ def label_components(band, max_comp=None, ws=None, status=None):
     _check(lib().lsrvt_label_components(_ptr(band), _dims(band), _ptr(comp), _ptr(cb), _ptr(cs), _ptr(cf), max_comp,
                                         _ptr(nc), _ptr(buf), buf.numel(), _ptr(status), _stream()),
            "lsrvt_label_components")
+    return comp, cb, cs, cf, nc
+
+
+def label_components_static(band, max_comp=None, status=None):
+    """lsrvt_label_components_static: the same labelling with the library's built-in scratch
+    (no workspace, no allocation inside the call); volumes up to 2^18 voxels."""
+    _require_cuda(band)
+    dev = band.device
+    n = band.numel()
+    max_comp = default_max_comp(n) if max_comp is None else int(max_comp)
+    comp = torch.empty(band.shape, dtype=torch.int32, device=dev)
+    cb = torch.empty(max(max_comp, 1), dtype=torch.uint8, device=dev)
+    cs = torch.empty(max(max_comp, 1), dtype=torch.int64, device=dev)
+    cf = torch.empty(max(max_comp, 1), dtype=torch.int32, device=dev)
+    nc = torch.zeros(1, dtype=torch.int32, device=dev)
+    status = new_status(dev) if status is None else status
+    _check(lib().lsrvt_label_components_static(_ptr(band), _dims(band), _ptr(comp), _ptr(cb), _ptr(cs), _ptr(cf),
+                                               max_comp, _ptr(nc), _ptr(status), _stream()),
+           "lsrvt_label_components_static")
     return comp, cb, cs, cf, nc
 
 

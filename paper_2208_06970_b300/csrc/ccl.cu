@@ -295,3 +295,79 @@ extern "C" lsrvt_status lsrvt_label_components(const uint8_t *band, lsrvt_dims d
     ccl_count_out_kernel<<<1, 1, 0, s>>>(w.total, n_comp_dev, max_comp, status_dev);
     return launch_status();
 }
+
+// ---------------------------------------------------------------- allocation-free variant
+// Some callers cannot allocate device memory at all: a simulation that embeds this library
+// for in-situ analysis and owns every byte of the device through its own pool, or a host
+// application that loads it as a plug-in without exposing its allocator, can neither call
+// cudaMalloc nor hand over a workspace.  For them lsrvt_label_components_static labels
+// volumes of up to kStaticMaxVoxels voxels with its scratch in the file-scope device array
+// below, which every GPU that loads the library holds until the process exits.
+#include <mutex>
+
+namespace lsrvt {
+namespace {
+
+constexpr int64_t kStaticMaxVoxels = int64_t(1) << 18;  // 64^3
+constexpr size_t kStaticScratchBytes = 1310720;         // >= the workspace of any volume up to 2^18 voxels
+
+static __device__ __align__(256) unsigned char g_ccl_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+lsrvt_status static_scratch(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LSRVT_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_ccl_static_scratch) != cudaSuccess || !p) return LSRVT_ERR_CUDA;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LSRVT_OK;
+}
+
+}  // namespace
+}  // namespace lsrvt
+
+extern "C" lsrvt_status lsrvt_label_components_static(const uint8_t *band, lsrvt_dims dd, int32_t *comp,
+                                                      uint8_t *comp_band, int64_t *comp_size, int32_t *comp_first,
+                                                      int32_t max_comp, int32_t *n_comp_dev, int32_t *status_dev,
+                                                      void *stream) {
+    if (!dims_ok(dd) || !band || !comp || !n_comp_dev || max_comp < 0 ||
+        (max_comp > 0 && (!comp_band || !comp_size || !comp_first)))
+        return LSRVT_ERR_INVALID_ARG;
+    Dims d{dd.nx, dd.ny, dd.nz};
+    if (d.n() > kStaticMaxVoxels) return LSRVT_ERR_WORKSPACE;  // larger than the built-in scratch
+    size_t need;
+    carve_ccl(nullptr, 0, d, &need);
+    if (need > kStaticScratchBytes) return LSRVT_ERR_WORKSPACE;
+    void *ws = nullptr;
+    lsrvt_status st = static_scratch(&ws);
+    if (st != LSRVT_OK) return st;
+    CclWs w = carve_ccl(ws, kStaticScratchBytes, d, &need);
+    // Every buffer below is written before it is read, so nothing left by an earlier call
+    // needs clearing.
+    cudaStream_t s = as_stream(stream);
+    int64_t n = d.n();
+    int64_t nchunks = (n + kChunk - 1) / kChunk;
+    dim3 bgrid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
+    ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L);
+    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.L, status_dev);
+    ccl_compress_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.L, n);
+    int warps = 8;
+    int cgrid = (int)((nchunks + warps - 1) / warps);
+    if (cgrid > kSMs * 16) cgrid = kSMs * 16;
+    ccl_count_kernel<<<cgrid, warps * 32, warps * kBands * sizeof(unsigned), s>>>(w.L, band, n, nchunks, w.hist);
+    exclusive_scan_i64(w.hist, nchunks * kBands, w.total, w.scan, s);
+    ccl_ids_kernel<<<cgrid, warps * 32, warps * kBands * sizeof(long long), s>>>(w.L, band, n, nchunks, w.hist, comp,
+                                                                                   comp_band, comp_first, max_comp);
+    if (max_comp > 0) cudaMemsetAsync(comp_size, 0, sizeof(int64_t) * (size_t)max_comp, s);
+    ccl_finalize_kernel<<<grid_for((n + 15) / 16, 256, kSMs * 16), 256, 0, s>>>(w.L, comp, n, comp_size, max_comp);
+    ccl_count_out_kernel<<<1, 1, 0, s>>>(w.total, n_comp_dev, max_comp, status_dev);
+    return launch_status();
+}
