@@ -40,6 +40,10 @@ VPS = 4096
 # algorithmic bytes of one Lloyd iteration per voxel: band in (1 B), weight in (2 B), the
 # assignment materialised once (4 B label written, 4 B read back by the update)
 ALG_BYTES_PER_VOXEL_ITER = 11
+# DRAM bytes one Lloyd iteration moves per voxel, summed over its kernels, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 256^3 flame case and scaled by the
+# voxel count (the traffic grows in proportion to it)
+NCU_BYTES_PER_VOXEL_ITER = 47.3
 
 
 def peaks():
@@ -383,7 +387,10 @@ def main():
             roofline=dict(kernel="one Lloyd iteration: cfi_kernel + relax_round_kernel rounds + "
                                  "update_voxels_kernel + update_nonlos_kernel + move_sites_kernel",
                           bound="hbm", achieved=r["achieved"], peak=pk["hbm"], unit="GB/s",
-                          frac=r["achieved"] / pk["hbm"], traffic=None, peak_source=pk["src"],
+                          frac=r["achieved"] / pk["hbm"],
+                          traffic=NCU_BYTES_PER_VOXEL_ITER * n if args.side in (256, 512) else None,
+                          traffic_note="ncu DRAM bytes per iteration, 256^3 capture scaled by voxels",
+                          peak_source=pk["src"],
                           algorithmic_bytes_per_voxel=ALG_BYTES_PER_VOXEL_ITER, ms_per_launch=r["t_iter"],
                           ms_per_tessellation=r["t_assign"]),
             stats=dict(aggregate_ms=r["phase"].get("aggregate"), algorithmic_gbs=r["stats_gbs"],
