@@ -13,6 +13,8 @@
 // histogram.  One FP64 atomic per (brick, cell, variable) and moment combines the bricks;
 // a finalize pass forms mean = c + S1/n and M2 = S2 - S1^2/n in FP64.  HBM traffic is the
 // algorithmic 4 B (cell) + 4 m B (variables) per voxel.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace lsrvt {
@@ -230,6 +232,194 @@ __global__ void aggregate_finalize_kernel(AggAcc acc, const int32_t *n_sites_dev
         out.count[c] = (int64_t)acc.cnt[c];
 }
 
+// ------------------------------------------------------------------ co-moments on tensor cores
+// C_ij = sum over the cell (x_i - mean_i)(x_j - mean_j): per 16x8x8 brick the values, centred
+// by c = float(mean) of their cell, are split d = hi + lo into two BF16 numbers (lo = the
+// exact float remainder rounded to BF16) and staged var-major in shared memory in the brick's
+// cell-sorted order.  One warp per cell run accumulates X^T X with mma.sync m16n8k16 (BF16 in,
+// FP32 accumulate) over 16-voxel chunks as hi.hi + hi.lo + lo.hi (the lo.lo term is below
+// 2^-16 relative), then adds its 32x32 tile into the FP64 totals.  The finalisation removes
+// the centring offset exactly: C = C' - n (mean_i - c_i)(mean_j - c_j), and takes the
+// diagonal from the float-float M2 of the moments pass.
+constexpr int CX = 16, CY = 8, CZ = 8, CV = CX * CY * CZ;  // 1024 voxels
+constexpr int kCovVars = 32;
+constexpr int kCovStride = CV + 8;  // bf16 elements per variable row (bank offset)
+constexpr size_t kCovSmem = (size_t)2 * kCovVars * kCovStride * 2 + (size_t)CV * 8 + (CV + 1) * 2 + 64;
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                               unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// two consecutive bf16 of row `var` at even position p, with elements at or beyond `end` zeroed
+__device__ __forceinline__ unsigned frag2(const unsigned short *rows, int var, int p, int end) {
+    if (p >= end) return 0u;
+    unsigned v = *reinterpret_cast<const unsigned *>(rows + (size_t)var * kCovStride + p);
+    if (p + 1 >= end) return v & 0xFFFFu;
+    return v;
+}
+
+__device__ __forceinline__ unsigned short bf16_bits(float f) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+__global__ void __launch_bounds__(256) covariance_kernel(const int32_t *__restrict__ cell, Dims d,
+                                                         const __grid_constant__ AggParams p,
+                                                         const double *__restrict__ mean, int32_t max_sites,
+                                                         double *comom) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned short *hi = (unsigned short *)smem_raw;
+    unsigned short *lo = hi + kCovVars * kCovStride;
+    unsigned long long *keys = (unsigned long long *)(lo + kCovVars * kCovStride);
+    unsigned short *inv = (unsigned short *)(keys + CV);  // local index -> sorted position
+    __shared__ unsigned short head[CV + 1];
+    __shared__ int nruns_s, nvalid_s, wcnt[8];
+    const int m = p.m, T = m * (m + 1) / 2;
+    const int nbx = (d.nx + CX - 1) / CX, nby = (d.ny + CY - 1) / CY, nbz = (d.nz + CZ - 1) / CZ;
+    const int64_t nbricks = (int64_t)nbx * nby * nbz;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int64_t br = blockIdx.x; br < nbricks; br += gridDim.x) {
+        const int ox = (int)(br % nbx) * CX, oy = (int)((br / nbx) % nby) * CY, oz = (int)(br / ((int64_t)nbx * nby)) * CZ;
+        for (int i = tid; i < CV; i += blockDim.x) {
+            int x = ox + i % CX, y = oy + (i / CX) % CY, z = oz + i / (CX * CY);
+            unsigned long long k = ~0ULL;
+            if (x < d.nx && y < d.ny && z < d.nz) {
+                int32_t c = cell[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)];
+                if (c >= 0 && c < max_sites) k = ((unsigned long long)(uint32_t)c << 32) | (uint32_t)i;
+            }
+            keys[i] = k;
+        }
+        block_bitonic_sort(keys, CV);
+        int carry = 0;
+        for (int base = 0; base < CV; base += blockDim.x) {
+            int i = base + tid;
+            unsigned long long k = keys[i];
+            if (k != ~0ULL) inv[(uint32_t)k] = (unsigned short)i;
+            bool h = k != ~0ULL && (i == 0 || (keys[i - 1] >> 32) != (k >> 32));
+            unsigned bal = __ballot_sync(0xffffffffu, h);
+            if (lane == 0) wcnt[w] = __popc(bal);
+            __syncthreads();
+            int before = carry;
+            for (int q = 0; q < w; ++q) before += wcnt[q];
+            if (h) head[before + __popc(bal & lanemask_lt())] = (unsigned short)i;
+            for (int q = 0; q < 8; ++q) carry += wcnt[q];
+            if (k != ~0ULL && (i + 1 == CV || keys[i + 1] == ~0ULL)) nvalid_s = i + 1;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            nruns_s = carry;
+            if (carry == 0) nvalid_s = 0;
+            head[carry] = (unsigned short)nvalid_s;
+        }
+        __syncthreads();
+        const int nruns = nruns_s;
+        if (nruns == 0) continue;
+        // stage centred values, var-major, in sorted order; padding variables are zero
+        for (int i = tid; i < CV; i += blockDim.x) {
+            int x = ox + i % CX, y = oy + (i / CX) % CY, z = oz + i / (CX * CY);
+            if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
+            const int64_t gidx = x + (int64_t)d.nx * (y + (int64_t)d.ny * z);
+            const int32_t c = cell[gidx];
+            if (c < 0 || c >= max_sites) continue;
+            const int pos = inv[i];
+            for (int j = 0; j < kCovVars; ++j) {
+                unsigned short h2 = 0, l2 = 0;
+                if (j < m) {
+                    float v = __ldcs(p.aux[j] + gidx);
+                    float cen = (float)mean[(int64_t)c * m + j];
+                    float dd = __fsub_rn(v, cen);
+                    h2 = bf16_bits(dd);
+                    float hf = __bfloat162float(__ushort_as_bfloat16(h2));
+                    l2 = bf16_bits(__fsub_rn(dd, hf));
+                }
+                hi[(size_t)j * kCovStride + pos] = h2;
+                lo[(size_t)j * kCovStride + pos] = l2;
+            }
+        }
+        __syncthreads();
+        const int nI = (m + 15) / 16, nJ = (m + 7) / 8;
+        for (int r = w; r < nruns; r += 8) {
+            const int s0 = head[r], s1 = head[r + 1];
+            const int32_t c = (int32_t)(keys[s0] >> 32);
+            float acc[2][4][4];
+#pragma unroll
+            for (int I = 0; I < 2; ++I)
+#pragma unroll
+                for (int J = 0; J < 4; ++J)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[I][J][e] = 0.0f;
+            for (int ch = s0 - (s0 & 1); ch < s1; ch += 16) {
+                // positions of this lane's elements: ch + 2t (+1) and ch + 2t + 8 (+1); elements
+                // before s0 belong to the previous run and are masked by starting at an even
+                // position and zeroing below s0
+                const int pa = ch + 2 * t, pb = ch + 2 * t + 8;
+#pragma unroll
+                for (int I = 0; I < 2; ++I) {
+                    if (I >= nI) break;
+                    const int vi0 = 16 * I + g, vi1 = vi0 + 8;
+                    unsigned ah[4], al[4];
+                    auto ld = [&](const unsigned short *rows, int var, int pp) {
+                        unsigned v = frag2(rows, var, pp, s1);
+                        if (pp < s0) v &= (pp + 1 < s0) ? 0u : 0xFFFF0000u;
+                        return v;
+                    };
+                    ah[0] = ld(hi, vi0, pa); ah[1] = ld(hi, vi1, pa); ah[2] = ld(hi, vi0, pb); ah[3] = ld(hi, vi1, pb);
+                    al[0] = ld(lo, vi0, pa); al[1] = ld(lo, vi1, pa); al[2] = ld(lo, vi0, pb); al[3] = ld(lo, vi1, pb);
+#pragma unroll
+                    for (int J = 0; J < 4; ++J) {
+                        if (J >= nJ) break;
+                        const int vj = 8 * J + g;
+                        unsigned bh0 = ld(hi, vj, pa), bh1 = ld(hi, vj, pb);
+                        unsigned bl0 = ld(lo, vj, pa), bl1 = ld(lo, vj, pb);
+                        mma_bf16_16816(acc[I][J], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                        mma_bf16_16816(acc[I][J], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                        mma_bf16_16816(acc[I][J], al[0], al[1], al[2], al[3], bh0, bh1);
+                    }
+                }
+            }
+            // accumulate the upper triangle in FP64
+#pragma unroll
+            for (int I = 0; I < 2; ++I)
+#pragma unroll
+                for (int J = 0; J < 4; ++J)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        int i = 16 * I + g + (e >= 2 ? 8 : 0);
+                        int j = 8 * J + 2 * t + (e & 1);
+                        if (i < m && j < m && i <= j) {
+                            int tri = i * m - i * (i - 1) / 2 + (j - i);
+                            atomicAdd(&comom[(int64_t)c * T + tri], (double)acc[I][J][e]);
+                        }
+                    }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void covariance_finalize_kernel(const int64_t *count, const double *mean, const double *m2,
+                                           int32_t max_sites, int32_t m, double *comom) {
+    const int T = m * (m + 1) / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)max_sites * T;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = idx / T;
+        int tri = (int)(idx - c * T);
+        int i = 0;
+        while (tri >= (i + 1) * m - i * (i + 1) / 2) ++i;  // row of the upper triangle
+        int j = i + (tri - (i * m - i * (i - 1) / 2));
+        int64_t n = count[c];
+        if (n == 0) { comom[idx] = 0.0; continue; }
+        if (i == j) { comom[idx] = m2[c * m + i]; continue; }
+        double mi = mean[c * m + i], mj = mean[c * m + j];
+        double di = mi - (double)(float)mi, dj = mj - (double)(float)mj;
+        comom[idx] = comom[idx] - (double)n * di * dj;
+    }
+}
+
 // ------------------------------------------------------------------ value ranges
 __global__ void range_init_kernel(unsigned *lo_bits, unsigned *hi_bits, int32_t m) {
     int j = threadIdx.x + blockIdx.x * blockDim.x;
@@ -351,7 +541,7 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
                                                                        !out.vmin || !out.vmax)) ||
         (want_hist && n_aux > 0 && (!out.hist || !lo_dev || !scale_dev)) || (want_cov && n_aux > 0 && !out.comom))
         return LSRVT_ERR_INVALID_ARG;
-    if (want_cov) return LSRVT_ERR_INVALID_ARG;  // co-moments: not available in this build
+    if (want_cov && n_aux > kCovVars) return LSRVT_ERR_INVALID_ARG;  // tensor-core path holds up to 32 variables
     AggParams p;
     for (int j = 0; j < 64; ++j) p.aux[j] = nullptr;
     for (int j = 0; j < n_aux; ++j) {
@@ -380,5 +570,15 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
                                                   status_dev);
     aggregate_finalize_kernel<<<grid_for((int64_t)max_sites * (n_aux > 0 ? n_aux : 1), 256, kSMs * 8), 256, 0, s>>>(
         w.acc, n_sites_dev, max_sites, n_aux, p, site_pos, out);
+    if (want_cov && n_aux > 0) {
+        const int T = n_aux * (n_aux + 1) / 2;
+        cudaMemsetAsync(out.comom, 0, sizeof(double) * (size_t)max_sites * T, s);
+        cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCovSmem);
+        int64_t ncb = (int64_t)((d.nx + CX - 1) / CX) * ((d.ny + CY - 1) / CY) * ((d.nz + CZ - 1) / CZ);
+        int cg = (int)(ncb < (int64_t)kSMs * 2 ? ncb : (int64_t)kSMs * 2);
+        covariance_kernel<<<cg, 256, kCovSmem, s>>>(cell, d, p, out.mean, max_sites, out.comom);
+        covariance_finalize_kernel<<<grid_for((int64_t)max_sites * T, 256, kSMs * 8), 256, 0, s>>>(
+            out.count, out.mean, out.m2, max_sites, n_aux, out.comom);
+    }
     return launch_status();
 }

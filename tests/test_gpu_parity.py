@@ -237,3 +237,30 @@ def test_decompose_pipeline_config1(pk):
     ref = oracle.aggregate(cell, w["aux"].numpy(), len(sp2), n_bins=32)
     assert np.array_equal(cpu(out["cells"]["count"])[:ns], ref["count"])
     assert np.array_equal(cpu(out["cells"]["hist"])[:ns].view(np.uint32), ref["hist"])
+
+
+@pytest.mark.parametrize("m,shape", [(32, (40, 36, 33)), (7, (64, 48, 40)), (20, (37, 29, 23))])
+def test_covariance_parity(pk, m, shape):
+    """Co-moments on tensor cores (BF16 split, FP32 accumulate, FP64 finalise) against the FP64
+    oracle: |C_ij - R_ij| <= 1e-4 sqrt(R_ii R_jj) (correlated Gaussians with non-zero means)."""
+    f = workloads.blob_field(shape[::-1], 21, "cpu").numpy()
+    band = oracle.classify(f, np.array([0.3, 0.6], np.float32))
+    comp, cb, cs, cf = oracle.label_components(band)
+    sp, sc, off, nc = oracle.seed(comp, None, len(cb), 300, 16, 2)
+    sp2, cell, dist, tr = oracle.cvt_iterate(band, None, sp, 1)
+    aux, cov, mu = workloads.correlated_aux(shape[::-1], m, 31, "cpu")
+    aux = aux.numpy()
+    ref = oracle.aggregate(cell, aux, len(sp2), n_bins=0, cov=True)
+    gaux = [torch.from_numpy(a).cuda() for a in aux]
+    st = pk.new_status()
+    got = pk.aggregate(torch.from_numpy(cell).cuda(), gaux, torch.from_numpy(sp2).cuda(),
+                       torch.tensor([len(sp2)], dtype=torch.int32, device="cuda"), n_bins=0, cov=True, status=st)
+    pk.check_status(st)
+    C = cpu(got["comom"])
+    R = ref["comom"]
+    iu = np.triu_indices(m)
+    diag_pos = [k for k, (i, j) in enumerate(zip(*iu)) if i == j]
+    for k, (i, j) in enumerate(zip(*iu)):
+        scale = np.sqrt(np.maximum(R[:, diag_pos[i]] * R[:, diag_pos[j]], 0.0))
+        assert np.all(np.abs(C[:, k] - R[:, k]) <= 1e-4 * scale + 1e-9), (i, j)
+    assert np.array_equal(cpu(got["count"]), ref["count"])
