@@ -1,0 +1,170 @@
+"""Execution forms of the hot path: batched blocks and a continuous-batching server.
+
+Both drive the C ABI (all compute in liblsrvt) from host worker threads, one CUDA stream and
+one workspace per slot; ctypes releases the GIL during library calls, so the slots' kernels
+overlap on the device.  The paper's distributed form processes independent blocks with no
+communication (Sec. 3.2 "Parallel Algorithm", Discussion "Block Based Distributed
+Parallelism"); here independent blocks / requests share one GPU instead.
+
+  BatchRunner(n_slots).run(jobs)     -> results in job order
+  Server(n_slots, hbm_budget).serve(requests, make_job) -> per-request records
+
+A job is a dict: field (CUDA float32 (nz, ny, nx)), iso, voxels_per_site, n_iters, aux (list
+of CUDA tensors), gamma, strat_block, rng_seed, n_bins.
+"""
+import queue
+import threading
+import time
+
+import torch
+
+from . import decompose, Workspace
+
+
+def request_bytes(n_voxels, n_aux, voxels_per_site, n_bins=32):
+    """Estimate of the device bytes one decomposition holds (inputs, outputs, workspaces)."""
+    per_voxel = 4 + 1 + 4 + 2 + 4 + 4 + 4 * n_aux  # field, band, comp, q, cell, dist, aux
+    work = 26 * n_voxels  # tessellation workspace (keys, parents, clearance, bit planes, bins)
+    rows = n_voxels // max(int(voxels_per_site), 1) + (n_voxels // 16) + 4096
+    stats = rows * (8 + n_aux * (8 + 8 + 4 + 4 + 4 * n_bins))
+    return n_voxels * per_voxel + work + stats
+
+
+def job_bytes(job):
+    return request_bytes(job["field"].numel(), len(job.get("aux", ())), job["voxels_per_site"], job.get("n_bins", 32))
+
+
+class Slot:
+    def __init__(self, device):
+        self.stream = torch.cuda.Stream(device=device)
+        self.ws = Workspace(device)
+
+
+def _run(slot, job):
+    with torch.cuda.stream(slot.stream):
+        out = decompose(job["field"], job["iso"], job["voxels_per_site"], job["n_iters"], aux=job.get("aux", ()),
+                        gamma=job.get("gamma", 0), strat_block=job.get("strat_block", 16),
+                        rng_seed=job.get("rng_seed", 0), n_bins=job.get("n_bins", 32), ws=slot.ws, check=False)
+        done = torch.cuda.Event()
+        done.record(slot.stream)
+    return out, done
+
+
+class BatchRunner:
+    """Runs many independent blocks concurrently on n_slots streams (a block per slot at a time)."""
+
+    def __init__(self, n_slots=4, device="cuda"):
+        self.slots = [Slot(device) for _ in range(n_slots)]
+
+    def run(self, jobs):
+        results = [None] * len(jobs)
+        q = queue.Queue()
+        for i, j in enumerate(jobs):
+            q.put(i)
+        errors = []
+
+        def worker(slot):
+            while True:
+                try:
+                    i = q.get_nowait()
+                except queue.Empty:
+                    return
+                try:
+                    out, done = _run(slot, jobs[i])
+                    done.synchronize()
+                    from . import check_status
+                    check_status(out["status"], "block %d" % i)
+                    results[i] = out
+                except Exception as e:  # surfaced after all workers stop
+                    errors.append(e)
+                    return
+
+        threads = [threading.Thread(target=worker, args=(s,)) for s in self.slots]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errors:
+            raise errors[0]
+        return results
+
+
+class Server:
+    """Continuous batching: requests are admitted in arrival order whenever a slot is free and
+    their estimated device bytes fit in the remaining HBM budget; admitted requests run
+    concurrently on the slots' streams.  Latency = completion - arrival (host clock)."""
+
+    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda"):
+        self.slots = [Slot(device) for _ in range(n_slots)]
+        self.budget = int(hbm_budget)
+
+    def serve(self, requests, make_job, keep_outputs=False):
+        """requests: list of dicts with 'arrival' (seconds from start); make_job(req) builds the
+        job (device tensors) when the request is admitted.  Returns one record per request."""
+        order = sorted(range(len(requests)), key=lambda i: requests[i]["arrival"])
+        records = [None] * len(requests)
+        cv = threading.Condition()
+        state = dict(used=0, next=0, free=list(range(len(self.slots))), active=0, error=None)
+        t0 = time.perf_counter()
+
+        def admit_loop(slot_id):
+            slot = self.slots[slot_id]
+            while True:
+                with cv:
+                    while True:
+                        if state["error"] is not None or state["next"] >= len(order):
+                            return
+                        i = order[state["next"]]
+                        now = time.perf_counter() - t0
+                        wait = requests[i]["arrival"] - now
+                        need = requests[i].get("bytes") or 0
+                        fits = state["used"] + need <= self.budget or state["active"] == 0
+                        if wait <= 0 and fits:
+                            state["next"] += 1
+                            state["used"] += need
+                            state["active"] += 1
+                            break
+                        cv.wait(timeout=max(min(wait, 0.05), 0.0005) if wait > 0 else 0.01)
+                try:
+                    admitted = time.perf_counter() - t0
+                    job = make_job(requests[i])
+                    out, done = _run(slot, job)
+                    done.synchronize()
+                    finished = time.perf_counter() - t0
+                    from . import check_status
+                    check_status(out["status"], "request %d" % i)
+                    records[i] = dict(arrival=requests[i]["arrival"], admitted=admitted, finished=finished,
+                                      latency=finished - requests[i]["arrival"], voxels=job["field"].numel(),
+                                      iters=job["n_iters"], out=out if keep_outputs else None)
+                except Exception as e:
+                    with cv:
+                        state["error"] = e
+                        cv.notify_all()
+                    return
+                finally:
+                    with cv:
+                        state["used"] -= need
+                        state["active"] -= 1
+                        cv.notify_all()
+
+        threads = [threading.Thread(target=admit_loop, args=(k,)) for k in range(len(self.slots))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if state["error"] is not None:
+            raise state["error"]
+        return records
+
+
+def latency_summary(records):
+    lat = sorted(r["latency"] for r in records)
+    n = len(lat)
+
+    def pct(p):
+        return lat[min(n - 1, max(0, int(round(p / 100.0 * n + 0.5)) - 1))] * 1e3
+
+    span = max(r["finished"] for r in records) - min(r["arrival"] for r in records)
+    vox_it = sum(r["voxels"] * r["iters"] for r in records)
+    return dict(n=n, p50_ms=pct(50), p99_ms=pct(99), mean_ms=1e3 * sum(lat) / n,
+                throughput_req_s=n / span, gvoxel_iters_s=vox_it / span / 1e9, span_s=span)

@@ -1,0 +1,70 @@
+"""Execution forms: blocks run concurrently (batched) and requests served with continuous
+batching give the same labels (bit for bit) and statistics (within the moment tolerance) as
+each run alone."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_06970_b300 as pkg
+    from paper_2208_06970_b300 import build
+    build.build()
+    return pkg
+
+
+def _jobs(n, lo, hi, seed):
+    jobs = []
+    for b in workloads.block_batch(n_blocks=n, seed=seed, lo=lo, hi=hi, device="cuda"):
+        jobs.append(dict(field=b["field"], iso=b["iso"], voxels_per_site=b["voxels_per_site"], n_iters=4,
+                         aux=[b["aux"][j] for j in range(b["aux"].shape[0])], gamma=0, strat_block=16,
+                         rng_seed=b["rng_seed"], n_bins=32))
+    return jobs
+
+
+def _same(pk, a, b):
+    ns = int(a["n_sites"].item())
+    assert ns == int(b["n_sites"].item())
+    for k in ("band", "comp", "cell", "dist"):
+        assert torch.equal(a[k], b[k]), k
+    assert torch.equal(a["site_pos"][:ns], b["site_pos"][:ns])
+    ca, cb = a["cells"], b["cells"]
+    for k in ("count", "min", "max", "hist"):
+        assert torch.equal(ca[k][:ns], cb[k][:ns]), k
+    ma, mb = ca["mean"][:ns].cpu().numpy(), cb["mean"][:ns].cpu().numpy()
+    assert np.all(np.abs(ma - mb) <= 1e-9 * np.maximum(np.abs(mb), 1e-3))
+
+
+def test_batched_blocks_equal_alone(pk):
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(6, 24, 72, 3)
+    alone = [pk.decompose(j["field"], j["iso"], j["voxels_per_site"], j["n_iters"], aux=j["aux"],
+                          rng_seed=j["rng_seed"]) for j in jobs]
+    mixed = runtime.BatchRunner(n_slots=3).run(jobs)
+    for a, b in zip(alone, mixed):
+        _same(pk, a, b)
+
+
+def test_served_requests_equal_alone(pk):
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(8, 24, 64, 5)
+    reqs = [dict(arrival=0.02 * i, k=i, bytes=runtime.job_bytes(j)) for i, j in enumerate(jobs)]
+    # a budget of about two requests forces admission to wait for memory
+    budget = 2 * max(r["bytes"] for r in reqs)
+    srv = runtime.Server(n_slots=3, hbm_budget=budget)
+    recs = srv.serve(reqs, lambda r: jobs[r["k"]], keep_outputs=True)
+    assert all(r is not None for r in recs)
+    assert all(r["finished"] >= r["arrival"] for r in recs)
+    for i, j in enumerate(jobs):
+        alone = pk.decompose(j["field"], j["iso"], j["voxels_per_site"], j["n_iters"], aux=j["aux"],
+                             rng_seed=j["rng_seed"])
+        _same(pk, alone, recs[i]["out"])
+    s = runtime.latency_summary(recs)
+    assert s["p99_ms"] >= s["p50_ms"] > 0
