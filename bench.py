@@ -326,6 +326,58 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def forms_arm(args, dev):
+    """Batched blocks (independent blocks with sides U{32..256}, 2-12 isovalues, 20 Lloyd
+    iterations, 3 aux) and a served Poisson request stream (50/s, sides U{64..hi}, 2-10
+    isovalues, 0-16 aux, 10-30 iterations), each against the plain one-at-a-time form on the
+    same GPU.  Throughput counts voxels x Lloyd iterations."""
+    import paper_2208_06970_b300 as pkg
+    import workloads
+    from paper_2208_06970_b300 import runtime
+    out = {}
+    # ---- batching
+    blocks = workloads.block_batch(n_blocks=args.blocks, seed=3, lo=32, hi=256, device=dev)
+    jobs = [dict(field=b["field"], iso=b["iso"], voxels_per_site=b["voxels_per_site"], n_iters=b["n_iters"],
+                 aux=[b["aux"][j] for j in range(b["aux"].shape[0])], gamma=0, strat_block=16,
+                 rng_seed=b["rng_seed"], n_bins=32) for b in blocks]
+    vox_it = sum(j["field"].numel() * j["n_iters"] for j in jobs)
+    res = {}
+    for name, slots in (("plain", 1), ("batched", args.slots)):
+        runner = runtime.BatchRunner(n_slots=slots, device=dev)
+        runner.run(jobs[:2])  # warm the slots' workspaces
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        runner.run(jobs)
+        torch.cuda.synchronize()
+        res[name] = vox_it / (time.perf_counter() - t0) / 1e9
+    out["batched"] = dict(blocks=len(jobs), voxels=int(sum(j["field"].numel() for j in jobs)), slots=args.slots,
+                          plain_gvoxel_iters_s=res["plain"], batched_gvoxel_iters_s=res["batched"],
+                          speedup=res["batched"] / res["plain"])
+    del jobs, blocks
+    torch.cuda.empty_cache()
+    # ---- serving
+    reqs = workloads.request_stream(n_requests=args.requests, rate=50.0, seed=5, lo=64, hi=args.serve_hi)
+    jobs = []
+    for r in reqs:
+        f = workloads.blob_field(r["dims"], r["seed"], dev)
+        aux = [workloads.blob_field(r["dims"], r["seed"] + 1 + j, dev, n_blobs=8, noise=0.1) for j in range(r["n_aux"])]
+        jobs.append(dict(field=f, iso=r["iso"], voxels_per_site=r["voxels_per_site"], n_iters=r["n_iters"], aux=aux,
+                         gamma=0, strat_block=16, rng_seed=r["seed"], n_bins=32))
+        r["bytes"] = runtime.job_bytes(jobs[-1])
+    for k, r in enumerate(reqs):
+        r["k"] = k
+    summ = {}
+    for name, slots in (("plain", 1), ("served", args.slots)):
+        srv = runtime.Server(n_slots=slots, hbm_budget=args.hbm_budget << 30, device=dev)
+        srv.serve([dict(arrival=0.0, k=0, bytes=reqs[0]["bytes"])], lambda r: jobs[r["k"]])  # warm-up
+        torch.cuda.synchronize()
+        recs = srv.serve(reqs, lambda r: jobs[r["k"]])
+        summ[name] = runtime.latency_summary(recs)
+    out["served"] = dict(requests=len(reqs), rate_per_s=50.0, sides="64..%d" % args.serve_hi, slots=args.slots,
+                         hbm_budget_gib=args.hbm_budget, plain=summ["plain"], served=summ["served"])
+    return out
+
+
 def profile_step(args):
     """Workload generation plus two identical steps, no extra instrumentation (ncu target)."""
     import paper_2208_06970_b300 as pkg
@@ -352,6 +404,12 @@ def main():
     ap.add_argument("--ref-side", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / served comparison")
+    ap.add_argument("--blocks", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-hi", type=int, default=384)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--hbm-budget", type=int, default=96, help="GiB admitted at once by the server")
     ap.add_argument("--profile-step", action="store_true",
                     help="generate the workload and run two plain steps (for ncu); prints nothing else")
     args = ap.parse_args()
@@ -371,6 +429,9 @@ def main():
     if rank == 0:
         n = r["n"]
         value = world * n * N_ITERS / (r["ms"] * 1e-3) / 1e9
+        forms = None
+        if not args.no_forms and world == 1:
+            forms = forms_arm(args, torch.device("cuda", local_rank))
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             v, dt, desc = oracle_sample(r["field"], r["aux"], r["iso"], side=args.ref_side, iters=args.ref_iters)
@@ -397,7 +458,8 @@ def main():
                        frac=(r["stats_gbs"] / pk["hbm"]) if r["stats_gbs"] else None),
             phases_ms=r["phase"], cvt_gvoxel_iters_per_s=n * N_ITERS / (r["cvt_ms"] * 1e-3) / 1e9,
             moved_per_iter=r["trace"][:, 0].tolist(), clocks=r["clk"], e2e=r["e2e"],
-            gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu)
+            gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu,
+            forms=forms)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
