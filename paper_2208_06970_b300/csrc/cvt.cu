@@ -76,10 +76,11 @@ __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
     return e;
 }
 
-__global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
-    const uint8_t *__restrict__ band, Dims d, BrickGeom bg, unsigned long long *key, const int32_t *__restrict__ list_in,
-    const int32_t *n_in, int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag, int32_t *work,
-    int32_t *status) {
+// One relaxation round: the CTAs of the grid take the queued bricks one at a time.
+__device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
+                                            unsigned long long *key, const int32_t *list_in, const int nin,
+                                            int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag,
+                                            int32_t *work, int32_t *status) {
     // packed keys: one aligned 64-bit access per read/write, so a reader never pairs the
     // distance of one update with the site of another
     __shared__ unsigned long long sk[HV];
@@ -89,13 +90,13 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
     __shared__ uint32_t touch;
     __shared__ int item;
     const int tid = threadIdx.x;
-    const int nin = *n_in;
     while (true) {
         if (tid == 0) item = atomicAdd(work, 1);
         __syncthreads();
         const int it = item;
+        __syncthreads();  // every thread has read `item` before thread 0 may overwrite it
         if (it >= nin) break;
-        const int brick = list_in[it];
+        const int brick = __ldcg(list_in + it);
         const int bx = brick % bg.nbx, by = (brick / bg.nbx) % bg.nby, bz = brick / (bg.nbx * bg.nby);
         const int ox = bx * RX, oy = by * RY, oz = bz * RZ;
         // ---- load halo
@@ -225,6 +226,69 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_round_kernel(
         }
         __syncthreads();
     }
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The last CTA to arrive
+// clears the queue that was just consumed, so the next round can append to it, then releases
+// the others.  Waits are bounded: past the limit the status word gets TIMEOUT and every CTA
+// leaves the loop at the next barrier (abort flag), so the kernel always ends.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int abort;
+};
+
+__device__ bool grid_barrier(GridBarrier *bar, int32_t *reset_n, int32_t *reset_work, int32_t *status) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &bar->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            bar->count = 0;
+            *reset_n = 0;
+            *reset_work = 0;
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                __nanosleep(64);
+                if (++spins > (1LL << 26) || *(volatile int *)&bar->abort) {
+                    set_status(status, LSRVT_ERR_TIMEOUT);
+                    atomicExch(&bar->abort, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)&bar->abort) ok = 0;
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// All relaxation rounds in one cooperative launch: round r consumes queue r & 1 and fills
+// the other; the loop ends when a round starts with an empty queue.  No host round trips.
+__global__ void __launch_bounds__(kRelaxThreads) relax_persistent_kernel(
+    const uint8_t *__restrict__ band, Dims d, BrickGeom bg, unsigned long long *key, int32_t *list0, int32_t *list1,
+    int32_t *counts, int32_t *works, uint32_t *flags, uint32_t tag0, int32_t max_rounds, GridBarrier *bar,
+    int32_t *status) {
+    int r = 0;
+    for (; r < max_rounds; ++r) {
+        const int cur = r & 1;
+        const int nin = __ldcg(counts + cur);
+        if (nin == 0) break;
+        relax_items(band, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
+                    tag0 + (uint32_t)r + 1u, works + cur, status);
+        if (!grid_barrier(bar, counts + cur, works + cur, status)) return;
+    }
+    if (r == max_rounds && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, LSRVT_ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------- clearance field
@@ -932,11 +996,6 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
     }
 }
 
-// reset the consumed queue (count + work counter) after a round
-__global__ void round_advance_kernel(int32_t *n_consumed, int32_t *work_consumed) {
-    *n_consumed = 0;
-    *work_consumed = 0;
-}
 
 // ---------------------------------------------------------------- voxel traversal
 // 6-connected Amanatides-Woo traversal of the segment joining the centres of voxels a
@@ -1160,6 +1219,7 @@ struct CvtWs {
     int4 *cell_list;
     int32_t *cell_count;
     uint32_t *pending;
+    GridBarrier *bar;
     void *scan;
 };
 
@@ -1194,12 +1254,12 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.cell_list = c.take<int4>(ncoarse * kCellList);
     w.cell_count = c.take<int32_t>(ncoarse);
     w.pending = c.take<uint32_t>((n + 31) / 32);
+    w.bar = c.take<GridBarrier>(1);
     w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
     *need = c.used;
     return w;
 }
 
-constexpr int kRoundsPerCheck = 8;
 constexpr int kMaxRounds = 1 << 16;
 
 }  // namespace
@@ -1261,33 +1321,25 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     }
 #endif
     int nb_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, relax_round_kernel, kRelaxThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, relax_persistent_kernel, kRelaxThreads, 0);
     if (nb_per_sm < 1) nb_per_sm = 1;
-    int grid = kSMs * nb_per_sm;
-    int cur = 0;
-    for (int r = 0; r < kMaxRounds; ++r) {
-        ++tag;
-        relax_round_kernel<<<grid, kRelaxThreads, 0, s>>>(band, d, bg, w.key, w.list[cur], w.counters + 1 + cur,
-                                                           w.list[1 - cur], w.counters + 1 + (1 - cur), w.flags, tag,
-                                                           w.counters + 3 + cur, status);
-        round_advance_kernel<<<1, 1, 0, s>>>(w.counters + 1 + cur, w.counters + 3 + cur);
-        cur = 1 - cur;
-#ifdef LSRVT_DEBUG
-        {
-            int32_t pend = 0;
-            cudaMemcpyAsync(&pend, w.counters + 1 + cur, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-            fprintf(stderr, "round %d next=%d\n", r, pend);
-        }
-#endif
-        if ((r + 1) % kRoundsPerCheck == 0) {
-            int32_t pending = 0;
-            cudaMemcpyAsync(&pending, w.counters + 1 + cur, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-            if (cudaStreamSynchronize(s) != cudaSuccess) return LSRVT_ERR_CUDA;
-            if (pending == 0) return launch_status();
-        }
-    }
-    return LSRVT_ERR_TIMEOUT;
+    int dev = 0, nsm = kSMs;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int grid = nsm * nb_per_sm;
+    cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), s);
+    uint32_t tag_round0 = tag;
+    int32_t max_rounds = kMaxRounds;
+    int32_t *list0 = w.list[0], *list1 = w.list[1], *counts = w.counters + 1, *works = w.counters + 3;
+    GridBarrier *bar = w.bar;
+    void *args[] = {(void *)&band, (void *)&d, (void *)&bg, (void *)&w.key, (void *)&list0, (void *)&list1,
+                    (void *)&counts, (void *)&works, (void *)&w.flags, (void *)&tag_round0, (void *)&max_rounds,
+                    (void *)&bar, (void *)&status};
+    if (cudaLaunchCooperativeKernel((const void *)relax_persistent_kernel, grid, kRelaxThreads, args, 0, s) !=
+        cudaSuccess)
+        return LSRVT_ERR_CUDA;
+    tag += (uint32_t)kMaxRounds + 1u;
+    return launch_status();
 }
 
 }  // namespace
