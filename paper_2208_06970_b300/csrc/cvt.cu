@@ -845,27 +845,44 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         }
         __syncthreads();
         const int nl = cell_count[cell];
-        const int4 *L = cell_list + cell * kCellList;
-        // brick-level bounds, then the survivors
-        for (int i = tid; i < nl; i += blockDim.x) {
-            int4 c = L[i];
-            int b = c.w >> 24;
-            if ((present[b >> 5] >> (b & 31)) & 1u)
-                atomicMin(&Ub[b], chamfer_box_max(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz));
+        // complete = the coarse cell's list is usable (it holds every site that can win);
+        // otherwise (dense regions overflow it) the brick takes the sites of the bricks within
+        // +-1 (x) / +-2 (y, z) bricks and settles a voxel only when its best is closer than
+        // any site outside that box can be
+        const bool complete = nl >= 0;
+        constexpr int FX = 1, FY = 2, FZ = 2, NFX = 2 * FX + 1, NFY = 2 * FY + 1, NFZ = 2 * FZ + 1;
+        // brick-level bounds, then the survivors (two passes over the same candidates)
+        for (int pass = 0; pass < 2; ++pass) {
+            auto visit = [&](const int4 &c) {
+                int b = c.w >> 24;
+                if (!((present[b >> 5] >> (b & 31)) & 1u)) return;
+                if (pass == 0) {
+                    atomicMin(&Ub[b], chamfer_box_max(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz));
+                } else if (chamfer_box_min(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz) <= Ub[b]) {
+                    int at = atomicAdd(&ncand_s, 1);
+                    if (at < kMaxCand) cs[at] = c;
+                }
+            };
+            if (complete) {
+                const int4 *L = cell_list + cell * kCellList;
+                for (int i = tid; i < nl; i += blockDim.x) visit(L[i]);
+            } else {
+                for (int qb = tid; qb < NFX * NFY * NFZ; qb += blockDim.x) {
+                    int cx = bx + qb % NFX - FX, cy = by + (qb / NFX) % NFY - FY, cz = bz + qb / (NFX * NFY) - FZ;
+                    if (cx < 0 || cx >= bg.nbx || cy < 0 || cy >= bg.nby || cz < 0 || cz >= bg.nbz) continue;
+                    int64_t bb = cx + (int64_t)bg.nbx * (cy + (int64_t)bg.nby * cz);
+                    for (int64_t r = fine_off[bb]; r < fine_off[bb + 1]; ++r) visit(fine_cand[r]);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int i = tid; i < nl; i += blockDim.x) {
-            int4 c = L[i];
-            int b = c.w >> 24;
-            if (!((present[b >> 5] >> (b & 31)) & 1u)) continue;
-            if (chamfer_box_min(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz) > Ub[b]) continue;
-            int at = atomicAdd(&ncand_s, 1);
-            if (at < kMaxCand) cs[at] = c;
-        }
-        __syncthreads();
         PHASE_ADD(0);
         const int nc = ncand_s;
-        const bool ok_list = nl >= 0 && nc <= kMaxCand;
+        const bool ok_list = nc <= kMaxCand;
+        // fine search box in voxels (used only when !complete)
+        const int flx = (bx - FX) * RX, fhx = (bx + FX + 1) * RX - 1;
+        const int fly = (by - FY) * RY, fhy = (by + FY + 1) * RY - 1;
+        const int flz = (bz - FZ) * RZ, fhz = (bz + FZ + 1) * RZ - 1;
         int npow2 = 1;
         if (ok_list) {
             while (npow2 < nc) npow2 <<= 1;
@@ -915,6 +932,16 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                     unsigned long long k2 = (cd << 32) | (unsigned)c.x;
                     if (k2 < best) { best = k2; bs = c; }
                 }
+            }
+            if (!complete && best != kInfKey) {
+                long long gap = 1LL << 40;
+                if (flx > 0) gap = min(gap, (long long)(x - flx + 1));
+                if (fhx < d.nx - 1) gap = min(gap, (long long)(fhx - x + 1));
+                if (fly > 0) gap = min(gap, (long long)(y - fly + 1));
+                if (fhy < d.ny - 1) gap = min(gap, (long long)(fhy - y + 1));
+                if (flz > 0) gap = min(gap, (long long)(z - flz + 1));
+                if (fhz < d.nz - 1) gap = min(gap, (long long)(fhz - z + 1));
+                if ((best >> 32) >= (unsigned long long)gap * kWFace) best = kInfKey;  // not settled
             }
             unsigned long long k = kInfKey;
             bool los = false, pend = false;
