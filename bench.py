@@ -148,8 +148,8 @@ class Pipeline:
         comps, bands, vol = pk.merge_hierarchy(cells, ns, off, cb, nc, self.max_comp, self.n_bands, N_BINS,
                                                ws=self.ws)
         mark("merge")
-        self.last = dict(band=band, cell=cell, site_pos=sp, n_sites=ns, n_comp=nc, cells=cells, volume=vol,
-                         trace=trace)
+        self.last = dict(band=band, cell=cell, site_pos=sp, n_sites=ns, n_comp=nc, cells=cells, comps=comps,
+                         bands=bands, volume=vol, trace=trace)
         return self.last
 
 

@@ -55,6 +55,7 @@ def lib():
         L.orc_assign.argtypes = [P, i32, i32, i32, P, i32, P, P]
         L.orc_los.argtypes = [P, i32, i32, i32, i32, i32]
         L.orc_update.argtypes = [P, P, i32, i32, i32, P, P, P, i32, P, P, P, P, P, P]
+        L.orc_update_selected.argtypes = [P, P, i32, i32, i32, P, P, P, i32, P, P, P]
         L.orc_cvt_iterate.argtypes = [P, P, i32, i32, i32, P, i32, i32, P, P, P]
         L.orc_aux_range.argtypes = [P, P, i32, i64, i32, P, P, P]
         L.orc_aggregate.argtypes = [P, P, i32, i64, i32, P, P, i32, i32, P, P, P, P, P, P, P]
@@ -183,6 +184,28 @@ def update(band, q, cell, dist, site_pos, diagnostics=False):
     if diagnostics:
         return out + (dict(parent=parent, los=losv.astype(bool), phi=phi, sums=sums[:S]),)
     return out
+
+
+def update_selected(band, q, cell, dist, site_pos, sites):
+    """Eq. 2 update restricted to the cells of `sites` (exact for those sites: parents,
+    line of sight and phi stay inside a cell).  Returns (new positions of `sites`, their
+    integer sums (len(sites), 4))."""
+    band = np.ascontiguousarray(band, dtype=np.uint8)
+    nx, ny, nz = _dims(band)
+    if q is not None:
+        q = np.ascontiguousarray(q, dtype=np.uint16)
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    dist = np.ascontiguousarray(dist, dtype=np.uint32)
+    site_pos = np.ascontiguousarray(site_pos, dtype=np.int32)
+    S = len(site_pos)
+    sites = np.asarray(sites, dtype=np.int64)
+    sel = np.zeros(max(S, 1), np.uint8)
+    sel[sites] = 1
+    new_pos = np.empty(max(S, 1), np.int32)
+    sums = np.zeros((max(S, 1), 4), np.int64)
+    _check(lib().orc_update_selected(_p(band), _p(q), nx, ny, nz, _p(cell), _p(dist), _p(site_pos), S, _p(sel),
+                                     _p(new_pos), _p(sums)), "update_selected")
+    return new_pos[sites].copy(), sums[sites].copy()
 
 
 def cvt_iterate(band, q, site_pos, n_iters):

@@ -584,10 +584,15 @@ int orc_los(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
 /* stats[0] = sites moved, stats[1] = sum of squared displacements.           */
 /* parent_out / los_out / phi_out / sums_out are optional (NULL) diagnostics. */
 /* ------------------------------------------------------------------------- */
-int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
-               const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
-               int32_t *new_pos, int64_t *stats,
-               int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
+/* site_sel (optional, one byte per site): when given, only the voxels of the  */
+/* selected cells are visited and only the selected sites move.  A cell's     */
+/* parents, line-of-sight tests and phi never leave the cell, so the selected */
+/* sites get exactly the positions of the full update; this lets one full-    */
+/* size replay check a sample of cells.                                       */
+static int update_impl(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+                       const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
+                       const uint8_t *site_sel, int32_t *new_pos, int64_t *stats,
+                       int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
 {
     int64_t n = (int64_t)nx * ny * nz;
     int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
@@ -600,6 +605,7 @@ int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, i
         parent[v] = -1; los[v] = 0; phi[v] = -1;
         int32_t s = cell[v];
         if (s < 0) continue;
+        if (site_sel && !site_sel[s]) continue;
         int32_t x = (int32_t)(v % nx), y = (int32_t)((v / nx) % ny), z = (int32_t)(v / ((int64_t)nx * ny));
         if (dist[v] == 0) { parent[v] = (int32_t)v; }
         else {
@@ -618,6 +624,7 @@ int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, i
     }
     for (int64_t v = 0; v < n; ++v) {
         if (cell[v] < 0) continue;
+        if (site_sel && !site_sel[cell[v]]) continue;
         int64_t u = v;
         int64_t guard = 0;
         while (!los[u]) {
@@ -660,6 +667,26 @@ int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, i
 done:
     free(parent); free(los); free(phi); free(S);
     return rc;
+}
+
+int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+               const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
+               int32_t *new_pos, int64_t *stats,
+               int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
+{
+    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, NULL, new_pos, stats,
+                       parent_out, los_out, phi_out, sums_out);
+}
+
+/* Update of the selected sites only (new_pos and sums_out hold all sites;   */
+/* unselected ones keep their position and zero sums).                        */
+int orc_update_selected(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+                        const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
+                        const uint8_t *site_sel, int32_t *new_pos, int64_t *sums_out)
+{
+    int64_t stats[2];
+    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, site_sel, new_pos, stats,
+                       NULL, NULL, NULL, sums_out);
 }
 
 /* ------------------------------------------------------------------------- */

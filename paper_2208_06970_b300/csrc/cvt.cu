@@ -228,6 +228,10 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
     }
 }
 
+#ifdef LSRVT_DEBUG
+__device__ unsigned long long g_relax_dbg[2];  // rounds, brick visits
+#endif
+
 // Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The last CTA to arrive
 // clears the queue that was just consumed, so the next round can append to it, then releases
 // the others.  Waits are bounded: past the limit the status word gets TIMEOUT and every CTA
@@ -284,6 +288,12 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_persistent_kernel(
         const int cur = r & 1;
         const int nin = __ldcg(counts + cur);
         if (nin == 0) break;
+#ifdef LSRVT_DEBUG
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicAdd(&g_relax_dbg[0], 1ULL);
+            atomicAdd(&g_relax_dbg[1], (unsigned long long)nin);
+        }
+#endif
         relax_items(band, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
                     tag0 + (uint32_t)r + 1u, works + cur, status);
         if (!grid_barrier(bar, counts + cur, works + cur, status)) return;
@@ -1344,7 +1354,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
         int32_t q0 = 0;
         cudaMemcpyAsync(&q0, w.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
-        fprintf(stderr, "cfi: %d of %lld bricks queued\n", q0, (long long)nbricks);
+        fprintf(stderr, "cfi: %d of %lld bricks queued", q0, (long long)nbricks);
     }
 #endif
     int nb_per_sm = 0;
@@ -1366,6 +1376,15 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
         cudaSuccess)
         return LSRVT_ERR_CUDA;
     tag += (uint32_t)kMaxRounds + 1u;
+#ifdef LSRVT_DEBUG
+    {
+        unsigned long long rd[2], z[2] = {0, 0};
+        cudaStreamSynchronize(s);
+        cudaMemcpyFromSymbol(rd, g_relax_dbg, sizeof(rd));
+        cudaMemcpyToSymbol(g_relax_dbg, z, sizeof(z));
+        fprintf(stderr, " | relax rounds %llu brick visits %llu\n", rd[0], rd[1]);
+    }
+#endif
     return launch_status();
 }
 

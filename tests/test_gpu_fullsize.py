@@ -1,0 +1,162 @@
+"""Full-size parity on the 512^3 flame workload, run exactly as the benchmark runs it
+(bench.Pipeline: same calls, buffers, workspace and launch configuration).
+
+The oracle cannot rerun 30 Lloyd iterations on 134 M voxels in test time, so:
+- classify, components, weights and seeding are compared with the oracle on the whole volume;
+- every assignment checked is certified exactly by the Bellman equations of the
+  lexicographic key (a unique fixed point; an O(26 N) host check);
+- one Lloyd update is replayed by the oracle on a sample of cells, from the GPU's
+  certified assignment of iteration 29, and must give the GPU's sites of iteration 30;
+- resuming (29 iterations, then 1) gives the 30-iteration sites and labels bit for bit;
+- statistics are compared on a sample of cells (the oracle sees only those voxels), with
+  the histogram ranges computed by the oracle over the whole volume;
+- the merge is compared with the oracle's merge of the same per-cell records.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import bench
+    import paper_2208_06970_b300 as pk
+    from paper_2208_06970_b300 import build
+    build.build()
+    w = workloads.flame_workload(side=512, seed=2, device="cuda", n_aux=bench.N_AUX, n_iters=bench.N_ITERS)
+    pipe = bench.Pipeline(pk, w["field"], [w["aux"][j] for j in range(bench.N_AUX)], w["iso"])
+    out = pipe.step()
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "full-size step")
+    f = cpu(w["field"])
+    band = oracle.classify(f, w["iso"])
+    return dict(pk=pk, bench=bench, w=w, pipe=pipe, out=out, f=f, band=band)
+
+
+def test_full_classify_components_weights_seeds(full):
+    pk, pipe, out, band, f = full["pk"], full["pipe"], full["out"], full["band"], full["f"]
+    assert np.array_equal(cpu(out["band"]), band)
+    comp, cb, cs, cf = oracle.label_components(band)
+    g = pk.label_components(out["band"], pipe.max_comp, pipe.ws, pipe.status)
+    nc = int(g[4].item())
+    assert nc == len(cb) == int(out["n_comp"].item())
+    assert np.array_equal(cpu(g[0]), comp)
+    assert np.array_equal(cpu(g[1])[:nc], cb) and np.array_equal(cpu(g[2])[:nc], cs)
+    assert np.array_equal(cpu(g[3])[:nc], cf)
+    q = oracle.saliency(f, 1)
+    gq = pk.saliency_grad(full["w"]["field"], 1, pipe.ws)
+    assert np.array_equal(cpu(gq).view(np.uint16), q)
+    bench = full["bench"]
+    sp, sc, off, _ = oracle.seed(comp, q, len(cb), bench.VPS, 16, 2)
+    gsp, gsc, goff, gns = pk.seed(g[0], gq, g[4], pipe.max_comp, bench.VPS, 16, 2, ws=pipe.ws, status=pipe.status)
+    ns = int(gns.item())
+    assert ns == len(sp)
+    assert np.array_equal(cpu(gsp)[:ns], sp) and np.array_equal(cpu(gsc)[:ns], sc)
+    assert np.array_equal(cpu(goff)[:nc + 1], off)
+    full.update(comp=comp, comp_band=cb, q=q, sites0=sp, gq=gq, gcomp=g, gsp0=gsp, gns=gns, off=off)
+
+
+def test_full_tessellation_certified_replayed_resumed(full):
+    if "sites0" not in full:
+        pytest.skip("needs the seeding comparison")
+    pk, pipe, out, band, bench = full["pk"], full["pipe"], full["out"], full["band"], full["bench"]
+    ns = int(full["gns"].item())
+    # 29 iterations, certified assignment of the last one
+    sp29 = full["gsp0"].clone()
+    cell29, dist29, _ = pk.cvt_iterate(out["band"], full["gq"], sp29, full["gns"], bench.N_ITERS - 1, ws=pipe.ws,
+                                       status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "29 iterations")
+    h_sp29, h_cell29, h_dist29 = cpu(sp29)[:ns], cpu(cell29), cpu(dist29).view(np.uint32)
+    assert oracle.certify(band, h_sp29, h_cell29, h_dist29) == 0
+    # the 30th iteration, resumed from there
+    sp30 = sp29.clone()
+    cell30, dist30, _ = pk.cvt_iterate(out["band"], full["gq"], sp30, full["gns"], 1, ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "resumed iteration")
+    h_sp30 = cpu(sp30)[:ns]
+    assert np.array_equal(h_sp30, cpu(out["site_pos"])[:ns])
+    assert np.array_equal(cpu(cell30), cpu(out["cell"]))
+    assert oracle.certify(band, h_sp30, cpu(cell30), cpu(dist30).view(np.uint32)) == 0
+    # oracle replay of the 30th update on a sample of cells: random ones plus the largest
+    rng = np.random.default_rng(30)
+    counts = np.bincount(h_cell29[h_cell29 >= 0].ravel(), minlength=ns)
+    sample = np.unique(np.concatenate([rng.choice(ns, size=min(ns, 192), replace=False),
+                                       np.argsort(counts)[-32:], np.flatnonzero(h_sp30 != h_sp29)[:32]]))
+    got, _ = oracle.update_selected(band, full["q"], h_cell29, h_dist29, h_sp29, sample)
+    assert np.array_equal(got, h_sp30[sample])
+    assert (h_sp30[sample] != h_sp29[sample]).any()
+
+
+def _moment_ok(got_mean, got_m2, ref_mean, ref_m2, count):
+    n = np.maximum(count, 1)[:, None].astype(np.float64)
+    var_r, var_g = ref_m2 / n, got_m2 / n
+    floor = 1e-6 * (var_r + ref_mean ** 2)
+    assert np.all(np.abs(got_mean - ref_mean) <= 1e-6 * np.maximum(np.abs(ref_mean), floor) + 1e-300)
+    assert np.all(np.abs(var_g - var_r) <= 1e-6 * np.maximum(np.abs(var_r), floor) + 1e-300)
+
+
+def test_full_statistics_sampled_cells_and_merge(full):
+    pk, pipe, out, bench = full["pk"], full["pipe"], full["out"], full["bench"]
+    aux = full["w"]["aux"]
+    m = bench.N_AUX
+    cell = out["cell"]
+    h_cell = cpu(cell)
+    ns = int(out["n_sites"].item())
+    # histogram ranges: the oracle over the whole volume, one variable at a time
+    lo = np.empty(m, np.float32)
+    sc = np.empty(m, np.float32)
+    for j in range(m):
+        l, _, s = oracle.aux_range(h_cell, cpu(aux[j])[None], bench.N_BINS)
+        lo[j], sc[j] = l[0], s[0]
+    glo, gsc = pk.aux_range(cell, [aux[j] for j in range(m)], bench.N_BINS, pipe.status)
+    assert np.array_equal(cpu(glo), lo) and np.array_equal(cpu(gsc), sc)
+    # sampled cells: the oracle aggregates only their voxels
+    rng = np.random.default_rng(31)
+    counts = np.bincount(h_cell[h_cell >= 0].ravel(), minlength=ns)
+    sample = np.unique(np.concatenate([rng.choice(ns, size=min(ns, 96), replace=False), np.argsort(counts)[-8:],
+                                       np.argsort(counts)[:8]]))
+    remap = torch.full((ns,), -1, dtype=torch.int32, device=cell.device)
+    remap[torch.from_numpy(sample).to(cell.device).long()] = torch.arange(len(sample), dtype=torch.int32,
+                                                                           device=cell.device)
+    flat = cell.reshape(-1)
+    sel = torch.nonzero(flat >= 0).squeeze(1)
+    sel = sel[remap[flat[sel].long()] >= 0]
+    sub_cell = cpu(remap[flat[sel].long()])
+    sub_aux = np.stack([cpu(aux[j].reshape(-1)[sel]) for j in range(m)])
+    ref = oracle.aggregate(sub_cell, sub_aux, len(sample), lo, sc, bench.N_BINS)
+    cells = out["cells"]
+    assert np.array_equal(cpu(cells["count"])[sample], ref["count"])
+    assert np.array_equal(cpu(cells["min"])[sample], ref["min"])
+    assert np.array_equal(cpu(cells["max"])[sample], ref["max"])
+    assert np.array_equal(cpu(cells["hist"])[sample].view(np.uint32), ref["hist"])
+    _moment_ok(cpu(cells["mean"])[sample], cpu(cells["m2"])[sample], ref["mean"], ref["m2"], ref["count"])
+    assert int(cpu(cells["count"])[:ns].sum()) == int((h_cell >= 0).sum())
+    # merge: the oracle's merge of the same per-cell records
+    if "comp_band" not in full:
+        pytest.skip("needs the seeding comparison")
+    rec = dict(count=cpu(cells["count"])[:ns], mean=cpu(cells["mean"])[:ns], m2=cpu(cells["m2"])[:ns],
+               min=cpu(cells["min"])[:ns], max=cpu(cells["max"])[:ns],
+               hist=cpu(cells["hist"])[:ns].view(np.uint32), comom=None)
+    site_comp = np.repeat(np.arange(len(full["comp_band"]), dtype=np.int32), np.diff(full["off"]))
+    rc, rb, rv = oracle.merge_hierarchy(rec, site_comp, full["comp_band"], len(full["w"]["iso"]) + 1)
+    last = pipe.last
+    gv = last["volume"]
+    gb, gc = last["bands"], last["comps"]
+    for g, r in ((gc, rc), (gb, rb), (gv, rv)):
+        k = len(r["count"])
+        assert np.array_equal(cpu(g["count"])[:k], r["count"])
+        assert np.array_equal(cpu(g["min"])[:k], r["min"]) and np.array_equal(cpu(g["max"])[:k], r["max"])
+        assert np.array_equal(cpu(g["hist"])[:k].view(np.uint32), r["hist"])
+        _moment_ok(cpu(g["mean"])[:k], cpu(g["m2"])[:k], r["mean"], r["m2"], r["count"])

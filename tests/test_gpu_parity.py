@@ -264,3 +264,28 @@ def test_covariance_parity(pk, m, shape):
         scale = np.sqrt(np.maximum(R[:, diag_pos[i]] * R[:, diag_pos[j]], 0.0))
         assert np.all(np.abs(C[:, k] - R[:, k]) <= 1e-4 * scale + 1e-9), (i, j)
     assert np.array_equal(cpu(got["count"]), ref["count"])
+
+
+def test_cvt_rerun_and_resume_bit_identical(pk):
+    # Algorithm 1 split as k1 + k2 iterations (the second call resumes from the first call's
+    # sites) equals one call of k1 + k2 iterations, and reruns repeat bit for bit
+    w = workloads.flame_workload(side=(70, 52, 45), seed=4, n_aux=0)
+    f = w["field"].cuda()
+    band = pk.classify(f, w["iso"])
+    mc = pk.default_max_comp(f.numel())
+    comp, cb, cs, cf, nc = pk.label_components(band, mc)
+    q = pk.saliency_grad(f, 1)
+    sp, sc, off, ns = pk.seed(comp, q, nc, mc, 256, 16, 4)
+    runs = []
+    for split in ((7, 0), (3, 4), (7, 0), (0, 7)):
+        s = sp.clone()
+        st = pk.new_status()
+        if split[0]:
+            pk.cvt_iterate(band, q, s, ns, split[0], status=st)
+        cell, dist, _ = pk.cvt_iterate(band, q, s, ns, split[1], status=st)
+        pk.check_status(st)
+        runs.append((cpu(s), cpu(cell), cpu(dist)))
+    for r in runs[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(r, runs[0]))
+    s_ref, c_ref, d_ref, _ = oracle.cvt_iterate(cpu(band), cpu(q).view(np.uint16), cpu(sp)[:int(ns.item())], 7)
+    assert np.array_equal(runs[0][0][:int(ns.item())], s_ref) and np.array_equal(runs[0][1], c_ref)

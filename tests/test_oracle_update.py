@@ -149,6 +149,24 @@ def test_update_invariants_contorted(orc):
     assert moved == int((new != sp).sum()) and sumsq == int((d * d).sum())
 
 
+def test_selected_update_matches_full(orc):
+    # restricting the update to a subset of cells gives those cells' sites exactly the
+    # positions and sums of the full update (the replay used for full-size volumes)
+    rng = np.random.default_rng(9)
+    import scipy.ndimage as ndi
+    f = ndi.gaussian_filter(rng.standard_normal((14, 16, 18)), 1.5).astype(np.float32)
+    band = orc.classify(f, np.array([-0.05, 0.05], np.float32))
+    comp, cb, cs, cf = orc.label_components(band)
+    q = orc.saliency(f, 1)
+    sp, sc, off, nc = orc.seed(comp, q, len(cb), 40, 8, 5)
+    cell, dist = orc.assign(band, sp)
+    new, _, diag = orc.update(band, q, cell, dist, sp, diagnostics=True)
+    sel = rng.choice(len(sp), size=len(sp) // 3, replace=False)
+    got, sums = orc.update_selected(band, q, cell, dist, sp, sel)
+    assert np.array_equal(got, new[sel]) and np.array_equal(sums, diag["sums"][sel])
+    assert (new[sel] != sp[sel]).any()
+
+
 def test_convergence_shape_like_paper(orc):
     import workloads
     ref = {}
