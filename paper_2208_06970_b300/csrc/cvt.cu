@@ -654,7 +654,7 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
 // band present has U_b below that bound; the buffer is pruned as U_b falls.
 // Outputs of the geodesically weighted update (Eq. 2) filled while tessellating: integer
 // moment sums of line-of-sight voxels, the line-of-sight bit of every voxel, and the
-// "pending" bit of voxels whose update needs final neighbour keys (no line of sight, or
+// list of "pending" voxels whose update needs final neighbour keys (no line of sight, or
 // key not settled here).  enabled = false for the final tessellation.
 struct UpdateOut {
     bool enabled;
@@ -663,7 +663,8 @@ struct UpdateOut {
     const int32_t *site_pos;
     unsigned long long *sums;
     uint32_t *los_bits;
-    uint32_t *pending;
+    int32_t *plist;    // pending voxels, appended per brick
+    int32_t *n_plist;
 };
 
 constexpr int kCellGather = 4096;   // shared buffer while searching
@@ -828,7 +829,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
     __shared__ unsigned long long Ub[256];
     __shared__ uint32_t present[8];
     __shared__ short band_start[257];
-    __shared__ int ncand_s, unknown_s;
+    __shared__ int ncand_s, unknown_s, pcount_s, pbase_s;
     const int tid = threadIdx.x;
     const int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
     for (int64_t brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
@@ -841,7 +842,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         PHASE_T0();
         if (tid < 8) present[tid] = 0;
         for (int b = tid; b < 256; b += blockDim.x) Ub[b] = ~0ULL;
-        if (tid == 0) { unknown_s = 0; ncand_s = 0; }
+        if (tid == 0) { unknown_s = 0; ncand_s = 0; pcount_s = 0; }
         __syncthreads();
         uint8_t vb[kVPT];
 #pragma unroll
@@ -920,6 +921,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         __syncthreads();
         PHASE_ADD(1);
         int unknown = 0;
+        uint32_t pmask = 0;
 #pragma unroll
         for (int j = 0; j < kVPT; ++j) {
             int i = tid + kRelaxThreads * j;
@@ -978,6 +980,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
             } else if (inb) {
                 key[g] = k;
             }
+            if (pend) pmask |= 1u << j;
             if (up.enabled) {
                 {
                     // one atomic per distinct bit-array word in the warp
@@ -985,11 +988,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                     const unsigned bit = inb ? (1u << (g & 31)) : 0u;
                     unsigned mw = __match_any_sync(0xffffffffu, word);
                     unsigned lb = __reduce_or_sync(mw, los ? bit : 0u);
-                    unsigned pb = __reduce_or_sync(mw, pend ? bit : 0u);
-                    if (inb && (mw & lanemask_lt()) == 0) {
-                        if (lb) atomicOr(&up.los_bits[word], lb);
-                        if (pb) atomicOr(&up.pending[word], pb);
-                    }
+                    if (inb && (mw & lanemask_lt()) == 0 && lb) atomicOr(&up.los_bits[word], lb);
                 }
                 // warp-aggregated integer moment sums of the line-of-sight voxels (Eq. 2, phi(v) = v)
                 const int32_t sid = los ? bs.x : -1;
@@ -1015,6 +1014,34 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
             }
         }
         if (unknown) unknown_s = 1;
+        if (up.enabled) {
+            // append the brick's pending voxels: warp offsets in shared memory, one global
+            // atomic per brick (entry order varies between runs; every use is order-free)
+            const int lane = tid & 31;
+            unsigned bal[kVPT];
+            int wtot = 0;
+#pragma unroll
+            for (int j = 0; j < kVPT; ++j) {
+                bal[j] = __ballot_sync(0xffffffffu, (pmask >> j) & 1u);
+                wtot += __popc(bal[j]);
+            }
+            int wbase = 0;
+            if (lane == 0 && wtot) wbase = atomicAdd(&pcount_s, wtot);
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            __syncthreads();
+            if (tid == 0) pbase_s = pcount_s ? atomicAdd(up.n_plist, pcount_s) : 0;
+            __syncthreads();
+            int off = pbase_s + wbase;
+#pragma unroll
+            for (int j = 0; j < kVPT; ++j) {
+                if ((pmask >> j) & 1u) {
+                    int i = tid + kRelaxThreads * j;
+                    int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
+                    up.plist[off + __popc(bal[j] & lanemask_lt())] = (int32_t)(x + (int64_t)d.nx * (y + (int64_t)d.ny * z));
+                }
+                off += __popc(bal[j]);
+            }
+        }
         __syncthreads();
         PHASE_ADD(3);
         // the brick's own sites: distance 0, lowest id (also where the list was unusable)
@@ -1076,20 +1103,24 @@ __device__ int walk(const uint8_t *__restrict__ band, Dims d, int ax, int ay, in
 __global__ void __launch_bounds__(256) update_voxels_kernel(
     const uint8_t *__restrict__ band, const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
     const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
-    uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const uint32_t *__restrict__ pending,
-    bool small_coords) {
-    int64_t n = d.n();
-    int64_t nw = (n + 31) >> 5;
-    int lane = threadIdx.x & 31;
-    for (int64_t wv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wv < nw;
-         wv += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const uint32_t pw = pending[wv];
-        if (pw == 0) continue;  // warp-uniform: nothing left to do for these 32 voxels
-        int64_t v = wv * 32 + lane;
+    uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const int32_t *__restrict__ plist,
+    const int32_t *n_plist, bool small_coords) {
+    const int32_t cnt = *n_plist;
+    // whole warps step through the list together (the warp-level reductions below need them)
+    for (int32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < cnt; base += gridDim.x * blockDim.x) {
+        const int32_t i = base + (threadIdx.x & 31);
+#ifdef LSRVT_DEBUG
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&g_phase[2], 1ULL);
+            atomicAdd(&g_phase[4], (unsigned long long)min(32, cnt - base));
+        }
+#endif
+        const int64_t v = i < cnt ? __ldg(plist + i) : -1;
+        const int64_t wv = v >> 5;
         bool los = false;
         int32_t s = -1;
         int x = 0, y = 0, z = 0;
-        if (v < n && ((pw >> lane) & 1u)) {
+        if (v >= 0) {
             unsigned long long k = key[v];
             if (k != kInfKey) {
                 s = (int32_t)(uint32_t)k;
@@ -1109,6 +1140,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
                     los = los_clear(band, clr, d, x, y, z, px, py, pz, __ldg(clr + p));
 #ifdef LSRVT_DEBUG
                     atomicAdd(&g_phase[6], (unsigned long long)(clock64() - _u0));
+                    if (los) atomicAdd(&g_phase[9], 1ULL);
 #endif
                 }
                 if (!los) {
@@ -1140,8 +1172,13 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
                 }
             }
         }
-        unsigned bal = __ballot_sync(0xffffffffu, los);
-        if (lane == 0 && bal) atomicOr(&los_bits[wv], bal);
+        {
+            // one atomic per distinct bit-array word in the warp
+            const unsigned bit = v >= 0 ? (1u << (v & 31)) : 0u;
+            unsigned mw = __match_any_sync(0xffffffffu, wv);
+            unsigned lb = __reduce_or_sync(mw, los ? bit : 0u);
+            if (v >= 0 && (mw & lanemask_lt()) == 0 && lb) atomicOr(&los_bits[wv], lb);
+        }
         // warp-aggregated integer moment sums of the LOS voxels
         int32_t grp = los ? s : -1;
         unsigned m = __match_any_sync(0xffffffffu, grp);
@@ -1242,7 +1279,7 @@ struct CvtWs {
     int32_t *par;
     uint32_t *los_bits;
     int32_t *nonlos;
-    int32_t *counters;  // [0] n_nonlos, [1..2] queue counts, [3..4] work counters
+    int32_t *counters;  // [0] n_nonlos, [1..2] queue counts, [3..4] work counters, [5] n_plist
     unsigned long long *sums;
     uint32_t *flags;
     int32_t *list[2];
@@ -1255,7 +1292,7 @@ struct CvtWs {
     uint32_t *cell_bands;
     int4 *cell_list;
     int32_t *cell_count;
-    uint32_t *pending;
+    int32_t *plist;
     GridBarrier *bar;
     void *scan;
 };
@@ -1290,7 +1327,7 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.cell_bands = c.take<uint32_t>(ncoarse * 8);
     w.cell_list = c.take<int4>(ncoarse * kCellList);
     w.cell_count = c.take<int32_t>(ncoarse);
-    w.pending = c.take<uint32_t>((n + 31) / 32);
+    w.plist = c.take<int32_t>(n);
     w.bar = c.take<GridBarrier>(1);
     w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
     *need = c.used;
@@ -1422,18 +1459,18 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     }
     uint32_t tag = 0;
     int vgrid = grid_for((n + 31) / 32 * 32, 256, kSMs * 16);
-    UpdateOut up{true, small, q, site_pos, w.sums, w.los_bits, w.pending};
-    UpdateOut no_up{false, small, q, site_pos, nullptr, nullptr, nullptr};
+    UpdateOut up{true, small, q, site_pos, w.sums, w.los_bits, w.plist, w.counters + 5};
+    UpdateOut no_up{false, small, q, site_pos, nullptr, nullptr, nullptr, nullptr};
     const int64_t nwords = (n + 31) / 32;
     for (int32_t it = 0; it < n_iters; ++it) {
         cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
         cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
-        cudaMemsetAsync(w.pending, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
+        cudaMemsetAsync(w.counters + 5, 0, sizeof(int32_t), s);
         lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, up);
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
-                                                   w.nonlos, w.counters, w.pending, small);
+                                                   w.nonlos, w.counters, w.plist, w.counters + 5, small);
         update_nonlos_kernel<<<kSMs * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
@@ -1447,10 +1484,10 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     {
         unsigned long long ph[12];
         cudaMemcpyFromSymbol(ph, g_phase, sizeof(ph));
-        fprintf(stderr, "cand total %llu stage-visits %llu chamfer-evals %llu unsettled-voxel-stages %llu\n", ph[8], ph[9],
-                ph[10], ph[11]);
-        fprintf(stderr, "phases: gather %.3g sort %.3g voxels %.3g path %.3g stages %llu | los-cycles %.3g nonlos %llu\n",
-                (double)ph[0], (double)ph[1], (double)ph[2], (double)ph[3], ph[5], (double)ph[6], ph[7]);
+        fprintf(stderr, "cfi chamfer-evals %llu | update: pending warps %llu pending voxels %llu los-walks true %llu "
+                "nonlos %llu los-cycles %.3g\n", ph[10], ph[2], ph[4], ph[9], ph[7], (double)ph[6]);
+        fprintf(stderr, "cfi phases (cycles, thread 0 of each CTA): gather %.3g sort %.3g path %.3g\n",
+                (double)ph[0], (double)ph[1], (double)ph[3]);
         unsigned long long z[12] = {0};
         cudaMemcpyToSymbol(g_phase, z, sizeof(z));
     }
