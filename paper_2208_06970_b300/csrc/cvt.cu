@@ -384,6 +384,33 @@ __global__ void clear_count_kernel(const uint32_t *__restrict__ planes, Dims d, 
     }
 }
 
+// Edge masks (once per call, like the clearance): bit o of emask[v] is set when the
+// 26-neighbour move v -> v + offset(o) is an edge, i.e. every voxel of the box it spans
+// is in v's band (o = (dz+1) 9 + (dy+1) 3 + (dx+1)).  Path checks then test one word per
+// move instead of up to seven band bytes.
+__global__ void edge_mask_kernel(const uint8_t *__restrict__ band, Dims d, uint32_t *__restrict__ emask) {
+    int64_t n = d.n();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % d.nx);
+        const int64_t r = v / d.nx;
+        const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+        const uint8_t b = band[v];
+        uint32_t e = 0;
+        if (b != kInvalidBand) {
+            uint32_t S = 0;
+#pragma unroll
+            for (int o = 0; o < 27; ++o) {
+                const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                const int ux = x + dx, uy = y + dy, uz = z + dz;
+                if (ux < 0 || ux >= d.nx || uy < 0 || uy >= d.ny || uz < 0 || uz >= d.nz) continue;
+                S |= (uint32_t)(__ldg(band + v + dx + (int64_t)d.nx * (dy + (int64_t)d.ny * dz)) == b) << o;
+            }
+            e = edges_from_same(S);
+        }
+        emask[v] = e;
+    }
+}
+
 // ---------------------------------------------------------------- closed-form initialisation
 // Lower bound: the unconstrained 26-neighbour chamfer distance C(v, s) = (a-b) W1 +
 // (b-c) W2 + c W3 (a >= b >= c the sorted |v - s|) never exceeds the restricted geodesic
@@ -432,8 +459,13 @@ __device__ __forceinline__ unsigned long long udiv(unsigned long long a, unsigne
 // the walk ended at most c(s) - 2 from s.  The 6-connected traversal of the segment v-s
 // stays within L-infinity 2 of the digital path (per axis the rounding errors of the path
 // and of the segment's voxel add up to at most 2), so margin 2 also certifies line of sight.
-__device__ int chamfer_path_in_band(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d,
-                                    int vx, int vy, int vz, int sx, int sy, int sz, uint8_t b, int cs) {
+#ifdef LSRVT_DEBUG
+__device__ unsigned long long g_path_dbg[8];  // checks cov=0, cov>0, steps, jumps, status 0/1/2
+#endif
+// mv_start > 0: the moves before it are already known to be in band with a margin of 2
+// (a brick tube certificate covered them); the walk starts there.
+__device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const uint8_t *__restrict__ clr, Dims d,
+                                    int vx, int vy, int vz, int sx, int sy, int sz, int cs, int mv_start) {
     const int D0 = sx - vx, D1 = sy - vy, D2 = sz - vz;
     const int A0 = abs(D0), A1 = abs(D1), A2 = abs(D2);
     // axes sorted by extent: i >= j >= k
@@ -449,12 +481,31 @@ __device__ int chamfer_path_in_band(const uint8_t *__restrict__ band, const uint
     const int64_t stride[3] = {1, d.nx, sxy};
     const int sgn[3] = {D0 < 0 ? -1 : 1, D1 < 0 ? -1 : 1, D2 < 0 ? -1 : 1};
     const int64_t si = stride[i] * sgn[i], sj = stride[j] * sgn[j], sk = stride[k] * sgn[k];
+    const int ow[3] = {1, 3, 9};
+    const int oi = 13 + ow[i] * sgn[i], oj = ow[j] * sgn[j], ok = ow[k] * sgn[k];  // edge-mask bit offsets
     const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
     const unsigned long long ai2 = 2ULL * Ai, aj2 = 2ULL * Aj;
     int mv = 0, jc = 0, kc = 0;
     // error terms: ej = 2 mv aj + ai - 2 ai jc in [0, 2ai); ek = 2 jc ak + aj - 2 aj kc in [0, 2aj)
     long long ej = Ai, ek = Aj;
     int64_t g = v0;
+#ifdef LSRVT_DEBUG
+#define PATH_DBG(i) atomicAdd(&g_path_dbg[i], 1ULL)
+#else
+#define PATH_DBG(i)
+#endif
+    if (mv_start > 0) {
+        mv = mv_start < Ai ? mv_start : Ai;
+        unsigned long long nj = 2ULL * mv * Aj + Ai;
+        jc = (int)udiv(nj, ai2);
+        ej = (long long)(nj - ai2 * jc);
+        if (Aj) {
+            unsigned long long nk = 2ULL * jc * Ak + Aj;
+            kc = (int)udiv(nk, aj2);
+            ek = (long long)(nk - aj2 * kc);
+        }
+        g = v0 + si * mv + sj * jc + sk * kc;
+    }
     while (mv < Ai) {
         // the rest of the path approaches s monotonically on every axis, so once within the
         // site's own clearance ball it stays in band
@@ -476,8 +527,10 @@ __device__ int chamfer_path_in_band(const uint8_t *__restrict__ band, const uint
             }
             mv = mv2;
             g = v0 + si * mv + sj * jc + sk * kc;
+            PATH_DBG(3);
             continue;
         }
+        PATH_DBG(2);
         margin = false;
         ej += 2LL * Aj;
         bool mj = ej >= (long long)ai2;
@@ -488,23 +541,55 @@ __device__ int chamfer_path_in_band(const uint8_t *__restrict__ band, const uint
             mk = ek >= (long long)aj2;
             if (mk) ek -= (long long)aj2;
         }
-        // box of the move g -> g + mi + (mj) + (mk), without g itself
-        const int64_t ci = si, cj = mj ? sj : 0, ck = mk ? sk : 0;
-        if (__ldg(band + g + ci) != b) return 0;
-        if (mj) {
-            if (__ldg(band + g + cj) != b || __ldg(band + g + ci + cj) != b) return 0;
-        }
-        if (mk) {
-            if (__ldg(band + g + ck) != b || __ldg(band + g + ci + ck) != b || __ldg(band + g + cj + ck) != b ||
-                __ldg(band + g + ci + cj + ck) != b)
-                return 0;
-        }
-        g += ci + cj + ck;
+        // the move g -> g + mi + (mj) + (mk) must be an edge (its box in band)
+        const int o = oi + (mj ? oj : 0) + (mk ? ok : 0);
+        if (!((__ldg(emask + g) >> o) & 1u)) return 0;
+        g += si + (mj ? sj : 0) + (mk ? sk : 0);
         ++mv;
         jc += mj;
         kc += mk;
     }
     return margin ? 2 : 1;
+}
+
+// Certificate for a whole brick at once.  Let C be the centre of the box [l, h], R its
+// largest half extent and P(t) = C + t (s - C).  For a voxel v of the box the point
+// v + t (s - v) is within L-infinity (1 - t) R of P(t); the move boxes of v's chamfer path
+// (above) and the voxels of v's 6-connected traversal to s lie within L-infinity 2 of the
+// points of v's segment.  So if every voxel within (1 - t) R + 2 of P(t), 0 <= t <= 1, is in
+// band, every voxel of the box whose winner is s has an exact key and line of sight.  The
+// tube is covered by clearance balls: at u = round(P(t_k)) with clearance c, the ball of
+// radius c holds the tube over [t_k, t_k + dt] when rho(t_k) + 1/2 + dt |s - C| <= c (rho
+// only shrinks along t).  Consecutive balls share a voxel, and the first holds the box's
+// voxels of band b, so all of them lie in band b.  Exact integer arithmetic in doubled
+// coordinates: k counts half voxels along the dominant axis of s - C (length L2).
+// Returns the covered extent: the tube is certified for t <= k / L2 (k >= L2: all of it).
+__device__ int brick_tube_in_band(const uint8_t *__restrict__ clr, Dims d, int lx, int ly, int lz, int hx, int hy,
+                                  int hz, int sx, int sy, int sz) {
+    const int cx2 = lx + hx, cy2 = ly + hy, cz2 = lz + hz;  // doubled centre
+    const int dx2 = 2 * sx - cx2, dy2 = 2 * sy - cy2, dz2 = 2 * sz - cz2;
+    const int L2 = max(abs(dx2), max(abs(dy2), abs(dz2)));
+    const int R2 = max(hx - lx, max(hy - ly, hz - lz));  // doubled largest half extent
+    if (L2 == 0) {
+        int c = __ldg(clr + (cx2 >> 1) + (int64_t)d.nx * ((cy2 >> 1) + (int64_t)d.ny * (cz2 >> 1)));
+        return 2 * c - 1 - (R2 + 4) >= 1 ? 1 : 0;
+    }
+    const unsigned den = 2u * (unsigned)L2;
+    int k = 0;
+    for (int guard = 0; guard < 4 * 4096; ++guard) {
+        // round half up of the doubled coordinates (c2 L2 + d2 k) / L2, halved; all >= 0
+        const int ux = (int)((unsigned)(cx2 * L2 + dx2 * k + L2) / den);
+        const int uy = (int)((unsigned)(cy2 * L2 + dy2 * k + L2) / den);
+        const int uz = (int)((unsigned)(cz2 * L2 + dz2 * k + L2) / den);
+        const int c = __ldg(clr + ux + (int64_t)d.nx * (uy + (int64_t)d.ny * uz));
+        // 2 rho(k), rounded up: R2 (L2 - k) / L2 + 4
+        const int two_rho = (int)(((unsigned)R2 * (unsigned)(L2 - k) + (unsigned)L2 - 1u) / (unsigned)L2) + 4;
+        const int delta = 2 * c - 1 - two_rho;
+        if (delta < 1) return k;
+        if (k + delta >= L2) return L2;
+        k += delta;
+    }
+    return k;
 }
 
 // site bins: one pass counts, a scan gives offsets, a second pass fills entries
@@ -817,7 +902,8 @@ __global__ void __launch_bounds__(kCellThreads) cell_list_kernel(Dims d, CoarseG
 // best (triangle inequality; R = the brick's chamfer radius).  Keys are exact where one
 // shortest chamfer path to the winner stays in band; elsewhere +inf and the brick is queued.
 __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__restrict__ band,
-                                                            const uint8_t *__restrict__ clr, Dims d, BrickGeom bg,
+                                                            const uint8_t *__restrict__ clr,
+                                                            const uint32_t *__restrict__ emask, Dims d, BrickGeom bg,
                                                             CoarseGeom cg, const int4 *__restrict__ cell_list,
                                                             const int32_t *__restrict__ cell_count,
                                                             const int64_t *__restrict__ fine_off,
@@ -830,6 +916,10 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
     __shared__ uint32_t present[8];
     __shared__ short band_start[257];
     __shared__ int ncand_s, unknown_s, pcount_s, pbase_s;
+    __shared__ unsigned long long vbest[RV];  // per voxel: best chamfer key
+    __shared__ short vwin[RV];                // per voxel: index of the winner in cs (-1 none)
+    __shared__ uint8_t wcert[kMaxCand];       // per candidate: 1 = wins a voxel, 2 = brick certificate holds
+    __shared__ int wcov[kMaxCand];            // per candidate: tube extent certified (half voxels)
     const int tid = threadIdx.x;
     const int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
     for (int64_t brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
@@ -842,6 +932,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         PHASE_T0();
         if (tid < 8) present[tid] = 0;
         for (int b = tid; b < 256; b += blockDim.x) Ub[b] = ~0ULL;
+        for (int c2 = tid; c2 < kMaxCand / 4; c2 += blockDim.x) reinterpret_cast<uint32_t *>(wcert)[c2] = 0u;
         if (tid == 0) { unknown_s = 0; ncand_s = 0; pcount_s = 0; }
         __syncthreads();
         uint8_t vb[kVPT];
@@ -920,16 +1011,14 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
         }
         __syncthreads();
         PHASE_ADD(1);
-        int unknown = 0;
-        uint32_t pmask = 0;
+        // (1) per voxel: the smallest chamfer key over the candidates of its band
 #pragma unroll
         for (int j = 0; j < kVPT; ++j) {
             int i = tid + kRelaxThreads * j;
             int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
             const bool inb = x < d.nx && y < d.ny && z < d.nz;
-            const int64_t g = inb ? x + (int64_t)d.nx * (y + (int64_t)d.ny * z) : 0;
             unsigned long long best = kInfKey;
-            int4 bs = make_int4(0, 0, 0, 0);
+            int bidx = -1;
             if (inb && vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL) {
                 const int t0 = band_start[vb[j]], t1 = band_start[vb[j] + 1];
                 for (int t = t0; t < t1; ++t) {
@@ -942,7 +1031,7 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                     unsigned long long cd = chamfer(c.y - x, c.z - y, (c.w & 0xFFFFFF) - z);
                     if (cd >= kInf32) continue;
                     unsigned long long k2 = (cd << 32) | (unsigned)c.x;
-                    if (k2 < best) { best = k2; bs = c; }
+                    if (k2 < best) { best = k2; bidx = (int)(e & 0xFFF); }
                 }
             }
             if (!complete && best != kInfKey) {
@@ -955,6 +1044,34 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                 if (fhz < d.nz - 1) gap = min(gap, (long long)(fhz - z + 1));
                 if ((best >> 32) >= (unsigned long long)gap * kWFace) best = kInfKey;  // not settled
             }
+            if (best == kInfKey) bidx = -1;
+            vbest[i] = best;
+            vwin[i] = (short)bidx;
+            if (bidx >= 0) wcert[bidx] = 1;
+        }
+        __syncthreads();
+        // (2) one tube certificate per (brick, winning site)
+        for (int c2 = tid; c2 < nc && ok_list; c2 += blockDim.x) {
+            if (wcert[c2] != 1) continue;
+            const int4 c = cs[c2];
+            const int cov = brick_tube_in_band(clr, d, lx, ly, lz, hx, hy, hz, c.y, c.z, c.w & 0xFFFFFF);
+            const int L2 = max(abs(2 * c.y - lx - hx), max(abs(2 * c.z - ly - hy), abs(2 * (c.w & 0xFFFFFF) - lz - hz)));
+            wcov[c2] = cov;
+            if (cov >= L2) wcert[c2] = 2;
+        }
+        __syncthreads();
+        // (3) per voxel: certificate, else its own path check; keys, update outputs
+        int unknown = 0;
+        uint32_t pmask = 0;
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j) {
+            int i = tid + kRelaxThreads * j;
+            int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
+            const bool inb = x < d.nx && y < d.ny && z < d.nz;
+            const int64_t g = inb ? x + (int64_t)d.nx * (y + (int64_t)d.ny * z) : 0;
+            const unsigned long long best = vbest[i];
+            const int bidx = vwin[i];
+            const int4 bs = bidx >= 0 ? cs[bidx] : make_int4(0, 0, 0, 0);
             unsigned long long k = kInfKey;
             bool los = false, pend = false;
             if (inb && vb[j] != kInvalidBand) {
@@ -962,8 +1079,31 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
                 int cs_site = 0;
                 const int bsz = bs.w & 0xFFFFFF;
                 if (best != kInfKey) {
-                    cs_site = __ldg(clr + bs.y + (int64_t)d.nx * (bs.z + (int64_t)d.ny * bsz));
-                    status = chamfer_path_in_band(band, clr, d, x, y, z, bs.y, bs.z, bsz, vb[j], cs_site);
+                    if (wcert[bidx] == 2) {
+                        status = 2;
+#ifdef LSRVT_DEBUG
+                        atomicAdd(&g_phase[5], 1ULL);
+#endif
+                    } else {
+#ifdef LSRVT_DEBUG
+                        atomicAdd(&g_phase[8], 1ULL);
+#endif
+                        cs_site = __ldg(clr + bs.y + (int64_t)d.nx * (bs.z + (int64_t)d.ny * bsz));
+                        // skip the moves the brick's tube already covers: t <= cov / L2
+                        int mv0 = 0;
+                        const int cov = wcov[bidx];
+                        if (cov > 0) {
+                            const int L2 = max(abs(2 * bs.y - lx - hx),
+                                               max(abs(2 * bs.z - ly - hy), abs(2 * bsz - lz - hz)));
+                            const int Av = max(abs(bs.y - x), max(abs(bs.z - y), abs(bsz - z)));
+                            mv0 = (int)(((long long)cov * Av) / L2);
+                        }
+                        status = chamfer_path_in_band(emask, clr, d, x, y, z, bs.y, bs.z, bsz, cs_site, mv0);
+#ifdef LSRVT_DEBUG
+                        atomicAdd(&g_path_dbg[mv0 > 0 ? 1 : 0], 1ULL);
+                        atomicAdd(&g_path_dbg[4 + status], 1ULL);
+#endif
+                    }
                 }
                 if (status) {
                     k = best;
@@ -1288,6 +1428,7 @@ struct CvtWs {
     int4 *fine_cand, *coarse_cand;
     int64_t *bin_total;
     uint8_t *clr;
+    uint32_t *emask;
     uint32_t *planes;
     uint32_t *cell_bands;
     int4 *cell_list;
@@ -1322,6 +1463,7 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.coarse_cand = c.take<int4>((int64_t)max_sites + 1);
     w.bin_total = c.take<int64_t>(2);
     w.clr = c.take<uint8_t>(n);
+    w.emask = c.take<uint32_t>(n);
     BitGeom bgm{(d.nx + 31) / 32};
     w.planes = c.take<uint32_t>(bgm.words(d) * kClearLevels);
     w.cell_bands = c.take<uint32_t>(ncoarse * 8);
@@ -1384,7 +1526,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cfi, cfi_kernel, kRelaxThreads, 0);
     if (nb_cfi < 1) nb_cfi = 1;
     int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
-    cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
+    cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
                                                w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, tag, up);
 #ifdef LSRVT_DEBUG
     {
@@ -1452,6 +1594,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
             clear_erode_kernel<<<grid_for(nw, 256, kSMs * 16), 256, 0, s>>>(w.planes + (int64_t)(k - 1) * nw, d, bgm,
                                                                           w.planes + (int64_t)k * nw);
         clear_count_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.planes, d, bgm, kClearLevels, w.clr);
+        edge_mask_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.emask);
         CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
         int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
         cell_bands_kernel<<<(int)(ncoarse < kSMs * 8 ? ncoarse : kSMs * 8), kCellThreads, 0, s>>>(band, d, cg,
@@ -1484,6 +1627,12 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     {
         unsigned long long ph[12];
         cudaMemcpyFromSymbol(ph, g_phase, sizeof(ph));
+        fprintf(stderr, "cfi tube-certified voxels %llu own path checks %llu\n", ph[5], ph[8]);
+        unsigned long long pd[8], pz[8] = {0};
+        cudaMemcpyFromSymbol(pd, g_path_dbg, sizeof(pd));
+        cudaMemcpyToSymbol(g_path_dbg, pz, sizeof(pz));
+        fprintf(stderr, "path checks: from start %llu after tube prefix %llu | steps %llu jumps %llu | status0 %llu "
+                "status1 %llu status2 %llu\n", pd[0], pd[1], pd[2], pd[3], pd[4], pd[5], pd[6]);
         fprintf(stderr, "cfi chamfer-evals %llu | update: pending warps %llu pending voxels %llu los-walks true %llu "
                 "nonlos %llu los-cycles %.3g\n", ph[10], ph[2], ph[4], ph[9], ph[7], (double)ph[6]);
         fprintf(stderr, "cfi phases (cycles, thread 0 of each CTA): gather %.3g sort %.3g path %.3g\n",
