@@ -424,8 +424,6 @@ __global__ void edge_mask_kernel(const uint8_t *__restrict__ band, Dims d, uint3
 // >= gap(v) W1, so a voxel is settled once its best is below that.  Voxels not settled,
 // or whose path check fails, start at +inf and their bricks are relaxed.
 constexpr int kMaxCand = 1024;
-// largest chamfer distance from the brick centre (RX/2, RY/2, RZ/2) to a brick voxel: (8, 4, 4)
-constexpr unsigned long long kBrickChamferRadius = (RX / 2 - RY / 2) * 65536ull + (RY / 2) * 113512ull;
 constexpr int kCoarse = 32, kCoarseShift = 5;
 constexpr int kMaxRho = 12;
 
@@ -901,7 +899,7 @@ __global__ void __launch_bounds__(kCellThreads) cell_list_kernel(Dims d, CoarseG
 // centre), and every voxel scans its band's segment until C(centre, s) - R exceeds its
 // best (triangle inequality; R = the brick's chamfer radius).  Keys are exact where one
 // shortest chamfer path to the winner stays in band; elsewhere +inf and the brick is queued.
-__global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__restrict__ band,
+__global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__restrict__ band,
                                                             const uint8_t *__restrict__ clr,
                                                             const uint32_t *__restrict__ emask, Dims d, BrickGeom bg,
                                                             CoarseGeom cg, const int4 *__restrict__ cell_list,
@@ -1021,9 +1019,12 @@ __global__ void __launch_bounds__(kRelaxThreads) cfi_kernel(const uint8_t *__res
             int bidx = -1;
             if (inb && vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL) {
                 const int t0 = band_start[vb[j]], t1 = band_start[vb[j] + 1];
+                // triangle inequality of the chamfer metric: C(v, s) >= C(c, s) - C(c, v) for the
+                // sort centre c, so the scan ends once C(c, s) - C(c, v) exceeds the best
+                const unsigned long long cv = chamfer(x - (ox + RX / 2), y - (oy + RY / 2), z - (oz + RZ / 2));
                 for (int t = t0; t < t1; ++t) {
                     unsigned long long e = ck[t];
-                    if (((e >> 12) & ((1ULL << 36) - 1)) > (best >> 32) + kBrickChamferRadius) break;
+                    if (((e >> 12) & ((1ULL << 36) - 1)) > (best >> 32) + cv) break;
                     int4 c = cs[(unsigned)(e & 0xFFF)];
 #ifdef LSRVT_DEBUG
                     atomicAdd(&g_phase[10], 1ULL);
