@@ -487,11 +487,6 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
     // error terms: ej = 2 mv aj + ai - 2 ai jc in [0, 2ai); ek = 2 jc ak + aj - 2 aj kc in [0, 2aj)
     long long ej = Ai, ek = Aj;
     int64_t g = v0;
-#ifdef LSRVT_DEBUG
-#define PATH_DBG(i) atomicAdd(&g_path_dbg[i], 1ULL)
-#else
-#define PATH_DBG(i)
-#endif
     if (mv_start > 0) {
         mv = mv_start < Ai ? mv_start : Ai;
         unsigned long long nj = 2ULL * mv * Aj + Ai;
@@ -525,10 +520,10 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
             }
             mv = mv2;
             g = v0 + si * mv + sj * jc + sk * kc;
-            PATH_DBG(3);
+
             continue;
         }
-        PATH_DBG(2);
+
         margin = false;
         ej += 2LL * Aj;
         bool mj = ej >= (long long)ai2;
@@ -636,8 +631,9 @@ __global__ void site_bin_fill_kernel(const int32_t *__restrict__ site_pos, const
 
 #ifdef LSRVT_DEBUG
 __device__ unsigned long long g_phase[12];
+__device__ unsigned long long g_cfi_ph[8];  // cfi phase cycles (thread 0 of each CTA)
 #define PHASE_T0() long long _t0 = clock64()
-#define PHASE_ADD(i) do { if (threadIdx.x == 0) atomicAdd(&g_phase[i], (unsigned long long)(clock64() - _t0)); _t0 = clock64(); } while (0)
+#define PHASE_ADD(i) do { if (threadIdx.x == 0) atomicAdd(&g_cfi_ph[i], (unsigned long long)(clock64() - _t0)); _t0 = clock64(); } while (0)
 #else
 #define PHASE_T0()
 #define PHASE_ADD(i)
@@ -1026,9 +1022,6 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                     unsigned long long e = ck[t];
                     if (((e >> 12) & ((1ULL << 36) - 1)) > (best >> 32) + cv) break;
                     int4 c = cs[(unsigned)(e & 0xFFF)];
-#ifdef LSRVT_DEBUG
-                    atomicAdd(&g_phase[10], 1ULL);
-#endif
                     unsigned long long cd = chamfer(c.y - x, c.z - y, (c.w & 0xFFFFFF) - z);
                     if (cd >= kInf32) continue;
                     unsigned long long k2 = (cd << 32) | (unsigned)c.x;
@@ -1051,6 +1044,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             if (bidx >= 0) wcert[bidx] = 1;
         }
         __syncthreads();
+        PHASE_ADD(2);
         // (2) one tube certificate per (brick, winning site)
         for (int c2 = tid; c2 < nc && ok_list; c2 += blockDim.x) {
             if (wcert[c2] != 1) continue;
@@ -1061,6 +1055,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             if (cov >= L2) wcert[c2] = 2;
         }
         __syncthreads();
+        PHASE_ADD(4);
         // (3) per voxel: certificate, else its own path check; keys, update outputs
         int unknown = 0;
         uint32_t pmask = 0;
@@ -1155,6 +1150,10 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             }
         }
         if (unknown) unknown_s = 1;
+#ifdef LSRVT_DEBUG
+        __syncthreads();
+        PHASE_ADD(3);
+#endif
         if (up.enabled) {
             // append the brick's pending voxels: warp offsets in shared memory, one global
             // atomic per brick (entry order varies between runs; every use is order-free)
@@ -1184,7 +1183,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             }
         }
         __syncthreads();
-        PHASE_ADD(3);
+        PHASE_ADD(5);
         // the brick's own sites: distance 0, lowest id (also where the list was unusable)
         for (int64_t r = fine_off[brick] + tid; r < fine_off[brick + 1]; r += blockDim.x) {
             int4 c = fine_cand[r];
@@ -1636,8 +1635,12 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
                 "status1 %llu status2 %llu\n", pd[0], pd[1], pd[2], pd[3], pd[4], pd[5], pd[6]);
         fprintf(stderr, "cfi chamfer-evals %llu | update: pending warps %llu pending voxels %llu los-walks true %llu "
                 "nonlos %llu los-cycles %.3g\n", ph[10], ph[2], ph[4], ph[9], ph[7], (double)ph[6]);
-        fprintf(stderr, "cfi phases (cycles, thread 0 of each CTA): gather %.3g sort %.3g path %.3g\n",
-                (double)ph[0], (double)ph[1], (double)ph[3]);
+        unsigned long long cp[8], cz[8] = {0};
+        cudaMemcpyFromSymbol(cp, g_cfi_ph, sizeof(cp));
+        cudaMemcpyToSymbol(g_cfi_ph, cz, sizeof(cz));
+        fprintf(stderr, "cfi phases (cycles, thread 0 of each CTA): gather %.3g sort %.3g scan %.3g tube %.3g "
+                "paths+outputs %.3g compaction %.3g\n", (double)cp[0], (double)cp[1], (double)cp[2], (double)cp[4],
+                (double)cp[3], (double)cp[5]);
         unsigned long long z[12] = {0};
         cudaMemcpyToSymbol(g_phase, z, sizeof(z));
     }
