@@ -43,7 +43,7 @@ ALG_BYTES_PER_VOXEL_ITER = 11
 # DRAM bytes one Lloyd iteration moves per voxel, summed over its kernels, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 256^3 flame case and scaled by the
 # voxel count (the traffic grows in proportion to it)
-NCU_BYTES_PER_VOXEL_ITER = 47.3
+NCU_BYTES_PER_VOXEL_ITER = 41.2
 
 
 def peaks():
@@ -445,11 +445,12 @@ def main():
                                  "%d aux vars, %d bins" % (args.side, N_ITERS, N_AUX, N_BINS),
                         voxels=n, sites=r["n_sites"], components=r["n_comp"], parallelism="replicas" if world > 1
                         else "single", l2="inputs larger than L2 (field 512 MiB + aux 8 GiB), no flush"),
-            roofline=dict(kernel="one Lloyd iteration: cfi_kernel + relax_round_kernel rounds + "
+            roofline=dict(kernel="one Lloyd iteration: site bins + cell lists + cfi_kernel + relax_persistent_kernel + "
                                  "update_voxels_kernel + update_nonlos_kernel + move_sites_kernel",
                           bound="hbm", achieved=r["achieved"], peak=pk["hbm"], unit="GB/s",
                           frac=r["achieved"] / pk["hbm"],
-                          traffic=NCU_BYTES_PER_VOXEL_ITER * n if args.side in (256, 512) else None,
+                          traffic=(NCU_BYTES_PER_VOXEL_ITER * n if NCU_BYTES_PER_VOXEL_ITER and args.side in (256, 512)
+                                   else None),
                           traffic_note="ncu DRAM bytes per iteration, 256^3 capture scaled by voxels",
                           peak_source=pk["src"],
                           algorithmic_bytes_per_voxel=ALG_BYTES_PER_VOXEL_ITER, ms_per_launch=r["t_iter"],
