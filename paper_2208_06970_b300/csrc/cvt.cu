@@ -85,7 +85,7 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
     // distance of one update with the site of another
     __shared__ unsigned long long sk[HV];
     __shared__ uint8_t sb[HV];
-    __shared__ uint32_t changed[kRows];
+    __shared__ uint32_t changed[2][kRows];  // double buffered: written in one step, cleared in the next
     __shared__ uint32_t dirty[kRows];
     __shared__ uint32_t touch;
     __shared__ int item;
@@ -114,7 +114,8 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
             sk[i] = k;
         }
         if (tid < kRows) {
-            changed[tid] = 0;
+            changed[0][tid] = 0;
+            changed[1][tid] = 0;
             dirty[tid] = 0xFFFFu;
         }
         if (tid == 0) touch = 0;
@@ -141,7 +142,7 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
         __syncthreads();
         // ---- relaxation steps
         int step = 0;
-        for (; step < kMaxSteps; ++step) {
+        for (int cur = 0; step < kMaxSteps; ++step, cur ^= 1) {
             int any = 0;
 #pragma unroll
             for (int j = 0; j < kVPT; ++j) {
@@ -157,22 +158,19 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
                 for (int o = 0; o < 27; ++o) {
                     if (o == 13) continue;
                     if (!((e >> o) & 1u)) continue;
-                    int u = h + halo_off(o);
-                    unsigned long long ku = sk[u];
-                    uint32_t du = (uint32_t)(ku >> 32);
-                    if (du == kInf32) continue;
-                    unsigned long long cd = (unsigned long long)du + weight_of(o);
-                    if (cd >= kInf32) {
-                        set_status(status, LSRVT_ERR_OVERFLOW);
+                    // packed keys: (d, s) + (w << 32) = (d + w, s) unless d + w reaches 2^32 - 1
+                    const unsigned long long lim = (unsigned long long)(kInf32 - weight_of(o)) << 32;
+                    const unsigned long long ku = sk[h + halo_off(o)];
+                    if (ku >= lim) {
+                        if ((uint32_t)(ku >> 32) != kInf32) set_status(status, LSRVT_ERR_OVERFLOW);
                         continue;
                     }
-                    if ((cd << 32) > best) continue;  // distance alone already worse
-                    unsigned long long cand = (cd << 32) | (ku & 0xFFFFFFFFull);
-                    if (cand < best) best = cand;
+                    const unsigned long long cand = ku + ((unsigned long long)weight_of(o) << 32);
+                    best = cand < best ? cand : best;
                 }
                 if (best < own) {
                     sk[h] = best;
-                    atomicOr(&changed[row], 1u << lx);
+                    atomicOr(&changed[cur][row], 1u << lx);
                     any = 1;
                 }
             }
@@ -184,13 +182,12 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
                     for (int dy = -1; dy <= 1; ++dy) {
                         int y2 = ly + dy, z2 = lz + dz;
                         if (y2 < 0 || y2 >= RY || z2 < 0 || z2 >= RZ) continue;
-                        uint32_t c = changed[y2 + RY * z2];
+                        uint32_t c = changed[cur][y2 + RY * z2];
                         m |= c | (c << 1) | (c >> 1);
                     }
                 dirty[tid] = m & 0xFFFFu;
+                changed[cur ^ 1][tid] = 0;  // last read before the previous barrier
             }
-            __syncthreads();
-            if (tid < kRows) changed[tid] = 0;
             __syncthreads();
         }
         // ---- write back and collect the neighbour bricks to requeue
