@@ -77,14 +77,13 @@ __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
 }
 
 // One relaxation round: the CTAs of the grid take the queued bricks one at a time.
-__device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
+__device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, Dims d, BrickGeom bg,
                                             unsigned long long *key, const int32_t *list_in, const int nin,
                                             int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag,
                                             int32_t *work, int32_t *status) {
     // packed keys: one aligned 64-bit access per read/write, so a reader never pairs the
     // distance of one update with the site of another
     __shared__ unsigned long long sk[HV];
-    __shared__ uint8_t sb[HV];
     __shared__ uint32_t changed[2][kRows];  // double buffered: written in one step, cleared in the next
     __shared__ uint32_t dirty[kRows];
     __shared__ uint32_t touch;
@@ -103,14 +102,9 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
         for (int i = tid; i < HV; i += kRelaxThreads) {
             int hx = i % HX, hy = (i / HX) % HY, hz = i / (HX * HY);
             int gx = ox + hx - 1, gy = oy + hy - 1, gz = oz + hz - 1;
-            uint8_t b = kInvalidBand;
             unsigned long long k = kInfKey;
-            if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 && gz < d.nz) {
-                int64_t g = gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz);
-                b = band[g];
-                k = __ldcg(key + g);
-            }
-            sb[i] = b;
+            if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 && gz < d.nz)
+                k = __ldcg(key + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz));
             sk[i] = k;
         }
         if (tid < kRows) {
@@ -120,26 +114,25 @@ __device__ __forceinline__ void relax_items(const uint8_t *__restrict__ band, Di
         }
         if (tid == 0) touch = 0;
         __syncthreads();
-        // ---- edge masks and original keys
+        // ---- edge masks (precomputed per call) and original keys
         unsigned long long orig[kVPT];
         uint32_t em[kVPT];
 #pragma unroll
         for (int j = 0; j < kVPT; ++j) {
             int i = tid + kRelaxThreads * j;
             int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
-            int h = (lx + 1) + HX * ((ly + 1) + HY * (lz + 1));
-            uint8_t b = sb[h];
-            uint32_t e = 0;
-            if (b != kInvalidBand) {
-                uint32_t S = 0;
-#pragma unroll
-                for (int o = 0; o < 27; ++o) S |= (uint32_t)(sb[h + halo_off(o)] == b) << o;
-                e = edges_from_same(S);
-            }
-            em[j] = e;
-            orig[j] = sk[h];
+            int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+            em[j] = (gx < d.nx && gy < d.ny && gz < d.nz)
+                        ? __ldg(emask + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz))
+                        : 0u;
         }
         __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kVPT; ++j) {
+            int i = tid + kRelaxThreads * j;
+            int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
+            orig[j] = sk[(lx + 1) + HX * ((ly + 1) + HY * (lz + 1))];
+        }
         // ---- relaxation steps
         int step = 0;
         for (int cur = 0; step < kMaxSteps; ++step, cur ^= 1) {
@@ -277,7 +270,7 @@ __device__ bool grid_barrier(GridBarrier *bar, int32_t *reset_n, int32_t *reset_
 // All relaxation rounds in one cooperative launch: round r consumes queue r & 1 and fills
 // the other; the loop ends when a round starts with an empty queue.  No host round trips.
 __global__ void __launch_bounds__(kRelaxThreads) relax_persistent_kernel(
-    const uint8_t *__restrict__ band, Dims d, BrickGeom bg, unsigned long long *key, int32_t *list0, int32_t *list1,
+    const uint32_t *__restrict__ emask, Dims d, BrickGeom bg, unsigned long long *key, int32_t *list0, int32_t *list1,
     int32_t *counts, int32_t *works, uint32_t *flags, uint32_t tag0, int32_t max_rounds, GridBarrier *bar,
     int32_t *status) {
     int r = 0;
@@ -291,7 +284,7 @@ __global__ void __launch_bounds__(kRelaxThreads) relax_persistent_kernel(
             atomicAdd(&g_relax_dbg[1], (unsigned long long)nin);
         }
 #endif
-        relax_items(band, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
+        relax_items(emask, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
                     tag0 + (uint32_t)r + 1u, works + cur, status);
         if (!grid_barrier(bar, counts + cur, works + cur, status)) return;
     }
@@ -1545,7 +1538,8 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int32_t max_rounds = kMaxRounds;
     int32_t *list0 = w.list[0], *list1 = w.list[1], *counts = w.counters + 1, *works = w.counters + 3;
     GridBarrier *bar = w.bar;
-    void *args[] = {(void *)&band, (void *)&d, (void *)&bg, (void *)&w.key, (void *)&list0, (void *)&list1,
+    const uint32_t *emask = w.emask;
+    void *args[] = {(void *)&emask, (void *)&d, (void *)&bg, (void *)&w.key, (void *)&list0, (void *)&list1,
                     (void *)&counts, (void *)&works, (void *)&w.flags, (void *)&tag_round0, (void *)&max_rounds,
                     (void *)&bar, (void *)&status};
     if (cudaLaunchCooperativeKernel((const void *)relax_persistent_kernel, grid, kRelaxThreads, args, 0, s) !=
