@@ -77,7 +77,11 @@ __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
 }
 
 // One relaxation round: the CTAs of the grid take the queued bricks one at a time.
-__device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, Dims d, BrickGeom bg,
+// Only voxels the candidate filter left unsettled can change (settled keys are exact), so
+// their exact bits (xmask, brick order) switch the others off, and only bricks holding
+// unsettled voxels (hasunk) are ever queued.
+__device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, const uint32_t *__restrict__ xmask,
+                                            const uint8_t *__restrict__ hasunk, Dims d, BrickGeom bg,
                                             unsigned long long *key, const int32_t *list_in, const int nin,
                                             int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag,
                                             int32_t *work, int32_t *status) {
@@ -122,7 +126,8 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
             int i = tid + kRelaxThreads * j;
             int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
             int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-            em[j] = (gx < d.nx && gy < d.ny && gz < d.nz)
+            const bool exact = (__ldcg(xmask + (int64_t)brick * 32 + (tid >> 5) + 8 * j) >> (tid & 31)) & 1u;
+            em[j] = (!exact && gx < d.nx && gy < d.ny && gz < d.nz)
                         ? __ldg(emask + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz))
                         : 0u;
         }
@@ -208,7 +213,7 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
             int nx2 = bx + tid % 3 - 1, ny2 = by + (tid / 3) % 3 - 1, nz2 = bz + tid / 9 - 1;
             if (nx2 >= 0 && nx2 < bg.nbx && ny2 >= 0 && ny2 < bg.nby && nz2 >= 0 && nz2 < bg.nbz) {
                 int nb = nx2 + bg.nbx * (ny2 + bg.nby * nz2);
-                if (atomicExch(&flags[nb], tag) != tag) {
+                if (__ldcg(hasunk + nb) && atomicExch(&flags[nb], tag) != tag) {
                     int pos = atomicAdd(n_out, 1);
                     list_out[pos] = nb;
                 }
@@ -220,6 +225,12 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
 
 #ifdef LSRVT_DEBUG
 __device__ unsigned long long g_relax_dbg[2];  // rounds, brick visits
+__device__ unsigned long long g_relax_rt[3][32];  // per round index: ns, bricks, launches
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 #endif
 
 // Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The last CTA to arrive
@@ -270,23 +281,31 @@ __device__ bool grid_barrier(GridBarrier *bar, int32_t *reset_n, int32_t *reset_
 // All relaxation rounds in one cooperative launch: round r consumes queue r & 1 and fills
 // the other; the loop ends when a round starts with an empty queue.  No host round trips.
 __global__ void __launch_bounds__(kRelaxThreads) relax_persistent_kernel(
-    const uint32_t *__restrict__ emask, Dims d, BrickGeom bg, unsigned long long *key, int32_t *list0, int32_t *list1,
-    int32_t *counts, int32_t *works, uint32_t *flags, uint32_t tag0, int32_t max_rounds, GridBarrier *bar,
-    int32_t *status) {
+    const uint32_t *__restrict__ emask, const uint32_t *__restrict__ xmask, const uint8_t *__restrict__ hasunk, Dims d,
+    BrickGeom bg, unsigned long long *key, int32_t *list0, int32_t *list1, int32_t *counts, int32_t *works,
+    uint32_t *flags, uint32_t tag0, int32_t max_rounds, GridBarrier *bar, int32_t *status) {
     int r = 0;
     for (; r < max_rounds; ++r) {
         const int cur = r & 1;
         const int nin = __ldcg(counts + cur);
         if (nin == 0) break;
 #ifdef LSRVT_DEBUG
+        unsigned long long t_round = gtimer();
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             atomicAdd(&g_relax_dbg[0], 1ULL);
             atomicAdd(&g_relax_dbg[1], (unsigned long long)nin);
+            if (r < 32) {
+                atomicAdd(&g_relax_rt[1][r], (unsigned long long)nin);
+                atomicAdd(&g_relax_rt[2][r], 1ULL);
+            }
         }
 #endif
-        relax_items(emask, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
+        relax_items(emask, xmask, hasunk, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
                     tag0 + (uint32_t)r + 1u, works + cur, status);
         if (!grid_barrier(bar, counts + cur, works + cur, status)) return;
+#ifdef LSRVT_DEBUG
+        if (blockIdx.x == 0 && threadIdx.x == 0 && r < 32) atomicAdd(&g_relax_rt[0][r], gtimer() - t_round);
+#endif
     }
     if (r == max_rounds && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, LSRVT_ERR_TIMEOUT);
 }
@@ -893,7 +912,8 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                                                             const int64_t *__restrict__ fine_off,
                                                             const int4 *__restrict__ fine_cand, unsigned long long *key,
                                                             int32_t *list_out, int32_t *n_out, uint32_t *flags,
-                                                            uint32_t tag, UpdateOut up) {
+                                                            uint32_t *xmask, uint8_t *hasunk, uint32_t tag,
+                                                            UpdateOut up) {
     __shared__ int4 cs[kMaxCand];
     __shared__ unsigned long long ck[kMaxCand];
     __shared__ unsigned long long Ub[256];
@@ -1107,6 +1127,12 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                 key[g] = k;
             }
             if (pend) pmask |= 1u << j;
+            {
+                // exact keys never change in the relaxation: one bit per voxel in brick order
+                const bool exact = !(inb && vb[j] != kInvalidBand) || k != kInfKey;
+                const unsigned xb = __ballot_sync(0xffffffffu, exact);
+                if ((tid & 31) == 0) xmask[brick * 32 + (tid >> 5) + 8 * j] = xb;
+            }
             if (up.enabled) {
                 {
                     // one atomic per distinct bit-array word in the warp
@@ -1180,8 +1206,9 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             int64_t g = c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * (c.w & 0xFFFFFF));
             atomicMin(key + g, (unsigned long long)(uint32_t)c.x);
         }
-        if (tid == 0 && unknown_s) {
-            if (atomicExch(&flags[brick], tag) != tag) {
+        if (tid == 0) {
+            hasunk[brick] = (uint8_t)(unknown_s != 0);
+            if (unknown_s && atomicExch(&flags[brick], tag) != tag) {
                 int pos = atomicAdd(n_out, 1);
                 list_out[pos] = (int32_t)brick;
             }
@@ -1419,6 +1446,8 @@ struct CvtWs {
     int64_t *bin_total;
     uint8_t *clr;
     uint32_t *emask;
+    uint32_t *xmask;   // per brick 32 words: exact-key bits written by the candidate filter
+    uint8_t *hasunk;   // per brick: unsettled voxels left by the candidate filter
     uint32_t *planes;
     uint32_t *cell_bands;
     int4 *cell_list;
@@ -1454,6 +1483,8 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.bin_total = c.take<int64_t>(2);
     w.clr = c.take<uint8_t>(n);
     w.emask = c.take<uint32_t>(n);
+    w.xmask = c.take<uint32_t>(nbricks * 32);
+    w.hasunk = c.take<uint8_t>(nbricks);
     BitGeom bgm{(d.nx + 31) / 32};
     w.planes = c.take<uint32_t>(bgm.words(d) * kClearLevels);
     w.cell_bands = c.take<uint32_t>(ncoarse * 8);
@@ -1517,7 +1548,8 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     if (nb_cfi < 1) nb_cfi = 1;
     int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
     cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
-                                               w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, tag, up);
+                                               w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, w.xmask,
+                                               w.hasunk, tag, up);
 #ifdef LSRVT_DEBUG
     {
         int32_t q0 = 0;
@@ -1539,7 +1571,9 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int32_t *list0 = w.list[0], *list1 = w.list[1], *counts = w.counters + 1, *works = w.counters + 3;
     GridBarrier *bar = w.bar;
     const uint32_t *emask = w.emask;
-    void *args[] = {(void *)&emask, (void *)&d, (void *)&bg, (void *)&w.key, (void *)&list0, (void *)&list1,
+    const uint32_t *xmask = w.xmask;
+    const uint8_t *hasunk = w.hasunk;
+    void *args[] = {(void *)&emask, (void *)&xmask, (void *)&hasunk, (void *)&d, (void *)&bg, (void *)&w.key, (void *)&list0, (void *)&list1,
                     (void *)&counts, (void *)&works, (void *)&w.flags, (void *)&tag_round0, (void *)&max_rounds,
                     (void *)&bar, (void *)&status};
     if (cudaLaunchCooperativeKernel((const void *)relax_persistent_kernel, grid, kRelaxThreads, args, 0, s) !=
@@ -1619,6 +1653,15 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         unsigned long long ph[12];
         cudaMemcpyFromSymbol(ph, g_phase, sizeof(ph));
         fprintf(stderr, "cfi tube-certified voxels %llu own path checks %llu\n", ph[5], ph[8]);
+        {
+            unsigned long long rt[3][32], rz[3][32] = {{0}};
+            cudaMemcpyFromSymbol(rt, g_relax_rt, sizeof(rt));
+            cudaMemcpyToSymbol(g_relax_rt, rz, sizeof(rz));
+            fprintf(stderr, "relax per round index (launches, bricks total, us total):");
+            for (int r = 0; r < 32 && rt[2][r]; ++r)
+                fprintf(stderr, " [%d: %llu, %llu, %.0f]", r, rt[2][r], rt[1][r], rt[0][r] / 1e3);
+            fprintf(stderr, "\n");
+        }
         unsigned long long pd[8], pz[8] = {0};
         cudaMemcpyFromSymbol(pd, g_path_dbg, sizeof(pd));
         cudaMemcpyToSymbol(g_path_dbg, pz, sizeof(pz));
