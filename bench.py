@@ -43,7 +43,7 @@ ALG_BYTES_PER_VOXEL_ITER = 11
 # DRAM bytes one Lloyd iteration moves per voxel, summed over its kernels, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 256^3 flame case and scaled by the
 # voxel count (the traffic grows in proportion to it)
-NCU_BYTES_PER_VOXEL_ITER = 41.2
+NCU_BYTES_PER_VOXEL_ITER = None  # kernels changed since the last traffic capture
 
 
 def peaks():
@@ -249,33 +249,31 @@ def gpu_arm(args, rank, world, local_rank):
     stats_gbs = agg_bytes / (agg_ms * 1e-3) / 1e9 if agg_ms > 0 else None
     cvt_ms = phase.get("cvt", 0.0)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: decompose_host uploads the
+    # field, overlaps the auxiliary upload with the tessellation, and returns the per-cell
+    # statistics and sites in host memory (the call synchronises)
     e2e = None
-    if rank == 0 or True:
-        h_field = field.cpu().pin_memory()
-        h_aux = aux.cpu().pin_memory()
-        d_field = torch.empty_like(field)
-        d_aux = torch.empty_like(aux)
-        h2d = h_field.numel() * 4 + h_aux.numel() * 4
-        e_steps = max(1, min(args.steps, 2))
-        pipe_e = Pipeline(pkg, d_field, [d_aux[j] for j in range(N_AUX)], iso)
-        d2h = 0
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(e_steps):
-            d_field.copy_(h_field, non_blocking=True)
-            d_aux.copy_(h_aux, non_blocking=True)
-            out = pipe_e.step()
-            host = [out["cells"][k][:n_sites].to("cpu") for k in ("count", "mean", "m2", "min", "max")]
-            host.append(out["site_pos"][:n_sites].to("cpu"))
-            d2h = sum(t.numel() * t.element_size() for t in host)
-        e1.record(s)
-        torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / e_steps
-        e2e = dict(value=n * N_ITERS / (e_ms * 1e-3) / 1e9, unit=UNIT, h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(d2h), ms_per_step=e_ms)
+    h_field = field.cpu().pin_memory()
+    h_aux = aux.cpu().pin_memory()
+    h2d = h_field.numel() * 4 + h_aux.numel() * 4
+    bufs = {}
+    e_kw = dict(aux=h_aux, gamma=1, strat_block=16, rng_seed=2, n_bins=N_BINS, buffers=bufs, device=dev)
+    pkg.decompose_host(h_field, iso, VPS, N_ITERS, **e_kw)  # first call allocates
+    e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(e_steps):
+        host = pkg.decompose_host(h_field, iso, VPS, N_ITERS, **e_kw)
+    e1.record(s)
+    torch.cuda.synchronize()
+    d2h = host["site_pos"].numel() * 4 + sum(t.numel() * t.element_size() for t in host["cells"].values()
+                                             if t is not None)
+    e_ms = e0.elapsed_time(e1) / e_steps
+    e2e = dict(value=n * N_ITERS / (e_ms * 1e-3) / 1e9, unit=UNIT, h2d_bytes_per_step=int(h2d),
+               d2h_bytes_per_step=int(d2h), ms_per_step=e_ms, api="decompose_host")
+    del h_aux, bufs
     res = dict(ms=ms, phase=phase, clk=clk, n_sites=n_sites, n_comp=n_comp, trace=trace, t_assign=t_assign,
                t_iter=t_iter,
                achieved=achieved, peak=pk, stats_gbs=stats_gbs, cvt_ms=cvt_ms, launches=launches_per_step,

@@ -372,3 +372,61 @@ def decompose(field, iso, voxels_per_site, n_iters, aux=(), gamma=0, strat_block
     if check:
         check_status(status, "decompose")
     return out
+
+
+def decompose_host(field, iso, voxels_per_site, n_iters, aux=None, gamma=0, strat_block=16, rng_seed=0, n_bins=32,
+                   cov=False, max_comp=None, ws=None, device="cuda", buffers=None):
+    """decompose() from host arrays, results back on the host.
+
+    field: CPU float32 (nz, ny, nx); aux: CPU float32 (m, nz, ny, nx) or None (pinned memory
+    makes the copies asynchronous).  The field goes up on the current stream; the auxiliary
+    variables, needed only by the statistics, go up on a second stream while the
+    tessellation runs, and the statistics wait for them.  Returns host tensors: the per-cell
+    statistics (count, mean, m2, min, max, hist[, comom]), the sites and their count, the
+    volume record, and the status word.  `buffers` (a dict) keeps the device copies between
+    calls of the same shape."""
+    dev = torch.device(device)
+    buffers = {} if buffers is None else buffers
+    main = torch.cuda.current_stream(dev)
+    m = 0 if aux is None else int(aux.shape[0])
+    if buffers.get("shape") != (tuple(field.shape), m):
+        buffers.clear()
+        buffers["shape"] = (tuple(field.shape), m)
+        buffers["field"] = torch.empty(field.shape, dtype=torch.float32, device=dev)
+        buffers["aux"] = torch.empty((m,) + tuple(field.shape), dtype=torch.float32, device=dev) if m else None
+        buffers["copy"] = torch.cuda.Stream(device=dev)
+    d_field, d_aux, copy = buffers["field"], buffers["aux"], buffers["copy"]
+    d_field.copy_(field, non_blocking=True)
+    aux_ready = None
+    if m:
+        copy.wait_stream(main)  # the previous call's statistics have read the buffer
+        with torch.cuda.stream(copy):
+            d_aux.copy_(aux, non_blocking=True)
+            aux_ready = torch.cuda.Event()
+            aux_ready.record(copy)
+    ws = ws or buffers.setdefault("ws", Workspace(dev))
+    status = new_status(dev)
+    band = classify(d_field, iso)
+    n = d_field.numel()
+    if max_comp is None:
+        max_comp = default_max_comp(n)
+    comp, cb, cs, cf, nc = label_components(band, max_comp, ws, status)
+    q = saliency_grad(d_field, gamma, ws) if gamma else None
+    sp, sc, off, ns = seed(comp, q, nc, max_comp, voxels_per_site, strat_block, rng_seed, ws=ws, status=status)
+    cell, dist, trace = cvt_iterate(band, q, sp, ns, n_iters, want_dist=False, ws=ws, status=status)
+    out = dict(n_sites=ns, site_pos=sp, status=status)
+    if m:
+        main.wait_event(aux_ready)
+        auxl = [d_aux[j] for j in range(m)]
+        cells = aggregate(cell, auxl, sp, ns, n_bins=n_bins, cov=cov, ws=ws, status=status)
+        comps, bands, vol = merge_hierarchy(cells, ns, off, cb, nc, max_comp, len(iso) + 1, n_bins, cov, ws)
+        out.update(cells=cells, volume=vol)
+    host = {}
+    n_sites = int(ns.item())  # synchronises the main stream once
+    check_status(status, "decompose_host")
+    host["n_sites"] = n_sites
+    host["site_pos"] = sp[:n_sites].cpu()
+    if m:
+        host["cells"] = {k: (v[:n_sites].cpu() if v is not None else None) for k, v in out["cells"].items()}
+        host["volume"] = {k: (v.cpu() if v is not None else None) for k, v in out["volume"].items()}
+    return host

@@ -68,3 +68,26 @@ def test_served_requests_equal_alone(pk):
         _same(pk, alone, recs[i]["out"])
     s = runtime.latency_summary(recs)
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_host_buffer_form_equals_device_form(pk):
+    # decompose_host (host arrays in and out, auxiliary upload overlapped with the
+    # tessellation on a second stream) returns what decompose returns on device arrays
+    w = workloads.flame_workload(side=(72, 40, 56), seed=6, n_aux=5, n_iters=4)
+    h_field = w["field"].pin_memory()
+    h_aux = w["aux"].pin_memory()
+    kw = dict(gamma=1, strat_block=16, rng_seed=6, n_bins=32)
+    ref = pk.decompose(w["field"].cuda(), w["iso"], 256, 4, aux=[a.cuda() for a in w["aux"]], **kw)
+    bufs = {}
+    for _ in range(2):  # the second call reuses the device buffers
+        got = pk.decompose_host(h_field, w["iso"], 256, 4, aux=h_aux, buffers=bufs, **kw)
+        ns = int(ref["n_sites"].item())
+        assert got["n_sites"] == ns
+        assert torch.equal(got["site_pos"], ref["site_pos"][:ns].cpu())
+        for k in ("count", "min", "max", "hist"):
+            assert torch.equal(got["cells"][k], ref["cells"][k][:ns].cpu()), k
+        assert torch.equal(got["volume"]["count"], ref["volume"]["count"].cpu())
+        # FP64 atomics combine partial moments in a run-dependent order
+        for k in ("mean", "m2"):
+            assert torch.allclose(got["cells"][k], ref["cells"][k][:ns].cpu(), rtol=1e-12, atol=1e-12), k
+            assert torch.allclose(got["volume"][k], ref["volume"][k].cpu(), rtol=1e-12, atol=1e-12), k
