@@ -126,7 +126,7 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
             int i = tid + kRelaxThreads * j;
             int lx = i & (RX - 1), ly = (i >> 4) & (RY - 1), lz = i >> 7;
             int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-            const bool exact = (__ldcg(xmask + (int64_t)brick * 32 + (tid >> 5) + 8 * j) >> (tid & 31)) & 1u;
+            const bool exact = (__ldcg(xmask + (int64_t)brick * 32 + (tid >> 5) + (kRelaxThreads / 32) * j) >> (tid & 31)) & 1u;
             em[j] = (!exact && gx < d.nx && gy < d.ny && gz < d.nz)
                         ? __ldg(emask + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz))
                         : 0u;
@@ -624,7 +624,7 @@ __global__ void site_bin_fill_kernel(const int32_t *__restrict__ site_pos, const
                                      int32_t max_sites, const uint8_t *__restrict__ band, Dims d, BrickGeom bg,
                                      CoarseGeom cg, const int64_t *__restrict__ fine_off, int32_t *fine_cur,
                                      int4 *fine_cand, const int64_t *__restrict__ coarse_off, int32_t *coarse_cur,
-                                     int4 *coarse_cand) {
+                                     int4 *coarse_cand, int32_t *status) {
     int32_t ns = min(*n_sites_dev, max_sites);
     int64_t n = d.n();
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
@@ -633,8 +633,16 @@ __global__ void site_bin_fill_kernel(const int32_t *__restrict__ site_pos, const
         int32_t x = p % d.nx, y = (p / d.nx) % d.ny, z = p / (d.nx * d.ny);
         int4 e = make_int4(s, x, y, z | ((int)band[p] << 24));
         int64_t fb = fine_bin(x, y, z, bg), cb = coarse_bin(x, y, z, cg);
-        fine_cand[fine_off[fb] + atomicAdd(&fine_cur[fb], 1)] = e;
-        coarse_cand[coarse_off[cb] + atomicAdd(&coarse_cur[cb], 1)] = e;
+        // the offsets come from a scan of the counts of the same sites, so the slots stay
+        // below ns; checked anyway, so that a bad offset is an error status, not a stray write
+        const int64_t fpos = fine_off[fb] + atomicAdd(&fine_cur[fb], 1);
+        const int64_t cpos = coarse_off[cb] + atomicAdd(&coarse_cur[cb], 1);
+        if (fpos < 0 || fpos >= ns || cpos < 0 || cpos >= ns) {
+            set_status(status, LSRVT_ERR_CAPACITY);
+            continue;
+        }
+        fine_cand[fpos] = e;
+        coarse_cand[cpos] = e;
     }
 }
 
@@ -753,6 +761,15 @@ struct UpdateOut {
     uint32_t *los_bits;
     int32_t *plist;    // pending voxels, appended per brick
     int32_t *n_plist;
+};
+
+// Voxels whose key needs their own path check (no brick tube covers them), handed from the
+// candidate filter to check_paths_kernel: voxel, winning site, first move to walk.
+struct CheckList {
+    int32_t *v;
+    int32_t *s;
+    int32_t *mv;
+    int32_t *n;
 };
 
 constexpr int kCellGather = 4096;   // shared buffer while searching
@@ -913,13 +930,13 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                                                             const int4 *__restrict__ fine_cand, unsigned long long *key,
                                                             int32_t *list_out, int32_t *n_out, uint32_t *flags,
                                                             uint32_t *xmask, uint8_t *hasunk, uint32_t tag,
-                                                            UpdateOut up) {
+                                                            UpdateOut up, CheckList chk) {
     __shared__ int4 cs[kMaxCand];
     __shared__ unsigned long long ck[kMaxCand];
     __shared__ unsigned long long Ub[256];
     __shared__ uint32_t present[8];
     __shared__ short band_start[257];
-    __shared__ int ncand_s, unknown_s, pcount_s, pbase_s;
+    __shared__ int ncand_s, unknown_s, pcount_s, pbase_s, ccount_s, cbase_s;
     __shared__ unsigned long long vbest[RV];  // per voxel: best chamfer key
     __shared__ short vwin[RV];                // per voxel: index of the winner in cs (-1 none)
     __shared__ uint8_t wcert[kMaxCand];       // per candidate: 1 = wins a voxel, 2 = brick certificate holds
@@ -937,7 +954,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         if (tid < 8) present[tid] = 0;
         for (int b = tid; b < 256; b += blockDim.x) Ub[b] = ~0ULL;
         for (int c2 = tid; c2 < kMaxCand / 4; c2 += blockDim.x) reinterpret_cast<uint32_t *>(wcert)[c2] = 0u;
-        if (tid == 0) { unknown_s = 0; ncand_s = 0; pcount_s = 0; }
+        if (tid == 0) { unknown_s = 0; ncand_s = 0; pcount_s = 0; ccount_s = 0; }
         __syncthreads();
         uint8_t vb[kVPT];
 #pragma unroll
@@ -1066,9 +1083,11 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         }
         __syncthreads();
         PHASE_ADD(4);
-        // (3) per voxel: certificate, else its own path check; keys, update outputs
+        // (3) per voxel: keys and update outputs; voxels that need their own path check are
+        // handed to check_paths_kernel (full warps, no barriers) with a tentative exact key
         int unknown = 0;
-        uint32_t pmask = 0;
+        uint32_t pmask = 0, cmask = 0;
+        int cmv[kVPT];
 #pragma unroll
         for (int j = 0; j < kVPT; ++j) {
             int i = tid + kRelaxThreads * j;
@@ -1080,21 +1099,17 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             const int4 bs = bidx >= 0 ? cs[bidx] : make_int4(0, 0, 0, 0);
             unsigned long long k = kInfKey;
             bool los = false, pend = false;
+            cmv[j] = 0;
             if (inb && vb[j] != kInvalidBand) {
                 int status = 0;
-                int cs_site = 0;
                 const int bsz = bs.w & 0xFFFFFF;
                 if (best != kInfKey) {
-                    if (wcert[bidx] == 2) {
+                    if (wcert[bidx] == 2 || (best >> 32) == 0) {
                         status = 2;
 #ifdef LSRVT_DEBUG
                         atomicAdd(&g_phase[5], 1ULL);
 #endif
                     } else {
-#ifdef LSRVT_DEBUG
-                        atomicAdd(&g_phase[8], 1ULL);
-#endif
-                        cs_site = __ldg(clr + bs.y + (int64_t)d.nx * (bs.z + (int64_t)d.ny * bsz));
                         // skip the moves the brick's tube already covers: t <= cov / L2
                         int mv0 = 0;
                         const int cov = wcov[bidx];
@@ -1104,14 +1119,14 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                             const int Av = max(abs(bs.y - x), max(abs(bs.z - y), abs(bsz - z)));
                             mv0 = (int)(((long long)cov * Av) / L2);
                         }
-                        status = chamfer_path_in_band(emask, clr, d, x, y, z, bs.y, bs.z, bsz, cs_site, mv0);
-#ifdef LSRVT_DEBUG
-                        atomicAdd(&g_path_dbg[mv0 > 0 ? 1 : 0], 1ULL);
-                        atomicAdd(&g_path_dbg[4 + status], 1ULL);
-#endif
+                        cmv[j] = mv0;
+                        cmask |= 1u << j;
+                        status = -1;  // tentative: exact key, no outputs until checked
                     }
                 }
-                if (status) {
+                if (status < 0) {
+                    k = best;
+                } else if (status) {
                     k = best;
                     if (up.enabled) {
                         // O(1) line-of-sight certificates only; other voxels are walked in the pending pass
@@ -1129,9 +1144,10 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             if (pend) pmask |= 1u << j;
             {
                 // exact keys never change in the relaxation: one bit per voxel in brick order
+                // (a failed path check clears its bit)
                 const bool exact = !(inb && vb[j] != kInvalidBand) || k != kInfKey;
                 const unsigned xb = __ballot_sync(0xffffffffu, exact);
-                if ((tid & 31) == 0) xmask[brick * 32 + (tid >> 5) + 8 * j] = xb;
+                if ((tid & 31) == 0) xmask[brick * 32 + (tid >> 5) + (kRelaxThreads / 32) * j] = xb;
             }
             if (up.enabled) {
                 {
@@ -1170,32 +1186,44 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         __syncthreads();
         PHASE_ADD(3);
 #endif
-        if (up.enabled) {
-            // append the brick's pending voxels: warp offsets in shared memory, one global
-            // atomic per brick (entry order varies between runs; every use is order-free)
+        {
+            // append the brick's pending voxels and path checks: warp offsets in shared memory,
+            // one global atomic per list per brick (entry order varies between runs; every use
+            // is order-free)
             const int lane = tid & 31;
-            unsigned bal[kVPT];
-            int wtot = 0;
+            unsigned bal[kVPT], cbal[kVPT];
+            int wtot = 0, ctot = 0;
 #pragma unroll
             for (int j = 0; j < kVPT; ++j) {
                 bal[j] = __ballot_sync(0xffffffffu, (pmask >> j) & 1u);
+                cbal[j] = __ballot_sync(0xffffffffu, (cmask >> j) & 1u);
                 wtot += __popc(bal[j]);
+                ctot += __popc(cbal[j]);
             }
-            int wbase = 0;
+            int wbase = 0, cbase = 0;
             if (lane == 0 && wtot) wbase = atomicAdd(&pcount_s, wtot);
+            if (lane == 0 && ctot) cbase = atomicAdd(&ccount_s, ctot);
             wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            cbase = __shfl_sync(0xffffffffu, cbase, 0);
             __syncthreads();
             if (tid == 0) pbase_s = pcount_s ? atomicAdd(up.n_plist, pcount_s) : 0;
+            if (tid == 32) cbase_s = ccount_s ? atomicAdd(chk.n, ccount_s) : 0;
             __syncthreads();
-            int off = pbase_s + wbase;
+            int off = pbase_s + wbase, coff = cbase_s + cbase;
 #pragma unroll
             for (int j = 0; j < kVPT; ++j) {
-                if ((pmask >> j) & 1u) {
-                    int i = tid + kRelaxThreads * j;
-                    int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
-                    up.plist[off + __popc(bal[j] & lanemask_lt())] = (int32_t)(x + (int64_t)d.nx * (y + (int64_t)d.ny * z));
+                int i = tid + kRelaxThreads * j;
+                int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
+                const int32_t g32 = (int32_t)(x + (int64_t)d.nx * (y + (int64_t)d.ny * z));
+                if ((pmask >> j) & 1u) up.plist[off + __popc(bal[j] & lanemask_lt())] = g32;
+                if ((cmask >> j) & 1u) {
+                    const int at = coff + __popc(cbal[j] & lanemask_lt());
+                    chk.v[at] = g32;
+                    chk.s[at] = cs[vwin[i]].x;
+                    chk.mv[at] = cmv[j];
                 }
                 off += __popc(bal[j]);
+                coff += __popc(cbal[j]);
             }
         }
         __syncthreads();
@@ -1217,6 +1245,101 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
     }
 }
 
+
+// Path checks of the voxels the brick tubes did not cover, one thread per voxel in whole
+// warps: status 0 (the path leaves the band) makes the key unknown (+inf, exact bit cleared,
+// brick queued for the relaxation); status 2 certifies line of sight (moments added);
+// status 1 leaves the update to the pending pass.
+__global__ void __launch_bounds__(256) check_paths_kernel(
+    const uint32_t *__restrict__ emask, const uint8_t *__restrict__ clr, Dims d, BrickGeom bg,
+    const int32_t *__restrict__ site_pos, unsigned long long *key, uint32_t *xmask, uint8_t *hasunk, uint32_t *flags,
+    uint32_t tag, int32_t *list_out, int32_t *n_out, CheckList chk, UpdateOut up) {
+    __shared__ int wcnt[8];
+    __shared__ int bbase;
+    const int32_t cnt = *chk.n;
+    const int lane = threadIdx.x & 31;
+    // whole blocks step through the list together (block-level compaction below)
+    for (int32_t bstart = blockIdx.x * blockDim.x; bstart < cnt; bstart += gridDim.x * blockDim.x) {
+        const int32_t i = bstart + threadIdx.x;
+        const bool valid = i < cnt;
+        int status = 2;
+        int x = 0, y = 0, z = 0;
+        int32_t s = -1;
+        int64_t g = -1;
+        if (valid) {
+            g = __ldg(chk.v + i);
+            s = __ldg(chk.s + i);
+            const int mv0 = __ldg(chk.mv + i);
+            x = (int)(g % d.nx);
+            const int64_t r = g / d.nx;
+            y = (int)(r % d.ny);
+            z = (int)(r / d.ny);
+            const int32_t p = __ldg(site_pos + s);
+            const int px = p % d.nx, py = (p / d.nx) % d.ny, pz = p / (d.nx * d.ny);
+            status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, __ldg(clr + p), mv0);
+            if (status == 0) {
+                key[g] = kInfKey;
+                const int64_t brick = x / RX + (int64_t)bg.nbx * (y / RY + (int64_t)bg.nby * (z / RZ));
+                const int li = (x & (RX - 1)) + RX * ((y & (RY - 1)) + RY * (z & (RZ - 1)));
+                atomicAnd(&xmask[brick * 32 + (li >> 5)], ~(1u << (li & 31)));
+                hasunk[brick] = 1;
+                if (atomicExch(&flags[brick], tag) != tag) {
+                    int pos = atomicAdd(n_out, 1);
+                    list_out[pos] = (int32_t)brick;
+                }
+            }
+        }
+        if (!up.enabled) continue;  // uniform over the launch
+        const bool los = valid && status == 2;
+        const bool pend = valid && status != 2;
+        {
+            // one atomic per distinct bit-array word in the warp
+            const int64_t word = valid ? (g >> 5) : -1;
+            const unsigned bit = valid ? (1u << (g & 31)) : 0u;
+            unsigned mw = __match_any_sync(0xffffffffu, word);
+            unsigned lb = __reduce_or_sync(mw, los ? bit : 0u);
+            if (valid && (mw & lanemask_lt()) == 0 && lb) atomicOr(&up.los_bits[word], lb);
+        }
+        // warp-aggregated integer moment sums of the line-of-sight voxels (Eq. 2, phi(v) = v)
+        const int32_t sid = los ? s : -1;
+        const unsigned w = los ? (up.q ? up.q[g] : 1u) : 0u;
+        if (up.small_coords) {
+            unsigned m = __match_any_sync(0xffffffffu, sid);
+            unsigned sx = __reduce_add_sync(m, w * (unsigned)x);
+            unsigned sy = __reduce_add_sync(m, w * (unsigned)y);
+            unsigned sz = __reduce_add_sync(m, w * (unsigned)z);
+            unsigned sw = __reduce_add_sync(m, w);
+            if (los && (m & lanemask_lt()) == 0) {
+                atomicAdd(&up.sums[4 * (int64_t)sid + 0], (unsigned long long)sx);
+                atomicAdd(&up.sums[4 * (int64_t)sid + 1], (unsigned long long)sy);
+                atomicAdd(&up.sums[4 * (int64_t)sid + 2], (unsigned long long)sz);
+                atomicAdd(&up.sums[4 * (int64_t)sid + 3], (unsigned long long)sw);
+            }
+        } else if (los) {
+            atomicAdd(&up.sums[4 * (int64_t)sid + 0], (unsigned long long)w * (unsigned)x);
+            atomicAdd(&up.sums[4 * (int64_t)sid + 1], (unsigned long long)w * (unsigned)y);
+            atomicAdd(&up.sums[4 * (int64_t)sid + 2], (unsigned long long)w * (unsigned)z);
+            atomicAdd(&up.sums[4 * (int64_t)sid + 3], (unsigned long long)w);
+        }
+        // pending voxels: one atomic per block and 256 consecutive entries, written in entry
+        // order, so that the update pass walks spatially coherent runs
+        const unsigned pb = __ballot_sync(0xffffffffu, pend);
+        if (lane == 0) wcnt[threadIdx.x >> 5] = __popc(pb);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int k = 0; k < 8; ++k) {
+                const int c = wcnt[k];
+                wcnt[k] = t;
+                t += c;
+            }
+            bbase = t ? atomicAdd(up.n_plist, t) : 0;
+        }
+        __syncthreads();
+        if (pend) up.plist[bbase + wcnt[threadIdx.x >> 5] + __popc(pb & lanemask_lt())] = (int32_t)g;
+        __syncthreads();
+    }
+}
 
 // ---------------------------------------------------------------- voxel traversal
 // 6-connected Amanatides-Woo traversal of the segment joining the centres of voxels a
@@ -1436,7 +1559,7 @@ struct CvtWs {
     int32_t *par;
     uint32_t *los_bits;
     int32_t *nonlos;
-    int32_t *counters;  // [0] n_nonlos, [1..2] queue counts, [3..4] work counters, [5] n_plist
+    int32_t *counters;  // [0] n_nonlos, [1..2] queue counts, [3..4] work counters, [5] n_plist, [6] checks
     unsigned long long *sums;
     uint32_t *flags;
     int32_t *list[2];
@@ -1524,7 +1647,12 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
     int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
     cudaMemsetAsync(w.counters + 1, 0, sizeof(int32_t) * 4, s);
+    cudaMemsetAsync(w.counters + 6, 0, sizeof(int32_t), s);
     cudaMemsetAsync(w.fine_off, 0, sizeof(int64_t) * (nbricks + 1), s);
+    // the path-check list lives in buffers that are idle while the assignment runs: the
+    // erosion planes (used once per call for the clearance, >= 4 bytes per voxel), and the
+    // parent and non-LOS arrays (written only by the update pass afterwards)
+    CheckList chk{reinterpret_cast<int32_t *>(w.planes), w.par, w.nonlos, w.counters + 6};
     cudaMemsetAsync(w.coarse_off, 0, sizeof(int64_t) * (ncoarse + 1), s);
     cudaMemsetAsync(w.fine_cur, 0, sizeof(int32_t) * nbricks, s);
     cudaMemsetAsync(w.coarse_cur, 0, sizeof(int32_t) * ncoarse, s);
@@ -1534,7 +1662,8 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     exclusive_scan_i64(w.coarse_off, ncoarse + 1, w.bin_total + 1, w.scan, s);
     site_bin_fill_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites, band, d,
                                                                            bg, cg, w.fine_off, w.fine_cur, w.fine_cand,
-                                                                           w.coarse_off, w.coarse_cur, w.coarse_cand);
+                                                                           w.coarse_off, w.coarse_cur, w.coarse_cand,
+                                                                           status);
     {
         size_t smem = kCellGather * sizeof(int4);
         cudaFuncSetAttribute(cell_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1549,7 +1678,9 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
     cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
                                                w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, w.xmask,
-                                               w.hasunk, tag, up);
+                                               w.hasunk, tag, up, chk);
+    check_paths_kernel<<<kSMs * 16, 256, 0, s>>>(w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
+                                                 tag, w.list[0], w.counters + 1, chk, up);
 #ifdef LSRVT_DEBUG
     {
         int32_t q0 = 0;
@@ -1564,7 +1695,8 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int dev = 0, nsm = kSMs;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int grid = nsm * nb_per_sm;
+    // at most one CTA per brick: small volumes leave the rest of the GPU to concurrent work
+    int grid = (int)((int64_t)nsm * nb_per_sm < nbricks ? (int64_t)nsm * nb_per_sm : nbricks);
     cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), s);
     uint32_t tag_round0 = tag;
     int32_t max_rounds = kMaxRounds;
