@@ -1249,9 +1249,11 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
 // Path checks of the voxels the brick tubes did not cover, one thread per voxel in whole
 // warps: status 0 (the path leaves the band) makes the key unknown (+inf, exact bit cleared,
 // brick queued for the relaxation); status 2 certifies line of sight (moments added);
-// status 1 leaves the update to the pending pass.
+// status 1 (exact key, no margin) walks Eq. 2's traversal here, and only voxels without
+// line of sight go to the pending pass (their parents need the final keys).
 __global__ void __launch_bounds__(256) check_paths_kernel(
-    const uint32_t *__restrict__ emask, const uint8_t *__restrict__ clr, Dims d, BrickGeom bg,
+    const uint8_t *__restrict__ band, const uint32_t *__restrict__ emask, const uint8_t *__restrict__ clr, Dims d,
+    BrickGeom bg,
     const int32_t *__restrict__ site_pos, unsigned long long *key, uint32_t *xmask, uint8_t *hasunk, uint32_t *flags,
     uint32_t tag, int32_t *list_out, int32_t *n_out, CheckList chk, UpdateOut up) {
     __shared__ int wcnt[8];
@@ -1276,7 +1278,11 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
             z = (int)(r / d.ny);
             const int32_t p = __ldg(site_pos + s);
             const int px = p % d.nx, py = (p / d.nx) % d.ny, pz = p / (d.nx * d.ny);
-            status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, __ldg(clr + p), mv0);
+            const int cs = __ldg(clr + p);
+            status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, cs, mv0);
+            // an exact key without the margin certificate: walk Eq. 2's traversal now (the
+            // update pass keeps only the voxels without line of sight, for their parents)
+            if (status == 1 && up.enabled && los_clear(band, clr, d, x, y, z, px, py, pz, cs)) status = 2;
             if (status == 0) {
                 key[g] = kInfKey;
                 const int64_t brick = x / RX + (int64_t)bg.nbx * (y / RY + (int64_t)bg.nby * (z / RZ));
@@ -1679,7 +1685,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
                                                w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, w.xmask,
                                                w.hasunk, tag, up, chk);
-    check_paths_kernel<<<kSMs * 16, 256, 0, s>>>(w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
+    check_paths_kernel<<<kSMs * 16, 256, 0, s>>>(band, w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
                                                  tag, w.list[0], w.counters + 1, chk, up);
 #ifdef LSRVT_DEBUG
     {
