@@ -6,8 +6,9 @@
 //
 // B300 design: a CTA takes a 32x8x8 brick (rows of 32 floats = 128-byte coalesced
 // loads), sorts the brick's (cell, local index) keys in shared memory so every cell is a
-// contiguous run, then streams the variables one at a time through shared memory.  A warp
-// owns a run: its lanes accumulate x - c (c = the variable at the cell's site voxel, a
+// contiguous run, then streams the variables eight at a time through shared memory.  The
+// warps share the (variable, run) items, so bricks with one or two cells keep every warp
+// busy.  For an item a warp's lanes accumulate x - c (c = the variable at the cell's site voxel, a
 // per-cell shift common to all bricks) and (x - c)^2 in float-float (TwoSum / FMA
 // error-free transforms, ~44 significant bits), min / max, and a per-warp shared
 // histogram.  One FP64 atomic per (brick, cell, variable) and moment combines the bricks;
@@ -24,6 +25,7 @@ constexpr int AX = 32, AY = 8, AZ = 8, AV = AX * AY * AZ;  // 2048 voxels
 constexpr int kAggThreads = 256;
 constexpr int kAggWarps = kAggThreads / 32;
 constexpr int kMaxBins = 256;
+constexpr size_t kAggDyn = sizeof(float) * kAggWarps * AV;  // staged variables (64 KB)
 
 struct AggParams {
     const float *aux[64];
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const int32_t *_
                                                                  int32_t max_sites, AggAcc acc, uint32_t *hist,
                                                                  int32_t *status) {
     __shared__ unsigned long long keys[AV];
-    __shared__ float xv[AV];
+    extern __shared__ float xs[];  // kAggWarps variables of the brick, [kAggWarps][AV]
     __shared__ unsigned short head[AV + 1];
     __shared__ unsigned whist[kAggWarps][kMaxBins];
     __shared__ int nruns_s, nvalid_s;
@@ -116,19 +118,27 @@ __global__ void __launch_bounds__(kAggThreads) aggregate_kernel(const int32_t *_
             int32_t c = (int32_t)(keys[head[r]] >> 32);
             atomicAdd(&acc.cnt[c], (unsigned long long)(head[r + 1] - head[r]));
         }
-        for (int j = 0; j < p.m; ++j) {
-            const float *x = p.aux[j];
+        // kAggWarps variables at a time; the warps share the (variable, cell run) items, so a
+        // brick with few cells still keeps every warp busy
+        for (int j0 = 0; j0 < p.m; j0 += kAggWarps) {
+            const int nj = p.m - j0 < kAggWarps ? p.m - j0 : kAggWarps;
             __syncthreads();
-            for (int i = tid; i < AV; i += kAggThreads) {
-                int lx = i % AX, ly = (i / AX) % AY, lz = i / (AX * AY);
-                int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-                float v = 0.0f;
-                if (gx < d.nx && gy < d.ny && gz < d.nz) v = __ldcs(x + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz));
-                xv[i] = v;
+            for (int jj = 0; jj < nj; ++jj) {
+                const float *x = p.aux[j0 + jj];
+                for (int i = tid; i < AV; i += kAggThreads) {
+                    int lx = i % AX, ly = (i / AX) % AY, lz = i / (AX * AY);
+                    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+                    float v = 0.0f;
+                    if (gx < d.nx && gy < d.ny && gz < d.nz)
+                        v = __ldcs(x + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz));
+                    xs[jj * AV + i] = v;
+                }
             }
             __syncthreads();
-            const float loj = B ? lo[j] : 0.0f, scj = B ? scale[j] : 0.0f;
-            for (int r = w; r < nruns; r += kAggWarps) {
+            for (int item = w; item < nruns * nj; item += kAggWarps) {
+                const int jj = item % nj, r = item / nj, j = j0 + jj;
+                const float *xv = xs + jj * AV;
+                const float loj = B ? lo[j] : 0.0f, scj = B ? scale[j] : 0.0f;
                 const int s0 = head[r], s1 = head[r + 1];
                 const int32_t c = (int32_t)(keys[s0] >> 32);
                 const float sh = __ldg(p.aux[j] + site_pos[c]);
@@ -563,10 +573,11 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
         w.acc, n_sites_dev, max_sites, n_aux, out);
     int64_t nbricks = (int64_t)((d.nx + AX - 1) / AX) * ((d.ny + AY - 1) / AY) * ((d.nz + AZ - 1) / AZ);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aggregate_kernel, kAggThreads, 0);
+    cudaFuncSetAttribute(aggregate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAggDyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aggregate_kernel, kAggThreads, kAggDyn);
     if (occ < 1) occ = 1;
     int grid = (int)(nbricks < (int64_t)kSMs * occ ? nbricks : (int64_t)kSMs * occ);
-    aggregate_kernel<<<grid, kAggThreads, 0, s>>>(cell, d, p, lo_dev, scale_dev, site_pos, max_sites, w.acc, out.hist,
+    aggregate_kernel<<<grid, kAggThreads, kAggDyn, s>>>(cell, d, p, lo_dev, scale_dev, site_pos, max_sites, w.acc, out.hist,
                                                   status_dev);
     aggregate_finalize_kernel<<<grid_for((int64_t)max_sites * (n_aux > 0 ? n_aux : 1), 256, kSMs * 8), 256, 0, s>>>(
         w.acc, n_sites_dev, max_sites, n_aux, p, site_pos, out);
