@@ -212,7 +212,9 @@ lsrvt_status lsrvt_aux_range(const int32_t *cell, const float *const *aux_host, 
  * FP64; co-moments use BF16 split products on tensor cores with FP32 accumulation.
  *   cell [N] int32 (in); aux_host[n_aux] device pointers to [N] float (in);
  *   lo_dev, scale_dev [n_aux] float (in, device; e.g. from lsrvt_aux_range);
- *   out: rows = max_sites.  NONFINITE if a value is NaN or infinite. */
+ *   out: rows = max_sites, of which rows < *n_sites_dev are written (the rest are left
+ *   untouched, so the row capacity costs memory but no traffic).  NONFINITE if a value is NaN
+ *   or infinite. */
 lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const *aux_host, int32_t n_aux, lsrvt_dims d,
                              const float *lo_dev, const float *scale_dev, int32_t n_bins, uint32_t flags,
                              const int32_t *site_pos, const int32_t *n_sites_dev, int32_t max_sites,
@@ -225,7 +227,8 @@ lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const *aux_host, 
  * LeVeque (1979) evaluated as sum n_i mean_i / n and sum (m2_i + n_i (mean_i-mean)^2).
  *   cells (rows max_sites, n_sites_dev valid); comp_site_off [n_comp+1] (from
  *   lsrvt_seed); comp_band [n_comp]; n_bands = number of isovalues + 1;
- *   comps (rows max_comp), bands (rows n_bands), volume (1 row) (out). */
+ *   comps (rows max_comp; rows < *n_comp_dev written), bands (rows n_bands), volume
+ *   (1 row) (out).  Cell rows < *n_sites_dev are read. */
 lsrvt_status lsrvt_merge_hierarchy(lsrvt_stats cells, const int32_t *n_sites_dev, int32_t max_sites,
                                    int32_t n_aux, int32_t n_bins, uint32_t flags,
                                    const int32_t *comp_site_off, const uint8_t *comp_band,

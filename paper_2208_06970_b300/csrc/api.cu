@@ -1,5 +1,8 @@
 // api.cu -- library-level entry points: status strings, version, workspace sizes.
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace lsrvt {
 size_t ccl_workspace(Dims d);
@@ -9,6 +12,55 @@ int64_t seed_default_strata(Dims d, int32_t sb, int32_t max_comp);
 size_t cvt_workspace(Dims d, int32_t max_sites);
 size_t aggregate_workspace(int32_t max_sites, int32_t m);
 size_t merge_workspace(int32_t max_sites, int32_t max_comp, int32_t n_bands, int32_t m);
+}  // namespace lsrvt
+
+namespace lsrvt {
+
+namespace {
+// the driver's encoder, looked up once through the runtime (no link-time libcuda dependency)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    return encode;
+}
+}  // namespace
+
+bool encode_volume_map(CUtensorMap *map, const void *base, CUtensorMapDataType type, int elem_bytes, int nx, int ny,
+                       int nz, int bx, int by, int bz) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode || !base || ((uintptr_t)base & 15) || ((int64_t)nx * elem_bytes) % 16) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * elem_bytes, (cuuint64_t)nx * ny * elem_bytes};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return encode(map, type, 3, const_cast<void *>(base), dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_stack_map(CUtensorMap *map, const void *base, CUtensorMapDataType type, int elem_bytes, int nx, int ny,
+                      int nz, int m, int64_t vol_pitch, int bx, int by, int bz, int bw) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode || !base || ((uintptr_t)base & 15) || ((int64_t)nx * elem_bytes) % 16 || vol_pitch <= 0 ||
+        vol_pitch % 16 || bw > 256)
+        return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)m};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * elem_bytes, (cuuint64_t)nx * ny * elem_bytes,
+                                   (cuuint64_t)vol_pitch};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)bw};
+    const cuuint32_t estride[4] = {1, 1, 1, 1};
+    return encode(map, type, 4, const_cast<void *>(base), dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace lsrvt
 
 using namespace lsrvt;

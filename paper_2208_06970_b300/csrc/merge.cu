@@ -33,7 +33,10 @@ __global__ void parent_of_kernel(const int32_t *off32, const int64_t *off64, con
     }
 }
 
-__global__ void merge_init_kernel(lsrvt_stats out, int32_t rows, int32_t m, int32_t B, unsigned *omin, unsigned *omax) {
+// clears the live parent rows only (rows < the device-side count)
+__global__ void merge_init_kernel(lsrvt_stats out, const int32_t *n_parent_dev, int32_t n_parent_max, int32_t m,
+                                  int32_t B, unsigned *omin, unsigned *omax) {
+    const int32_t rows = n_parent_dev ? min(*n_parent_dev, n_parent_max) : n_parent_max;
     int64_t rm = (int64_t)rows * m;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rm; i += (int64_t)gridDim.x * blockDim.x) {
         omin[i] = float_to_ordered(__int_as_float(0x7f800000));
@@ -197,8 +200,7 @@ void merge_level(lsrvt_stats child, const int32_t *n_child_dev, int32_t n_child_
                  const int64_t *off64, const int32_t *n_parent_dev, int32_t n_parent_max, int32_t m, int32_t B,
                  bool cov, lsrvt_stats parent_out, MergeWs &w, cudaStream_t s) {
     parent_of_kernel<<<kSMs * 4, 128, 0, s>>>(off32, off64, n_parent_dev, n_parent_max, w.parent);
-    merge_init_kernel<<<grid_for((int64_t)n_parent_max * (m > 0 ? m : 1) * (B > 0 ? B : 1), 256, kSMs * 8), 256, 0,
-                        s>>>(parent_out, n_parent_max, m, B, w.omin, w.omax);
+    merge_init_kernel<<<kSMs * 8, 256, 0, s>>>(parent_out, n_parent_dev, n_parent_max, m, B, w.omin, w.omax);
     merge_exact_kernel<<<grid_for((int64_t)n_child_max * (m > 0 ? m : 1), 256, kSMs * 8), 256, 0, s>>>(
         as_level(child), n_child_dev, n_child_max, w.parent, m, B, parent_out, w.omin, w.omax);
     merge_moments_kernel<<<kSMs * 4, kMergeThreads, 0, s>>>(as_level(child), off32, off64, n_parent_dev, n_parent_max,

@@ -223,6 +223,37 @@ def test_aggregate_and_merge_parity(pk):
         _moment_ok(cpu(g["mean"]), cpu(g["m2"]), r["mean"], r["m2"], r["count"])
 
 
+@pytest.mark.parametrize("dims,m,n_bins", [((44, 30, 21), 20, 31), ((37, 29, 23), 5, 32), ((96, 40, 9), 16, 64)])
+def test_aggregate_parity_shapes(pk, dims, m, n_bins):
+    """Statistics sweep on volumes staged by TMA tile loads (row pitch a multiple of 16 bytes:
+    nx = 44, 96) and by plain loads (nx = 37), with two variable tiles (m = 20), an odd bin
+    count, and more bins than the lane-private histograms hold (64)."""
+    f = workloads.blob_field(dims, 7, "cpu", n_blobs=8).numpy()
+    band = oracle.classify(f, np.array([0.3, 0.6], np.float32))
+    comp, cb, cs, cf = oracle.label_components(band)
+    sp, sc, off, nc = oracle.seed(comp, None, len(cb), 200, 16, 3)
+    sp2, cell, dist, tr = oracle.cvt_iterate(band, None, sp, 1)
+    aux = workloads.correlated_aux(dims, m, 9, "cpu")[0].numpy()
+    lo, hi, scale = oracle.aux_range(cell, aux, n_bins)
+    ref = oracle.aggregate(cell, aux, len(sp2), lo, scale, n_bins)
+    gcell = torch.from_numpy(cell).cuda()
+    st = pk.new_status()
+    # separate allocations (one tensor map per variable) and one stacked tensor (a single 4-D
+    # tensor map for all variables)
+    separate = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in aux]
+    stacked = list(torch.from_numpy(aux).cuda().unbind(0))
+    glo, gsc = pk.aux_range(gcell, separate, n_bins, st)
+    assert np.array_equal(cpu(glo), lo) and np.array_equal(cpu(gsc), scale)
+    for gaux in (separate, stacked, stacked):  # repeated calls reuse the accumulators
+        got = pk.aggregate(gcell, gaux, torch.from_numpy(sp2).cuda(),
+                           torch.tensor([len(sp2)], dtype=torch.int32, device="cuda"), glo, gsc, n_bins, status=st)
+        pk.check_status(st)
+        assert np.array_equal(cpu(got["count"]), ref["count"])
+        assert np.array_equal(cpu(got["min"]), ref["min"]) and np.array_equal(cpu(got["max"]), ref["max"])
+        assert np.array_equal(cpu(got["hist"]).view(np.uint32), ref["hist"])
+        _moment_ok(cpu(got["mean"]), cpu(got["m2"]), ref["mean"], ref["m2"], ref["count"])
+
+
 def test_decompose_pipeline_config1(pk):
     w = blob_case(64)
     f = w["field"]
