@@ -16,7 +16,8 @@
 // halves of the warp have to be combined when a cell ends.  A lane accumulates x - c and
 // (x - c)^2 (c = the variable at the cell's site voxel, a shift common to all bricks of the
 // cell) in float-float (TwoSum / FMA error-free transforms) over at most 51 elements, then
-// folds them into FP64; min / max are exact; the histogram goes to lane-private 16-bit
+// folds them into a normalised float-float sum by accurate double-word additions (FP64 only
+// once per cell and warp, for the atomics); min / max are exact; the histogram goes to lane-private 16-bit
 // counters in shared memory (no bank conflicts, no atomics).  One FP64 atomic
 // per (brick, cell, variable) and moment combines the bricks; a finalize pass forms
 // mean = c + S1/n and M2 = S2 - S1^2/n in FP64.  HBM traffic is the algorithmic 4 B (cell)
@@ -51,6 +52,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// s + e = a + b exactly, for |a| >= |b| (Dekker)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (xh, xl) += (yh, yl): accurate double-word addition (Joldes, Muller & Popescu 2017,
+// relative error below 3 u^2), FP32 operations only
+__device__ __forceinline__ void dw_add(float &xh, float &xl, float yh, float yl) {
+    float sh, sl, th, tl, vh, vl;
+    two_sum(xh, yh, sh, sl);
+    two_sum(xl, yl, th, tl);
+    fast_two_sum(sh, __fadd_rn(sl, th), vh, vl);
+    fast_two_sum(vh, __fadd_rn(tl, vl), xh, xl);
+}
+
 // ------------------------------------------------------------------ statistics sweep
 constexpr int GX = 32, GY = 4, GZ = 4, GV = GX * GY * GZ;  // 512-voxel brick, rows of 128 bytes
 constexpr int kG = 16;                   // variables per tile: one per lane of a half warp
@@ -63,6 +80,7 @@ constexpr int kHashN = 2 * GV;           // twice the brick's voxels: the table 
 constexpr int kLaneBins = 32;            // lane-private histograms up to 32 bins
 constexpr int kShiftSlots = 64;          // slots per brick whose shifts are staged in shared memory
 constexpr int kStackBox = 4;             // stacked variables per 4-D tensor box (8 KB)
+constexpr int kRun = 16;                 // consecutive bricks (along x) a CTA takes at a time
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 
 struct AggMaps {
@@ -94,6 +112,21 @@ struct AggSmem {
 };
 constexpr size_t kAggSmem = sizeof(AggSmem) + 1024;
 static_assert(2 * (kAggSmem + 1024) <= 228 * 1024, "two statistics CTAs must fit one SM");
+
+// Bricks go to CTAs in runs of kRun consecutive bricks (x-neighbours in the x-fastest order),
+// runs dealt round-robin over the grid; only the last run of the volume can be short.
+struct RunMap {
+    int64_t nbricks, nruns;
+    __device__ RunMap(int64_t nb) : nbricks(nb), nruns((nb + kRun - 1) / kRun) {}
+    __device__ int64_t my_bricks() const {
+        if ((int64_t)blockIdx.x >= nruns) return 0;
+        const int64_t runs = (nruns - 1 - blockIdx.x) / gridDim.x + 1;
+        const int64_t last = blockIdx.x + (runs - 1) * (int64_t)gridDim.x;
+        return (runs - 1) * kRun + (nbricks - last * kRun < kRun ? nbricks - last * kRun : kRun);
+    }
+    // the bi-th brick of this CTA
+    __device__ int64_t brick(int64_t bi) const { return (blockIdx.x + (bi / kRun) * (int64_t)gridDim.x) * kRun + bi % kRun; }
+};
 
 // exclusive scan of two ints over the consumer threads; totals in ta, tb.  `buf` alternates
 // between calls so one barrier suffices.
@@ -282,8 +315,8 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
     const int64_t nbricks = (int64_t)nbx * nby * nbz;
     const int m = p.m, B = p.n_bins;
     const int npass = m > 0 ? (m + kG - 1) / kG : 1;
-    const int64_t my_bricks = blockIdx.x < nbricks ? (nbricks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t ntiles = my_bricks * npass;
+    const RunMap runs(nbricks);
+    const int64_t ntiles = runs.my_bricks() * npass;
     if (tid == 0) {
         mbar_init(&S.full[0], 1);
         mbar_init(&S.full[1], 1);
@@ -315,7 +348,7 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
                     alive = false;
                     break;
                 }
-                const int64_t brick = blockIdx.x + (t / npass) * (int64_t)gridDim.x;
+                const int64_t brick = runs.brick(t / npass);
                 const int pass = (int)(t % npass);
                 const int j0 = pass * kG, G = m - j0 < kG ? m - j0 : kG;
                 const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
@@ -346,16 +379,101 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
     uint32_t *hw = &S.hist[warp][0][lane];  // this lane's 16 words, stride 32
     const bool lane_hist = B > 0 && B <= kLaneBins;
     const float Bm1 = (float)(B > 0 ? B - 1 : 0);
+    // Accumulator state, carried from brick to brick of a run while this warp stays in the same
+    // cell (one variable tile per brick): a cell that spans many bricks is flushed once per run.
+    int cur_cell = -1, kacc = 0;
+    bool act = false;
+    int jv = 0;
+    float nsh = 0.0f;
+    // two independent float-float accumulator sets (even / odd steps) for instruction-level
+    // parallelism
+    float h1[2] = {0.0f, 0.0f}, l1[2] = {0.0f, 0.0f}, h2[2] = {0.0f, 0.0f}, l2[2] = {0.0f, 0.0f};
+    // second level: normalised float-float sums (accurate double-word additions), FP64 only
+    // once per flush
+    float H1 = 0.0f, L1 = 0.0f, H2 = 0.0f, L2 = 0.0f;
+    float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
+    int64_t cj = 0;
+    auto fold = [&]() {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            float a, b;
+            two_sum(h1[u], l1[u], a, b);  // normalise the first-level pair
+            dw_add(H1, L1, a, b);
+            two_sum(h2[u], l2[u], a, b);
+            dw_add(H2, L2, a, b);
+            h1[u] = l1[u] = h2[u] = l2[u] = 0.0f;
+        }
+        kacc = 0;
+    };
+    auto flush = [&]() {
+        fold();
+        dw_add(H1, L1, __shfl_down_sync(0xffffffffu, H1, 16), __shfl_down_sync(0xffffffffu, L1, 16));
+        dw_add(H2, L2, __shfl_down_sync(0xffffffffu, H2, 16), __shfl_down_sync(0xffffffffu, L2, 16));
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, 16));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, 16));
+        if (hh == 0 && act) {
+            const double D1 = (double)H1 + (double)L1, D2 = (double)H2 + (double)L2;
+            atomicAdd(&acc.s1[cj], D1);
+            atomicAdd(&acc.s2[cj], D2);
+            atomicMin(&acc.vmin[cj], float_to_ordered(mn));
+            atomicMax(&acc.vmax[cj], float_to_ordered(mx));
+            if (!isfinite(D1) || !isfinite(D2)) set_status(status, LSRVT_ERR_NONFINITE);
+        }
+        if (lane_hist) {
+            const int words = B < 16 ? B : 16;
+            for (int w2 = 0; w2 < words; ++w2) {
+                const uint32_t own = hw[w2 * 32];
+                const uint32_t tot = own + __shfl_down_sync(0xffffffffu, own, 16);
+                hw[w2 * 32] = 0u;
+                if (hh == 0 && act) {
+                    const uint32_t c0 = tot & 0xFFFFu, c1 = tot >> 16;
+                    if (c0) atomicAdd(&hist[cj * B + w2], c0);
+                    if (c1) atomicAdd(&hist[cj * B + w2 + 16], c1);
+                }
+            }
+        }
+        H1 = L1 = H2 = L2 = 0.0f;
+        mn = __int_as_float(0x7f800000);
+        mx = -__int_as_float(0x7f800000);
+        cur_cell = -1;
+    };
+    float loj = 0.0f, scj = 0.0f;
+    auto acc_one = [&](const float x, int u) {
+        mn = fminf(mn, x);
+        mx = fmaxf(mx, x);
+        float dh, dl, s_, e_;
+        two_sum(x, nsh, dh, dl);  // x - c = dh + dl exactly
+        two_sum(h1[u], dh, s_, e_);
+        h1[u] = s_;
+        l1[u] = __fadd_rn(l1[u], __fadd_rn(e_, dl));
+        const float pp = __fmul_rn(dh, dh);
+        const float corr = __fmaf_rn(__fadd_rn(dh, dh), dl, __fmaf_rn(dh, dh, -pp));  // (dh+dl)^2 - pp
+        two_sum(h2[u], pp, s_, e_);
+        h2[u] = s_;
+        l2[u] = __fadd_rn(l2[u], __fadd_rn(e_, corr));
+        if (B) {
+            float tt = __fmul_rn(__fsub_rn(x, loj), scj);
+            tt = fminf(fmaxf(tt, 0.0f), Bm1);  // NaN and t <= 0 -> bin 0, t >= B -> B - 1
+            // x + 2^23 rounded toward zero is 2^23 + floor(x) for 0 <= x < 2^23: its low
+            // mantissa bits are the bin
+            const uint32_t bits = __float_as_uint(__fadd_rz(tt, 8388608.0f));
+            // the lane's own words: a reduction with no result keeps the steps independent
+            if (lane_hist) atomicAdd(hw + ((bits & 15u) << 5), 1u << (bits & 16u));
+            else atomicAdd(&hist[cj * B + (bits - 0x4B000000u)], 1u);
+        }
+    };
     for (int64_t t = 0; t < ntiles; ++t) {
         const int st = kTma ? (int)(t & 1) : 0;
-        const int64_t brick = blockIdx.x + (t / npass) * (int64_t)gridDim.x;
+        const int64_t bi = t / npass;
+        const int64_t brick = runs.brick(bi);
         const int pass = (int)(t % npass);
         const int j0 = pass * kG, G = m - j0 < kG ? m - j0 : kG;
         const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
                   oz = (int)(brick / ((int64_t)nbx * nby)) * GZ;
-        const bool act = j < G;
-        const int jv = j0 + (act ? j : 0);
-        const float loj = (B && act) ? lo[jv] : 0.0f, scj = (B && act) ? scale[jv] : 0.0f;  // issued before the wait
+        act = j < G;
+        jv = j0 + (act ? j : 0);
+        loj = (B && act) ? lo[jv] : 0.0f;  // issued before the wait
+        scj = (B && act) ? scale[jv] : 0.0f;
         bool ok = true;
         if (kTma) {
             ok = mbar_wait(&S.full[st], (uint32_t)(t >> 1) & 1u, kWaitNs);
@@ -383,84 +501,14 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
         const int ns = S.nslots, T = S.nchunks;
         const int q0 = (int)((int64_t)warp * T / kCW), q1 = (int)((int64_t)(warp + 1) * T / kCW);
         const float *xt = S.vars[st][j];
-        int cur_s = -1, kacc = 0;
-        float nsh = 0.0f;
-        // two independent float-float accumulator sets (even / odd steps) for instruction-level
-        // parallelism
-        float h1[2] = {0.0f, 0.0f}, l1[2] = {0.0f, 0.0f}, h2[2] = {0.0f, 0.0f}, l2[2] = {0.0f, 0.0f};
-        double D1 = 0.0, D2 = 0.0;
-        float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
-        int64_t cj = 0;
-        auto fold = [&]() {
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                D1 += (double)h1[u] + (double)l1[u];
-                D2 += (double)h2[u] + (double)l2[u];
-                h1[u] = l1[u] = h2[u] = l2[u] = 0.0f;
-            }
-            kacc = 0;
-        };
-        auto flush = [&]() {
-            fold();
-            D1 += __shfl_down_sync(0xffffffffu, D1, 16);
-            D2 += __shfl_down_sync(0xffffffffu, D2, 16);
-            mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, 16));
-            mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, 16));
-            if (hh == 0 && act) {
-                atomicAdd(&acc.s1[cj], D1);
-                atomicAdd(&acc.s2[cj], D2);
-                atomicMin(&acc.vmin[cj], float_to_ordered(mn));
-                atomicMax(&acc.vmax[cj], float_to_ordered(mx));
-                if (!isfinite(D1) || !isfinite(D2)) set_status(status, LSRVT_ERR_NONFINITE);
-            }
-            if (lane_hist) {
-                const int words = B < 16 ? B : 16;
-                for (int w2 = 0; w2 < words; ++w2) {
-                    const uint32_t own = hw[w2 * 32];
-                    const uint32_t tot = own + __shfl_down_sync(0xffffffffu, own, 16);
-                    hw[w2 * 32] = 0u;
-                    if (hh == 0 && act) {
-                        const uint32_t c0 = tot & 0xFFFFu, c1 = tot >> 16;
-                        if (c0) atomicAdd(&hist[cj * B + w2], c0);
-                        if (c1) atomicAdd(&hist[cj * B + w2 + 16], c1);
-                    }
-                }
-            }
-            D1 = D2 = 0.0;
-            mn = __int_as_float(0x7f800000);
-            mx = -__int_as_float(0x7f800000);
-        };
-        auto acc_one = [&](float x, int u) {
-            mn = fminf(mn, x);
-            mx = fmaxf(mx, x);
-            float dh, dl, s_, e_;
-            two_sum(x, nsh, dh, dl);  // x - c = dh + dl exactly
-            two_sum(h1[u], dh, s_, e_);
-            h1[u] = s_;
-            l1[u] = __fadd_rn(l1[u], __fadd_rn(e_, dl));
-            const float pp = __fmul_rn(dh, dh);
-            const float corr = __fmaf_rn(__fadd_rn(dh, dh), dl, __fmaf_rn(dh, dh, -pp));  // (dh+dl)^2 - pp
-            two_sum(h2[u], pp, s_, e_);
-            h2[u] = s_;
-            l2[u] = __fadd_rn(l2[u], __fadd_rn(e_, corr));
-            if (B) {
-                float tt = __fmul_rn(__fsub_rn(x, loj), scj);
-                tt = fminf(fmaxf(tt, 0.0f), Bm1);  // NaN and t <= 0 -> bin 0, t >= B -> B - 1
-                // x + 2^23 rounded toward zero is 2^23 + floor(x) for 0 <= x < 2^23: its low
-                // mantissa bits are the bin
-                const uint32_t bits = __float_as_uint(__fadd_rz(tt, 8388608.0f));
-                // the lane's own words: a reduction with no result keeps the steps independent
-                if (lane_hist) atomicAdd(hw + ((bits & 15u) << 5), 1u << (bits & 16u));
-                else atomicAdd(&hist[cj * B + (bits - 0x4B000000u)], 1u);
-            }
-        };
         int s = 0;
         for (int q = q0; q < q1; ++q) {
             while (s + 1 < ns && S.cho[s + 1] <= q) ++s;  // slot of chunk q (chunks are in slot order)
-            if (s != cur_s) {
-                if (cur_s >= 0) flush();
-                cur_s = s;
-                cj = (int64_t)S.cellOf[s] * m + jv;
+            const int c = S.cellOf[s];
+            if (c != cur_cell) {
+                if (cur_cell >= 0) flush();
+                cur_cell = c;
+                cj = (int64_t)c * m + jv;
                 nsh = !act ? 0.0f : (s < kShiftSlots ? -S.shift[s][j] : -__ldg(shift_tab + cj));
             }
             const int p0 = S.off[s] + (q - S.cho[s]) * kChunk;
@@ -488,9 +536,12 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
             }
             if (act && (L & 1) && hh == 0) acc_one(xt[S.sorted[pe - 1]], 1);
             kacc += (Le >> 1) + 1;
-            if (kacc > 34) fold();  // at most 51 float-float additions before an FP64 fold
+            if (kacc > 34) fold();  // at most 51 float-float additions before a fold
         }
-        if (cur_s >= 0) flush();
+        // flush at the end of a run, and after every tile when the variables come in several
+        // tiles per brick (the next tile holds other variables)
+        const bool run_end = npass > 1 || bi % kRun == kRun - 1 || t + 1 == ntiles;
+        if (run_end && cur_cell >= 0) flush();
         __syncwarp();
         if (kTma && lane == 0) mbar_arrive(&S.empty[st]);
     }
@@ -943,7 +994,8 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kAggBlock, kAggSmem);
             if (occ < 1) occ = 1;
-            const int grid = (int)(nbricks < (int64_t)nsm * occ ? nbricks : (int64_t)nsm * occ);
+            const int64_t nruns = (nbricks + kRun - 1) / kRun;
+            const int grid = (int)(nruns < (int64_t)nsm * occ ? nruns : (int64_t)nsm * occ);
             kern<<<grid, kAggBlock, kAggSmem, s>>>(cell, d, p, maps, lo_dev, scale_dev, w.shift, max_sites, w.acc,
                                                    out.hist, status_dev);
         };
@@ -954,7 +1006,6 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
     aggregate_finalize_kernel<<<kSMs * 8, 256, 0, s>>>(
         w.acc, n_sites_dev, max_sites, n_aux, p, site_pos, out);
     if (want_cov && n_aux > 0) {
-        const int T = n_aux * (n_aux + 1) / 2;
         cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCovSmem);
         int64_t ncb = (int64_t)((d.nx + CX - 1) / CX) * ((d.ny + CY - 1) / CY) * ((d.nz + CZ - 1) / CZ);
         int cg = (int)(ncb < (int64_t)kSMs * 2 ? ncb : (int64_t)kSMs * 2);
