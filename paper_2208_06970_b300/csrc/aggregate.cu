@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 namespace lsrvt {
@@ -594,173 +595,293 @@ __global__ void aggregate_finalize_kernel(AggAcc acc, const int32_t *n_sites_dev
         out.count[c] = (int64_t)acc.cnt[c];
 }
 
-// ------------------------------------------------------------------ co-moments on tensor cores
-// C_ij = sum over the cell (x_i - mean_i)(x_j - mean_j): per 16x8x8 brick the values, centred
-// by c = float(mean) of their cell, are split d = hi + lo into two BF16 numbers (lo = the
-// exact float remainder rounded to BF16) and staged var-major in shared memory in the brick's
-// cell-sorted order.  One warp per cell run accumulates X^T X with mma.sync m16n8k16 (BF16 in,
-// FP32 accumulate) over 16-voxel chunks as hi.hi + hi.lo + lo.hi (the lo.lo term is below
-// 2^-16 relative), then adds its 32x32 tile into the FP64 totals.  The finalisation removes
-// the centring offset exactly: C = C' - n (mean_i - c_i)(mean_j - c_j), and takes the
-// diagonal from the float-float M2 of the moments pass.
-constexpr int CX = 16, CY = 8, CZ = 8, CV = CX * CY * CZ;  // 1024 voxels
-constexpr int kCovVars = 32;
-constexpr int kCovStride = CV + 8;  // bf16 elements per variable row (bank offset)
-constexpr size_t kCovSmem = (size_t)2 * kCovVars * kCovStride * 2 + (size_t)CV * 8 + (CV + 1) * 2 + 64;
+// ------------------------------------------------------------------ co-moments on tcgen05 tensor cores
+// C_ij = sum over the cell (x_i - mean_i)(x_j - mean_j).  Per 32x4x4 brick the voxels are
+// grouped by cell (counting sort), each cell's run is padded to 16-voxel chunks, and the values
+// centred by c = float(mean) of their cell are split d = hi + lo into two BF16 numbers (lo =
+// the float remainder rounded to BF16) and staged in shared memory in the K-major canonical
+// layout of the tensor core: a chunk holds 64 rows (32 hi variables, then 32 lo) x 16 voxels as
+// 2 K-cores x 8 row groups of 8 x 16-byte core matrices.  One thread issues, per chunk,
+// tcgen05.mma kind::f16 with M = 128 (A = the chunk's 64 rows; rows 64..127 read the next
+// bytes and land in accumulator rows nobody reads), N = 32 (B = the 32 hi rows), K = 16, FP32
+// accumulation in a 32-column TMEM accumulator per cell.  TMEM lanes 0..31 then hold
+// hi.hi^T and lanes 32..63 lo.hi^T, so C = hi.hi^T + lo.hi^T + (lo.hi^T)^T (the lo.lo term is
+// below 2^-16 relative).  The finalisation removes the centring offset exactly,
+// C = C' - n (mean_i - c_i)(mean_j - c_j), and takes the diagonal from the float-float M2 of
+// the moments pass.
+constexpr int kCovVars = 32;                 // variables the contraction holds
+constexpr int kCoThreads = 256;
+constexpr int kCoWarps = kCoThreads / 32;
+constexpr int kCoChunkBytes = 2048;          // one K-step (16 voxels) of A
+constexpr int kCoChunks = 32;                // chunks staged per round (a brick's run has <= 32)
+// Bytes past the last chunk the descriptors may touch: an M = 128 read covers 16 row groups and
+// 2 K-cores; even with the two strides exchanged it stays below 15 * 1024 + 128 + 128 bytes.
+constexpr int kCoSlack = 16384;
+constexpr int kCoSlots = 8;                  // cells per round, one 32-column accumulator each
+constexpr uint32_t kCoTmemCols = 256;
+constexpr uint32_t kCoIdesc = umma_idesc_bf16_f32(128, 32);
 
-__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                               unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// two consecutive bf16 of row `var` at even position p, with elements at or beyond `end` zeroed
-__device__ __forceinline__ unsigned frag2(const unsigned short *rows, int var, int p, int end) {
-    if (p >= end) return 0u;
-    unsigned v = *reinterpret_cast<const unsigned *>(rows + (size_t)var * kCovStride + p);
-    if (p + 1 >= end) return v & 0xFFFFu;
-    return v;
-}
+struct CoSmem {
+    unsigned char a[kCoChunks * kCoChunkBytes + kCoSlack];  // tensor-core operands (first)
+    int32_t cells[GV];
+    int32_t tab[kHashN];
+    int16_t tslot[kHashN];
+    int16_t vt[GV];
+    uint16_t sorted[GV];
+    int32_t off[GV + 1];
+    int32_t cur[GV];
+    int32_t cellOf[GV];
+    float mean_f[kCoSlots][kCovVars];
+    float tr[2][32][33];                     // lo.hi^T blocks for the transposition
+    int32_t chunk0[kCoSlots + 1];            // first chunk of each cell of the round
+    uint64_t mma_bar;
+    uint32_t tmem_base;
+    int32_t wsa[2][kCoWarps], wsb[2][kCoWarps];
+    int32_t nslots;
+};
+constexpr size_t kCoSmem = sizeof(CoSmem) + 1024;
+static_assert(2 * (kCoSmem + 1024) <= 228 * 1024, "two co-moment CTAs must fit one SM");
 
 __device__ __forceinline__ unsigned short bf16_bits(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
-__global__ void __launch_bounds__(256) covariance_kernel(const int32_t *__restrict__ cell, Dims d,
-                                                         const __grid_constant__ AggParams p,
-                                                         const double *__restrict__ mean, int32_t max_sites,
-                                                         double *comom) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned short *hi = (unsigned short *)smem_raw;
-    unsigned short *lo = hi + kCovVars * kCovStride;
-    unsigned long long *keys = (unsigned long long *)(lo + kCovVars * kCovStride);
-    unsigned short *inv = (unsigned short *)(keys + CV);  // local index -> sorted position
-    __shared__ unsigned short head[CV + 1];
-    __shared__ int nruns_s, nvalid_s, wcnt[8];
-    const int m = p.m, T = m * (m + 1) / 2;
-    const int nbx = (d.nx + CX - 1) / CX, nby = (d.ny + CY - 1) / CY, nbz = (d.nz + CZ - 1) / CZ;
-    const int64_t nbricks = (int64_t)nbx * nby * nbz;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    for (int64_t br = blockIdx.x; br < nbricks; br += gridDim.x) {
-        const int ox = (int)(br % nbx) * CX, oy = (int)((br / nbx) % nby) * CY, oz = (int)(br / ((int64_t)nbx * nby)) * CZ;
-        for (int i = tid; i < CV; i += blockDim.x) {
-            int x = ox + i % CX, y = oy + (i / CX) % CY, z = oz + i / (CX * CY);
-            unsigned long long k = ~0ULL;
-            if (x < d.nx && y < d.ny && z < d.nz) {
-                int32_t c = cell[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)];
-                if (c >= 0 && c < max_sites) k = ((unsigned long long)(uint32_t)c << 32) | (uint32_t)i;
-            }
-            keys[i] = k;
-        }
-        block_bitonic_sort(keys, CV);
-        int carry = 0;
-        for (int base = 0; base < CV; base += blockDim.x) {
-            int i = base + tid;
-            unsigned long long k = keys[i];
-            if (k != ~0ULL) inv[(uint32_t)k] = (unsigned short)i;
-            bool h = k != ~0ULL && (i == 0 || (keys[i - 1] >> 32) != (k >> 32));
-            unsigned bal = __ballot_sync(0xffffffffu, h);
-            if (lane == 0) wcnt[w] = __popc(bal);
-            __syncthreads();
-            int before = carry;
-            for (int q = 0; q < w; ++q) before += wcnt[q];
-            if (h) head[before + __popc(bal & lanemask_lt())] = (unsigned short)i;
-            for (int q = 0; q < 8; ++q) carry += wcnt[q];
-            if (k != ~0ULL && (i + 1 == CV || keys[i + 1] == ~0ULL)) nvalid_s = i + 1;
-            __syncthreads();
-        }
-        if (tid == 0) {
-            nruns_s = carry;
-            if (carry == 0) nvalid_s = 0;
-            head[carry] = (unsigned short)nvalid_s;
-        }
-        __syncthreads();
-        const int nruns = nruns_s;
-        if (nruns == 0) continue;
-        // stage centred values, var-major, in sorted order; padding variables are zero
-        for (int i = tid; i < CV; i += blockDim.x) {
-            int x = ox + i % CX, y = oy + (i / CX) % CY, z = oz + i / (CX * CY);
-            if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
-            const int64_t gidx = x + (int64_t)d.nx * (y + (int64_t)d.ny * z);
-            const int32_t c = cell[gidx];
-            if (c < 0 || c >= max_sites) continue;
-            const int pos = inv[i];
-            for (int j = 0; j < kCovVars; ++j) {
-                unsigned short h2 = 0, l2 = 0;
-                if (j < m) {
-                    float v = __ldcs(p.aux[j] + gidx);
-                    float cen = (float)mean[(int64_t)c * m + j];
-                    float dd = __fsub_rn(v, cen);
-                    h2 = bf16_bits(dd);
-                    float hf = __bfloat162float(__ushort_as_bfloat16(h2));
-                    l2 = bf16_bits(__fsub_rn(dd, hf));
-                }
-                hi[(size_t)j * kCovStride + pos] = h2;
-                lo[(size_t)j * kCovStride + pos] = l2;
-            }
-        }
-        __syncthreads();
-        const int nI = (m + 15) / 16, nJ = (m + 7) / 8;
-        for (int r = w; r < nruns; r += 8) {
-            const int s0 = head[r], s1 = head[r + 1];
-            const int32_t c = (int32_t)(keys[s0] >> 32);
-            float acc[2][4][4];
+// exclusive block scan of one int over the kCoThreads threads; total in tot
+__device__ __forceinline__ int co_scan(CoSmem &S, int buf, int a, int &tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ia = a;
 #pragma unroll
-            for (int I = 0; I < 2; ++I)
-#pragma unroll
-                for (int J = 0; J < 4; ++J)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[I][J][e] = 0.0f;
-            for (int ch = s0 - (s0 & 1); ch < s1; ch += 16) {
-                // positions of this lane's elements: ch + 2t (+1) and ch + 2t + 8 (+1); elements
-                // before s0 belong to the previous run and are masked by starting at an even
-                // position and zeroing below s0
-                const int pa = ch + 2 * t, pb = ch + 2 * t + 8;
-#pragma unroll
-                for (int I = 0; I < 2; ++I) {
-                    if (I >= nI) break;
-                    const int vi0 = 16 * I + g, vi1 = vi0 + 8;
-                    unsigned ah[4], al[4];
-                    auto ld = [&](const unsigned short *rows, int var, int pp) {
-                        unsigned v = frag2(rows, var, pp, s1);
-                        if (pp < s0) v &= (pp + 1 < s0) ? 0u : 0xFFFF0000u;
-                        return v;
-                    };
-                    ah[0] = ld(hi, vi0, pa); ah[1] = ld(hi, vi1, pa); ah[2] = ld(hi, vi0, pb); ah[3] = ld(hi, vi1, pb);
-                    al[0] = ld(lo, vi0, pa); al[1] = ld(lo, vi1, pa); al[2] = ld(lo, vi0, pb); al[3] = ld(lo, vi1, pb);
-#pragma unroll
-                    for (int J = 0; J < 4; ++J) {
-                        if (J >= nJ) break;
-                        const int vj = 8 * J + g;
-                        unsigned bh0 = ld(hi, vj, pa), bh1 = ld(hi, vj, pb);
-                        unsigned bl0 = ld(lo, vj, pa), bl1 = ld(lo, vj, pb);
-                        mma_bf16_16816(acc[I][J], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
-                        mma_bf16_16816(acc[I][J], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-                        mma_bf16_16816(acc[I][J], al[0], al[1], al[2], al[3], bh0, bh1);
-                    }
-                }
-            }
-            // accumulate the upper triangle in FP64
-#pragma unroll
-            for (int I = 0; I < 2; ++I)
-#pragma unroll
-                for (int J = 0; J < 4; ++J)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        int i = 16 * I + g + (e >= 2 ? 8 : 0);
-                        int j = 8 * J + 2 * t + (e & 1);
-                        if (i < m && j < m && i <= j) {
-                            int tri = i * m - i * (i - 1) / 2 + (j - i);
-                            atomicAdd(&comom[(int64_t)c * T + tri], (double)acc[I][J][e]);
-                        }
-                    }
-        }
-        __syncthreads();
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, ia, o);
+        if (lane >= o) ia += u;
     }
+    if (lane == 31) S.wsa[buf][w] = ia;
+    __syncthreads();
+    int pre = 0;
+    tot = 0;
+#pragma unroll
+    for (int q = 0; q < kCoWarps; ++q) {
+        const int v = S.wsa[buf][q];
+        if (q < w) pre += v;
+        tot += v;
+    }
+    return pre + ia - a;
+}
+
+// Groups the brick's voxels by cell (slots in hash-table order, run offsets, sorted local
+// indices).  The hash table is empty on entry and on exit.
+__device__ void co_sort_brick(CoSmem &S, Dims d, int ox, int oy, int oz, int32_t max_sites) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    bool val[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int v = tid + r * kCoThreads;
+        const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
+        const int32_t c = S.cells[v];
+        const bool valid = gx < d.nx && gy < d.ny && gz < d.nz && c >= 0 && c < max_sites;
+        const unsigned mm = __match_any_sync(0xffffffffu, valid ? c : -1);
+        const int leader = __ffs(mm) - 1;
+        int h = 0;
+        if (valid && lane == leader) {
+            h = (int)(((uint32_t)c * 2654435761u) >> (32 - 10));
+            for (int probe = 0; probe < kHashN; ++probe) {
+                const int old = atomicCAS(&S.tab[h], -1, c);
+                if (old == -1 || old == c) break;
+                h = (h + 1) & (kHashN - 1);
+            }
+        }
+        h = __shfl_sync(0xffffffffu, h, leader);
+        S.vt[v] = valid ? (int16_t)h : (int16_t)-1;
+        val[r] = valid;
+    }
+    __syncthreads();
+    {
+        constexpr int E = kHashN / kCoThreads;
+        int f = 0;
+#pragma unroll
+        for (int q = 0; q < E; ++q) f += S.tab[tid * E + q] != -1;
+        for (int i = tid; i <= GV; i += kCoThreads) S.off[i] = 0;
+        int tot;
+        int e0 = co_scan(S, 0, f, tot);
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int h = tid * E + q;
+            const int c = S.tab[h];
+            if (c != -1) {
+                S.tslot[h] = (int16_t)e0;
+                S.cellOf[e0] = c;
+                ++e0;
+            }
+        }
+        if (tid == 0) S.nslots = tot;
+    }
+    __syncthreads();
+    int sl[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int v = tid + r * kCoThreads;
+        const int s = val[r] ? (int)S.tslot[S.vt[v]] : -1;
+        sl[r] = s;
+        const unsigned mm = __match_any_sync(0xffffffffu, s);
+        if (s >= 0 && lane == __ffs(mm) - 1) atomicAdd(&S.off[s], __popc(mm));
+    }
+    for (int i = tid; i < kHashN; i += kCoThreads) S.tab[i] = -1;
+    __syncthreads();
+    {
+        const int ns = S.nslots;
+        const int i0 = 2 * tid, i1 = 2 * tid + 1;
+        const int a0 = i0 < ns ? S.off[i0] : 0, a1 = i1 < ns ? S.off[i1] : 0;
+        int tot;
+        const int e = co_scan(S, 1, a0 + a1, tot);
+        if (i0 < ns) { S.off[i0] = e; S.cur[i0] = e; }
+        if (i1 < ns) { S.off[i1] = e + a0; S.cur[i1] = e + a0; }
+        if (tid == 0) S.off[ns] = tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int v = tid + r * kCoThreads;
+        const int s = sl[r];
+        const unsigned mm = __match_any_sync(0xffffffffu, s);
+        const int leader = __ffs(mm) - 1;
+        int base = 0;
+        if (s >= 0 && lane == leader) base = atomicAdd(&S.cur[s], __popc(mm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (s >= 0) S.sorted[base + __popc(mm & lanemask_lt())] = (uint16_t)v;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCoThreads, 2) covariance_kernel(const int32_t *__restrict__ cell, Dims d,
+                                                                   const __grid_constant__ AggParams p,
+                                                                   const double *__restrict__ mean, int32_t max_sites,
+                                                                   double *comom, int32_t *status) {
+    extern __shared__ __align__(16) unsigned char co_smem_raw[];
+    const uint32_t raw_addr = smem_u32(co_smem_raw);
+    CoSmem &S = *reinterpret_cast<CoSmem *>(co_smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = p.m, T = m * (m + 1) / 2;
+    const int nbx = (d.nx + GX - 1) / GX, nby = (d.ny + GY - 1) / GY, nbz = (d.nz + GZ - 1) / GZ;
+    const int64_t nbricks = (int64_t)nbx * nby * nbz;
+    if (tid == 0) {
+        mbar_init(&S.mma_bar, 1);
+        fence_mbar_init();
+    }
+    for (int i = tid; i < kHashN; i += kCoThreads) S.tab[i] = -1;
+    if (warp == 0) tmem_alloc(&S.tmem_base, kCoTmemCols);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = S.tmem_base;
+    const uint32_t a_base = smem_u32(S.a);
+    uint32_t round = 0;  // MMA rounds completed (mbarrier phase)
+    bool failed = false;
+    for (int64_t br = blockIdx.x; br < nbricks && !failed; br += gridDim.x) {
+        const int ox = (int)(br % nbx) * GX, oy = (int)((br / nbx) % nby) * GY, oz = (int)(br / ((int64_t)nbx * nby)) * GZ;
+        for (int v = tid; v < GV; v += kCoThreads) {
+            const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
+            S.cells[v] = (gx < d.nx && gy < d.ny && gz < d.nz) ? __ldg(cell + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)) : -1;
+        }
+        __syncthreads();
+        co_sort_brick(S, d, ox, oy, oz, max_sites);
+        const int ns = S.nslots;
+        for (int r0 = 0; r0 < ns;) {
+            // a round: consecutive cells, at most kCoSlots of them and kCoChunks chunks
+            int r1 = r0, nch = 0;
+            while (r1 < ns && r1 - r0 < kCoSlots) {
+                const int c = (S.off[r1 + 1] - S.off[r1] + 15) / 16;
+                if (nch + c > kCoChunks) break;
+                nch += c;
+                ++r1;
+            }
+            const int nk = r1 - r0;
+            if (tid <= nk) {
+                int c0 = 0;
+                for (int k = 0; k < tid; ++k) c0 += (S.off[r0 + k + 1] - S.off[r0 + k] + 15) / 16;
+                S.chunk0[tid] = c0;
+            }
+            for (int i = tid; i < nk * kCovVars; i += kCoThreads) {
+                const int k = i / kCovVars, j = i % kCovVars;
+                S.mean_f[k][j] = j < m ? (float)mean[(int64_t)S.cellOf[r0 + k] * m + j] : 0.0f;
+            }
+            __syncthreads();
+            // stage centred hi / lo values: element e = (variable j, position pp) with positions
+            // fastest, so consecutive threads read consecutive voxels of one variable
+            const int npos = nch * 16;
+            for (int e = tid; e < npos * kCovVars; e += kCoThreads) {
+                const int j = e / npos, pp = e - j * npos;
+                const int c = pp >> 4, k16 = pp & 15;
+                int k = 0;
+                while (k + 1 < nk && S.chunk0[k + 1] <= c) ++k;
+                const int q = pp - S.chunk0[k] * 16;
+                const int slot = r0 + k;
+                float dd = 0.0f;
+                if (j < m && q < S.off[slot + 1] - S.off[slot]) {
+                    const int v = S.sorted[S.off[slot] + q];
+                    const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
+                    const float x = __ldg(p.aux[j] + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz));
+                    dd = __fsub_rn(x, S.mean_f[k][j]);
+                }
+                const unsigned short h2 = bf16_bits(dd);
+                const unsigned short l2 = bf16_bits(__fsub_rn(dd, __bfloat162float(__ushort_as_bfloat16(h2))));
+                // chunk c, K-core k16 / 8, row group row / 8, row row % 8, element k16 % 8
+                unsigned char *ck = S.a + (size_t)c * kCoChunkBytes + (k16 >> 3) * 1024 + (k16 & 7) * 2;
+                *reinterpret_cast<unsigned short *>(ck + (j >> 3) * 128 + (j & 7) * 16) = h2;
+                *reinterpret_cast<unsigned short *>(ck + ((j + 32) >> 3) * 128 + (j & 7) * 16) = l2;
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after_sync();
+                for (int k = 0; k < nk; ++k)
+                    for (int c = S.chunk0[k]; c < S.chunk0[k + 1]; ++c) {
+                        const uint64_t ad = umma_sdesc(a_base + (uint32_t)c * kCoChunkBytes, 1024, 128);
+                        umma_bf16(tmem + (uint32_t)k * 32, ad, ad, kCoIdesc, c > S.chunk0[k]);
+                    }
+                umma_commit(&S.mma_bar);
+            }
+            bool ok = mbar_wait(&S.mma_bar, round & 1u, kWaitNs);
+            ++round;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    set_status(status, LSRVT_ERR_TIMEOUT);
+                    mbar_wait(&S.mma_bar, (round - 1) & 1u, kWaitNs);  // the MMAs may still be running
+                }
+                failed = true;
+                break;
+            }
+            tc_fence_after_sync();
+            // epilogue: warps 0 / 4 read hi.hi^T (lanes 0..31), warps 1 / 5 lo.hi^T (lanes 32..63);
+            // the two warp pairs take alternate cells
+            const int pair = warp >> 2, wq = warp & 3;
+            if (wq < 2) {
+                for (int k = pair; k < nk; k += 2) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)k * 32, v);
+                    if (wq == 1) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) S.tr[pair][lane][jj] = v[jj];
+                    }
+                    named_bar_sync(2 + pair, 64);
+                    if (wq == 0 && lane < m) {
+                        const int i = lane;
+                        const int64_t base = (int64_t)S.cellOf[r0 + k] * T + (int64_t)i * m - (int64_t)i * (i - 1) / 2 - i;
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj)
+                            if (jj >= i && jj < m)
+                                atomicAdd(&comom[base + jj], (double)(v[jj] + S.tr[pair][i][jj] + S.tr[pair][jj][i]));
+                    }
+                    named_bar_sync(2 + pair, 64);
+                }
+            }
+            tc_fence_before_sync();
+            __syncthreads();
+            r0 = r1;
+        }
+    }
+    __syncthreads();
+    tc_fence_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, kCoTmemCols);
 }
 
 __global__ void covariance_finalize_kernel(const int64_t *count, const double *mean, const double *m2,
@@ -1006,10 +1127,18 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
     aggregate_finalize_kernel<<<kSMs * 8, 256, 0, s>>>(
         w.acc, n_sites_dev, max_sites, n_aux, p, site_pos, out);
     if (want_cov && n_aux > 0) {
-        cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCovSmem);
-        int64_t ncb = (int64_t)((d.nx + CX - 1) / CX) * ((d.ny + CY - 1) / CY) * ((d.nz + CZ - 1) / CZ);
-        int cg = (int)(ncb < (int64_t)kSMs * 2 ? ncb : (int64_t)kSMs * 2);
-        covariance_kernel<<<cg, 256, kCovSmem, s>>>(cell, d, p, out.mean, max_sites, out.comom);
+        cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoSmem);
+        cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, covariance_kernel, kCoThreads, kCoSmem);
+        if (occ < 1) occ = 1;
+        if (occ > 2) occ = 2;  // two CTAs x 256 TMEM columns fill an SM's 512
+        int dev2 = 0, nsm2 = kSMs;
+        cudaGetDevice(&dev2);
+        cudaDeviceGetAttribute(&nsm2, cudaDevAttrMultiProcessorCount, dev2);
+        const int64_t ncb = (int64_t)((d.nx + GX - 1) / GX) * ((d.ny + GY - 1) / GY) * ((d.nz + GZ - 1) / GZ);
+        const int cgrid = (int)(ncb < (int64_t)nsm2 * occ ? ncb : (int64_t)nsm2 * occ);
+        covariance_kernel<<<cgrid, kCoThreads, kCoSmem, s>>>(cell, d, p, out.mean, max_sites, out.comom, status_dev);
         covariance_finalize_kernel<<<kSMs * 8, 256, 0, s>>>(out.count, out.mean, out.m2, n_sites_dev, max_sites, n_aux,
                                                             out.comom);
     }
