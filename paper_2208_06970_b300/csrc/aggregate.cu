@@ -596,48 +596,44 @@ __global__ void aggregate_finalize_kernel(AggAcc acc, const int32_t *n_sites_dev
 }
 
 // ------------------------------------------------------------------ co-moments on tcgen05 tensor cores
-// C_ij = sum over the cell (x_i - mean_i)(x_j - mean_j).  Per 32x4x4 brick the voxels are
-// grouped by cell (counting sort), each cell's run is padded to 16-voxel chunks, and the values
-// centred by c = float(mean) of their cell are split d = hi + lo into two BF16 numbers (lo =
-// the float remainder rounded to BF16) and staged in shared memory in the K-major canonical
-// layout of the tensor core: a chunk holds 64 rows (32 hi variables, then 32 lo) x 16 voxels as
-// 2 K-cores x 8 row groups of 8 x 16-byte core matrices.  One thread issues, per chunk,
-// tcgen05.mma kind::f16 with M = 128 (A = the chunk's 64 rows; rows 64..127 read the next
-// bytes and land in accumulator rows nobody reads), N = 32 (B = the 32 hi rows), K = 16, FP32
-// accumulation in a 32-column TMEM accumulator per cell.  TMEM lanes 0..31 then hold
-// hi.hi^T and lanes 32..63 lo.hi^T, so C = hi.hi^T + lo.hi^T + (lo.hi^T)^T (the lo.lo term is
-// below 2^-16 relative).  The finalisation removes the centring offset exactly,
+// C_ij = sum over the cell (x_i - mean_i)(x_j - mean_j), a grouped contraction X_c^T X_c over
+// the cells.  The voxels are first ordered by cell (a counting sort with the counts of the
+// moments pass), so each cell is contracted by exactly one CTA and its co-moments are written
+// once, with no atomics.  A CTA takes groups of kCoGroup consecutive cells from a work counter;
+// each cell's voxels are gathered in 16-voxel chunks (the last one zero-padded), centred by
+// c = float(mean) of the cell, split d = hi + lo into two BF16 numbers (lo = the float remainder
+// rounded to BF16), and staged in the K-major canonical layout of the tensor core: a chunk holds
+// 64 rows (32 hi variables, then 32 lo) x 16 voxels as 2 K-cores x 8 row groups of 8 x 16-byte
+// core matrices.  One thread issues, per chunk, tcgen05.mma kind::f16 with M = 128 (A = the
+// chunk's 64 rows; rows 64..127 read the following bytes and land in accumulator rows nobody
+// reads), N = 32 (B = the 32 hi rows), K = 16, FP32 accumulation in the cell's 32-column TMEM
+// accumulator; cells longer than a staging round keep accumulating across rounds.  TMEM lanes
+// 0..31 then hold hi.hi^T and lanes 32..63 lo.hi^T, so C' = hi.hi^T + lo.hi^T + (lo.hi^T)^T
+// (the lo.lo term is below 2^-16 relative); the epilogue removes the centring offset exactly,
 // C = C' - n (mean_i - c_i)(mean_j - c_j), and takes the diagonal from the float-float M2 of
 // the moments pass.
 constexpr int kCovVars = 32;                 // variables the contraction holds
 constexpr int kCoThreads = 256;
 constexpr int kCoWarps = kCoThreads / 32;
 constexpr int kCoChunkBytes = 2048;          // one K-step (16 voxels) of A
-constexpr int kCoChunks = 32;                // chunks staged per round (a brick's run has <= 32)
+constexpr int kCoChunks = 32;                // chunks staged per round
 // Bytes past the last chunk the descriptors may touch: an M = 128 read covers 16 row groups and
 // 2 K-cores; even with the two strides exchanged it stays below 15 * 1024 + 128 + 128 bytes.
 constexpr int kCoSlack = 16384;
-constexpr int kCoSlots = 8;                  // cells per round, one 32-column accumulator each
+constexpr int kCoGroup = 8;                  // cells per group, one 32-column accumulator each
 constexpr uint32_t kCoTmemCols = 256;
 constexpr uint32_t kCoIdesc = umma_idesc_bf16_f32(128, 32);
 
 struct CoSmem {
     unsigned char a[kCoChunks * kCoChunkBytes + kCoSlack];  // tensor-core operands (first)
-    int32_t cells[GV];
-    int32_t tab[kHashN];
-    int16_t tslot[kHashN];
-    int16_t vt[GV];
-    uint16_t sorted[GV];
-    int32_t off[GV + 1];
-    int32_t cur[GV];
-    int32_t cellOf[GV];
-    float mean_f[kCoSlots][kCovVars];
+    float mean_f[kCoGroup][kCovVars];
     float tr[2][32][33];                     // lo.hi^T blocks for the transposition
-    int32_t chunk0[kCoSlots + 1];            // first chunk of each cell of the round
+    int64_t start[kCoGroup];                 // first sorted position of each cell of the group
+    int32_t count[kCoGroup];
+    int32_t chunk0[kCoGroup + 1];            // first chunk of each cell of the group
     uint64_t mma_bar;
     uint32_t tmem_base;
-    int32_t wsa[2][kCoWarps], wsb[2][kCoWarps];
-    int32_t nslots;
+    int32_t group;
 };
 constexpr size_t kCoSmem = sizeof(CoSmem) + 1024;
 static_assert(2 * (kCoSmem + 1024) <= 228 * 1024, "two co-moment CTAs must fit one SM");
@@ -646,262 +642,184 @@ __device__ __forceinline__ unsigned short bf16_bits(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
-// exclusive block scan of one int over the kCoThreads threads; total in tot
-__device__ __forceinline__ int co_scan(CoSmem &S, int buf, int a, int &tot) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int ia = a;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, ia, o);
-        if (lane >= o) ia += u;
-    }
-    if (lane == 31) S.wsa[buf][w] = ia;
-    __syncthreads();
-    int pre = 0;
-    tot = 0;
-#pragma unroll
-    for (int q = 0; q < kCoWarps; ++q) {
-        const int v = S.wsa[buf][q];
-        if (q < w) pre += v;
-        tot += v;
-    }
-    return pre + ia - a;
+// cell offsets of the voxel order: off[c] = counts of the cells before c (counts of rows
+// beyond the live sites are zero)
+__global__ void cell_count_kernel(const int64_t *__restrict__ count, const int32_t *n_sites_dev, int32_t max_sites,
+                                  int64_t *off) {
+    const int32_t ns = min(*n_sites_dev, max_sites);
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= max_sites; c += (int64_t)gridDim.x * blockDim.x)
+        off[c] = c < ns ? count[c] : 0;
 }
 
-// Groups the brick's voxels by cell (slots in hash-table order, run offsets, sorted local
-// indices).  The hash table is empty on entry and on exit.
-__device__ void co_sort_brick(CoSmem &S, Dims d, int ox, int oy, int oz, int32_t max_sites) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    bool val[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int v = tid + r * kCoThreads;
-        const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
-        const int32_t c = S.cells[v];
-        const bool valid = gx < d.nx && gy < d.ny && gz < d.nz && c >= 0 && c < max_sites;
-        const unsigned mm = __match_any_sync(0xffffffffu, valid ? c : -1);
+// perm[off[c] + k] = the k-th voxel of cell c (the order inside a cell follows the atomics)
+__global__ void cell_scatter_kernel(const int32_t *__restrict__ cell, int64_t n, const int32_t *n_sites_dev,
+                                    int32_t max_sites, const int64_t *__restrict__ off, int32_t *cur, int32_t *perm,
+                                    int32_t *status) {
+    const int32_t ns = min(*n_sites_dev, max_sites);
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + (threadIdx.x & 31);
+        const int32_t c0 = v < n ? cell[v] : -1;
+        const int32_t c = (c0 >= 0 && c0 < ns) ? c0 : -1;
+        const unsigned mm = __match_any_sync(0xffffffffu, c);
         const int leader = __ffs(mm) - 1;
-        int h = 0;
-        if (valid && lane == leader) {
-            h = (int)(((uint32_t)c * 2654435761u) >> (32 - 10));
-            for (int probe = 0; probe < kHashN; ++probe) {
-                const int old = atomicCAS(&S.tab[h], -1, c);
-                if (old == -1 || old == c) break;
-                h = (h + 1) & (kHashN - 1);
-            }
+        int pos = 0;
+        if (c >= 0 && (int)(threadIdx.x & 31) == leader) pos = atomicAdd(&cur[c], __popc(mm));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (c >= 0) {
+            // the counts come from the moments pass; a position past the cell's range means
+            // they do not describe these labels
+            const int64_t at = off[c] + pos + __popc(mm & lanemask_lt());
+            if (at < off[c + 1]) perm[at] = (int32_t)v;
+            else set_status(status, LSRVT_ERR_CAPACITY);
         }
-        h = __shfl_sync(0xffffffffu, h, leader);
-        S.vt[v] = valid ? (int16_t)h : (int16_t)-1;
-        val[r] = valid;
     }
-    __syncthreads();
-    {
-        constexpr int E = kHashN / kCoThreads;
-        int f = 0;
-#pragma unroll
-        for (int q = 0; q < E; ++q) f += S.tab[tid * E + q] != -1;
-        for (int i = tid; i <= GV; i += kCoThreads) S.off[i] = 0;
-        int tot;
-        int e0 = co_scan(S, 0, f, tot);
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            const int h = tid * E + q;
-            const int c = S.tab[h];
-            if (c != -1) {
-                S.tslot[h] = (int16_t)e0;
-                S.cellOf[e0] = c;
-                ++e0;
-            }
-        }
-        if (tid == 0) S.nslots = tot;
-    }
-    __syncthreads();
-    int sl[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int v = tid + r * kCoThreads;
-        const int s = val[r] ? (int)S.tslot[S.vt[v]] : -1;
-        sl[r] = s;
-        const unsigned mm = __match_any_sync(0xffffffffu, s);
-        if (s >= 0 && lane == __ffs(mm) - 1) atomicAdd(&S.off[s], __popc(mm));
-    }
-    for (int i = tid; i < kHashN; i += kCoThreads) S.tab[i] = -1;
-    __syncthreads();
-    {
-        const int ns = S.nslots;
-        const int i0 = 2 * tid, i1 = 2 * tid + 1;
-        const int a0 = i0 < ns ? S.off[i0] : 0, a1 = i1 < ns ? S.off[i1] : 0;
-        int tot;
-        const int e = co_scan(S, 1, a0 + a1, tot);
-        if (i0 < ns) { S.off[i0] = e; S.cur[i0] = e; }
-        if (i1 < ns) { S.off[i1] = e + a0; S.cur[i1] = e + a0; }
-        if (tid == 0) S.off[ns] = tot;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int v = tid + r * kCoThreads;
-        const int s = sl[r];
-        const unsigned mm = __match_any_sync(0xffffffffu, s);
-        const int leader = __ffs(mm) - 1;
-        int base = 0;
-        if (s >= 0 && lane == leader) base = atomicAdd(&S.cur[s], __popc(mm));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (s >= 0) S.sorted[base + __popc(mm & lanemask_lt())] = (uint16_t)v;
-    }
-    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kCoThreads, 2) covariance_kernel(const int32_t *__restrict__ cell, Dims d,
+__global__ void __launch_bounds__(kCoThreads, 2) covariance_kernel(const int32_t *__restrict__ perm,
+                                                                   const int64_t *__restrict__ off,
                                                                    const __grid_constant__ AggParams p,
-                                                                   const double *__restrict__ mean, int32_t max_sites,
-                                                                   double *comom, int32_t *status) {
+                                                                   const int64_t *__restrict__ count,
+                                                                   const double *__restrict__ mean,
+                                                                   const double *__restrict__ m2,
+                                                                   const int32_t *n_sites_dev, int32_t max_sites,
+                                                                   int32_t *work, double *comom, int32_t *status) {
     extern __shared__ __align__(16) unsigned char co_smem_raw[];
     const uint32_t raw_addr = smem_u32(co_smem_raw);
     CoSmem &S = *reinterpret_cast<CoSmem *>(co_smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = p.m, T = m * (m + 1) / 2;
-    const int nbx = (d.nx + GX - 1) / GX, nby = (d.ny + GY - 1) / GY, nbz = (d.nz + GZ - 1) / GZ;
-    const int64_t nbricks = (int64_t)nbx * nby * nbz;
+    const int32_t ns = min(*n_sites_dev, max_sites);
     if (tid == 0) {
         mbar_init(&S.mma_bar, 1);
         fence_mbar_init();
     }
-    for (int i = tid; i < kHashN; i += kCoThreads) S.tab[i] = -1;
     if (warp == 0) tmem_alloc(&S.tmem_base, kCoTmemCols);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = S.tmem_base;
     const uint32_t a_base = smem_u32(S.a);
-    uint32_t round = 0;  // MMA rounds completed (mbarrier phase)
+    uint32_t rounds = 0;  // MMA rounds completed (mbarrier phase)
     bool failed = false;
-    for (int64_t br = blockIdx.x; br < nbricks && !failed; br += gridDim.x) {
-        const int ox = (int)(br % nbx) * GX, oy = (int)((br / nbx) % nby) * GY, oz = (int)(br / ((int64_t)nbx * nby)) * GZ;
-        for (int v = tid; v < GV; v += kCoThreads) {
-            const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
-            S.cells[v] = (gx < d.nx && gy < d.ny && gz < d.nz) ? __ldg(cell + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)) : -1;
+    while (!failed) {
+        if (tid == 0) S.group = atomicAdd(work, kCoGroup);
+        __syncthreads();
+        const int32_t g0 = S.group;
+        if (g0 >= ns) break;
+        const int nk = ns - g0 < kCoGroup ? ns - g0 : kCoGroup;
+        if (tid < nk) {
+            const int32_t c = g0 + tid;
+            S.start[tid] = off[c];
+            S.count[tid] = (int32_t)count[c];
+        }
+        for (int i = tid; i < nk * kCovVars; i += kCoThreads) {
+            const int k = i / kCovVars, j = i % kCovVars;
+            S.mean_f[k][j] = j < m ? (float)mean[(int64_t)(g0 + k) * m + j] : 0.0f;
         }
         __syncthreads();
-        co_sort_brick(S, d, ox, oy, oz, max_sites);
-        const int ns = S.nslots;
-        for (int r0 = 0; r0 < ns;) {
-            // a round: consecutive cells, at most kCoSlots of them and kCoChunks chunks
-            int r1 = r0, nch = 0;
-            while (r1 < ns && r1 - r0 < kCoSlots) {
-                const int c = (S.off[r1 + 1] - S.off[r1] + 15) / 16;
-                if (nch + c > kCoChunks) break;
-                nch += c;
-                ++r1;
+        if (tid == 0) {
+            int c0 = 0;
+            for (int k = 0; k < nk; ++k) {
+                S.chunk0[k] = c0;
+                c0 += (S.count[k] + 15) / 16;
             }
-            const int nk = r1 - r0;
-            if (tid <= nk) {
-                int c0 = 0;
-                for (int k = 0; k < tid; ++k) c0 += (S.off[r0 + k + 1] - S.off[r0 + k] + 15) / 16;
-                S.chunk0[tid] = c0;
-            }
-            for (int i = tid; i < nk * kCovVars; i += kCoThreads) {
-                const int k = i / kCovVars, j = i % kCovVars;
-                S.mean_f[k][j] = j < m ? (float)mean[(int64_t)S.cellOf[r0 + k] * m + j] : 0.0f;
-            }
-            __syncthreads();
-            // stage centred hi / lo values: element e = (variable j, position pp) with positions
-            // fastest, so consecutive threads read consecutive voxels of one variable
-            const int npos = nch * 16;
-            for (int e = tid; e < npos * kCovVars; e += kCoThreads) {
-                const int j = e / npos, pp = e - j * npos;
-                const int c = pp >> 4, k16 = pp & 15;
+            S.chunk0[nk] = c0;
+        }
+        __syncthreads();
+        const int total = S.chunk0[nk];
+        for (int r0 = 0; r0 < total && !failed; r0 += kCoChunks) {
+            const int nch = total - r0 < kCoChunks ? total - r0 : kCoChunks;
+            // stage: thread per position of the round, all variables of that voxel (up to 32
+            // independent loads in flight)
+            for (int pp = tid; pp < nch * 16; pp += kCoThreads) {
+                const int cg = r0 + (pp >> 4), k16 = pp & 15;
                 int k = 0;
-                while (k + 1 < nk && S.chunk0[k + 1] <= c) ++k;
-                const int q = pp - S.chunk0[k] * 16;
-                const int slot = r0 + k;
-                float dd = 0.0f;
-                if (j < m && q < S.off[slot + 1] - S.off[slot]) {
-                    const int v = S.sorted[S.off[slot] + q];
-                    const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
-                    const float x = __ldg(p.aux[j] + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz));
-                    dd = __fsub_rn(x, S.mean_f[k][j]);
+                while (k + 1 < nk && S.chunk0[k + 1] <= cg) ++k;
+                const int q = (cg - S.chunk0[k]) * 16 + k16;
+                const bool live = q < S.count[k];
+                const int v = live ? __ldg(perm + S.start[k] + q) : 0;
+                unsigned char *ck = S.a + (size_t)(pp >> 4) * kCoChunkBytes + (k16 >> 3) * 1024 + (k16 & 7) * 2;
+                float xv[kCovVars];
+#pragma unroll
+                for (int j = 0; j < kCovVars; ++j) xv[j] = (live && j < m) ? __ldg(p.aux[j] + v) : 0.0f;  // all in flight
+#pragma unroll
+                for (int j = 0; j < kCovVars; ++j) {
+                    float dd = 0.0f;
+                    if (live && j < m) dd = __fsub_rn(xv[j], S.mean_f[k][j]);
+                    const unsigned short h2 = bf16_bits(dd);
+                    const unsigned short l2 = bf16_bits(__fsub_rn(dd, __bfloat162float(__ushort_as_bfloat16(h2))));
+                    *reinterpret_cast<unsigned short *>(ck + (j >> 3) * 128 + (j & 7) * 16) = h2;
+                    *reinterpret_cast<unsigned short *>(ck + ((j + 32) >> 3) * 128 + (j & 7) * 16) = l2;
                 }
-                const unsigned short h2 = bf16_bits(dd);
-                const unsigned short l2 = bf16_bits(__fsub_rn(dd, __bfloat162float(__ushort_as_bfloat16(h2))));
-                // chunk c, K-core k16 / 8, row group row / 8, row row % 8, element k16 % 8
-                unsigned char *ck = S.a + (size_t)c * kCoChunkBytes + (k16 >> 3) * 1024 + (k16 & 7) * 2;
-                *reinterpret_cast<unsigned short *>(ck + (j >> 3) * 128 + (j & 7) * 16) = h2;
-                *reinterpret_cast<unsigned short *>(ck + ((j + 32) >> 3) * 128 + (j & 7) * 16) = l2;
             }
             fence_proxy_async_smem();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after_sync();
-                for (int k = 0; k < nk; ++k)
-                    for (int c = S.chunk0[k]; c < S.chunk0[k + 1]; ++c) {
-                        const uint64_t ad = umma_sdesc(a_base + (uint32_t)c * kCoChunkBytes, 1024, 128);
-                        umma_bf16(tmem + (uint32_t)k * 32, ad, ad, kCoIdesc, c > S.chunk0[k]);
-                    }
+                int k = 0;
+                for (int lc = 0; lc < nch; ++lc) {
+                    const int cg = r0 + lc;
+                    while (k + 1 < nk && S.chunk0[k + 1] <= cg) ++k;
+                    const uint64_t ad = umma_sdesc(a_base + (uint32_t)lc * kCoChunkBytes, 1024, 128);
+                    umma_bf16(tmem + (uint32_t)k * 32, ad, ad, kCoIdesc, cg > S.chunk0[k]);
+                }
                 umma_commit(&S.mma_bar);
             }
-            bool ok = mbar_wait(&S.mma_bar, round & 1u, kWaitNs);
-            ++round;
+            const bool ok = mbar_wait(&S.mma_bar, rounds & 1u, kWaitNs);
+            ++rounds;
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     set_status(status, LSRVT_ERR_TIMEOUT);
-                    mbar_wait(&S.mma_bar, (round - 1) & 1u, kWaitNs);  // the MMAs may still be running
+                    mbar_wait(&S.mma_bar, (rounds - 1) & 1u, kWaitNs);  // the MMAs may still be running
                 }
                 failed = true;
-                break;
             }
             tc_fence_after_sync();
-            // epilogue: warps 0 / 4 read hi.hi^T (lanes 0..31), warps 1 / 5 lo.hi^T (lanes 32..63);
-            // the two warp pairs take alternate cells
-            const int pair = warp >> 2, wq = warp & 3;
-            if (wq < 2) {
-                for (int k = pair; k < nk; k += 2) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)k * 32, v);
-                    if (wq == 1) {
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) S.tr[pair][lane][jj] = v[jj];
-                    }
-                    named_bar_sync(2 + pair, 64);
-                    if (wq == 0 && lane < m) {
-                        const int i = lane;
-                        const int64_t base = (int64_t)S.cellOf[r0 + k] * T + (int64_t)i * m - (int64_t)i * (i - 1) / 2 - i;
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj)
-                            if (jj >= i && jj < m)
-                                atomicAdd(&comom[base + jj], (double)(v[jj] + S.tr[pair][i][jj] + S.tr[pair][jj][i]));
-                    }
-                    named_bar_sync(2 + pair, 64);
-                }
-            }
-            tc_fence_before_sync();
-            __syncthreads();
-            r0 = r1;
         }
+        if (failed) break;
+        // epilogue: warps 0 / 4 read hi.hi^T (lanes 0..31), warps 1 / 5 lo.hi^T (lanes 32..63);
+        // the two warp pairs take alternate cells; each co-moment is written once
+        const int pair = warp >> 2, wq = warp & 3;
+        if (wq < 2) {
+            for (int k = pair; k < nk; k += 2) {
+                const int64_t c = g0 + k;
+                const int64_t n = S.count[k];
+                float v[32];
+                if (n > 0) tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)k * 32, v);
+                if (wq == 1 && n > 0) {
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) S.tr[pair][lane][jj] = v[jj];
+                }
+                if (pair == 0) named_bar_sync(2, 64); else named_bar_sync(3, 64);
+                if (wq == 0 && lane < m) {
+                    const int i = lane;
+                    const int64_t base = c * T + (int64_t)i * m - (int64_t)i * (i - 1) / 2 - i;
+                    const double mi = mean[c * m + i], di = mi - (double)(float)mi;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) {
+                        if (jj < i || jj >= m) continue;
+                        double val = 0.0;
+                        if (n > 0) {
+                            if (jj == i) {
+                                val = m2[c * m + i];
+                            } else {
+                                const double mj = mean[c * m + jj], dj = mj - (double)(float)mj;
+                                val = (double)(v[jj] + S.tr[pair][i][jj] + S.tr[pair][jj][i]) - (double)n * di * dj;
+                            }
+                        }
+                        comom[base + jj] = val;
+                    }
+                }
+                if (pair == 0) named_bar_sync(2, 64); else named_bar_sync(3, 64);
+            }
+        }
+        tc_fence_before_sync();
+        __syncthreads();
     }
     __syncthreads();
     tc_fence_after_sync();
     if (warp == 0) tmem_dealloc(tmem, kCoTmemCols);
-}
-
-__global__ void covariance_finalize_kernel(const int64_t *count, const double *mean, const double *m2,
-                                           const int32_t *n_sites_dev, int32_t max_sites, int32_t m, double *comom) {
-    const int T = m * (m + 1) / 2;
-    const int32_t ns = min(*n_sites_dev, max_sites);
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)ns * T;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t c = idx / T;
-        int tri = (int)(idx - c * T);
-        int i = 0;
-        while (tri >= (i + 1) * m - i * (i + 1) / 2) ++i;  // row of the upper triangle
-        int j = i + (tri - (i * m - i * (i - 1) / 2));
-        int64_t n = count[c];
-        if (n == 0) { comom[idx] = 0.0; continue; }
-        if (i == j) { comom[idx] = m2[c * m + i]; continue; }
-        double mi = mean[c * m + i], mj = mean[c * m + j];
-        double di = mi - (double)(float)mi, dj = mj - (double)(float)mj;
-        comom[idx] = comom[idx] - (double)n * di * dj;
-    }
 }
 
 // ------------------------------------------------------------------ value ranges
@@ -990,10 +908,15 @@ __global__ void range_finalize_kernel(float *lo, float *scale, int32_t m, int32_
 
 struct AggWs {
     AggAcc acc;
-    float *shift;  // [max_sites][m]: the variable at each site voxel
+    float *shift;     // [max_sites][m]: the variable at each site voxel
+    int32_t *perm;    // [N]: voxels ordered by cell (co-moments)
+    int64_t *off;     // [max_sites + 1]: first position of each cell in perm
+    int32_t *cur;     // [max_sites]: scatter cursors
+    int32_t *work;    // co-moment work counter
+    void *scan;       // scan temporaries
 };
 
-AggWs carve_agg(void *ws, size_t bytes, int32_t max_sites, int32_t m, size_t *need) {
+AggWs carve_agg(void *ws, size_t bytes, Dims d, int32_t max_sites, int32_t m, size_t *need) {
     Carver c(ws, bytes);
     AggWs w;
     int64_t sm = (int64_t)max_sites * (m > 0 ? m : 1);
@@ -1003,15 +926,20 @@ AggWs carve_agg(void *ws, size_t bytes, int32_t max_sites, int32_t m, size_t *ne
     w.acc.vmax = c.take<unsigned>(sm);
     w.acc.cnt = c.take<unsigned long long>(max_sites > 0 ? max_sites : 1);
     w.shift = c.take<float>(sm);
+    w.perm = c.take<int32_t>(d.n());
+    w.off = c.take<int64_t>((int64_t)max_sites + 1);
+    w.cur = c.take<int32_t>(max_sites > 0 ? max_sites : 1);
+    w.work = c.take<int32_t>(1);
+    w.scan = c.take<char>(scan_temp_bytes((int64_t)max_sites + 1));
     *need = c.used;
     return w;
 }
 
 }  // namespace
 
-size_t aggregate_workspace(int32_t max_sites, int32_t m) {
+size_t aggregate_workspace(Dims d, int32_t max_sites, int32_t m) {
     size_t need;
-    carve_agg(nullptr, 0, max_sites, m, &need);
+    carve_agg(nullptr, 0, d, max_sites, m, &need);
     return need;
 }
 
@@ -1067,14 +995,14 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
     p.n_bins = want_hist ? n_bins : 0;
     p.flags = flags;
     size_t need;
-    AggWs w = carve_agg(ws, ws_bytes, max_sites, n_aux, &need);
+    AggWs w = carve_agg(ws, ws_bytes, Dims{dd.nx, dd.ny, dd.nz}, max_sites, n_aux, &need);
     size_t cov_need = 0;
     if (!ws || ws_bytes < need + cov_need || ((uintptr_t)ws & 255)) return LSRVT_ERR_WORKSPACE;
     cudaStream_t s = as_stream(stream);
     Dims d{dd.nx, dd.ny, dd.nz};
     aggregate_init_kernel<<<kSMs * 8, 256, 0, s>>>(w.acc, n_sites_dev, max_sites, n_aux,
                                                    (want_hist && n_aux > 0) ? n_bins : 0,
-                                                   (want_cov && n_aux > 0) ? n_aux * (n_aux + 1) / 2 : 0, out);
+                                                   0, out);  // co-moments are written whole, no clearing
     {
         // TMA tile loads when every array can be described by a tensor map (row pitch a
         // multiple of 16 bytes, 16-byte aligned bases); otherwise plain-load staging
@@ -1127,6 +1055,15 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
     aggregate_finalize_kernel<<<kSMs * 8, 256, 0, s>>>(
         w.acc, n_sites_dev, max_sites, n_aux, p, site_pos, out);
     if (want_cov && n_aux > 0) {
+        // voxels ordered by cell, then one CTA per group of cells
+        const int64_t n = d.n();
+        cell_count_kernel<<<grid_for((int64_t)max_sites + 1, 256, kSMs * 4), 256, 0, s>>>(out.count, n_sites_dev,
+                                                                                           max_sites, w.off);
+        exclusive_scan_i64(w.off, (int64_t)max_sites + 1, nullptr, w.scan, s);
+        cudaMemsetAsync(w.cur, 0, sizeof(int32_t) * (size_t)(max_sites > 0 ? max_sites : 1), s);
+        cudaMemsetAsync(w.work, 0, sizeof(int32_t), s);
+        cell_scatter_kernel<<<grid_for(n, 256, kSMs * 8), 256, 0, s>>>(cell, n, n_sites_dev, max_sites, w.off, w.cur,
+                                                                        w.perm, status_dev);
         cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoSmem);
         cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         int occ = 0;
@@ -1136,11 +1073,9 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
         int dev2 = 0, nsm2 = kSMs;
         cudaGetDevice(&dev2);
         cudaDeviceGetAttribute(&nsm2, cudaDevAttrMultiProcessorCount, dev2);
-        const int64_t ncb = (int64_t)((d.nx + GX - 1) / GX) * ((d.ny + GY - 1) / GY) * ((d.nz + GZ - 1) / GZ);
-        const int cgrid = (int)(ncb < (int64_t)nsm2 * occ ? ncb : (int64_t)nsm2 * occ);
-        covariance_kernel<<<cgrid, kCoThreads, kCoSmem, s>>>(cell, d, p, out.mean, max_sites, out.comom, status_dev);
-        covariance_finalize_kernel<<<kSMs * 8, 256, 0, s>>>(out.count, out.mean, out.m2, n_sites_dev, max_sites, n_aux,
-                                                            out.comom);
+        covariance_kernel<<<nsm2 * occ, kCoThreads, kCoSmem, s>>>(w.perm, w.off, p, out.count, out.mean, out.m2,
+                                                                   n_sites_dev, max_sites, w.work, out.comom,
+                                                                   status_dev);
     }
     return launch_status();
 }

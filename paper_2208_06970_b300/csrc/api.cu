@@ -10,7 +10,7 @@ size_t saliency_workspace(Dims d);
 size_t seed_workspace(Dims d, int32_t sb, int32_t max_comp, int64_t max_rec);
 int64_t seed_default_strata(Dims d, int32_t sb, int32_t max_comp);
 size_t cvt_workspace(Dims d, int32_t max_sites);
-size_t aggregate_workspace(int32_t max_sites, int32_t m);
+size_t aggregate_workspace(Dims d, int32_t max_sites, int32_t m);
 size_t merge_workspace(int32_t max_sites, int32_t max_comp, int32_t n_bands, int32_t m);
 }  // namespace lsrvt
 
@@ -98,7 +98,7 @@ extern "C" size_t lsrvt_workspace_bytes(lsrvt_step step, lsrvt_dims dd, int32_t 
             return a > b ? a : b;
         }
         case LSRVT_STEP_CVT: return cvt_workspace(d, max_sites);
-        case LSRVT_STEP_AGGREGATE: return aggregate_workspace(max_sites, n_aux);
+        case LSRVT_STEP_AGGREGATE: return aggregate_workspace(d, max_sites, n_aux);
         case LSRVT_STEP_MERGE: return merge_workspace(max_sites, max_comp, 255, n_aux);
     }
     return 0;
