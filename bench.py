@@ -376,6 +376,62 @@ def forms_arm(args, dev):
     return out
 
 
+def precision_setup(pkg, side, dev, m=32):
+    """The precision form's inputs and labels: blob field (seed 4), 32 correlated variables,
+    classify -> components -> seeds (512 voxels per site) -> 10 Lloyd iterations."""
+    import workloads
+    f = workloads.blob_field((side,) * 3, 4, dev)
+    aux = workloads.correlated_aux((side,) * 3, m, 4, dev)[0]
+    ws = pkg.Workspace(dev)
+    st = pkg.new_status(dev)
+    n = f.numel()
+    mc = pkg.default_max_comp(n)
+    band = pkg.classify(f, np.array([0.2, 0.4, 0.6, 0.8], np.float32))
+    comp, cb, cs, cf, nc = pkg.label_components(band, mc, ws, st)
+    sp, sc, off, ns = pkg.seed(comp, None, nc, mc, 512, 16, 4, ws=ws, status=st)
+    cell, _, _ = pkg.cvt_iterate(band, None, sp, ns, 10, want_dist=False, want_trace=False, ws=ws, status=st)
+    del f, band, comp
+    return dict(side=side, m=m, n=n, cell=cell, aux=aux, auxl=[aux[j] for j in range(m)], sp=sp, ns=ns, ws=ws, st=st)
+
+
+def precision_arm(args, dev):
+    """Precision form on its own workload: a 640^3 blob field (the 64^3 generator at the same
+    blob density, 4 isovalues, 512 voxels per site, 10 Lloyd iterations) with 32 correlated
+    Gaussian variables; per-cell moments (float-float, FP64 finalise) and co-moments (BF16
+    split products on tcgen05 tensor cores, FP32 accumulation, FP64 finalise), timed with CUDA
+    events on the launching stream; errors against the FP64 oracle are checked by the
+    full-size tests."""
+    import paper_2208_06970_b300 as pkg
+    P = precision_setup(pkg, args.prec_side, dev)
+    side, m, n, cell, auxl, sp, ns, ws, st = (P[k] for k in ("side", "m", "n", "cell", "auxl", "sp", "ns", "ws", "st"))
+    s = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(reps):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    mom = timed(lambda: pkg.aggregate(cell, auxl, sp, ns, None, None, 0, ws=ws, status=st))
+    both = timed(lambda: pkg.aggregate(cell, auxl, sp, ns, None, None, 0, cov=True, ws=ws, status=st))
+    pkg.check_status(st, "precision form")
+    gb = n * 4 * (1 + m) / 1e9
+    res = dict(workload="blobs %d^3, 4 isovalues, 1 site/512 voxels, 10 Lloyd iters, %d correlated aux vars" % (side, m),
+               voxels=n, sites=int(ns.item()), moments_ms=mom, moments_gbs=gb / (mom * 1e-3),
+               comoments_ms=both - mom, comoments_gbs=gb / ((both - mom) * 1e-3),
+               comoments_flop_per_voxel=3 * 2 * 32 * 32,
+               precision="moments: float-float sums per brick, FP64 finalise; co-moments: BF16 hi+lo split, "
+                         "hi.hi + hi.lo + lo.hi on tcgen05 (FP32 accumulate), FP64 finalise")
+    del P, auxl, cell
+    torch.cuda.empty_cache()
+    return res
+
+
 def profile_step(args):
     """Workload generation plus two identical steps, no extra instrumentation (ncu target)."""
     import paper_2208_06970_b300 as pkg
@@ -408,6 +464,8 @@ def main():
     ap.add_argument("--serve-hi", type=int, default=384)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--hbm-budget", type=int, default=96, help="GiB admitted at once by the server")
+    ap.add_argument("--prec-side", type=int, default=640, help="side of the precision-form workload")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
     ap.add_argument("--profile-step", action="store_true",
                     help="generate the workload and run two plain steps (for ncu); prints nothing else")
     args = ap.parse_args()
@@ -430,6 +488,9 @@ def main():
         forms = None
         if not args.no_forms and world == 1:
             forms = forms_arm(args, torch.device("cuda", local_rank))
+        precision = None
+        if not args.no_precision and world == 1:
+            precision = precision_arm(args, torch.device("cuda", local_rank))
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             v, dt, desc = oracle_sample(r["field"], r["aux"], r["iso"], side=args.ref_side, iters=args.ref_iters)
@@ -458,7 +519,7 @@ def main():
             phases_ms=r["phase"], cvt_gvoxel_iters_per_s=n * N_ITERS / (r["cvt_ms"] * 1e-3) / 1e9,
             moved_per_iter=r["trace"][:, 0].tolist(), clocks=r["clk"], e2e=r["e2e"],
             gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu,
-            forms=forms)
+            forms=forms, precision=precision)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -160,3 +160,55 @@ def test_full_statistics_sampled_cells_and_merge(full):
         assert np.array_equal(cpu(g["min"])[:k], r["min"]) and np.array_equal(cpu(g["max"])[:k], r["max"])
         assert np.array_equal(cpu(g["hist"])[:k].view(np.uint32), r["hist"])
         _moment_ok(cpu(g["mean"])[:k], cpu(g["m2"])[:k], r["mean"], r["m2"], r["count"])
+
+
+@pytest.fixture(scope="module")
+def precision():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import bench
+    import paper_2208_06970_b300 as pk
+    from paper_2208_06970_b300 import build
+    build.build()
+    P = bench.precision_setup(pk, 640, torch.device("cuda"))
+    P["stats"] = pk.aggregate(P["cell"], P["auxl"], P["sp"], P["ns"], None, None, 0, cov=True, ws=P["ws"],
+                              status=P["st"])
+    torch.cuda.synchronize()
+    pk.check_status(P["st"], "precision form")
+    return P
+
+
+def test_full_precision_moments_and_comoments_sampled_cells(precision):
+    """Precision form at full size (640^3, 32 correlated variables), run as the benchmark runs
+    it: per-cell counts exact, moments within 1e-6 (float-float, FP64 finalise) and co-moments
+    within 1e-4 sqrt(R_ii R_jj) (BF16 split on tcgen05) of the FP64 oracle, on sampled cells
+    (random, largest, smallest) whose voxels alone the oracle aggregates."""
+    P = precision
+    cell, m = P["cell"], P["m"]
+    ns = int(P["ns"].item())
+    h_cell = cpu(cell).ravel()
+    counts = np.bincount(h_cell[h_cell >= 0], minlength=ns)
+    got = P["stats"]
+    assert np.array_equal(cpu(got["count"])[:ns], counts)
+    rng = np.random.default_rng(41)
+    live = np.flatnonzero(counts)
+    sample = np.unique(np.concatenate([rng.choice(live, size=min(len(live), 64), replace=False),
+                                       np.argsort(counts)[-8:], live[np.argsort(counts[live])[:8]]]))
+    remap = torch.full((ns,), -1, dtype=torch.int32, device=cell.device)
+    remap[torch.from_numpy(sample).to(cell.device).long()] = torch.arange(len(sample), dtype=torch.int32,
+                                                                           device=cell.device)
+    flat = cell.reshape(-1)
+    sel = torch.nonzero(flat >= 0).squeeze(1)
+    sel = sel[remap[flat[sel].long()] >= 0]
+    sub_cell = cpu(remap[flat[sel].long()])
+    sub_aux = np.stack([cpu(P["auxl"][j].reshape(-1)[sel]) for j in range(m)])
+    ref = oracle.aggregate(sub_cell, sub_aux, len(sample), n_bins=0, cov=True)
+    assert np.array_equal(cpu(got["count"])[sample], ref["count"])
+    assert np.array_equal(cpu(got["min"])[sample], ref["min"]) and np.array_equal(cpu(got["max"])[sample], ref["max"])
+    _moment_ok(cpu(got["mean"])[sample], cpu(got["m2"])[sample], ref["mean"], ref["m2"], ref["count"])
+    C, R = cpu(got["comom"])[sample], ref["comom"]
+    iu = np.triu_indices(m)
+    diag = {i: k for k, (i, j) in enumerate(zip(*iu)) if i == j}
+    for k, (i, j) in enumerate(zip(*iu)):
+        scale = np.sqrt(np.maximum(R[:, diag[i]] * R[:, diag[j]], 0.0))
+        assert np.all(np.abs(C[:, k] - R[:, k]) <= 1e-4 * scale + 1e-9), (i, j)
