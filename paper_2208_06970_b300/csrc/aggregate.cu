@@ -616,12 +616,12 @@ constexpr int kCovVars = 32;                 // variables the contraction holds
 constexpr int kCoThreads = 256;
 constexpr int kCoWarps = kCoThreads / 32;
 constexpr int kCoChunkBytes = 2048;          // one K-step (16 voxels) of A
-constexpr int kCoChunks = 32;                // chunks staged per round
+constexpr int kCoChunks = 16;                // chunks staged per round
 // Bytes past the last chunk the descriptors may touch: an M = 128 read covers 16 row groups and
 // 2 K-cores; even with the two strides exchanged it stays below 15 * 1024 + 128 + 128 bytes.
 constexpr int kCoSlack = 16384;
-constexpr int kCoGroup = 8;                  // cells per group, one 32-column accumulator each
-constexpr uint32_t kCoTmemCols = 256;
+constexpr int kCoGroup = 4;                  // cells per group, one 32-column accumulator each
+constexpr uint32_t kCoTmemCols = 128;
 constexpr uint32_t kCoIdesc = umma_idesc_bf16_f32(128, 32);
 
 struct CoSmem {
@@ -636,7 +636,7 @@ struct CoSmem {
     int32_t group;
 };
 constexpr size_t kCoSmem = sizeof(CoSmem) + 1024;
-static_assert(2 * (kCoSmem + 1024) <= 228 * 1024, "two co-moment CTAs must fit one SM");
+static_assert(3 * (kCoSmem + 1024) <= 228 * 1024, "three co-moment CTAs must fit one SM");
 
 __device__ __forceinline__ unsigned short bf16_bits(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
@@ -676,7 +676,7 @@ __global__ void cell_scatter_kernel(const int32_t *__restrict__ cell, int64_t n,
     }
 }
 
-__global__ void __launch_bounds__(kCoThreads, 2) covariance_kernel(const int32_t *__restrict__ perm,
+__global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t *__restrict__ perm,
                                                                    const int64_t *__restrict__ off,
                                                                    const __grid_constant__ AggParams p,
                                                                    const int64_t *__restrict__ count,
@@ -1066,10 +1066,11 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
                                                                         w.perm, status_dev);
         cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoSmem);
         cudaFuncSetAttribute(covariance_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, covariance_kernel, kCoThreads, kCoSmem);
-        if (occ < 1) occ = 1;
-        if (occ > 2) occ = 2;  // two CTAs x 256 TMEM columns fill an SM's 512
+        // three CTAs per SM (shared memory, registers and barriers allow it; 3 x 128 TMEM columns
+        // fit an SM's 512), set directly: the occupancy query reports one for this kernel.  The
+        // CTAs take cell groups from a work counter, so a CTA that does not find room simply
+        // starts later.
+        const int occ = 3;
         int dev2 = 0, nsm2 = kSMs;
         cudaGetDevice(&dev2);
         cudaDeviceGetAttribute(&nsm2, cudaDevAttrMultiProcessorCount, dev2);
