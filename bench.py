@@ -448,6 +448,20 @@ def profile_step(args):
     print("profile step ok: %d sites" % int(pipe.last["n_sites"].item()))
 
 
+def profile_precision(args):
+    """The precision form's inputs, then two moment + co-moment aggregations (ncu target)."""
+    import paper_2208_06970_b300 as pkg
+    from paper_2208_06970_b300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    P = precision_setup(pkg, args.prec_side, dev)
+    for _ in range(2):
+        pkg.aggregate(P["cell"], P["auxl"], P["sp"], P["ns"], None, None, 0, cov=True, ws=P["ws"], status=P["st"])
+    torch.cuda.synchronize()
+    pkg.check_status(P["st"], "profile precision")
+    print("profile precision ok: %d sites" % int(P["ns"].item()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +480,8 @@ def main():
     ap.add_argument("--hbm-budget", type=int, default=96, help="GiB admitted at once by the server")
     ap.add_argument("--prec-side", type=int, default=640, help="side of the precision-form workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
+    ap.add_argument("--profile-precision", action="store_true",
+                    help="build the precision-form inputs and run two co-moment aggregations (for ncu)")
     ap.add_argument("--profile-step", action="store_true",
                     help="generate the workload and run two plain steps (for ncu); prints nothing else")
     args = ap.parse_args()
@@ -478,6 +494,9 @@ def main():
         return
     if args.profile_step:
         profile_step(args)
+        return
+    if args.profile_precision:
+        profile_precision(args)
         return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
