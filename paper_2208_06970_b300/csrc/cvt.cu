@@ -455,6 +455,20 @@ __device__ __forceinline__ unsigned long long udiv(unsigned long long a, unsigne
     return a / b;
 }
 
+// floor(a / b) for b >= 1: below 2^22 both operands are exact floats and the float quotient
+// a * rcp(b) (two roundings, relative error below 2^-23) is within 0.5 of a / b < 2^22, so its
+// truncation is off by at most one and one remainder test corrects it; larger operands take the
+// integer division
+__device__ __forceinline__ unsigned long long udiv_fast(unsigned long long a, unsigned long long b) {
+    if (((a | b) >> 22) != 0) return udiv(a, b);
+    const unsigned ua = (unsigned)a, ub = (unsigned)b;
+    unsigned q = __float2uint_rz(__fmul_rn((float)ua, __frcp_rn((float)ub)));
+    const int r = (int)(ua - q * ub);
+    if (r < 0) --q;
+    else if (r >= (int)ub) ++q;
+    return q;
+}
+
 // One shortest chamfer path from v to s (26-connected digital line: the dominant axis i
 // advances every move, the middle axis j after move t has advanced round(t aj / ai)
 // times, the smallest axis k after m middle-axis advances round(m ak / aj) times, so it
@@ -520,11 +534,11 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
             else margin = false;
             int mv2 = mv + step < Ai ? mv + step : Ai;
             unsigned long long nj = 2ULL * mv2 * Aj + Ai;
-            jc = (int)udiv(nj, ai2);
+            jc = (int)udiv_fast(nj, ai2);
             ej = (long long)(nj - ai2 * jc);
             if (Aj) {
                 unsigned long long nk = 2ULL * jc * Ak + Aj;
-                kc = (int)udiv(nk, aj2);
+                kc = (int)udiv_fast(nk, aj2);
                 ek = (long long)(nk - aj2 * kc);
             }
             mv = mv2;
@@ -713,9 +727,9 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
             long long mt = km + c - 1;
             if (mt > Am) mt = Am;
             unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
-            k0 = m == 0 ? (int)mt : (int)udiv(num * A0 + Am, den);
-            k1 = m == 1 ? (int)mt : (int)udiv(num * A1 + Am, den);
-            k2 = m == 2 ? (int)mt : (int)udiv(num * A2 + Am, den);
+            k0 = m == 0 ? (int)mt : (int)udiv_fast(num * A0 + Am, den);
+            k1 = m == 1 ? (int)mt : (int)udiv_fast(num * A1 + Am, den);
+            k2 = m == 2 ? (int)mt : (int)udiv_fast(num * A2 + Am, den);
             T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
             T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
             T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;
@@ -1256,11 +1270,9 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
     BrickGeom bg,
     const int32_t *__restrict__ site_pos, unsigned long long *key, uint32_t *xmask, uint8_t *hasunk, uint32_t *flags,
     uint32_t tag, int32_t *list_out, int32_t *n_out, CheckList chk, UpdateOut up) {
-    __shared__ int wcnt[8];
-    __shared__ int bbase;
     const int32_t cnt = *chk.n;
     const int lane = threadIdx.x & 31;
-    // whole blocks step through the list together (block-level compaction below)
+    // whole warps step through the list together (warp-level reductions and appends below)
     for (int32_t bstart = blockIdx.x * blockDim.x; bstart < cnt; bstart += gridDim.x * blockDim.x) {
         const int32_t i = bstart + threadIdx.x;
         const bool valid = i < cnt;
@@ -1327,23 +1339,13 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
             atomicAdd(&up.sums[4 * (int64_t)sid + 2], (unsigned long long)w * (unsigned)z);
             atomicAdd(&up.sums[4 * (int64_t)sid + 3], (unsigned long long)w);
         }
-        // pending voxels: one atomic per block and 256 consecutive entries, written in entry
-        // order, so that the update pass walks spatially coherent runs
+        // pending voxels: one atomic per warp, 32 consecutive entries in entry order (spatially
+        // coherent runs for the update pass)
         const unsigned pb = __ballot_sync(0xffffffffu, pend);
-        if (lane == 0) wcnt[threadIdx.x >> 5] = __popc(pb);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int k = 0; k < 8; ++k) {
-                const int c = wcnt[k];
-                wcnt[k] = t;
-                t += c;
-            }
-            bbase = t ? atomicAdd(up.n_plist, t) : 0;
-        }
-        __syncthreads();
-        if (pend) up.plist[bbase + wcnt[threadIdx.x >> 5] + __popc(pb & lanemask_lt())] = (int32_t)g;
-        __syncthreads();
+        int wbase = 0;
+        if (lane == 0 && pb) wbase = atomicAdd(up.n_plist, __popc(pb));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (pend) up.plist[wbase + __popc(pb & lanemask_lt())] = (int32_t)g;
     }
 }
 
