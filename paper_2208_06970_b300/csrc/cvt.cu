@@ -62,6 +62,14 @@ __host__ __device__ constexpr int halo_off(int o) {
     return (o % 3 - 1) + HX * ((o / 3) % 3 - 1 + HY * (o / 9 - 1));
 }
 
+// voxel coordinates of a linear index (N < 2^31, so 32-bit unsigned division is exact)
+__device__ __forceinline__ void decode_voxel(uint32_t v, Dims d, int &x, int &y, int &z) {
+    const uint32_t r = v / (uint32_t)d.nx;
+    x = (int)(v - r * (uint32_t)d.nx);
+    z = (int)(r / (uint32_t)d.ny);
+    y = (int)(r - (uint32_t)z * (uint32_t)d.ny);
+}
+
 // 26-bit edge mask from the 27-bit "same band" mask S (bit 13 = the voxel itself)
 __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
     uint32_t e = 0;
@@ -380,8 +388,9 @@ __global__ void clear_count_kernel(const uint32_t *__restrict__ planes, Dims d, 
     int64_t n = d.n();
     int64_t nw = bgm.words(d);
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int x = (int)(v % d.nx);
-        int64_t row = v / d.nx;
+        const uint32_t row32 = (uint32_t)v / (uint32_t)d.nx;  // N < 2^31
+        const int x = (int)((uint32_t)v - row32 * (uint32_t)d.nx);
+        const int64_t row = row32;
         int64_t wi = row * bgm.W + (x >> 5);
         uint32_t bit = 1u << (x & 31);
         int c = 0;
@@ -400,9 +409,8 @@ __global__ void clear_count_kernel(const uint32_t *__restrict__ planes, Dims d, 
 __global__ void edge_mask_kernel(const uint8_t *__restrict__ band, Dims d, uint32_t *__restrict__ emask) {
     int64_t n = d.n();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % d.nx);
-        const int64_t r = v / d.nx;
-        const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+        int x, y, z;
+        decode_voxel((uint32_t)v, d, x, y, z);
         const uint8_t b = band[v];
         uint32_t e = 0;
         if (b != kInvalidBand) {
@@ -513,11 +521,11 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
     if (mv_start > 0) {
         mv = mv_start < Ai ? mv_start : Ai;
         unsigned long long nj = 2ULL * mv * Aj + Ai;
-        jc = (int)udiv(nj, ai2);
+        jc = (int)udiv_fast(nj, ai2);
         ej = (long long)(nj - ai2 * jc);
         if (Aj) {
             unsigned long long nk = 2ULL * jc * Ak + Aj;
-            kc = (int)udiv(nk, aj2);
+            kc = (int)udiv_fast(nk, aj2);
             ek = (long long)(nk - aj2 * kc);
         }
         g = v0 + si * mv + sj * jc + sk * kc;
@@ -1284,12 +1292,10 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
             g = __ldg(chk.v + i);
             s = __ldg(chk.s + i);
             const int mv0 = __ldg(chk.mv + i);
-            x = (int)(g % d.nx);
-            const int64_t r = g / d.nx;
-            y = (int)(r % d.ny);
-            z = (int)(r / d.ny);
+            decode_voxel((uint32_t)g, d, x, y, z);
             const int32_t p = __ldg(site_pos + s);
-            const int px = p % d.nx, py = (p / d.nx) % d.ny, pz = p / (d.nx * d.ny);
+            int px, py, pz;
+            decode_voxel((uint32_t)p, d, px, py, pz);
             const int cs = __ldg(clr + p);
             status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, cs, mv0);
             // an exact key without the margin certificate: walk Eq. 2's traversal now (the
@@ -1413,10 +1419,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
             if (k != kInfKey) {
                 s = (int32_t)(uint32_t)k;
                 uint32_t dist = (uint32_t)(k >> 32);
-                x = (int)(v % d.nx);
-                int64_t r = v / d.nx;
-                y = (int)(r % d.ny);
-                z = (int)(r / d.ny);
+                decode_voxel((uint32_t)v, d, x, y, z);
                 if (dist == 0) {
                     los = true;
                 } else {
@@ -1424,7 +1427,8 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
                     long long _u0 = clock64();
 #endif
                     int32_t p = site_pos[s];
-                    int px = p % d.nx, py = (p / d.nx) % d.ny, pz = p / (d.nx * d.ny);
+                    int px, py, pz;
+                    decode_voxel((uint32_t)p, d, px, py, pz);
                     los = los_clear(band, clr, d, x, y, z, px, py, pz, __ldg(clr + p));
 #ifdef LSRVT_DEBUG
                     atomicAdd(&g_phase[6], (unsigned long long)(clock64() - _u0));
@@ -1515,7 +1519,8 @@ __global__ void update_nonlos_kernel(const uint16_t *__restrict__ q, Dims d, con
         }
         int32_t s = (int32_t)(uint32_t)key[v];
         unsigned long long w = q ? q[v] : 1u;
-        int ux = u % d.nx, uy = (u / d.nx) % d.ny, uz = u / (d.nx * d.ny);
+        int ux, uy, uz;
+        decode_voxel((uint32_t)u, d, ux, uy, uz);
         atomicAdd(&sums[4 * (int64_t)s + 0], w * (unsigned)ux);
         atomicAdd(&sums[4 * (int64_t)s + 1], w * (unsigned)uy);
         atomicAdd(&sums[4 * (int64_t)s + 2], w * (unsigned)uz);
