@@ -1054,43 +1054,94 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         }
         __syncthreads();
         PHASE_ADD(1);
-        // (1) per voxel: the smallest chamfer key over the candidates of its band
+        // (1) per voxel: the smallest chamfer key over the candidates of its band.  Triangle
+        // inequality of the chamfer metric: C(v, s) >= C(c, s) - C(c, v) for the sort centre c,
+        // so a voxel's scan ends once C(c, s) - C(c, v) exceeds its best; C(c, s) never decreases
+        // along a band's segment and the best only falls, so a voxel that stops never restarts.
+        // When a thread's voxels share one band they scan its segment together: each candidate
+        // is loaded once and evaluated for every voxel still scanning (4 independent chains).
+        {
+            unsigned long long bestv[kVPT], cvv[kVPT];
+            int bidxv[kVPT], xv[kVPT], yv[kVPT], zv[kVPT];
+            bool scanv[kVPT];
+            bool same = true;
+            int b0 = -1;
 #pragma unroll
-        for (int j = 0; j < kVPT; ++j) {
-            int i = tid + kRelaxThreads * j;
-            int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
-            const bool inb = x < d.nx && y < d.ny && z < d.nz;
-            unsigned long long best = kInfKey;
-            int bidx = -1;
-            if (inb && vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL) {
-                const int t0 = band_start[vb[j]], t1 = band_start[vb[j] + 1];
-                // triangle inequality of the chamfer metric: C(v, s) >= C(c, s) - C(c, v) for the
-                // sort centre c, so the scan ends once C(c, s) - C(c, v) exceeds the best
-                const unsigned long long cv = chamfer(x - (ox + RX / 2), y - (oy + RY / 2), z - (oz + RZ / 2));
-                for (int t = t0; t < t1; ++t) {
-                    unsigned long long e = ck[t];
-                    if (((e >> 12) & ((1ULL << 36) - 1)) > (best >> 32) + cv) break;
-                    int4 c = cs[(unsigned)(e & 0xFFF)];
-                    unsigned long long cd = chamfer(c.y - x, c.z - y, (c.w & 0xFFFFFF) - z);
-                    if (cd >= kInf32) continue;
-                    unsigned long long k2 = (cd << 32) | (unsigned)c.x;
-                    if (k2 < best) { best = k2; bidx = (int)(e & 0xFFF); }
+            for (int j = 0; j < kVPT; ++j) {
+                const int i = tid + kRelaxThreads * j;
+                xv[j] = ox + (i & (RX - 1));
+                yv[j] = oy + ((i >> 4) & (RY - 1));
+                zv[j] = oz + (i >> 7);
+                const bool inb = xv[j] < d.nx && yv[j] < d.ny && zv[j] < d.nz;
+                scanv[j] = inb && vb[j] != kInvalidBand && ok_list && Ub[vb[j]] != ~0ULL;
+                bestv[j] = kInfKey;
+                bidxv[j] = -1;
+                cvv[j] = chamfer(xv[j] - (ox + RX / 2), yv[j] - (oy + RY / 2), zv[j] - (oz + RZ / 2));
+                if (scanv[j]) {
+                    if (b0 < 0) b0 = vb[j];
+                    else if (vb[j] != b0) same = false;
                 }
             }
-            if (!complete && best != kInfKey) {
-                long long gap = 1LL << 40;
-                if (flx > 0) gap = min(gap, (long long)(x - flx + 1));
-                if (fhx < d.nx - 1) gap = min(gap, (long long)(fhx - x + 1));
-                if (fly > 0) gap = min(gap, (long long)(y - fly + 1));
-                if (fhy < d.ny - 1) gap = min(gap, (long long)(fhy - y + 1));
-                if (flz > 0) gap = min(gap, (long long)(z - flz + 1));
-                if (fhz < d.nz - 1) gap = min(gap, (long long)(fhz - z + 1));
-                if ((best >> 32) >= (unsigned long long)gap * kWFace) best = kInfKey;  // not settled
+            if (same && b0 >= 0) {
+                const int t0 = band_start[b0], t1 = band_start[b0 + 1];
+                for (int t = t0; t < t1; ++t) {
+                    const unsigned long long e = ck[t];
+                    const unsigned long long dc = (e >> 12) & ((1ULL << 36) - 1);
+                    bool act[kVPT], any = false;
+#pragma unroll
+                    for (int j = 0; j < kVPT; ++j) {
+                        act[j] = scanv[j] && dc <= (bestv[j] >> 32) + cvv[j];
+                        any |= act[j];
+                    }
+                    if (!any) break;
+                    const int4 c = cs[(unsigned)(e & 0xFFF)];
+                    const int cz = c.w & 0xFFFFFF;
+#pragma unroll
+                    for (int j = 0; j < kVPT; ++j) {
+                        if (!act[j]) continue;
+                        const unsigned long long cd = chamfer(c.y - xv[j], c.z - yv[j], cz - zv[j]);
+                        if (cd >= kInf32) continue;
+                        const unsigned long long k2 = (cd << 32) | (unsigned)c.x;
+                        if (k2 < bestv[j]) { bestv[j] = k2; bidxv[j] = (int)(e & 0xFFF); }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kVPT; ++j) {
+                    if (!scanv[j]) continue;
+                    const int t0 = band_start[vb[j]], t1 = band_start[vb[j] + 1];
+                    for (int t = t0; t < t1; ++t) {
+                        const unsigned long long e = ck[t];
+                        if (((e >> 12) & ((1ULL << 36) - 1)) > (bestv[j] >> 32) + cvv[j]) break;
+                        const int4 c = cs[(unsigned)(e & 0xFFF)];
+                        const unsigned long long cd = chamfer(c.y - xv[j], c.z - yv[j], (c.w & 0xFFFFFF) - zv[j]);
+                        if (cd >= kInf32) continue;
+                        const unsigned long long k2 = (cd << 32) | (unsigned)c.x;
+                        if (k2 < bestv[j]) { bestv[j] = k2; bidxv[j] = (int)(e & 0xFFF); }
+                    }
+                }
             }
-            if (best == kInfKey) bidx = -1;
-            vbest[i] = best;
-            vwin[i] = (short)bidx;
-            if (bidx >= 0) wcert[bidx] = 1;
+#pragma unroll
+            for (int j = 0; j < kVPT; ++j) {
+                const int i = tid + kRelaxThreads * j;
+                const int x = xv[j], y = yv[j], z = zv[j];
+                unsigned long long best = bestv[j];
+                int bidx = bidxv[j];
+                if (!complete && best != kInfKey) {
+                    long long gap = 1LL << 40;
+                    if (flx > 0) gap = min(gap, (long long)(x - flx + 1));
+                    if (fhx < d.nx - 1) gap = min(gap, (long long)(fhx - x + 1));
+                    if (fly > 0) gap = min(gap, (long long)(y - fly + 1));
+                    if (fhy < d.ny - 1) gap = min(gap, (long long)(fhy - y + 1));
+                    if (flz > 0) gap = min(gap, (long long)(z - flz + 1));
+                    if (fhz < d.nz - 1) gap = min(gap, (long long)(fhz - z + 1));
+                    if ((best >> 32) >= (unsigned long long)gap * kWFace) best = kInfKey;  // not settled
+                }
+                if (best == kInfKey) bidx = -1;
+                vbest[i] = best;
+                vwin[i] = (short)bidx;
+                if (bidx >= 0) wcert[bidx] = 1;
+            }
         }
         __syncthreads();
         PHASE_ADD(2);
