@@ -236,6 +236,14 @@ lsrvt_status lsrvt_merge_hierarchy(lsrvt_stats cells, const int32_t *n_sites_dev
                                    lsrvt_stats comps, lsrvt_stats bands, lsrvt_stats volume, void *ws,
                                    size_t ws_bytes, void *stream);
 
+/* Execution resources (the execution forms of Sec. 3.2 "Parallel Algorithm": independent
+ * blocks processed side by side).  Kernels launched on `stream` size their grids to `percent`
+ * of the GPU's SMs (1..100; 100 restores the whole GPU), so decompositions running
+ * concurrently on several streams share the GPU instead of each taking all of it.  Results
+ * do not depend on the share.  The setting is host-side, process-wide, and applies to
+ * launches made after the call; INVALID_ARG if percent is outside 1..100. */
+lsrvt_status lsrvt_set_stream_share(void *stream, int32_t percent);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,9 +77,11 @@ def lib():
         L.lsrvt_aggregate.argtypes = [P, P, i32, Dims, P, P, i32, u32, P, P, i32, Stats, P, sz, P, P]
         L.lsrvt_merge_hierarchy.argtypes = [Stats, P, i32, i32, i32, u32, P, P, P, i32, i32, Stats, Stats, Stats, P,
                                             sz, P]
+        L.lsrvt_set_stream_share.argtypes = [P, i32]
         for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
                      "lsrvt_saliency_grad", "lsrvt_seed",
-                     "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy"):
+                     "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy",
+                     "lsrvt_set_stream_share"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -88,7 +90,14 @@ def lib():
 def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
             "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
-            "lsrvt_aggregate", "lsrvt_merge_hierarchy"]
+            "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share"]
+
+
+def set_stream_share(percent, stream=None):
+    """Kernels launched on `stream` (default: the current stream) size their grids to `percent`
+    of the SMs (1..100), so decompositions on several streams run side by side."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().lsrvt_set_stream_share(C.c_void_p(s.cuda_stream), int(percent)), "lsrvt_set_stream_share")
 
 
 # --------------------------------------------------------------------------- helpers

@@ -1029,9 +1029,7 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
             }
         }
         const int64_t nbricks = (int64_t)((d.nx + GX - 1) / GX) * ((d.ny + GY - 1) / GY) * ((d.nz + GZ - 1) / GZ);
-        int dev = 0, nsm = kSMs;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int nsm = stream_sms(s);  // this stream's share of the SMs
         if (n_aux > 0)
             shift_table_kernel<<<grid_for((int64_t)max_sites * n_aux, 256, kSMs * 4), 256, 0, s>>>(
                 p, site_pos, n_sites_dev, max_sites, w.shift);
@@ -1071,9 +1069,7 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
         // CTAs take cell groups from a work counter, so a CTA that does not find room simply
         // starts later.
         const int occ = 3;
-        int dev2 = 0, nsm2 = kSMs;
-        cudaGetDevice(&dev2);
-        cudaDeviceGetAttribute(&nsm2, cudaDevAttrMultiProcessorCount, dev2);
+        const int nsm2 = stream_sms(s);
         covariance_kernel<<<nsm2 * occ, kCoThreads, kCoSmem, s>>>(w.perm, w.off, p, out.count, out.mean, out.m2,
                                                                    n_sites_dev, max_sites, w.work, out.comom,
                                                                    status_dev);

@@ -1,6 +1,9 @@
 // api.cu -- library-level entry points: status strings, version, workspace sizes.
 #include <cudaTypedefs.h>
 
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -61,9 +64,44 @@ bool encode_stack_map(CUtensorMap *map, const void *base, CUtensorMapDataType ty
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+namespace {
+std::mutex g_share_mu;
+std::vector<std::pair<cudaStream_t, int>> g_share;  // stream -> percent of the SMs
+}  // namespace
+
+int stream_sms(cudaStream_t s) {
+    static const int nsm = []() {
+        int dev = 0, n = kSMs;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : kSMs;
+    }();
+    std::lock_guard<std::mutex> lk(g_share_mu);
+    for (const auto &e : g_share)
+        if (e.first == s) {
+            const int k = (int)((int64_t)nsm * e.second / 100);
+            return k > 0 ? k : 1;
+        }
+    return nsm;
+}
+
 }  // namespace lsrvt
 
 using namespace lsrvt;
+
+extern "C" lsrvt_status lsrvt_set_stream_share(void *stream, int32_t percent) {
+    if (percent < 1 || percent > 100) return LSRVT_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    std::lock_guard<std::mutex> lk(g_share_mu);
+    for (size_t i = 0; i < g_share.size(); ++i)
+        if (g_share[i].first == s) {
+            if (percent == 100) g_share.erase(g_share.begin() + (long)i);
+            else g_share[i].second = percent;
+            return LSRVT_OK;
+        }
+    if (percent < 100) g_share.emplace_back(s, percent);
+    return LSRVT_OK;
+}
 
 extern "C" const char *lsrvt_status_string(lsrvt_status s) {
     switch (s) {

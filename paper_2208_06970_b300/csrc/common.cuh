@@ -60,6 +60,10 @@ inline int grid_for(int64_t work, int threads, int max_blocks) {
     return (int)b;
 }
 
+// SMs that grid-wide launches on stream s may size their grids to (the stream's share of the
+// GPU, lsrvt_set_stream_share; the whole GPU by default)
+int stream_sms(cudaStream_t s);
+
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -1711,6 +1711,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     (void)n;
     CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
     int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
+    const int sms = stream_sms(s);  // this stream's share of the SMs
     cudaMemsetAsync(w.counters + 1, 0, sizeof(int32_t) * 4, s);
     cudaMemsetAsync(w.counters + 6, 0, sizeof(int32_t), s);
     cudaMemsetAsync(w.fine_off, 0, sizeof(int64_t) * (nbricks + 1), s);
@@ -1732,7 +1733,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     {
         size_t smem = kCellGather * sizeof(int4);
         cudaFuncSetAttribute(cell_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int cgrid2 = (int)(ncoarse < (int64_t)kSMs * 4 ? ncoarse : (int64_t)kSMs * 4);
+        int cgrid2 = (int)(ncoarse < (int64_t)sms * 4 ? ncoarse : (int64_t)sms * 4);
         cell_list_kernel<<<cgrid2, kCellThreads, smem, s>>>(d, cg, w.cell_bands, w.coarse_off, w.coarse_cand,
                                                             w.cell_list, w.cell_count);
     }
@@ -1740,11 +1741,11 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int nb_cfi = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cfi, cfi_kernel, kRelaxThreads, 0);
     if (nb_cfi < 1) nb_cfi = 1;
-    int cgrid = (int)(nbricks < (int64_t)kSMs * nb_cfi ? nbricks : (int64_t)kSMs * nb_cfi);
+    int cgrid = (int)(nbricks < (int64_t)sms * nb_cfi ? nbricks : (int64_t)sms * nb_cfi);
     cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
                                                w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, w.xmask,
                                                w.hasunk, tag, up, chk);
-    check_paths_kernel<<<kSMs * 16, 256, 0, s>>>(band, w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
+    check_paths_kernel<<<sms * 16, 256, 0, s>>>(band, w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
                                                  tag, w.list[0], w.counters + 1, chk, up);
 #ifdef LSRVT_DEBUG
     {
@@ -1757,9 +1758,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int nb_per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, relax_persistent_kernel, kRelaxThreads, 0);
     if (nb_per_sm < 1) nb_per_sm = 1;
-    int dev = 0, nsm = kSMs;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nsm = sms;
     // at most one CTA per brick: small volumes leave the rest of the GPU to concurrent work
     int grid = (int)((int64_t)nsm * nb_per_sm < nbricks ? (int64_t)nsm * nb_per_sm : nbricks);
     cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), s);
@@ -1823,7 +1822,8 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
                                                                                                 w.cell_bands);
     }
     uint32_t tag = 0;
-    int vgrid = grid_for((n + 31) / 32 * 32, 256, kSMs * 16);
+    const int sms = stream_sms(s);
+    int vgrid = grid_for((n + 31) / 32 * 32, 256, sms * 16);
     UpdateOut up{true, small, q, site_pos, w.sums, w.los_bits, w.plist, w.counters + 5};
     UpdateOut no_up{false, small, q, site_pos, nullptr, nullptr, nullptr, nullptr};
     const int64_t nwords = (n + 31) / 32;
@@ -1836,7 +1836,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
                                                    w.nonlos, w.counters, w.plist, w.counters + 5, small);
-        update_nonlos_kernel<<<kSMs * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
+        update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
             band, d, site_pos, n_sites_dev, max_sites, w.sums,

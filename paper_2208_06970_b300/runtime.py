@@ -1,8 +1,9 @@
 """Execution forms of the hot path: batched blocks and a continuous-batching server.
 
 Both drive the C ABI (all compute in liblsrvt) from host worker threads, one CUDA stream and
-one workspace per slot; ctypes releases the GIL during library calls, so the slots' kernels
-overlap on the device.  The paper's distributed form processes independent blocks with no
+one workspace per slot; ctypes releases the GIL during library calls, and each slot's stream
+sizes its grids to a share of the SMs (lsrvt_set_stream_share), so the slots' kernels run side
+by side on the device.  The paper's distributed form processes independent blocks with no
 communication (Sec. 3.2 "Parallel Algorithm", Discussion "Block Based Distributed
 Parallelism"); here independent blocks / requests share one GPU instead.
 
@@ -18,7 +19,7 @@ import time
 
 import torch
 
-from . import decompose, Workspace
+from . import decompose, set_stream_share, Workspace
 
 
 def request_bytes(n_voxels, n_aux, voxels_per_site, n_bins=32):
@@ -34,10 +35,17 @@ def job_bytes(job):
     return request_bytes(job["field"].numel(), len(job.get("aux", ())), job["voxels_per_site"], job.get("n_bins", 32))
 
 
+def default_share(n_slots):
+    """Share of the SMs each of n_slots concurrent slots sizes its grids to: 150 / n_slots
+    percent (a mild oversubscription, so a slot running alone still gets a fair part)."""
+    return max(1, min(100, 150 // max(int(n_slots), 1)))
+
+
 class Slot:
-    def __init__(self, device):
+    def __init__(self, device, share=100):
         self.stream = torch.cuda.Stream(device=device)
         self.ws = Workspace(device)
+        set_stream_share(share, self.stream)
 
 
 def _run(slot, job):
@@ -53,8 +61,9 @@ def _run(slot, job):
 class BatchRunner:
     """Runs many independent blocks concurrently on n_slots streams (a block per slot at a time)."""
 
-    def __init__(self, n_slots=4, device="cuda"):
-        self.slots = [Slot(device) for _ in range(n_slots)]
+    def __init__(self, n_slots=4, device="cuda", share=None):
+        share = default_share(n_slots) if share is None else share
+        self.slots = [Slot(device, share) for _ in range(n_slots)]
 
     def run(self, jobs):
         results = [None] * len(jobs)
@@ -94,8 +103,9 @@ class Server:
     their estimated device bytes fit in the remaining HBM budget; admitted requests run
     concurrently on the slots' streams.  Latency = completion - arrival (host clock)."""
 
-    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda"):
-        self.slots = [Slot(device) for _ in range(n_slots)]
+    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda", share=None):
+        share = default_share(n_slots) if share is None else share
+        self.slots = [Slot(device, share) for _ in range(n_slots)]
         self.budget = int(hbm_budget)
 
     def serve(self, requests, make_job, keep_outputs=False):
