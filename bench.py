@@ -348,9 +348,24 @@ def forms_arm(args, dev):
         runner.run(jobs)
         torch.cuda.synchronize()
         res[name] = vox_it / (time.perf_counter() - t0) / 1e9
+    # the same batch captured once as one CUDA graph (all blocks on the slots' streams), then
+    # replayed: one launch per batch
+    gb = runtime.GraphBatch(jobs, n_slots=args.slots, device=dev)
+    gb.replay()
+    torch.cuda.synchronize()
+    gb.check()
+    reps = 2
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        gb.replay()
+    torch.cuda.synchronize()
+    res["graph"] = reps * vox_it / (time.perf_counter() - t0) / 1e9
+    del gb
+    torch.cuda.empty_cache()
     out["batched"] = dict(blocks=len(jobs), voxels=int(sum(j["field"].numel() for j in jobs)), slots=args.slots,
                           plain_gvoxel_iters_s=res["plain"], batched_gvoxel_iters_s=res["batched"],
-                          speedup=res["batched"] / res["plain"])
+                          speedup=res["batched"] / res["plain"], graph_gvoxel_iters_s=res["graph"],
+                          graph_speedup=res["graph"] / res["plain"])
     del jobs, blocks
     torch.cuda.empty_cache()
     # ---- serving

@@ -8,6 +8,7 @@ communication (Sec. 3.2 "Parallel Algorithm", Discussion "Block Based Distribute
 Parallelism"); here independent blocks / requests share one GPU instead.
 
   BatchRunner(n_slots).run(jobs)     -> results in job order
+  GraphBatch(jobs, n_slots).replay() -> results in job order, the batch replayed as one CUDA graph
   Server(n_slots, hbm_budget).serve(requests, make_job) -> per-request records
 
 A job is a dict: field (CUDA float32 (nz, ny, nx)), iso, voxels_per_site, n_iters, aux (list
@@ -96,6 +97,57 @@ class BatchRunner:
         if errors:
             raise errors[0]
         return results
+
+
+class GraphBatch:
+    """A batch of independent blocks captured once into one CUDA graph and replayed with one
+    launch per batch: the blocks are dealt to n_slots streams (forked from and joined back into
+    the capturing stream), each stream runs its blocks in order, and every step of every
+    block is a library kernel recorded in the graph.  Inputs are read from the jobs' tensors at
+    replay time, so new data written into the same tensors (the next time step of a volume)
+    is decomposed by the next replay; outputs live in the graph's memory pool and are
+    overwritten by each replay.  All data-dependent control (queues, counters, rounds) is on
+    the device, so no host synchronisation breaks the capture."""
+
+    def __init__(self, jobs, n_slots=4, device="cuda", share=None):
+        share = default_share(n_slots) if share is None else share
+        self.jobs = jobs
+        self.slots = [Slot(device, share) for _ in range(n_slots)]
+        self.device = device
+        # eager warm-up: sizes every slot's workspace and loads the kernels before capture
+        for k, job in enumerate(jobs):
+            slot = self.slots[k % n_slots]
+            out, done = _run(slot, job)
+            done.synchronize()
+        torch.cuda.synchronize(device)
+        self.graph = torch.cuda.CUDAGraph()
+        main = torch.cuda.Stream(device=device)
+        main.wait_stream(torch.cuda.current_stream(device))
+        self.outputs = [None] * len(jobs)
+        with torch.cuda.graph(self.graph, stream=main):
+            for slot in self.slots:
+                slot.stream.wait_stream(main)
+            for k, job in enumerate(jobs):
+                slot = self.slots[k % n_slots]
+                with torch.cuda.stream(slot.stream):
+                    self.outputs[k] = decompose(job["field"], job["iso"], job["voxels_per_site"], job["n_iters"],
+                                                aux=job.get("aux", ()), gamma=job.get("gamma", 0),
+                                                strat_block=job.get("strat_block", 16),
+                                                rng_seed=job.get("rng_seed", 0), n_bins=job.get("n_bins", 32),
+                                                ws=slot.ws, check=False)
+            for slot in self.slots:
+                main.wait_stream(slot.stream)
+        torch.cuda.synchronize(device)
+
+    def replay(self):
+        """One launch of the whole batch; returns the per-block outputs (graph-owned tensors)."""
+        self.graph.replay()
+        return self.outputs
+
+    def check(self):
+        from . import check_status
+        for k, out in enumerate(self.outputs):
+            check_status(out["status"], "block %d" % k)
 
 
 class Server:

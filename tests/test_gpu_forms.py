@@ -52,6 +52,26 @@ def test_batched_blocks_equal_alone(pk):
         _same(pk, a, b)
 
 
+def test_graph_batch_equals_alone(pk):
+    # the batch captured as one CUDA graph: every replay decomposes what the input tensors hold
+    # at replay time, and equals each block run alone (labels bit for bit)
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(5, 24, 64, 9)
+    gb = runtime.GraphBatch(jobs, n_slots=2)
+    for step in range(2):
+        if step == 1:  # the next "time step": new data in the same tensors
+            for k, j in enumerate(jobs):
+                nxt = workloads.blob_field(tuple(j["field"].shape[::-1]), 100 + k, "cuda")
+                j["field"].copy_(nxt)
+        got = gb.replay()
+        torch.cuda.synchronize()
+        gb.check()
+        for j, g in zip(jobs, got):
+            alone = pk.decompose(j["field"], j["iso"], j["voxels_per_site"], j["n_iters"], aux=j["aux"],
+                                 rng_seed=j["rng_seed"])
+            _same(pk, alone, g)
+
+
 def test_served_requests_equal_alone(pk):
     from paper_2208_06970_b300 import runtime
     jobs = _jobs(8, 24, 64, 5)
