@@ -339,9 +339,12 @@ def forms_arm(args, dev):
                  aux=[b["aux"][j] for j in range(b["aux"].shape[0])], gamma=0, strat_block=16,
                  rng_seed=b["rng_seed"], n_bins=32) for b in blocks]
     vox_it = sum(j["field"].numel() * j["n_iters"] for j in jobs)
+    # the batching schedule (slots, SM share per slot) picked by the autotuner on a sample of
+    # 16 blocks (untimed; every candidate is checked to reproduce the labels)
+    best, tune_times = runtime.tune_batch(jobs[:16], device=dev)
     res = {}
-    for name, slots in (("plain", 1), ("batched", args.slots)):
-        runner = runtime.BatchRunner(n_slots=slots, device=dev)
+    for name, (slots, share) in (("plain", (1, 100)), ("batched", best)):
+        runner = runtime.BatchRunner(n_slots=slots, device=dev, share=share)
         runner.run(jobs[:2])  # warm the slots' workspaces
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -350,7 +353,7 @@ def forms_arm(args, dev):
         res[name] = vox_it / (time.perf_counter() - t0) / 1e9
     # the same batch captured once as one CUDA graph (all blocks on the slots' streams), then
     # replayed: one launch per batch
-    gb = runtime.GraphBatch(jobs, n_slots=args.slots, device=dev)
+    gb = runtime.GraphBatch(jobs, n_slots=best[0], device=dev, share=best[1])
     gb.replay()
     torch.cuda.synchronize()
     gb.check()
@@ -362,7 +365,8 @@ def forms_arm(args, dev):
     res["graph"] = reps * vox_it / (time.perf_counter() - t0) / 1e9
     del gb
     torch.cuda.empty_cache()
-    out["batched"] = dict(blocks=len(jobs), voxels=int(sum(j["field"].numel() for j in jobs)), slots=args.slots,
+    out["batched"] = dict(blocks=len(jobs), voxels=int(sum(j["field"].numel() for j in jobs)), slots=best[0],
+                          share_pct=best[1], tuned={"%d/%d" % k: v for k, v in tune_times.items()},
                           plain_gvoxel_iters_s=res["plain"], batched_gvoxel_iters_s=res["batched"],
                           speedup=res["batched"] / res["plain"], graph_gvoxel_iters_s=res["graph"],
                           graph_speedup=res["graph"] / res["plain"])

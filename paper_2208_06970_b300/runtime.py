@@ -10,6 +10,7 @@ Parallelism"); here independent blocks / requests share one GPU instead.
   BatchRunner(n_slots).run(jobs)     -> results in job order
   GraphBatch(jobs, n_slots).replay() -> results in job order, the batch replayed as one CUDA graph
   Server(n_slots, hbm_budget).serve(requests, make_job) -> per-request records
+  tune_batch(sample_jobs) -> the fastest (slots, share) schedule, checked to leave results unchanged
 
 A job is a dict: field (CUDA float32 (nz, ny, nx)), iso, voxels_per_site, n_iters, aux (list
 of CUDA tensors), gamma, strat_block, rng_seed, n_bins.
@@ -217,6 +218,31 @@ class Server:
         if state["error"] is not None:
             raise state["error"]
         return records
+
+
+def tune_batch(jobs, candidates=((1, 100), (2, 75), (4, 37), (4, 25), (8, 18)), device="cuda", reps=1):
+    """Autotuner of the batching schedule: runs the sample `jobs` under each (slots, share)
+    candidate, checks that every candidate reproduces the first one's labels bit for bit
+    (the schedule must not change results), and returns (best candidate, {candidate: seconds})."""
+    times, ref = {}, None
+    for slots, share in candidates:
+        runner = BatchRunner(n_slots=slots, device=device, share=share)
+        runner.run(jobs[: min(len(jobs), slots)])  # warm the slots' workspaces
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            outs = runner.run(jobs)
+        torch.cuda.synchronize(device)
+        times[(slots, share)] = (time.perf_counter() - t0) / reps
+        if ref is None:
+            ref = outs
+        else:
+            for a, b in zip(ref, outs):
+                for k in ("band", "comp", "cell"):
+                    if not torch.equal(a[k], b[k]):
+                        raise RuntimeError("schedule (%d, %d) changed %s" % (slots, share, k))
+    best = min(times, key=times.get)
+    return best, times
 
 
 def latency_summary(records):

@@ -72,6 +72,13 @@ def test_graph_batch_equals_alone(pk):
             _same(pk, alone, g)
 
 
+def test_autotuner_picks_a_schedule_without_changing_results(pk):
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(4, 24, 56, 13)
+    best, times = runtime.tune_batch(jobs, candidates=((1, 100), (2, 75), (4, 25)))
+    assert best in times and len(times) == 3 and all(t > 0 for t in times.values())
+
+
 def test_served_requests_equal_alone(pk):
     from paper_2208_06970_b300 import runtime
     jobs = _jobs(8, 24, 64, 5)
