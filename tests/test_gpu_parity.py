@@ -320,3 +320,59 @@ def test_cvt_rerun_and_resume_bit_identical(pk):
         assert all(np.array_equal(a, b) for a, b in zip(r, runs[0]))
     s_ref, c_ref, d_ref, _ = oracle.cvt_iterate(cpu(band), cpu(q).view(np.uint16), cpu(sp)[:int(ns.item())], 7)
     assert np.array_equal(runs[0][0][:int(ns.item())], s_ref) and np.array_equal(runs[0][1], c_ref)
+
+
+def _oracle_pipeline(f, iso, P, n_iters, aux, n_bins=32):
+    band = oracle.classify(f, iso)
+    comp, cb, cs, cf = oracle.label_components(band)
+    sp, sc, off, nc = oracle.seed(comp, None, len(cb), P, 16, 7)
+    sp2, cell, dist, tr = oracle.cvt_iterate(band, None, sp, n_iters)
+    stats = oracle.aggregate(cell, aux, len(sp2), n_bins=n_bins) if len(sp2) else None
+    return band, comp, cb, sp2, cell, dist, stats
+
+
+@pytest.mark.parametrize("case", ["all_invalid", "single_voxel", "constant", "single_seed", "checkerboard"])
+def test_degenerate_volumes_end_to_end(pk, case):
+    """The whole path on degenerate inputs against the oracle pipeline: a volume with no graph
+    nodes (all NaN), one voxel, a constant field (one band, one component: a plain discrete
+    CVT of the box), one site for the whole component, and a checkerboard where every voxel is
+    its own component and site."""
+    iso = np.array([0.2, 0.4, 0.6, 0.8], np.float32)
+    P, n_iters = 512, 3
+    if case == "all_invalid":
+        f = np.full((8, 8, 8), np.nan, np.float32)
+    elif case == "single_voxel":
+        f = np.full((1, 1, 1), 0.5, np.float32)
+    elif case == "constant":
+        f = np.full((16, 20, 24), 0.5, np.float32)
+    elif case == "single_seed":
+        f = np.full((16, 16, 16), 0.5, np.float32)
+        P = 1 << 20
+    else:
+        z, y, x = np.indices((8, 9, 10))
+        f = ((x + y + z) % 2).astype(np.float32) * np.float32(0.9)
+        iso = np.array([0.5], np.float32)
+    aux = np.stack([np.where(np.isnan(f), 0.0, f).astype(np.float32),
+                    (np.arange(f.size, dtype=np.float32).reshape(f.shape) * np.float32(0.01))])
+    band, comp, cb, sp, cell, dist, stats = _oracle_pipeline(f, iso, P, n_iters, aux)
+    out = pk.decompose(torch.from_numpy(f).cuda(), iso, P, n_iters, aux=[torch.from_numpy(a).cuda() for a in aux],
+                       rng_seed=7)
+    ns = int(out["n_sites"].item())
+    assert ns == len(sp)
+    assert int(out["n_comp"].item()) == len(cb)
+    assert np.array_equal(cpu(out["band"]), band)
+    assert np.array_equal(cpu(out["comp"]), comp)
+    assert np.array_equal(cpu(out["site_pos"])[:ns], sp)
+    assert np.array_equal(cpu(out["cell"]), cell)
+    assert np.array_equal(cpu(out["dist"]).view(np.uint32), dist.view(np.uint32))
+    if case == "single_seed":
+        assert ns == 1 and np.all(cell == 0)
+    if case == "checkerboard":
+        # every voxel is its own component, site and cell (site ids follow the (band, component) order)
+        assert ns == f.size and np.array_equal(sp[cell.ravel()], np.arange(f.size))
+    if stats is not None:
+        got = out["cells"]
+        assert np.array_equal(cpu(got["count"])[:ns], stats["count"])
+        assert np.array_equal(cpu(got["min"])[:ns], stats["min"]) and np.array_equal(cpu(got["max"])[:ns], stats["max"])
+        assert np.array_equal(cpu(got["hist"])[:ns].view(np.uint32), stats["hist"])
+        _moment_ok(cpu(got["mean"])[:ns], cpu(got["m2"])[:ns], stats["mean"], stats["m2"], stats["count"])
