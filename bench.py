@@ -148,8 +148,8 @@ class Pipeline:
         comps, bands, vol = pk.merge_hierarchy(cells, ns, off, cb, nc, self.max_comp, self.n_bands, N_BINS,
                                                ws=self.ws)
         mark("merge")
-        self.last = dict(band=band, cell=cell, site_pos=sp, n_sites=ns, n_comp=nc, cells=cells, comps=comps,
-                         bands=bands, volume=vol, trace=trace)
+        self.last = dict(band=band, cell=cell, site_pos=sp, n_sites=ns, n_comp=nc, comp_site_off=off,
+                         comp_band=cb, cells=cells, comps=comps, bands=bands, volume=vol, trace=trace)
         return self.last
 
 
@@ -274,11 +274,46 @@ def gpu_arm(args, rank, world, local_rank):
     e2e = dict(value=n * N_ITERS / (e_ms * 1e-3) / 1e9, unit=UNIT, h2d_bytes_per_step=int(h2d),
                d2h_bytes_per_step=int(d2h), ms_per_step=e_ms, api="decompose_host")
     del h_aux, bufs
+    layout = layout_arm(pkg, pipe, s)
     res = dict(ms=ms, phase=phase, clk=clk, n_sites=n_sites, n_comp=n_comp, trace=trace, t_assign=t_assign,
                t_iter=t_iter,
                achieved=achieved, peak=pk, stats_gbs=stats_gbs, cvt_ms=cvt_ms, launches=launches_per_step,
-               kernels=kernel_names, e2e=e2e, n=n, field=field, aux=aux, iso=iso)
+               kernels=kernel_names, e2e=e2e, n=n, field=field, aux=aux, iso=iso, layout=layout)
     return res
+
+
+def layout_arm(pkg, pipe, s, reps=3):
+    """The structured hierarchical layout of the last step's decomposition (all bands, every
+    variable): compaction, stable radix sort by cell, offsets, extraction of the variables.
+    Algorithmic bytes: the cell labels read once, one coordinate written and every variable
+    read and written once per kept voxel."""
+    L = pipe.last
+    m = len(pipe.aux)
+    max_sites = L["site_pos"].numel()
+
+    def run(out=None):
+        return pkg.structured_layout(L["cell"], L["n_sites"], max_sites, L["comp_site_off"], L["comp_band"],
+                                     L["n_comp"], pipe.max_comp, aux=pipe.aux, ws=pipe.ws, status=pipe.status,
+                                     out=out)
+    out = run()
+    torch.cuda.synchronize()
+    pkg.check_status(pipe.status, "layout")
+    r = int(out["n_kept"].item())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        run(out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    alg = pipe.n * 4 + r * (4 + 8 * m)
+    gbs = alg / (ms * 1e-3) / 1e9
+    pk = peaks()
+    return dict(ms=ms, kept_voxels=r, variables=m, algorithmic_bytes=int(alg), algorithmic_gbs=gbs,
+                frac=gbs / pk["hbm"], peak_source=pk["src"],
+                what="voxels of all bands ordered by (band, component, cell, index) + offsets + "
+                     "extraction of every variable in layout order")
 
 
 # --------------------------------------------------------------------------- oracle arm
@@ -557,7 +592,7 @@ def main():
             phases_ms=r["phase"], cvt_gvoxel_iters_per_s=n * N_ITERS / (r["cvt_ms"] * 1e-3) / 1e9,
             moved_per_iter=r["trace"][:, 0].tolist(), clocks=r["clk"], e2e=r["e2e"],
             gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu,
-            forms=forms, precision=precision)
+            layout=r["layout"], forms=forms, precision=precision)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -61,7 +61,8 @@ typedef enum {
     LSRVT_STEP_SEED = 3,
     LSRVT_STEP_CVT = 4,
     LSRVT_STEP_AGGREGATE = 5,
-    LSRVT_STEP_MERGE = 6
+    LSRVT_STEP_MERGE = 6,
+    LSRVT_STEP_LAYOUT = 7
 } lsrvt_step;
 
 /* Seeding parameters (Sec. 3.2 "Stratified Random Initial Site Distribution", Eq. nc;
@@ -235,6 +236,35 @@ lsrvt_status lsrvt_merge_hierarchy(lsrvt_stats cells, const int32_t *n_sites_dev
                                    const int32_t *n_comp_dev, int32_t max_comp, int32_t n_bands,
                                    lsrvt_stats comps, lsrvt_stats bands, lsrvt_stats volume, void *ws,
                                    size_t ws_bytes, void *stream);
+
+/* Structured hierarchical data layout (Sec. 3.2 "Data Reduction and Structured Data Layout",
+ * Fig. hierarchy): the voxels of the kept isobands ordered by (band, component, cell) and,
+ * inside a cell, by linear index, so that every band, component and cell is one contiguous,
+ * directly indexable range, with the raw variables extracted in the same order (one
+ * coordinate -- the linear index -- plus n_aux values per kept voxel).
+ * Site ids must be grouped by component in ascending order and components ordered by band,
+ * as lsrvt_label_components and lsrvt_seed number them.
+ *   cell [N] int32 (in; -1 = not a node; 16-byte aligned);
+ *   comp_site_off [n_comp+1] int32 (from lsrvt_seed), comp_band [n_comp] uint8 (in);
+ *   band_mask_host [8] uint32 (host; bit b%32 of word b/32 keeps band b; NULL = all bands);
+ *   aux_host[n_aux] device pointers to [N] float (in); values_host[n_aux] device pointers to
+ *   [N] float (out, 16-byte aligned; entries < *n_kept_dev written), n_aux <= 64;
+ *   order [N] int32 (out, 16-byte aligned): linear voxel index of each layout position
+ *   (entries < *n_kept_dev written; the rest are scratch);
+ *   cell_off [max_sites+1], comp_off [max_comp+1] int64 (out): cell s occupies
+ *   [cell_off[s], cell_off[s+1]), component c [comp_off[c], comp_off[c+1]); entries
+ *   <= *n_sites_dev / *n_comp_dev written;
+ *   band_off [257] int64 (out): band b occupies [band_off[b], band_off[b+1]);
+ *   n_kept_dev [1] int64 (out): number of voxels in the layout.
+ * Deterministic (stable sort).  Errors: INVALID_ARG synchronously (dims, NULL, alignment,
+ * n_aux), and in status_dev when a cell id has no site or the numbering is not hierarchical. */
+lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims d, const int32_t *n_sites_dev,
+                                     int32_t max_sites, const int32_t *comp_site_off, const uint8_t *comp_band,
+                                     const int32_t *n_comp_dev, int32_t max_comp, const uint32_t *band_mask_host,
+                                     const float *const *aux_host, int32_t n_aux, float *const *values_host,
+                                     int32_t *order, int64_t *cell_off, int64_t *comp_off, int64_t *band_off,
+                                     int64_t *n_kept_dev, void *ws, size_t ws_bytes, int32_t *status_dev,
+                                     void *stream);
 
 /* Execution resources (the execution forms of Sec. 3.2 "Parallel Algorithm": independent
  * blocks processed side by side).  Kernels launched on `stream` size their grids to `percent`

@@ -21,6 +21,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                       invariants (sites stay in their component)
   aggregate           numpy per-cell statistics (np.var/np.cov definitions)
   merge               direct per-component / per-band statistics
+  layout              brute-force contiguity and membership of every band, component and
+                      cell range; per-cell counts and means against aggregate
 """
 import ctypes as C
 import numpy as np
@@ -63,6 +65,7 @@ def lib():
         L.orc_certify.argtypes = [P, i32, i32, i32, P, i32, P, P]
         L.orc_certify.restype = i64
         L.orc_sssp.argtypes = [P, i32, i32, i32, i32, P]
+        L.orc_layout.argtypes = [P, i64, P, i32, P, i32, P, P, i32, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -281,6 +284,34 @@ def merge_hierarchy(cell_stats, site_comp, comp_band, n_bands):
     bands = merge(comps, np.asarray(comp_band, dtype=np.int32), n_bands)
     vol = merge(bands, np.zeros(n_bands, np.int32), 1)
     return comps, bands, vol
+
+
+def layout(cell, site_comp, comp_band, aux=None, bands=None):
+    """Structured data layout (Sec. 3.2 "Data Reduction and Structured Data Layout"): kept
+    voxels ordered by (band, component, cell, linear index).  bands: iterable of kept band
+    ids (None = all).  Returns dict(order, values (m, r), cell_off, comp_off, band_off, n_kept)."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32).ravel()
+    site_comp = np.ascontiguousarray(site_comp, dtype=np.int32)
+    comp_band = np.ascontiguousarray(comp_band, dtype=np.uint8)
+    n = cell.size
+    aux = np.zeros((0, n), np.float32) if aux is None or np.asarray(aux).size == 0 else \
+        np.ascontiguousarray(aux, dtype=np.float32).reshape(-1, n)
+    m = aux.shape[0]
+    mask = np.zeros(8, np.uint32)
+    for b in (range(256) if bands is None else bands):
+        mask[int(b) >> 5] |= np.uint32(1 << (int(b) & 31))
+    S, K = site_comp.size, comp_band.size
+    order = np.empty(max(n, 1), np.int32)
+    values = np.empty((max(m, 1), n), np.float32)
+    cell_off = np.empty(S + 1, np.int64)
+    comp_off = np.empty(K + 1, np.int64)
+    band_off = np.empty(257, np.int64)
+    nk = np.zeros(1, np.int64)
+    _check(lib().orc_layout(_p(cell), n, _p(site_comp), S, _p(comp_band), K, _p(mask), _p(aux), m, _p(order),
+                            _p(values), _p(cell_off), _p(comp_off), _p(band_off), _p(nk)), "layout")
+    r = int(nk[0])
+    return dict(order=order[:r], values=values[:m, :r], cell_off=cell_off, comp_off=comp_off, band_off=band_off,
+                n_kept=r)
 
 
 # --------------------------------------------------------------------------- checkers

@@ -961,3 +961,87 @@ int orc_sssp(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz, int32_t sr
     free(h.a);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Structured data layout.  Sec. 3.2 "Data Reduction and Structured Data      */
+/* Layout" and Fig. hierarchy: the kept data is ordered hierarchically by     */
+/* layer (isoband) and connected component so that each layer and component  */
+/* is contiguous and directly indexable through offsets; the raw values are   */
+/* extracted next to one coordinate per voxel.                                */
+/* Readings: a voxel is kept when the band of its cell's component is in the  */
+/* caller's band set; the order is (band, component, cell, linear index), the */
+/* coordinate is the linear index, and offsets are given for bands,           */
+/* components and cells (the position where each would start, also when it   */
+/* holds no kept voxel).  The keys are compared as tuples, so the result does */
+/* not depend on how the ids happen to be numbered.                           */
+/* ------------------------------------------------------------------------- */
+typedef struct { int32_t band, comp, cell, v; } orc_lkey;
+
+static int lkey_cmp(const void *a, const void *b)
+{
+    const orc_lkey *p = (const orc_lkey *)a, *q = (const orc_lkey *)b;
+    if (p->band != q->band) return p->band < q->band ? -1 : 1;
+    if (p->comp != q->comp) return p->comp < q->comp ? -1 : 1;
+    if (p->cell != q->cell) return p->cell < q->cell ? -1 : 1;
+    if (p->v != q->v) return p->v < q->v ? -1 : 1;
+    return 0;
+}
+
+int orc_layout(const int32_t *cell, int64_t n, const int32_t *site_comp, int32_t n_sites,
+               const uint8_t *comp_band, int32_t n_comp, const uint32_t *band_mask,
+               const float *aux, int32_t m, int32_t *order, float *values,
+               int64_t *cell_off, int64_t *comp_off, int64_t *band_off, int64_t *n_kept)
+{
+    if (n < 0 || n_sites < 0 || n_comp < 0 || m < 0) return ORC_EINVAL;
+    for (int32_t s = 0; s < n_sites; ++s)
+        if (site_comp[s] < 0 || site_comp[s] >= n_comp) return ORC_EINVAL;
+    orc_lkey *keys = (orc_lkey *)malloc(sizeof(orc_lkey) * (size_t)(n > 0 ? n : 1));
+    int64_t *ccnt = (int64_t *)calloc((size_t)n_sites + 1, sizeof(int64_t));
+    int64_t *kcnt = (int64_t *)calloc((size_t)n_comp + 1, sizeof(int64_t));
+    orc_lkey *cells = (orc_lkey *)malloc(sizeof(orc_lkey) * ((size_t)n_sites + 1));
+    orc_lkey *comps = (orc_lkey *)malloc(sizeof(orc_lkey) * ((size_t)n_comp + 1));
+    if (!keys || !ccnt || !kcnt || !cells || !comps) {
+        free(keys); free(ccnt); free(kcnt); free(cells); free(comps);
+        return ORC_ENOMEM;
+    }
+    int64_t r = 0, bcnt[257];
+    memset(bcnt, 0, sizeof(bcnt));
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t s = cell[v];
+        if (s < 0) continue;
+        if (s >= n_sites) {
+            free(keys); free(ccnt); free(kcnt); free(cells); free(comps);
+            return ORC_EINVAL;
+        }
+        int32_t c = site_comp[s];
+        int32_t b = comp_band[c];
+        if (!((band_mask[b >> 5] >> (b & 31)) & 1u)) continue;
+        keys[r].band = b; keys[r].comp = c; keys[r].cell = s; keys[r].v = (int32_t)v;
+        ++r;
+        ++ccnt[s]; ++kcnt[c]; ++bcnt[b];
+    }
+    qsort(keys, (size_t)r, sizeof(orc_lkey), lkey_cmp);
+    for (int64_t p = 0; p < r; ++p) {
+        order[p] = keys[p].v;
+        for (int32_t j = 0; j < m; ++j) values[(int64_t)j * n + p] = aux[(int64_t)j * n + keys[p].v];
+    }
+    /* cells in layout order: (band, component, cell) */
+    for (int32_t s = 0; s < n_sites; ++s) {
+        cells[s].band = comp_band[site_comp[s]]; cells[s].comp = site_comp[s]; cells[s].cell = s; cells[s].v = 0;
+    }
+    qsort(cells, (size_t)n_sites, sizeof(orc_lkey), lkey_cmp);
+    int64_t run = 0;
+    for (int32_t k = 0; k < n_sites; ++k) { cell_off[cells[k].cell] = run; run += ccnt[cells[k].cell]; }
+    cell_off[n_sites] = r;
+    for (int32_t c = 0; c < n_comp; ++c) { comps[c].band = comp_band[c]; comps[c].comp = c; comps[c].cell = 0; comps[c].v = 0; }
+    qsort(comps, (size_t)n_comp, sizeof(orc_lkey), lkey_cmp);
+    run = 0;
+    for (int32_t k = 0; k < n_comp; ++k) { comp_off[comps[k].comp] = run; run += kcnt[comps[k].comp]; }
+    comp_off[n_comp] = r;
+    run = 0;
+    for (int b = 0; b < 256; ++b) { band_off[b] = run; run += bcnt[b]; }
+    band_off[256] = r;
+    *n_kept = r;
+    free(keys); free(ccnt); free(kcnt); free(cells); free(comps);
+    return ORC_OK;
+}

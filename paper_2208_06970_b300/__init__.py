@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(HERE, "liblsrvt.so")
 STATUS = {0: "ok", 1: "invalid argument", 2: "isovalues not strictly increasing", 3: "capacity exceeded",
           4: "non-finite input value", 5: "device loop limit reached", 6: "geodesic distance overflow",
           7: "CUDA launch failure", 8: "workspace missing, misaligned or too small"}
-STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6)
+STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7)
 STATS_HIST = 1
 STATS_COV = 2
 
@@ -78,10 +78,11 @@ def lib():
         L.lsrvt_merge_hierarchy.argtypes = [Stats, P, i32, i32, i32, u32, P, P, P, i32, i32, Stats, Stats, Stats, P,
                                             sz, P]
         L.lsrvt_set_stream_share.argtypes = [P, i32]
+        L.lsrvt_structured_layout.argtypes = [P, Dims, P, i32, P, P, P, i32, P, P, i32, P, P, P, P, P, P, P, sz, P, P]
         for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
                      "lsrvt_saliency_grad", "lsrvt_seed",
                      "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy",
-                     "lsrvt_set_stream_share"):
+                     "lsrvt_set_stream_share", "lsrvt_structured_layout"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -90,7 +91,7 @@ def lib():
 def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
             "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
-            "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share"]
+            "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout"]
 
 
 def set_stream_share(percent, stream=None):
@@ -350,6 +351,48 @@ def merge_hierarchy(cells, n_sites_dev, comp_site_off, comp_band, n_comp_dev, ma
                                        int(n_bands), _stats_struct(comps), _stats_struct(bands), _stats_struct(vol),
                                        _ptr(buf), buf.numel(), _stream()), "lsrvt_merge_hierarchy")
     return comps, bands, vol
+
+
+def structured_layout(cell, n_sites_dev, max_sites, comp_site_off, comp_band, n_comp_dev, max_comp, aux=(),
+                      bands=None, ws=None, status=None, out=None):
+    """Structured hierarchical layout (Sec. 3.2 "Data Reduction and Structured Data Layout"):
+    the voxels of the kept bands (`bands`: iterable of band ids, None = all) ordered by
+    (band, component, cell, linear index), with offsets per cell / component / band and the
+    variables gathered in the same order.  Returns a dict of device tensors: order [N] int32
+    and values (m, N) float32 (first n_kept entries valid), cell_off [max_sites+1],
+    comp_off [max_comp+1], band_off [257] int64, n_kept [1] int64."""
+    aux = [a.contiguous() for a in aux]
+    _require_cuda(cell, comp_site_off, comp_band, *aux)
+    dev = cell.device
+    n = cell.numel()
+    m = len(aux)
+    status = new_status(dev) if status is None else status
+    if out is None:
+        out = dict(order=torch.empty(n, dtype=torch.int32, device=dev),
+                   # rows padded to a multiple of 4 floats: every row starts 16-byte aligned
+                   values=torch.empty((max(m, 1), (n + 3) // 4 * 4), dtype=torch.float32, device=dev)[:, :n],
+                   cell_off=torch.empty(max_sites + 1, dtype=torch.int64, device=dev),
+                   comp_off=torch.empty(max_comp + 1, dtype=torch.int64, device=dev),
+                   band_off=torch.empty(257, dtype=torch.int64, device=dev),
+                   n_kept=torch.empty(1, dtype=torch.int64, device=dev))
+    mask = None
+    if bands is not None:
+        words = [0] * 8
+        for b in bands:
+            words[int(b) >> 5] |= 1 << (int(b) & 31)
+        mask = (C.c_uint32 * 8)(*words)
+    ws = ws or Workspace(dev)
+    buf = ws.get(workspace_bytes("layout", _dims(cell), max_sites=max_sites))
+    ins = _aux_ptrs(aux)
+    outs = (C.c_void_p * max(m, 1))(*[out["values"][j].data_ptr() for j in range(m)])
+    _check(lib().lsrvt_structured_layout(_ptr(cell), _dims(cell), _ptr(n_sites_dev), int(max_sites),
+                                         _ptr(comp_site_off), _ptr(comp_band), _ptr(n_comp_dev), int(max_comp),
+                                         C.cast(mask, C.c_void_p) if mask is not None else None,
+                                         C.cast(ins, C.c_void_p), m, C.cast(outs, C.c_void_p), _ptr(out["order"]),
+                                         _ptr(out["cell_off"]), _ptr(out["comp_off"]), _ptr(out["band_off"]),
+                                         _ptr(out["n_kept"]), _ptr(buf), buf.numel(), _ptr(status), _stream()),
+           "lsrvt_structured_layout")
+    return out
 
 
 def _dims_of_nothing():

@@ -15,6 +15,7 @@ int64_t seed_default_strata(Dims d, int32_t sb, int32_t max_comp);
 size_t cvt_workspace(Dims d, int32_t max_sites);
 size_t aggregate_workspace(Dims d, int32_t max_sites, int32_t m);
 size_t merge_workspace(int32_t max_sites, int32_t max_comp, int32_t n_bands, int32_t m);
+size_t layout_workspace(Dims d, int32_t max_sites);
 }  // namespace lsrvt
 
 namespace lsrvt {
@@ -138,6 +139,7 @@ extern "C" size_t lsrvt_workspace_bytes(lsrvt_step step, lsrvt_dims dd, int32_t 
         case LSRVT_STEP_CVT: return cvt_workspace(d, max_sites);
         case LSRVT_STEP_AGGREGATE: return aggregate_workspace(d, max_sites, n_aux);
         case LSRVT_STEP_MERGE: return merge_workspace(max_sites, max_comp, 255, n_aux);
+        case LSRVT_STEP_LAYOUT: return layout_workspace(d, max_sites > 0 ? max_sites : 1);
     }
     return 0;
 }

@@ -100,6 +100,9 @@ __host__ __device__ __forceinline__ float ordered_to_float(unsigned u) {
 // Temporary storage: scan_temp_bytes(n).
 size_t scan_temp_bytes(int64_t n);
 void exclusive_scan_i64(int64_t *data, int64_t n, int64_t *total, void *temp, cudaStream_t s);
+// The same over the first *n_dev (device) entries, n_dev <= n; temp sized for n.
+void exclusive_scan_i64_dev(int64_t *data, int64_t n, const int64_t *n_dev, int64_t *total, void *temp,
+                           cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) uint32 pairs by the low `bits` bits of key.
 size_t radix_temp_bytes(int64_t n);

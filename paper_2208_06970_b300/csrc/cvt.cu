@@ -489,7 +489,8 @@ __device__ __forceinline__ unsigned long long udiv_fast(unsigned long long a, un
 // stays within L-infinity 2 of the digital path (per axis the rounding errors of the path
 // and of the segment's voxel add up to at most 2), so margin 2 also certifies line of sight.
 #ifdef LSRVT_DEBUG
-__device__ unsigned long long g_path_dbg[8];  // checks cov=0, cov>0, steps, jumps, status 0/1/2
+__device__ unsigned long long g_path_dbg[12];  // checks cov=0, cov>0, -, -, status 0/1/2, sub-box tubes
+                                               // 4x4x4 / 8x4x4 / 2x2x2 that would certify, los upgrades
 #endif
 // mv_start > 0: the moves before it are already known to be in band with a margin of 2
 // (a brick tube certificate covered them); the walk starts there.
@@ -1350,9 +1351,26 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
             decode_voxel((uint32_t)p, d, px, py, pz);
             const int cs = __ldg(clr + p);
             status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, cs, mv0);
+#ifdef LSRVT_DEBUG
+            atomicAdd(&g_path_dbg[mv0 > 0 ? 1 : 0], 1ULL);
+            atomicAdd(&g_path_dbg[4 + status], 1ULL);
+            for (int sb = 0; sb < 3; ++sb) {
+                const int mx = sb == 0 ? 3 : (sb == 1 ? 7 : 1), myz = sb == 2 ? 1 : 3;
+                const int lx = x & ~mx, ly = y & ~myz, lz = z & ~myz;
+                const int hx = min(lx + mx, d.nx - 1), hy = min(ly + myz, d.ny - 1), hz = min(lz + myz, d.nz - 1);
+                const int cov = brick_tube_in_band(clr, d, lx, ly, lz, hx, hy, hz, px, py, pz);
+                const int L2 = max(abs(2 * px - lx - hx), max(abs(2 * py - ly - hy), abs(2 * pz - lz - hz)));
+                if (cov >= max(L2, 1)) atomicAdd(&g_path_dbg[7 + sb], 1ULL);
+            }
+#endif
             // an exact key without the margin certificate: walk Eq. 2's traversal now (the
             // update pass keeps only the voxels without line of sight, for their parents)
-            if (status == 1 && up.enabled && los_clear(band, clr, d, x, y, z, px, py, pz, cs)) status = 2;
+            if (status == 1 && up.enabled && los_clear(band, clr, d, x, y, z, px, py, pz, cs)) {
+                status = 2;
+#ifdef LSRVT_DEBUG
+                atomicAdd(&g_path_dbg[10], 1ULL);
+#endif
+            }
             if (status == 0) {
                 key[g] = kInfKey;
                 const int64_t brick = x / RX + (int64_t)bg.nbx * (y / RY + (int64_t)bg.nby * (z / RZ));
@@ -1859,11 +1877,12 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
                 fprintf(stderr, " [%d: %llu, %llu, %.0f]", r, rt[2][r], rt[1][r], rt[0][r] / 1e3);
             fprintf(stderr, "\n");
         }
-        unsigned long long pd[8], pz[8] = {0};
+        unsigned long long pd[12], pz[12] = {0};
         cudaMemcpyFromSymbol(pd, g_path_dbg, sizeof(pd));
         cudaMemcpyToSymbol(g_path_dbg, pz, sizeof(pz));
-        fprintf(stderr, "path checks: from start %llu after tube prefix %llu | steps %llu jumps %llu | status0 %llu "
-                "status1 %llu status2 %llu\n", pd[0], pd[1], pd[2], pd[3], pd[4], pd[5], pd[6]);
+        fprintf(stderr, "path checks: from start %llu after tube prefix %llu | status0 %llu status1 %llu status2 %llu "
+                "| sub-box tubes 4x4x4 %llu 8x4x4 %llu 2x2x2 %llu | los upgrades %llu\n", pd[0], pd[1], pd[4], pd[5],
+                pd[6], pd[7], pd[8], pd[9], pd[10]);
         fprintf(stderr, "cfi chamfer-evals %llu | update: pending warps %llu pending voxels %llu los-walks true %llu "
                 "nonlos %llu los-cycles %.3g\n", ph[10], ph[2], ph[4], ph[9], ph[7], (double)ph[6]);
         unsigned long long cp[8], cz[8] = {0};

@@ -42,7 +42,19 @@ __device__ int64_t block_exclusive_scan(int64_t v, int64_t *out_excl) {
     return total;
 }
 
-__global__ void scan_reduce_kernel(const int64_t *data, int64_t n, int64_t *tile_sums) {
+// n_dev (nullable): a device-side count <= n; entries at and beyond it are left alone
+__device__ __forceinline__ int64_t scan_n(int64_t n, const int64_t *n_dev) {
+    if (!n_dev) return n;
+    const int64_t m = *n_dev;
+    return m < n ? (m < 0 ? 0 : m) : n;
+}
+
+__global__ void scan_reduce_kernel(const int64_t *data, int64_t n, const int64_t *n_dev, int64_t *tile_sums) {
+    n = scan_n(n, n_dev);
+    if ((int64_t)blockIdx.x * kScanTile >= n) {  // a tile past the live entries sums to 0
+        if (threadIdx.x == 0) tile_sums[blockIdx.x] = 0;
+        return;
+    }
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t s = 0;
 #pragma unroll
@@ -67,7 +79,9 @@ __global__ void scan_tiles_kernel(int64_t *tile_sums, int64_t ntiles, int64_t *t
     if (threadIdx.x == 0 && total) *total = carry;
 }
 
-__global__ void scan_apply_kernel(int64_t *data, int64_t n, const int64_t *tile_offs) {
+__global__ void scan_apply_kernel(int64_t *data, int64_t n, const int64_t *n_dev, const int64_t *tile_offs) {
+    n = scan_n(n, n_dev);
+    if ((int64_t)blockIdx.x * kScanTile >= n) return;
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
     int64_t s = 0;
@@ -100,66 +114,83 @@ __device__ __forceinline__ int64_t radix_n(int64_t n, const int32_t *n_dev) {
     return n;
 }
 
+// Tiles of the live items (device count): ceil(n / kRadixTile).  The histogram is digit-major
+// over the live tiles, hist[d * ntiles + tile], so its exclusive scan (over 256 * ntiles entries)
+// gives every (digit, tile) its output offset.  Kernels loop over the live tiles with a fixed
+// grid, so a large capacity costs no idle blocks.
+__device__ __forceinline__ int64_t radix_tiles(int64_t n) { return (n + kRadixTile - 1) / kRadixTile; }
+
+__global__ void radix_count_kernel(int64_t n_max, const int32_t *n_dev, int64_t *hist_n) {
+    *hist_n = radix_tiles(radix_n(n_max, n_dev)) * 256;
+}
+
 __global__ void radix_hist_kernel(const uint32_t *keys, int64_t n_max, const int32_t *n_dev, int shift,
-                                  int64_t ntiles, int64_t *hist) {
+                                  int64_t *hist) {
     __shared__ unsigned cnt[256];
-    int64_t n = radix_n(n_max, n_dev);
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    for (int i = threadIdx.x; i < kRadixTile; i += blockDim.x) {
-        int64_t j = base + i;
-        if (j < n) atomicAdd(&cnt[(keys[j] >> shift) & 255u], 1u);
+    const int64_t n = radix_n(n_max, n_dev);
+    const int64_t ntiles = radix_tiles(n);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        const int64_t base = tile * kRadixTile;
+        for (int i = threadIdx.x; i < kRadixTile; i += blockDim.x) {
+            const int64_t j = base + i;
+            if (j < n) atomicAdd(&cnt[(keys[j] >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntiles + tile] = cnt[d];
+        __syncthreads();
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = cnt[d];
 }
 
 __global__ void radix_scatter_kernel(const uint32_t *keys, const uint32_t *vals, uint32_t *okeys, uint32_t *ovals,
-                                     int64_t n_max, const int32_t *n_dev, int shift, int64_t ntiles,
-                                     const int64_t *offs) {
+                                     int64_t n_max, const int32_t *n_dev, int shift, const int64_t *offs) {
     __shared__ unsigned wcnt[kRadixWarps][256];
-    int64_t n = radix_n(n_max, n_dev);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    int64_t wbase = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * kRadixPerWarp;
-    // pass 1: per-warp digit counts
-    for (int r = 0; r < kRadixPerWarp; r += 32) {
-        int64_t j = wbase + r + lane;
-        bool ok = j < n;
-        unsigned d = ok ? ((keys[j] >> shift) & 255u) : 256u;
-        unsigned m = __match_any_sync(0xffffffffu, d);
-        if (ok && (m & lanemask_lt()) == 0) wcnt[w][d] += __popc(m);
-        __syncwarp();
-    }
-    __syncthreads();
-    // exclusive prefix over warps per digit, plus the global offset of this tile
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-        unsigned run = 0;
-        for (int k = 0; k < kRadixWarps; ++k) {
-            unsigned c = wcnt[k][d];
-            wcnt[k][d] = run;
-            run += c;
+    const int64_t n = radix_n(n_max, n_dev);
+    const int64_t ntiles = radix_tiles(n);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t wbase = tile * kRadixTile + (int64_t)w * kRadixPerWarp;
+        // pass 1: per-warp digit counts
+        for (int r = 0; r < kRadixPerWarp; r += 32) {
+            const int64_t j = wbase + r + lane;
+            const bool ok = j < n;
+            const unsigned d = ok ? ((keys[j] >> shift) & 255u) : 256u;
+            const unsigned m = __match_any_sync(0xffffffffu, d);
+            if (ok && (m & lanemask_lt()) == 0) wcnt[w][d] += __popc(m);
+            __syncwarp();
         }
-    }
-    __syncthreads();
-    // pass 2: stable placement
-    for (int r = 0; r < kRadixPerWarp; r += 32) {
-        int64_t j = wbase + r + lane;
-        bool ok = j < n;
-        uint32_t key = ok ? keys[j] : 0u;
-        unsigned d = ok ? ((key >> shift) & 255u) : 256u;
-        unsigned m = __match_any_sync(0xffffffffu, d);
-        if (ok) {
-            unsigned rank = __popc(m & lanemask_lt());
-            int64_t pos = offs[(int64_t)d * ntiles + blockIdx.x] + wcnt[w][d] + rank;
-            okeys[pos] = key;
-            ovals[pos] = vals[j];
+        __syncthreads();
+        // exclusive prefix over warps per digit
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+            unsigned run = 0;
+            for (int k = 0; k < kRadixWarps; ++k) {
+                const unsigned c = wcnt[k][d];
+                wcnt[k][d] = run;
+                run += c;
+            }
         }
-        __syncwarp();
-        if (ok && (m & lanemask_lt()) == 0) wcnt[w][d] += __popc(m);
-        __syncwarp();
+        __syncthreads();
+        // pass 2: stable placement
+        for (int r = 0; r < kRadixPerWarp; r += 32) {
+            const int64_t j = wbase + r + lane;
+            const bool ok = j < n;
+            const uint32_t key = ok ? keys[j] : 0u;
+            const unsigned d = ok ? ((key >> shift) & 255u) : 256u;
+            const unsigned m = __match_any_sync(0xffffffffu, d);
+            if (ok) {
+                const unsigned rank = __popc(m & lanemask_lt());
+                const int64_t pos = offs[(int64_t)d * ntiles + tile] + wcnt[w][d] + rank;
+                okeys[pos] = key;
+                ovals[pos] = vals[j];
+            }
+            __syncwarp();
+            if (ok && (m & lanemask_lt()) == 0) wcnt[w][d] += __popc(m);
+            __syncwarp();
+        }
+        __syncthreads();
     }
 }
 
@@ -170,16 +201,21 @@ size_t scan_temp_bytes(int64_t n) {
     return (size_t)(ntiles > 0 ? ntiles : 1) * sizeof(int64_t) + 256;
 }
 
-void exclusive_scan_i64(int64_t *data, int64_t n, int64_t *total, void *temp, cudaStream_t s) {
+void exclusive_scan_i64_dev(int64_t *data, int64_t n, const int64_t *n_dev, int64_t *total, void *temp,
+                           cudaStream_t s) {
     int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     int64_t *tile = (int64_t *)temp;
     if (ntiles == 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(int64_t), s);
         return;
     }
-    scan_reduce_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(data, n, tile);
+    scan_reduce_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(data, n, n_dev, tile);
     scan_tiles_kernel<<<1, 1024, 0, s>>>(tile, ntiles, total);
-    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(data, n, tile);
+    scan_apply_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(data, n, n_dev, tile);
+}
+
+void exclusive_scan_i64(int64_t *data, int64_t n, int64_t *total, void *temp, cudaStream_t s) {
+    exclusive_scan_i64_dev(data, n, nullptr, total, temp, s);
 }
 
 size_t radix_temp_bytes(int64_t n) {
@@ -189,6 +225,7 @@ size_t radix_temp_bytes(int64_t n) {
     b += ((size_t)n * 4 + 256) * 2;                  // ping-pong keys + values
     b += (size_t)ntiles * 256 * sizeof(int64_t) + 256;  // histograms
     b += scan_temp_bytes(ntiles * 256) + 256;
+    b += 256;                                        // live histogram length
     return b;
 }
 
@@ -201,17 +238,20 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, const int32_t *
     uint32_t *v2 = c.take<uint32_t>(n);
     int64_t *hist = c.take<int64_t>(ntiles * 256);
     void *stemp = c.take<char>(scan_temp_bytes(ntiles * 256));
+    int64_t *hist_n = c.take<int64_t>(1);
     uint32_t *ka = keys, *va = vals, *kb = k2, *vb = v2;
     int passes = (bits + 7) / 8;
     if (passes < 1) passes = 1;
     if (passes & 1) passes += 1;  // even number of passes: the result lands back in keys/vals
+    const int sms = stream_sms(s);
+    const int grid = (int)(ntiles < sms * 8 ? ntiles : sms * 8);
+    radix_count_kernel<<<1, 1, 0, s>>>(n, n_dev, hist_n);
     for (int p = 0; p < passes; ++p) {
         int shift = p * 8;
         if (shift >= 32) shift = 24;  // padding pass on an already-sorted top digit is stable
-        radix_hist_kernel<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(ka, n, n_dev, shift, ntiles, hist);
-        exclusive_scan_i64(hist, ntiles * 256, nullptr, stemp, s);
-        radix_scatter_kernel<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, ntiles,
-                                                                      hist);
+        radix_hist_kernel<<<grid, kRadixThreads, 0, s>>>(ka, n, n_dev, shift, hist);
+        exclusive_scan_i64_dev(hist, ntiles * 256, hist_n, nullptr, stemp, s);
+        radix_scatter_kernel<<<grid, kRadixThreads, 0, s>>>(ka, va, kb, vb, n, n_dev, shift, hist);
         uint32_t *t = ka; ka = kb; kb = t;
         t = va; va = vb; vb = t;
     }

@@ -162,6 +162,52 @@ def test_full_statistics_sampled_cells_and_merge(full):
         _moment_ok(cpu(g["mean"])[:k], cpu(g["m2"])[:k], r["mean"], r["m2"], r["count"])
 
 
+def test_full_layout_properties(full):
+    """The structured layout of the full-size decomposition (all bands, every variable),
+    checked by the properties that define a stable sort by (band, component, cell, index):
+    the kept voxels are the graph nodes, (cell, index) strictly increases along the layout,
+    the cell ranges hold the per-cell counts, component and band offsets are the cell offsets
+    of their first cells and the band prefix counts, and the values are the variables at the
+    recorded coordinates.  A band subset equals the full layout's band ranges concatenated."""
+    pk, pipe, out, bench = full["pk"], full["pipe"], full["out"], full["bench"]
+    aux = [full["w"]["aux"][j] for j in range(bench.N_AUX)]
+    max_sites = out["site_pos"].numel()
+    args = (out["cell"], out["n_sites"], max_sites, out["comp_site_off"], out["comp_band"], out["n_comp"],
+            pipe.max_comp)
+    lay = pk.structured_layout(*args, aux=aux, ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "layout")
+    flat = out["cell"].reshape(-1)
+    r = int(lay["n_kept"].item())
+    assert r == int((flat >= 0).sum().item())
+    order = lay["order"][:r].long()
+    key = flat[order].long() * (1 << 32) + order
+    assert bool((key[1:] > key[:-1]).all())
+    del key
+    ns, nc = int(out["n_sites"].item()), int(out["n_comp"].item())
+    cnt = torch.bincount(flat[flat >= 0].long(), minlength=ns)
+    co = lay["cell_off"]
+    assert int(co[0].item()) == 0 and torch.equal(co[1:ns + 1] - co[:ns], cnt)
+    off = out["comp_site_off"][:nc + 1].long()
+    assert torch.equal(lay["comp_off"][:nc + 1], co[off])
+    band = out["band"].reshape(-1)
+    bc = torch.bincount(band[band != 255].long(), minlength=256)[:256]
+    want = torch.zeros(257, dtype=torch.int64, device=bc.device)
+    want[1:] = torch.cumsum(bc, 0)
+    assert torch.equal(lay["band_off"], want)
+    for j in range(len(aux)):
+        assert torch.equal(lay["values"][j, :r], aux[j].reshape(-1)[order])
+    keep = [3, 4]
+    sub = pk.structured_layout(*args, aux=aux[:2], bands=keep, ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "layout subset")
+    bo = lay["band_off"].tolist()
+    rs = int(sub["n_kept"].item())
+    assert rs == bo[5] - bo[3]
+    assert torch.equal(sub["order"][:rs], lay["order"][bo[3]:bo[5]])
+    assert torch.equal(sub["values"][:2, :rs], lay["values"][:2, bo[3]:bo[5]])
+
+
 @pytest.fixture(scope="module")
 def precision():
     if not torch.cuda.is_available():
