@@ -502,6 +502,27 @@ def profile_step(args):
     print("profile step ok: %d sites" % int(pipe.last["n_sites"].item()))
 
 
+def profile_layout(args):
+    """One step of the workload, then two structured layouts of it (ncu target)."""
+    import paper_2208_06970_b300 as pkg
+    import workloads
+    from paper_2208_06970_b300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    w = workloads.flame_workload(side=args.side, seed=2, device=dev, n_aux=N_AUX, n_iters=N_ITERS)
+    pipe = Pipeline(pkg, w["field"], [w["aux"][j] for j in range(N_AUX)], w["iso"])
+    pipe.step()
+    L = pipe.last
+    out = None
+    for _ in range(2):
+        out = pkg.structured_layout(L["cell"], L["n_sites"], L["site_pos"].numel(), L["comp_site_off"],
+                                    L["comp_band"], L["n_comp"], pipe.max_comp, aux=pipe.aux, ws=pipe.ws,
+                                    status=pipe.status, out=out)
+    torch.cuda.synchronize()
+    pkg.check_status(pipe.status, "profile layout")
+    print("profile layout ok: %d voxels" % int(out["n_kept"].item()))
+
+
 def profile_precision(args):
     """The precision form's inputs, then two moment + co-moment aggregations (ncu target)."""
     import paper_2208_06970_b300 as pkg
@@ -536,6 +557,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
     ap.add_argument("--profile-precision", action="store_true",
                     help="build the precision-form inputs and run two co-moment aggregations (for ncu)")
+    ap.add_argument("--profile-layout", action="store_true",
+                    help="one step, then two structured layouts of it (for ncu)")
     ap.add_argument("--profile-step", action="store_true",
                     help="generate the workload and run two plain steps (for ncu); prints nothing else")
     args = ap.parse_args()
@@ -551,6 +574,9 @@ def main():
         return
     if args.profile_precision:
         profile_precision(args)
+        return
+    if args.profile_layout:
+        profile_layout(args)
         return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))

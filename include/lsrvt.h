@@ -248,16 +248,17 @@ lsrvt_status lsrvt_merge_hierarchy(lsrvt_stats cells, const int32_t *n_sites_dev
  *   comp_site_off [n_comp+1] int32 (from lsrvt_seed), comp_band [n_comp] uint8 (in);
  *   band_mask_host [8] uint32 (host; bit b%32 of word b/32 keeps band b; NULL = all bands);
  *   aux_host[n_aux] device pointers to [N] float (in); values_host[n_aux] device pointers to
- *   [N] float (out, 16-byte aligned; entries < *n_kept_dev written), n_aux <= 64;
- *   order [N] int32 (out, 16-byte aligned): linear voxel index of each layout position
- *   (entries < *n_kept_dev written; the rest are scratch);
+ *   [N] float (out; entries < *n_kept_dev written), n_aux <= 64;
+ *   order [N] int32 (out): linear voxel index of each layout position (entries < *n_kept_dev
+ *   written);
  *   cell_off [max_sites+1], comp_off [max_comp+1] int64 (out): cell s occupies
  *   [cell_off[s], cell_off[s+1]), component c [comp_off[c], comp_off[c+1]); entries
  *   <= *n_sites_dev / *n_comp_dev written;
  *   band_off [257] int64 (out): band b occupies [band_off[b], band_off[b+1]);
  *   n_kept_dev [1] int64 (out): number of voxels in the layout.
- * Deterministic (stable sort).  Errors: INVALID_ARG synchronously (dims, NULL, alignment,
- * n_aux), and in status_dev when a cell id has no site or the numbering is not hierarchical. */
+ * Deterministic (stable sort).  Errors: INVALID_ARG synchronously (dims, NULL, cell not
+ * 16-byte aligned, n_aux), and in status_dev when a cell id has no site or the numbering is
+ * not hierarchical. */
 lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims d, const int32_t *n_sites_dev,
                                      int32_t max_sites, const int32_t *comp_site_off, const uint8_t *comp_band,
                                      const int32_t *n_comp_dev, int32_t max_comp, const uint32_t *band_mask_host,
