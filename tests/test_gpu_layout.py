@@ -122,3 +122,23 @@ def test_layout_reports_non_hierarchical_numbering(pk):
     got, st = _gpu_layout(pk, cell2, off, cb, np.zeros((0,) + cell.shape, np.float32), None, slack=10)
     torch.cuda.synchronize()
     assert int(st.item()) == 1
+
+
+def test_layout_store_roundtrip(pk, tmp_path):
+    # the GPU layout written to disk and read back one component at a time equals the oracle's
+    from paper_2208_06970_b300 import store
+    dims = (40, 33, 27)
+    cell, sc, off, cb = _case(dims, 13)
+    aux = workloads.correlated_aux(dims, 3, 13, "cpu")[0].numpy()
+    got, st = _gpu_layout(pk, cell, off, cb, aux, [1, 2], slack=7)
+    pk.check_status(st, "layout")
+    ref = oracle.layout(cell, sc, cb, aux, bands=[1, 2])
+    path = str(tmp_path / "g.lsrvt")
+    store.save(path, got, int(off[-1]), len(cb))
+    s = store.open_store(path)
+    assert s.meta["n_kept"] == ref["n_kept"]
+    for c in range(len(cb)):
+        coords, vals = s.component(c)
+        lo, hi = ref["comp_off"][c], ref["comp_off"][c + 1]
+        assert np.array_equal(coords, ref["order"][lo:hi])
+        assert np.array_equal(vals, ref["values"][:, lo:hi])
