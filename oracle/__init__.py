@@ -21,6 +21,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                       invariants (sites stay in their component)
   aggregate           numpy per-cell statistics (np.var/np.cov definitions)
   merge               direct per-component / per-band statistics
+  joint_moments       numpy einsum per region; shift invariance; symmetric data (odd
+                      orders vanish); merged records equal direct records of the union
   layout              brute-force contiguity and membership of every band, component and
                       cell range; per-cell counts and means against aggregate
 """
@@ -66,6 +68,8 @@ def lib():
         L.orc_certify.restype = i64
         L.orc_sssp.argtypes = [P, i32, i32, i32, i32, P]
         L.orc_layout.argtypes = [P, i64, P, i32, P, i32, P, P, i32, P, P, P, P, P, P]
+        L.orc_joint_ranges.argtypes = [P, i32, i64, P, P, i32, P, P, P, P, P]
+        L.orc_joint_merge.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -312,6 +316,46 @@ def layout(cell, site_comp, comp_band, aux=None, bands=None):
     r = int(nk[0])
     return dict(order=order[:r], values=values[:m, :r], cell_off=cell_off, comp_off=comp_off, band_off=band_off,
                 n_kept=r)
+
+
+def _tcounts(m):
+    from math import comb
+    return comb(m + 1, 2), comb(m + 2, 3), comb(m + 3, 4)
+
+
+def joint_moments(aux, order, off):
+    """Joint central moments of orders 2..4 (m <= 8 variables) over the ranges
+    [off[r], off[r+1]) of the voxel list `order` (e.g. a structured layout).  aux: (m, N).
+    Returns dict(count, mean (R, m), m2 (R, T2), m3 (R, T3), m4 (R, T4)); tuples i<=j<=k<=l
+    in lexicographic order."""
+    aux = np.ascontiguousarray(aux, dtype=np.float32)
+    aux = aux.reshape(aux.shape[0], -1)
+    m, n = aux.shape
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    R = off.size - 1
+    T2, T3, T4 = _tcounts(m)
+    out = dict(count=np.empty(R, np.int64), mean=np.empty((R, m)), m2=np.empty((R, T2)), m3=np.empty((R, T3)),
+               m4=np.empty((R, T4)))
+    _check(lib().orc_joint_ranges(_p(aux), m, n, _p(order), _p(off), R, _p(out["count"]), _p(out["mean"]),
+                                  _p(out["m2"]), _p(out["m3"]), _p(out["m4"])), "joint_moments")
+    return out
+
+
+def joint_merge(rec, child_off):
+    """Pairwise (Pebay 2008) merge of joint-moment records: parent p combines the children
+    [child_off[p], child_off[p+1]) in id order."""
+    child_off = np.ascontiguousarray(child_off, dtype=np.int64)
+    P = child_off.size - 1
+    m = rec["mean"].shape[1]
+    T2, T3, T4 = _tcounts(m)
+    out = dict(count=np.empty(P, np.int64), mean=np.empty((P, m)), m2=np.empty((P, T2)), m3=np.empty((P, T3)),
+               m4=np.empty((P, T4)))
+    c = {k: np.ascontiguousarray(v) for k, v in rec.items()}
+    _check(lib().orc_joint_merge(m, P, _p(child_off), _p(c["count"]), _p(c["mean"]), _p(c["m2"]), _p(c["m3"]),
+                                 _p(c["m4"]), _p(out["count"]), _p(out["mean"]), _p(out["m2"]), _p(out["m3"]),
+                                 _p(out["m4"])), "joint_merge")
+    return out
 
 
 # --------------------------------------------------------------------------- checkers

@@ -1045,3 +1045,174 @@ int orc_layout(const int32_t *cell, int64_t n, const int32_t *site_comp, int32_t
     free(keys); free(ccnt); free(kcnt); free(cells); free(comps);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Joint central moments of orders 2..4 (Sec. 3.3 and the joint-plot section: */
+/* mean, covariance, coskewness and cokurtosis of the variables of a region,  */
+/* compared between summaries and raw data).  For a set of n voxels with      */
+/* means mu and deviations d = x - mu (m <= 8 variables):                     */
+/*   M2[i<=j] = sum d_i d_j, M3[i<=j<=k] = sum d_i d_j d_k,                   */
+/*   M4[i<=j<=k<=l] = sum d_i d_j d_k d_l,                                    */
+/* tuples in lexicographic order.  Two passes in FP64 (mean, then sums).      */
+/* Regions are the ranges [off[r], off[r+1]) of a list of voxel indices (a    */
+/* structured layout), so cells, components and bands use the same code.      */
+/* ------------------------------------------------------------------------- */
+static int64_t binom_small(int64_t a, int64_t b)
+{
+    int64_t r = 1;
+    for (int64_t i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+    return r;
+}
+
+int orc_joint_ranges(const float *aux, int32_t m, int64_t n, const int32_t *order, const int64_t *off,
+                     int32_t n_ranges, int64_t *count, double *mean, double *m2, double *m3, double *m4)
+{
+    if (m < 1 || m > 8 || n < 0 || n_ranges < 0) return ORC_EINVAL;
+    int64_t T2 = binom_small(m + 1, 2), T3 = binom_small(m + 2, 3), T4 = binom_small(m + 3, 4);
+    for (int32_t r = 0; r < n_ranges; ++r) {
+        int64_t lo = off[r], hi = off[r + 1];
+        double mu[8] = {0};
+        for (int64_t p = lo; p < hi; ++p)
+            for (int32_t j = 0; j < m; ++j) mu[j] += (double)aux[(int64_t)j * n + order[p]];
+        int64_t c = hi - lo;
+        for (int32_t j = 0; j < m; ++j) mu[j] = c ? mu[j] / (double)c : 0.0;
+        double *o2 = m2 + (int64_t)r * T2, *o3 = m3 + (int64_t)r * T3, *o4 = m4 + (int64_t)r * T4;
+        for (int64_t t = 0; t < T2; ++t) o2[t] = 0.0;
+        for (int64_t t = 0; t < T3; ++t) o3[t] = 0.0;
+        for (int64_t t = 0; t < T4; ++t) o4[t] = 0.0;
+        for (int64_t p = lo; p < hi; ++p) {
+            double d[8];
+            for (int32_t j = 0; j < m; ++j) d[j] = (double)aux[(int64_t)j * n + order[p]] - mu[j];
+            int64_t t2 = 0, t3 = 0, t4 = 0;
+            for (int i = 0; i < m; ++i)
+                for (int j = i; j < m; ++j) {
+                    o2[t2++] += d[i] * d[j];
+                    for (int k = j; k < m; ++k) {
+                        o3[t3++] += d[i] * d[j] * d[k];
+                        for (int l = k; l < m; ++l) o4[t4++] += d[i] * d[j] * d[k] * d[l];
+                    }
+                }
+        }
+        count[r] = c;
+        for (int32_t j = 0; j < m; ++j) mean[(int64_t)r * m + j] = mu[j];
+    }
+    return ORC_OK;
+}
+
+/* index of a sorted tuple in the lexicographic list of non-decreasing tuples of length q over m */
+static int64_t tuple_index(const int *t, int q, int m)
+{
+    /* count the tuples that come before t: for each position, the tuples with a smaller
+       value there and the same prefix */
+    int64_t idx = 0;
+    int prev = 0;
+    for (int pos = 0; pos < q; ++pos) {
+        for (int v = prev; v < t[pos]; ++v) idx += binom_small(m - v + (q - pos - 1) - 1, q - pos - 1);
+        prev = t[pos];
+    }
+    return idx;
+}
+
+static double get_sym(const double *a, int q, int m, int i, int j, int k, int l)
+{
+    int t[4] = {i, j, k, l};
+    /* sort the first q indices */
+    for (int x = 1; x < q; ++x)
+        for (int y = x; y > 0 && t[y - 1] > t[y]; --y) { int s = t[y]; t[y] = t[y - 1]; t[y - 1] = s; }
+    return a[tuple_index(t, q, m)];
+}
+
+/* Pairwise merge of two joint-moment records (Pebay, "Formulas for robust, one-pass parallel
+   computation of covariances and arbitrary-order statistical moments", Sandia SAND2008-6212,
+   2008): with n = nA + nB and delta = muB - muA,
+     M2 = M2A + M2B + dd nA nB / n
+     M3 = M3A + M3B + ddd nA nB (nA - nB) / n^2 + (1/n) sum_3 d_i (nA M2B_jk - nB M2A_jk)
+     M4 = M4A + M4B + dddd nA nB (nA^2 - nA nB + nB^2) / n^3
+          + (1/n^2) sum_6 d_i d_j (nA^2 M2B_kl + nB^2 M2A_kl) + (1/n) sum_4 d_i (nA M3B_jkl - nB M3A_jkl)
+   the sums running over the distinct ways to split the index tuple. */
+static void joint_merge_into(int m, int64_t *nA_, double *muA, double *A2, double *A3, double *A4, int64_t nB_,
+                             const double *muB, const double *B2, const double *B3, const double *B4)
+{
+    if (nB_ == 0) return;
+    int64_t T2 = binom_small(m + 1, 2), T3 = binom_small(m + 2, 3), T4 = binom_small(m + 3, 4);
+    if (*nA_ == 0) {
+        *nA_ = nB_;
+        for (int j = 0; j < m; ++j) muA[j] = muB[j];
+        for (int64_t t = 0; t < T2; ++t) A2[t] = B2[t];
+        for (int64_t t = 0; t < T3; ++t) A3[t] = B3[t];
+        for (int64_t t = 0; t < T4; ++t) A4[t] = B4[t];
+        return;
+    }
+    double nA = (double)*nA_, nB = (double)nB_, n = nA + nB;
+    double d[8];
+    for (int j = 0; j < m; ++j) d[j] = muB[j] - muA[j];
+    double *N2 = (double *)malloc(sizeof(double) * (size_t)(T2 + T3 + T4));
+    double *N3 = N2 + T2, *N4 = N3 + T3;
+    int64_t t2 = 0, t3 = 0, t4 = 0;
+    for (int i = 0; i < m; ++i)
+        for (int j = i; j < m; ++j) {
+            N2[t2] = A2[t2] + B2[t2] + d[i] * d[j] * nA * nB / n;
+            ++t2;
+            for (int k = j; k < m; ++k) {
+                double s3 = d[i] * (nA * get_sym(B2, 2, m, j, k, 0, 0) - nB * get_sym(A2, 2, m, j, k, 0, 0)) +
+                            d[j] * (nA * get_sym(B2, 2, m, i, k, 0, 0) - nB * get_sym(A2, 2, m, i, k, 0, 0)) +
+                            d[k] * (nA * get_sym(B2, 2, m, i, j, 0, 0) - nB * get_sym(A2, 2, m, i, j, 0, 0));
+                N3[t3] = A3[t3] + B3[t3] + d[i] * d[j] * d[k] * nA * nB * (nA - nB) / (n * n) + s3 / n;
+                ++t3;
+                for (int l = k; l < m; ++l) {
+                    int ix[4] = {i, j, k, l};
+                    double s6 = 0.0, s4 = 0.0;
+                    for (int a = 0; a < 4; ++a)
+                        for (int b = a + 1; b < 4; ++b) {
+                            int rest[2], q = 0;
+                            for (int c = 0; c < 4; ++c)
+                                if (c != a && c != b) rest[q++] = ix[c];
+                            s6 += d[ix[a]] * d[ix[b]] *
+                                  (nA * nA * get_sym(B2, 2, m, rest[0], rest[1], 0, 0) +
+                                   nB * nB * get_sym(A2, 2, m, rest[0], rest[1], 0, 0));
+                        }
+                    for (int a = 0; a < 4; ++a) {
+                        int rest[3], q = 0;
+                        for (int c = 0; c < 4; ++c)
+                            if (c != a) rest[q++] = ix[c];
+                        s4 += d[ix[a]] * (nA * get_sym(B3, 3, m, rest[0], rest[1], rest[2], 0) -
+                                          nB * get_sym(A3, 3, m, rest[0], rest[1], rest[2], 0));
+                    }
+                    N4[t4] = A4[t4] + B4[t4] +
+                             d[i] * d[j] * d[k] * d[l] * nA * nB * (nA * nA - nA * nB + nB * nB) / (n * n * n) +
+                             s6 / (n * n) + s4 / n;
+                    ++t4;
+                }
+            }
+        }
+    for (int j = 0; j < m; ++j) muA[j] += d[j] * nB / n;
+    for (int64_t t = 0; t < T2; ++t) A2[t] = N2[t];
+    for (int64_t t = 0; t < T3; ++t) A3[t] = N3[t];
+    for (int64_t t = 0; t < T4; ++t) A4[t] = N4[t];
+    *nA_ += nB_;
+    free(N2);
+}
+
+/* Merge child records into parents: parent p takes the children [child_off[p], child_off[p+1])
+   in id order. */
+int orc_joint_merge(int32_t m, int32_t n_parent, const int64_t *child_off, const int64_t *count,
+                    const double *mean, const double *m2, const double *m3, const double *m4, int64_t *pcount,
+                    double *pmean, double *pm2, double *pm3, double *pm4)
+{
+    if (m < 1 || m > 8 || n_parent < 0) return ORC_EINVAL;
+    int64_t T2 = binom_small(m + 1, 2), T3 = binom_small(m + 2, 3), T4 = binom_small(m + 3, 4);
+    for (int32_t p = 0; p < n_parent; ++p) {
+        int64_t n = 0;
+        double *mu = pmean + (int64_t)p * m, *A2 = pm2 + (int64_t)p * T2, *A3 = pm3 + (int64_t)p * T3,
+               *A4 = pm4 + (int64_t)p * T4;
+        for (int j = 0; j < m; ++j) mu[j] = 0.0;
+        for (int64_t t = 0; t < T2; ++t) A2[t] = 0.0;
+        for (int64_t t = 0; t < T3; ++t) A3[t] = 0.0;
+        for (int64_t t = 0; t < T4; ++t) A4[t] = 0.0;
+        for (int64_t c = child_off[p]; c < child_off[p + 1]; ++c)
+            joint_merge_into(m, &n, mu, A2, A3, A4, count[c], mean + c * m, m2 + c * T2, m3 + c * T3,
+                             m4 + c * T4);
+        pcount[p] = n;
+    }
+    return ORC_OK;
+}
