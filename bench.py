@@ -310,10 +310,52 @@ def layout_arm(pkg, pipe, s, reps=3):
     alg = pipe.n * 4 + r * (4 + 8 * m)
     gbs = alg / (ms * 1e-3) / 1e9
     pk = peaks()
-    return dict(ms=ms, kept_voxels=r, variables=m, algorithmic_bytes=int(alg), algorithmic_gbs=gbs,
-                frac=gbs / pk["hbm"], peak_source=pk["src"],
-                what="voxels of all bands ordered by (band, component, cell, index) + offsets + "
-                     "extraction of every variable in layout order")
+    res = dict(ms=ms, kept_voxels=r, variables=m, algorithmic_bytes=int(alg), algorithmic_gbs=gbs,
+               frac=gbs / pk["hbm"], peak_source=pk["src"],
+               what="voxels of all bands ordered by (band, component, cell, index) + offsets + "
+                    "extraction of every variable in layout order")
+    res["joint"] = joint_arm(pkg, pipe, out, s)
+    return res
+
+
+JOINT_VARS = 4
+
+
+def joint_arm(pkg, pipe, lay, s, reps=3):
+    """Joint central moments of orders 2..4 of the first four variables over every cell of the
+    layout, then their merge up the hierarchy.  Bound: FP32 FMA issue (each voxel contributes
+    E = m + m(m+1)/2 + C(m+2,3) + C(m+3,4) products; 69 at m = 4)."""
+    from math import comb
+    L = pipe.last
+    m = JOINT_VARS
+    E = m + comb(m + 1, 2) + comb(m + 2, 3) + comb(m + 3, 4)
+    ns = L["n_sites"]
+    rows = L["site_pos"].numel()
+    vals = [lay["values"][j] for j in range(m)]
+    out = pkg.joint_moments(vals, lay["cell_off"], ns, rows, ws=pipe.ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        pkg.joint_moments(vals, lay["cell_off"], ns, rows, ws=pipe.ws, out=out)
+    e1.record(s)
+    for _ in range(reps):
+        pkg.merge_joint_hierarchy(out, ns, L["comp_site_off"], L["comp_band"], L["n_comp"], pipe.max_comp,
+                                  pipe.n_bands, ws=pipe.ws)
+    e2.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    r = int(lay["n_kept"].item())
+    fma = r * E
+    clk = 2.032e9  # maximum SM clock
+    peak = 148 * 128 * clk / 1e12  # FP32 FMA lanes x clock, T FMA/s
+    ach = fma / (ms * 1e-3) / 1e12
+    return dict(ms=ms, merge_ms=e1.elapsed_time(e2) / reps, variables=m, products_per_voxel=E, voxels=r,
+                bound="alu", achieved=ach, peak=peak, unit="T FMA/s", frac=ach / peak,
+                read_gbs=r * 4 * m / (ms * 1e-3) / 1e9,
+                peak_note="148 SMs x 128 FP32 lanes x 2.032 GHz (unit counts and maximum clock)")
 
 
 # --------------------------------------------------------------------------- oracle arm

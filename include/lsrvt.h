@@ -62,7 +62,8 @@ typedef enum {
     LSRVT_STEP_CVT = 4,
     LSRVT_STEP_AGGREGATE = 5,
     LSRVT_STEP_MERGE = 6,
-    LSRVT_STEP_LAYOUT = 7
+    LSRVT_STEP_LAYOUT = 7,
+    LSRVT_STEP_JOINT = 8 /* max_sites = range capacity, max_comp, n_aux = variables; dims: positions */
 } lsrvt_step;
 
 /* Seeding parameters (Sec. 3.2 "Stratified Random Initial Site Distribution", Eq. nc;
@@ -93,6 +94,20 @@ typedef struct {
     uint32_t *hist;
     double *comom;
 } lsrvt_stats;
+
+/* Joint central moments of up to 8 variables (orders 2..4): one row per region.
+ *   count[rows] int64; mean[rows][m] double;
+ *   m2[rows][m(m+1)/2]          sum d_i d_j            (i <= j)
+ *   m3[rows][m(m+1)(m+2)/6]     sum d_i d_j d_k        (i <= j <= k; coskewness sums)
+ *   m4[rows][m(m+1)(m+2)(m+3)/24] sum d_i d_j d_k d_l  (i <= j <= k <= l; cokurtosis sums)
+ * with d = x - mean over the region's voxels; index tuples in lexicographic order. */
+typedef struct {
+    int64_t *count;
+    double *mean;
+    double *m2;
+    double *m3;
+    double *m4;
+} lsrvt_joint;
 
 #define LSRVT_STATS_HIST 1u
 #define LSRVT_STATS_COV 2u
@@ -266,6 +281,30 @@ lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims d, const in
                                      int32_t *order, int64_t *cell_off, int64_t *comp_off, int64_t *band_off,
                                      int64_t *n_kept_dev, void *ws, size_t ws_bytes, int32_t *status_dev,
                                      void *stream);
+
+/* Joint central moments of orders 2..4 of m (1..8) variables over contiguous ranges of
+ * voxel records: cells, components or bands of a structured layout (the joint-plot section
+ * compares mean, covariance, coskewness and cokurtosis of summaries and raw data; Sec. 3.3).
+ *   values_host[m]: device pointers to the variables in layout order (n_positions each);
+ *   range_off [max_ranges+1] int64 (device): range r is [range_off[r], range_off[r+1]);
+ *   n_ranges_dev (device, nullable = max_ranges): live ranges; rows < it are written.
+ * FP32 products summed over at most 32 voxels, then FP64; central moments from exact FP64
+ * shift formulas around a per-range shift (the mean of the range's first 32 voxels).
+ * Workspace: lsrvt_workspace_bytes(LSRVT_STEP_JOINT, {n_positions, 1, 1}, 0, max_ranges, m). */
+lsrvt_status lsrvt_joint_moments(const float *const *values_host, int32_t m, int64_t n_positions,
+                                 const int64_t *range_off, const int32_t *n_ranges_dev, int32_t max_ranges,
+                                 lsrvt_joint out, void *ws, size_t ws_bytes, void *stream);
+
+/* Merge joint-moment records cell -> component -> band -> volume by the pairwise formulas of
+ * Pebay (2008) in FP64, children in id order (arguments as lsrvt_merge_hierarchy; rows < *n_comp_dev
+ * of comps, n_bands rows of bands, 1 row of volume written).  Two levels per merge: blocks of 64
+ * children merged in parallel, then each parent's blocks in order.  Workspace:
+ * lsrvt_workspace_bytes(LSRVT_STEP_JOINT, dims, max_comp, max_sites, m). */
+lsrvt_status lsrvt_merge_joint_hierarchy(lsrvt_joint cells, const int32_t *n_sites_dev, int32_t max_sites,
+                                         int32_t m, const int32_t *comp_site_off, const uint8_t *comp_band,
+                                         const int32_t *n_comp_dev, int32_t max_comp, int32_t n_bands,
+                                         lsrvt_joint comps, lsrvt_joint bands, lsrvt_joint volume, void *ws,
+                                         size_t ws_bytes, void *stream);
 
 /* Execution resources (the execution forms of Sec. 3.2 "Parallel Algorithm": independent
  * blocks processed side by side).  Kernels launched on `stream` size their grids to `percent`

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(HERE, "liblsrvt.so")
 STATUS = {0: "ok", 1: "invalid argument", 2: "isovalues not strictly increasing", 3: "capacity exceeded",
           4: "non-finite input value", 5: "device loop limit reached", 6: "geodesic distance overflow",
           7: "CUDA launch failure", 8: "workspace missing, misaligned or too small"}
-STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7)
+STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7, joint=8)
 STATS_HIST = 1
 STATS_COV = 2
 
@@ -54,6 +54,11 @@ class Stats(C.Structure):
 _lib = None
 
 
+class Joint(C.Structure):
+    _fields_ = [("count", C.c_void_p), ("mean", C.c_void_p), ("m2", C.c_void_p), ("m3", C.c_void_p),
+                ("m4", C.c_void_p)]
+
+
 def lib():
     """Load liblsrvt.so (built in-tree by build.py); raises if it is missing."""
     global _lib
@@ -79,10 +84,13 @@ def lib():
                                             sz, P]
         L.lsrvt_set_stream_share.argtypes = [P, i32]
         L.lsrvt_structured_layout.argtypes = [P, Dims, P, i32, P, P, P, i32, P, P, i32, P, P, P, P, P, P, P, sz, P, P]
+        L.lsrvt_joint_moments.argtypes = [P, i32, i64, P, P, i32, Joint, P, sz, P]
+        L.lsrvt_merge_joint_hierarchy.argtypes = [Joint, P, i32, i32, P, P, P, i32, i32, Joint, Joint, Joint, P, sz, P]
         for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
                      "lsrvt_saliency_grad", "lsrvt_seed",
                      "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy",
-                     "lsrvt_set_stream_share", "lsrvt_structured_layout"):
+                     "lsrvt_set_stream_share", "lsrvt_structured_layout", "lsrvt_joint_moments",
+                     "lsrvt_merge_joint_hierarchy"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -91,7 +99,8 @@ def lib():
 def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
             "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
-            "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout"]
+            "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout",
+            "lsrvt_joint_moments", "lsrvt_merge_joint_hierarchy"]
 
 
 def set_stream_share(percent, stream=None):
@@ -393,6 +402,59 @@ def structured_layout(cell, n_sites_dev, max_sites, comp_site_off, comp_band, n_
                                          _ptr(out["n_kept"]), _ptr(buf), buf.numel(), _ptr(status), _stream()),
            "lsrvt_structured_layout")
     return out
+
+
+def alloc_joint(rows, m, device="cuda"):
+    from math import comb
+    r = max(int(rows), 1)
+    return dict(count=torch.empty(r, dtype=torch.int64, device=device),
+                mean=torch.empty((r, m), dtype=torch.float64, device=device),
+                m2=torch.empty((r, comb(m + 1, 2)), dtype=torch.float64, device=device),
+                m3=torch.empty((r, comb(m + 2, 3)), dtype=torch.float64, device=device),
+                m4=torch.empty((r, comb(m + 3, 4)), dtype=torch.float64, device=device))
+
+
+def _joint_struct(j):
+    return Joint(j["count"].data_ptr(), j["mean"].data_ptr(), j["m2"].data_ptr(), j["m3"].data_ptr(),
+                 j["m4"].data_ptr())
+
+
+def joint_moments(values, range_off, n_ranges_dev=None, max_ranges=None, ws=None, out=None):
+    """Joint central moments of orders 2..4 (covariance, coskewness and cokurtosis sums) of
+    m <= 8 variables over the ranges [range_off[r], range_off[r+1]) of layout-ordered values
+    (e.g. structured_layout(...)["values"][:m] with its cell_off / comp_off / band_off).
+    Returns a dict of device tensors: count, mean (R, m), m2, m3, m4 (R, T_q)."""
+    vals = [v for v in values]
+    m = len(vals)
+    _require_cuda(range_off)
+    dev = range_off.device
+    n_pos = int(vals[0].numel()) if m else 0
+    max_ranges = int(range_off.numel() - 1) if max_ranges is None else int(max_ranges)
+    out = out or alloc_joint(max_ranges, m, dev)
+    ws = ws or Workspace(dev)
+    buf = ws.get(workspace_bytes("joint", (max(n_pos, 1), 1, 1), max_sites=max_ranges, n_aux=m))
+    ptrs = (C.c_void_p * max(m, 1))(*[v.data_ptr() for v in vals])
+    _check(lib().lsrvt_joint_moments(C.cast(ptrs, C.c_void_p), m, n_pos, _ptr(range_off), _ptr(n_ranges_dev),
+                                     max_ranges, _joint_struct(out), _ptr(buf), buf.numel(), _stream()),
+           "lsrvt_joint_moments")
+    return out
+
+
+def merge_joint_hierarchy(cells, n_sites_dev, comp_site_off, comp_band, n_comp_dev, max_comp, n_bands, ws=None):
+    """Joint-moment records merged cell -> component -> band -> volume (Pebay 2008)."""
+    dev = cells["count"].device
+    m = cells["mean"].shape[1]
+    comps = alloc_joint(max_comp, m, dev)
+    bands = alloc_joint(n_bands, m, dev)
+    vol = alloc_joint(1, m, dev)
+    ws = ws or Workspace(dev)
+    buf = ws.get(workspace_bytes("joint", (1, 1, 1), max_comp=max_comp, max_sites=cells["count"].numel(), n_aux=m))
+    _check(lib().lsrvt_merge_joint_hierarchy(_joint_struct(cells), _ptr(n_sites_dev), cells["count"].numel(), m,
+                                             _ptr(comp_site_off), _ptr(comp_band), _ptr(n_comp_dev), int(max_comp),
+                                             int(n_bands), _joint_struct(comps), _joint_struct(bands),
+                                             _joint_struct(vol), _ptr(buf), buf.numel(), _stream()),
+           "lsrvt_merge_joint_hierarchy")
+    return comps, bands, vol
 
 
 def _dims_of_nothing():
