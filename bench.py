@@ -545,7 +545,8 @@ def profile_step(args):
 
 
 def profile_layout(args):
-    """One step of the workload, then two structured layouts of it (ncu target)."""
+    """One step of the workload, then two structured layouts of it, each followed by the joint
+    moments of its cells and their merge (ncu target)."""
     import paper_2208_06970_b300 as pkg
     import workloads
     from paper_2208_06970_b300 import build
@@ -560,6 +561,10 @@ def profile_layout(args):
         out = pkg.structured_layout(L["cell"], L["n_sites"], L["site_pos"].numel(), L["comp_site_off"],
                                     L["comp_band"], L["n_comp"], pipe.max_comp, aux=pipe.aux, ws=pipe.ws,
                                     status=pipe.status, out=out)
+        jm = pkg.joint_moments([out["values"][j] for j in range(JOINT_VARS)], out["cell_off"], L["n_sites"],
+                               L["site_pos"].numel(), ws=pipe.ws)
+        pkg.merge_joint_hierarchy(jm, L["n_sites"], L["comp_site_off"], L["comp_band"], L["n_comp"], pipe.max_comp,
+                                  pipe.n_bands, ws=pipe.ws)
     torch.cuda.synchronize()
     pkg.check_status(pipe.status, "profile layout")
     print("profile layout ok: %d voxels" % int(out["n_kept"].item()))
@@ -600,7 +605,7 @@ def main():
     ap.add_argument("--profile-precision", action="store_true",
                     help="build the precision-form inputs and run two co-moment aggregations (for ncu)")
     ap.add_argument("--profile-layout", action="store_true",
-                    help="one step, then two structured layouts of it (for ncu)")
+                    help="one step, then two structured layouts and joint moments of it (for ncu)")
     ap.add_argument("--profile-step", action="store_true",
                     help="generate the workload and run two plain steps (for ncu); prints nothing else")
     args = ap.parse_args()

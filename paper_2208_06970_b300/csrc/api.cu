@@ -16,7 +16,7 @@ size_t cvt_workspace(Dims d, int32_t max_sites);
 size_t aggregate_workspace(Dims d, int32_t max_sites, int32_t m);
 size_t merge_workspace(int32_t max_sites, int32_t max_comp, int32_t n_bands, int32_t m);
 size_t layout_workspace(Dims d, int32_t max_sites);
-size_t joint_workspace(int32_t max_ranges, int64_t n_positions);
+size_t joint_workspace(int32_t max_ranges, int64_t n_positions, int32_t m);
 size_t joint_merge_workspace(int32_t max_sites, int32_t max_comp, int32_t m);
 }  // namespace lsrvt
 
@@ -145,7 +145,7 @@ extern "C" size_t lsrvt_workspace_bytes(lsrvt_step step, lsrvt_dims dd, int32_t 
         case LSRVT_STEP_JOINT: {
             // the moments over max_sites ranges of d.n() positions, and the merge of max_sites cell
             // records into max_comp components (n_aux = the variable count)
-            const size_t a = joint_workspace(max_sites, d.n()), b = joint_merge_workspace(max_sites, max_comp, n_aux);
+            const size_t a = joint_workspace(max_sites, d.n(), n_aux), b = joint_merge_workspace(max_sites, max_comp, n_aux);
             return a > b ? a : b;
         }
     }

@@ -24,7 +24,7 @@ constexpr int kJZ = 1 + kJMax + 36;      // z entries: 1, d_i, d_i d_j (i <= j)
 constexpr int kJE = kJMax + 36 + 120 + 330;  // accumulated sums at m = 8
 constexpr int kJT = 36 + 120 + 330;      // output co-moments at m = 8
 constexpr int kJWarps = 8;
-constexpr int kJChunk = 8192;            // positions per work item of a long range
+constexpr int kJChunk = 1024;            // positions per work item (longer ranges are split)
 
 __host__ __device__ constexpr int binom2(int a) { return a * (a - 1) / 2; }
 __host__ __device__ constexpr int binom3(int a) { return a * (a - 1) * (a - 2) / 6; }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(32 * kJWarps) joint_ranges_kernel(JVars V, con
             joint_finalize(T, lane, end - beg, c, S, r, out);
             __syncwarp();
         } else {
-            double *A = acc + slot_off[r] * (int64_t)kJE;
+            double *A = acc + slot_off[r] * (int64_t)E;
 #pragma unroll
             for (int q = 0; q < QN; ++q)
                 if (lane + 32 * q < E) atomicAdd(A + lane + 32 * q, ad[q]);
@@ -279,9 +279,9 @@ __global__ void __launch_bounds__(32 * kJWarps) joint_ranges_kernel(JVars V, con
     }
 }
 
-__global__ void joint_zero_kernel(double *acc, const int64_t *slot_off, const int32_t *n_dev, int32_t cap) {
+__global__ void joint_zero_kernel(double *acc, const int64_t *slot_off, const int32_t *n_dev, int32_t cap, int E) {
     const int64_t R = n_live(n_dev, cap);
-    const int64_t n = (R > 0 ? slot_off[R] : 0) * (int64_t)kJE;
+    const int64_t n = (R > 0 ? slot_off[R] : 0) * (int64_t)E;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         acc[i] = 0.0;
 }
@@ -295,7 +295,7 @@ __global__ void joint_long_finalize_kernel(JVars V, const int64_t *__restrict__ 
     const int64_t R = n_live(n_dev, cap);
     for (int64_t r = (int64_t)blockIdx.x * kJWarps + w; r < R; r += (int64_t)gridDim.x * kJWarps) {
         if (slot_off[r + 1] == slot_off[r]) continue;  // a single-item range, written already
-        const double *A = acc + slot_off[r] * (int64_t)kJE;
+        const double *A = acc + slot_off[r] * (int64_t)T.E;
         for (int e = lane; e < T.E; e += 32) S[w][e] = A[e];
         float c[kJMax];
         range_shift(V, T.m, off[r], off[r + 1], lane, c);
@@ -494,7 +494,7 @@ struct JointWs {
     double *acc;
 };
 
-JointWs carve_joint(void *ws, size_t bytes, int32_t max_ranges, int64_t n_positions, size_t *need) {
+JointWs carve_joint(void *ws, size_t bytes, int32_t max_ranges, int64_t n_positions, int E, size_t *need) {
     Carver c(ws, bytes);
     JointWs w;
     const int64_t R = (int64_t)max_ranges + 1;
@@ -503,7 +503,7 @@ JointWs carve_joint(void *ws, size_t bytes, int32_t max_ranges, int64_t n_positi
     w.scan_items = c.take<char>(scan_temp_bytes(R));
     w.scan_slots = c.take<char>(scan_temp_bytes(R));
     // long ranges hold more than kJChunk positions each: at most n_positions / kJChunk of them
-    w.acc = c.take<double>((n_positions / kJChunk + 1) * (int64_t)kJE);
+    w.acc = c.take<double>((n_positions / kJChunk + 1) * (int64_t)E);
     *need = c.used;
     return w;
 }
@@ -557,9 +557,11 @@ void joint_merge_level(lsrvt_joint child, const int32_t *off32, const int64_t *o
 
 }  // namespace
 
-size_t joint_workspace(int32_t max_ranges, int64_t n_positions) {
+int joint_sums(int m) { return m + m * (m + 1) / 2 + m * (m + 1) * (m + 2) / 6 + m * (m + 1) * (m + 2) * (m + 3) / 24; }
+
+size_t joint_workspace(int32_t max_ranges, int64_t n_positions, int32_t m) {
     size_t need;
-    carve_joint(nullptr, 0, max_ranges, n_positions, &need);
+    carve_joint(nullptr, 0, max_ranges, n_positions, joint_sums(m < 1 ? 1 : (m > kJMax ? kJMax : m)), &need);
     return need;
 }
 
@@ -587,7 +589,7 @@ extern "C" lsrvt_status lsrvt_joint_moments(const float *const *values_host, int
         if (!V.p[i]) return LSRVT_ERR_INVALID_ARG;
     }
     size_t need;
-    JointWs w = carve_joint(ws, ws_bytes, max_ranges, n_positions, &need);
+    JointWs w = carve_joint(ws, ws_bytes, max_ranges, n_positions, joint_sums(m), &need);
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return LSRVT_ERR_WORKSPACE;
     if (max_ranges == 0) return LSRVT_OK;
     const JointTables T = make_tables(m);
@@ -597,7 +599,7 @@ extern "C" lsrvt_status lsrvt_joint_moments(const float *const *values_host, int
                                                                            w.items, w.slots);
     exclusive_scan_i64(w.items, (int64_t)max_ranges + 1, nullptr, w.scan_items, s);
     exclusive_scan_i64(w.slots, (int64_t)max_ranges + 1, nullptr, w.scan_slots, s);
-    joint_zero_kernel<<<sms * 4, 256, 0, s>>>(w.acc, w.slots, n_ranges_dev, max_ranges);
+    joint_zero_kernel<<<sms * 4, 256, 0, s>>>(w.acc, w.slots, n_ranges_dev, max_ranges, T.E);
     const int qn = (T.E + 31) / 32;
 #define LSRVT_JOINT_LAUNCH(Q)                                                                                \
     joint_ranges_kernel<Q><<<sms * 4, 32 * kJWarps, 0, s>>>(V, range_off, n_ranges_dev, max_ranges, w.items, \
