@@ -23,6 +23,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
   merge               direct per-component / per-band statistics
   joint_moments       numpy einsum per region; shift invariance; symmetric data (odd
                       orders vanish); merged records equal direct records of the union
+  site_graph          brute-force face adjacency of the cells; weights against exact
+                      integer square roots; SSSP against Floyd-Warshall; Euclidean lower bound
   layout              brute-force contiguity and membership of every band, component and
                       cell range; per-cell counts and means against aggregate
 """
@@ -70,6 +72,11 @@ def lib():
         L.orc_layout.argtypes = [P, i64, P, i32, P, i32, P, P, i32, P, P, P, P, P, P]
         L.orc_joint_ranges.argtypes = [P, i32, i64, P, P, i32, P, P, P, P, P]
         L.orc_joint_merge.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, P]
+        L.orc_site_weight.argtypes = [i32, i32, i32]
+        L.orc_site_weight.restype = C.c_uint32
+        L.orc_site_edges.argtypes = [P, P, i32, i32, i32, i64, P, P]
+        L.orc_site_edges.restype = i64
+        L.orc_site_sssp.argtypes = [i32, P, P, P, i32, P]
         _lib = L
     return _lib
 
@@ -356,6 +363,52 @@ def joint_merge(rec, child_off):
                                  _p(c["m4"]), _p(out["count"]), _p(out["mean"]), _p(out["m2"]), _p(out["m3"]),
                                  _p(out["m4"])), "joint_merge")
     return out
+
+
+def site_weight(dx, dy, dz):
+    """Edge weight between two sites: ceil(2^16 * ||(dx, dy, dz)||_2) (an integer)."""
+    return int(lib().orc_site_weight(int(dx), int(dy), int(dz)))
+
+
+def site_graph(cell, band, site_pos):
+    """Voronoi site graph ("Voronoi Cell Views": connectivity from region adjacency): cells are
+    adjacent when two of their voxels are face neighbours.  Returns dict(edges (E, 2) a < b in
+    (a, b) order, weight (E,) uint32, off (S+1,) int64, dst (2E,) int32, w (2E,) uint32) with the
+    CSR holding both directions, neighbours in increasing order."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    band = np.ascontiguousarray(band, dtype=np.uint8)
+    nx, ny, nz = _dims(cell)
+    site_pos = np.asarray(site_pos, dtype=np.int64)
+    S = site_pos.size
+    cap = max(16, 13 * cell.size)
+    ea = np.empty(cap, np.int32)
+    eb = np.empty(cap, np.int32)
+    E = lib().orc_site_edges(_p(cell), _p(band), nx, ny, nz, cap, _p(ea), _p(eb))
+    if E < 0:
+        raise OracleError(int(E), "site_edges")
+    ea, eb = ea[:E], eb[:E]
+    px, py, pz = site_pos % nx, (site_pos // nx) % ny, site_pos // (nx * ny)
+    w = np.array([site_weight(px[b] - px[a], py[b] - py[a], pz[b] - pz[a]) for a, b in zip(ea, eb)], np.uint32)
+    src = np.concatenate([ea, eb])
+    dst = np.concatenate([eb, ea]).astype(np.int32)
+    ww = np.concatenate([w, w])
+    order = np.lexsort((dst, src))
+    src, dst, ww = src[order], dst[order], ww[order]
+    off = np.zeros(S + 1, np.int64)
+    np.add.at(off, src + 1, 1)
+    off = np.cumsum(off)
+    return dict(edges=np.stack([ea, eb], 1), weight=w, off=off, dst=dst, w=ww)
+
+
+def site_sssp(graph, src):
+    """Shortest path lengths (weight units) from site `src` to every site (Dijkstra);
+    2^64 - 1 where unreachable."""
+    off = np.ascontiguousarray(graph["off"], dtype=np.int64)
+    S = off.size - 1
+    d = np.empty(S, np.uint64)
+    _check(lib().orc_site_sssp(S, _p(off), _p(np.ascontiguousarray(graph["dst"], np.int32)),
+                               _p(np.ascontiguousarray(graph["w"], np.uint32)), int(src), _p(d)), "site_sssp")
+    return d
 
 
 # --------------------------------------------------------------------------- checkers

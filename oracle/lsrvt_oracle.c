@@ -1216,3 +1216,137 @@ int orc_joint_merge(int32_t m, int32_t n_parent, const int64_t *child_off, const
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Voronoi site graph and geodesic site distances (Sec. "Voronoi Cell Views": */
+/* the connectivity of the sites from region adjacency, then shortest paths   */
+/* between adjacent sites, restricted to the component, and the distance      */
+/* ||x_i - x_j|| / gd(s_i, s_j), or c when no path exists).                   */
+/* Readings: two cells are adjacent when a voxel of one and a voxel of the    */
+/* other are face neighbours (6-adjacency, as for the components; such voxels */
+/* share a band, so edges never leave a component); the edge between sites a  */
+/* and b weighs ceil(2^16 ||x_a - x_b||_2), an integer, so path lengths are   */
+/* exact sums and every shortest-path algorithm gives the same numbers.       */
+/* ------------------------------------------------------------------------- */
+static uint64_t isqrt_floor_u64(uint64_t v)
+{
+    uint64_t lo = 0, hi = (uint64_t)1 << 32;  /* hi^2 > v for v < 2^64 */
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (mid * mid <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+uint32_t orc_site_weight(int32_t dx, int32_t dy, int32_t dz)
+{
+    uint64_t D = (uint64_t)((int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz);
+    uint64_t v = D << 32;  /* (2^16)^2 D */
+    uint64_t r = isqrt_floor_u64(v);
+    return (uint32_t)(r * r == v ? r : r + 1);
+}
+
+static int pair_cmp(const void *a, const void *b)
+{
+    const int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Undirected edges (a < b) in increasing (a, b) order; returns the count (or < 0). */
+int64_t orc_site_edges(const int32_t *cell, const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+                       int64_t max_edges, int32_t *ea, int32_t *eb)
+{
+    int64_t n = (int64_t)nx * ny * nz, cnt = 0, cap = 1024;
+    int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    if (!pairs) return ORC_ENOMEM;
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t x = (int32_t)(v % nx), y = (int32_t)((v / nx) % ny), z = (int32_t)(v / ((int64_t)nx * ny));
+        if (cell[v] < 0) continue;
+        int64_t nb[3] = {x + 1 < nx ? v + 1 : -1, y + 1 < ny ? v + nx : -1, z + 1 < nz ? v + (int64_t)nx * ny : -1};
+        for (int k = 0; k < 3; ++k) {
+            int64_t u = nb[k];
+            if (u < 0 || cell[u] < 0 || cell[u] == cell[v] || band[u] != band[v]) continue;
+            int32_t a = cell[v] < cell[u] ? cell[v] : cell[u], b = cell[v] < cell[u] ? cell[u] : cell[v];
+            if (cnt == cap) {
+                cap *= 2;
+                int64_t *np = (int64_t *)realloc(pairs, sizeof(int64_t) * (size_t)cap);
+                if (!np) { free(pairs); return ORC_ENOMEM; }
+                pairs = np;
+            }
+            pairs[cnt++] = ((int64_t)a << 32) | (int64_t)b;
+        }
+    }
+    qsort(pairs, (size_t)cnt, sizeof(int64_t), pair_cmp);
+    int64_t m = 0;
+    for (int64_t i = 0; i < cnt; ++i) {
+        if (i > 0 && pairs[i] == pairs[i - 1]) continue;
+        if (m >= max_edges) { free(pairs); return ORC_ECAPACITY; }
+        ea[m] = (int32_t)(pairs[i] >> 32);
+        eb[m] = (int32_t)(pairs[i] & 0xffffffff);
+        ++m;
+    }
+    free(pairs);
+    return m;
+}
+
+/* Dijkstra from `src` over the undirected site graph given as a CSR (both directions):
+   dist[t] = shortest path length in weight units, UINT64_MAX if unreachable. */
+int orc_site_sssp(int32_t n_sites, const int64_t *off, const int32_t *dst, const uint32_t *w, int32_t src,
+                  uint64_t *dist)
+{
+    if (src < 0 || src >= n_sites) return ORC_EINVAL;
+    for (int32_t i = 0; i < n_sites; ++i) dist[i] = UINT64_MAX;
+    uint8_t *done = (uint8_t *)calloc((size_t)n_sites + 1, 1);
+    /* binary heap of (dist, node) */
+    int64_t cap = 64, hn = 0;
+    uint64_t *hd = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)cap);
+    int32_t *hv = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    if (!done || !hd || !hv) { free(done); free(hd); free(hv); return ORC_ENOMEM; }
+    dist[src] = 0;
+    hd[0] = 0; hv[0] = src; hn = 1;
+    while (hn > 0) {
+        uint64_t d = hd[0];
+        int32_t u = hv[0];
+        --hn;
+        /* sift the last entry down from the root */
+        {
+            uint64_t kd = hd[hn];
+            int32_t kv = hv[hn];
+            int64_t i = 0;
+            for (;;) {
+                int64_t c = 2 * i + 1;
+                if (c >= hn) break;
+                if (c + 1 < hn && (hd[c + 1] < hd[c] || (hd[c + 1] == hd[c] && hv[c + 1] < hv[c]))) ++c;
+                if (hd[c] < kd || (hd[c] == kd && hv[c] < kv)) { hd[i] = hd[c]; hv[i] = hv[c]; i = c; }
+                else break;
+            }
+            hd[i] = kd; hv[i] = kv;
+        }
+        if (done[u] || d != dist[u]) continue;
+        done[u] = 1;
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            int32_t t = dst[e];
+            uint64_t nd = d + w[e];
+            if (nd < dist[t]) {
+                dist[t] = nd;
+                if (hn == cap) {
+                    cap *= 2;
+                    uint64_t *a = (uint64_t *)realloc(hd, sizeof(uint64_t) * (size_t)cap);
+                    int32_t *b = (int32_t *)realloc(hv, sizeof(int32_t) * (size_t)cap);
+                    if (!a || !b) { free(done); free(a ? a : hd); free(b ? b : hv); return ORC_ENOMEM; }
+                    hd = a; hv = b;
+                }
+                int64_t i = hn++;
+                while (i > 0) {
+                    int64_t p = (i - 1) / 2;
+                    if (hd[p] < nd || (hd[p] == nd && hv[p] <= t)) break;
+                    hd[i] = hd[p]; hv[i] = hv[p]; i = p;
+                }
+                hd[i] = nd; hv[i] = t;
+            }
+        }
+    }
+    free(done); free(hd); free(hv);
+    return ORC_OK;
+}
