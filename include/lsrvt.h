@@ -63,7 +63,8 @@ typedef enum {
     LSRVT_STEP_AGGREGATE = 5,
     LSRVT_STEP_MERGE = 6,
     LSRVT_STEP_LAYOUT = 7,
-    LSRVT_STEP_JOINT = 8 /* max_sites = range capacity, max_comp, n_aux = variables; dims: positions */
+    LSRVT_STEP_JOINT = 8, /* max_sites = range capacity, max_comp, n_aux = variables; dims: positions */
+    LSRVT_STEP_GRAPH = 9  /* site graph of a volume of dims d */
 } lsrvt_step;
 
 /* Seeding parameters (Sec. 3.2 "Stratified Random Initial Site Distribution", Eq. nc;
@@ -305,6 +306,31 @@ lsrvt_status lsrvt_merge_joint_hierarchy(lsrvt_joint cells, const int32_t *n_sit
                                          const int32_t *n_comp_dev, int32_t max_comp, int32_t n_bands,
                                          lsrvt_joint comps, lsrvt_joint bands, lsrvt_joint volume, void *ws,
                                          size_t ws_bytes, void *stream);
+
+/* Voronoi site graph ("Voronoi Cell Views" section: site connectivity from region adjacency):
+ * cells a and b are adjacent when a voxel of each are face neighbours of one band; the edge
+ * weighs ceil(2^16 ||x_a - x_b||_2) (exact integer; path lengths are exact sums).
+ *   cell [N] int32, band [N] uint8 (in); site_pos [max_sites] int32 (in);
+ *   adj_off [max_sites+1] int64 (out): CSR rows (both directions, neighbours increasing);
+ *   adj [max_arcs] int32, adj_w [max_arcs] uint32 (out); *n_edges_dev (out, int64): undirected
+ *   edges (arcs = 2x).  CAPACITY in status_dev when the arcs exceed max_arcs or the candidate
+ *   list overflows.  Workspace: lsrvt_workspace_bytes(LSRVT_STEP_GRAPH, d, 0, 0, 0). */
+lsrvt_status lsrvt_site_graph(const int32_t *cell, const uint8_t *band, lsrvt_dims d, const int32_t *site_pos,
+                              const int32_t *n_sites_dev, int32_t max_sites, int64_t *adj_off, int32_t *adj,
+                              uint32_t *adj_w, int64_t max_arcs, int64_t *n_edges_dev, void *ws, size_t ws_bytes,
+                              int32_t *status_dev, void *stream);
+
+/* Geodesic site distances within the sites [s0, s1) (a union of components, closed under
+ * adjacency): dist[i][j] (k x k, k = s1 - s0, uint32 weight units, 0xFFFFFFFF = no path) by
+ * Bellman-Ford per source over frontier bitmaps, exact; optionally ratio[i][j] =
+ * ||x_i - x_j|| / gd(s_i, s_j) (float; 1 on the diagonal, c_far where no path exists), the
+ * distance of the "Voronoi Cell Views" section.  INVALID_ARG in status_dev when an arc leaves
+ * the range, OVERFLOW when a path reaches 2^32 - 1, TIMEOUT past k rounds.
+ * Workspace: 2 * min(k, 4 * SMs) * ceil(k / 32) * 4 + 512 bytes (see the Python binding). */
+lsrvt_status lsrvt_site_geodesics(const int64_t *adj_off, const int32_t *adj, const uint32_t *adj_w,
+                                  const int32_t *site_pos, lsrvt_dims d, int32_t s0, int32_t s1, uint32_t *dist,
+                                  float *ratio, float c_far, void *ws, size_t ws_bytes, int32_t *status_dev,
+                                  void *stream);
 
 /* Execution resources (the execution forms of Sec. 3.2 "Parallel Algorithm": independent
  * blocks processed side by side).  Kernels launched on `stream` size their grids to `percent`

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(HERE, "liblsrvt.so")
 STATUS = {0: "ok", 1: "invalid argument", 2: "isovalues not strictly increasing", 3: "capacity exceeded",
           4: "non-finite input value", 5: "device loop limit reached", 6: "geodesic distance overflow",
           7: "CUDA launch failure", 8: "workspace missing, misaligned or too small"}
-STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7, joint=8)
+STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7, joint=8, graph=9)
 STATS_HIST = 1
 STATS_COV = 2
 
@@ -86,11 +86,13 @@ def lib():
         L.lsrvt_structured_layout.argtypes = [P, Dims, P, i32, P, P, P, i32, P, P, i32, P, P, P, P, P, P, P, sz, P, P]
         L.lsrvt_joint_moments.argtypes = [P, i32, i64, P, P, i32, Joint, P, sz, P]
         L.lsrvt_merge_joint_hierarchy.argtypes = [Joint, P, i32, i32, P, P, P, i32, i32, Joint, Joint, Joint, P, sz, P]
+        L.lsrvt_site_graph.argtypes = [P, P, Dims, P, P, i32, P, P, P, i64, P, P, sz, P, P]
+        L.lsrvt_site_geodesics.argtypes = [P, P, P, P, Dims, i32, i32, P, P, C.c_float, P, sz, P, P]
         for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
                      "lsrvt_saliency_grad", "lsrvt_seed",
                      "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy",
                      "lsrvt_set_stream_share", "lsrvt_structured_layout", "lsrvt_joint_moments",
-                     "lsrvt_merge_joint_hierarchy"):
+                     "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -100,7 +102,7 @@ def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
             "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
             "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout",
-            "lsrvt_joint_moments", "lsrvt_merge_joint_hierarchy"]
+            "lsrvt_joint_moments", "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics"]
 
 
 def set_stream_share(percent, stream=None):
@@ -455,6 +457,50 @@ def merge_joint_hierarchy(cells, n_sites_dev, comp_site_off, comp_band, n_comp_d
                                              _joint_struct(vol), _ptr(buf), buf.numel(), _stream()),
            "lsrvt_merge_joint_hierarchy")
     return comps, bands, vol
+
+
+def site_graph(cell, band, site_pos, n_sites_dev, ws=None, status=None, max_arcs=None):
+    """Voronoi site graph (region adjacency, the "Voronoi Cell Views" section): CSR over the
+    site capacity, both directions, weights ceil(2^16 * Euclidean site distance).  Returns
+    dict(off [S+1] int64, adj [A] int32, w [A] int32 (uint32 bits), n_edges [1] int64)."""
+    _require_cuda(cell, band, site_pos)
+    dev = cell.device
+    n = cell.numel()
+    S = site_pos.numel()
+    if max_arcs is None:
+        max_arcs = 2 * min(3 * n, max(n // 8, 1 << 20))
+    out = dict(off=torch.empty(S + 1, dtype=torch.int64, device=dev),
+               adj=torch.empty(max(max_arcs, 1), dtype=torch.int32, device=dev),
+               w=torch.empty(max(max_arcs, 1), dtype=torch.int32, device=dev),
+               n_edges=torch.empty(1, dtype=torch.int64, device=dev))
+    status = new_status(dev) if status is None else status
+    ws = ws or Workspace(dev)
+    buf = ws.get(workspace_bytes("graph", _dims(cell)))
+    _check(lib().lsrvt_site_graph(_ptr(cell), _ptr(band), _dims(cell), _ptr(site_pos), _ptr(n_sites_dev), S,
+                                  _ptr(out["off"]), _ptr(out["adj"]), _ptr(out["w"]), int(max_arcs),
+                                  _ptr(out["n_edges"]), _ptr(buf), buf.numel(), _ptr(status), _stream()),
+           "lsrvt_site_graph")
+    return out
+
+
+def site_geodesics(graph, site_pos, dims, s0, s1, c_far=None, ws=None, status=None):
+    """Geodesic distances between the sites [s0, s1) (a union of components): (k, k) int32
+    tensor of uint32 weight units (0xFFFFFFFF = no path) and, with c_far given, the paper's
+    ratio ||x_i - x_j|| / gd (c_far where no path exists; 1 on the diagonal)."""
+    dev = graph["off"].device
+    k = int(s1) - int(s0)
+    dist = torch.empty((max(k, 1), max(k, 1)), dtype=torch.int32, device=dev)
+    ratio = torch.empty((max(k, 1), max(k, 1)), dtype=torch.float32, device=dev) if c_far is not None else None
+    status = new_status(dev) if status is None else status
+    ws = ws or Workspace(dev)
+    grid = min(max(k, 1), 4 * 148)
+    buf = ws.get(2 * grid * ((k + 31) // 32) * 4 + 512)
+    d = dims if isinstance(dims, Dims) else Dims(*[int(v) for v in dims])
+    _check(lib().lsrvt_site_geodesics(_ptr(graph["off"]), _ptr(graph["adj"]), _ptr(graph["w"]), _ptr(site_pos), d,
+                                      int(s0), int(s1), _ptr(dist), _ptr(ratio),
+                                      float(c_far if c_far is not None else 0.0), _ptr(buf), buf.numel(),
+                                      _ptr(status), _stream()), "lsrvt_site_geodesics")
+    return dist[:k, :k], (ratio[:k, :k] if ratio is not None else None)
 
 
 def _dims_of_nothing():

@@ -18,6 +18,7 @@ size_t merge_workspace(int32_t max_sites, int32_t max_comp, int32_t n_bands, int
 size_t layout_workspace(Dims d, int32_t max_sites);
 size_t joint_workspace(int32_t max_ranges, int64_t n_positions, int32_t m);
 size_t joint_merge_workspace(int32_t max_sites, int32_t max_comp, int32_t m);
+size_t graph_workspace(Dims d);
 }  // namespace lsrvt
 
 namespace lsrvt {
@@ -142,6 +143,7 @@ extern "C" size_t lsrvt_workspace_bytes(lsrvt_step step, lsrvt_dims dd, int32_t 
         case LSRVT_STEP_AGGREGATE: return aggregate_workspace(d, max_sites, n_aux);
         case LSRVT_STEP_MERGE: return merge_workspace(max_sites, max_comp, 255, n_aux);
         case LSRVT_STEP_LAYOUT: return layout_workspace(d, max_sites > 0 ? max_sites : 1);
+        case LSRVT_STEP_GRAPH: return graph_workspace(d);
         case LSRVT_STEP_JOINT: {
             // the moments over max_sites ranges of d.n() positions, and the merge of max_sites cell
             // records into max_comp components (n_aux = the variable count)
