@@ -275,10 +275,11 @@ def gpu_arm(args, rank, world, local_rank):
                d2h_bytes_per_step=int(d2h), ms_per_step=e_ms, api="decompose_host")
     del h_aux, bufs
     layout = layout_arm(pkg, pipe, s)
+    graph = graph_arm(pkg, pipe, s)
     res = dict(ms=ms, phase=phase, clk=clk, n_sites=n_sites, n_comp=n_comp, trace=trace, t_assign=t_assign,
                t_iter=t_iter,
                achieved=achieved, peak=pk, stats_gbs=stats_gbs, cvt_ms=cvt_ms, launches=launches_per_step,
-               kernels=kernel_names, e2e=e2e, n=n, field=field, aux=aux, iso=iso, layout=layout)
+               kernels=kernel_names, e2e=e2e, n=n, field=field, aux=aux, iso=iso, layout=layout, graph=graph)
     return res
 
 
@@ -319,6 +320,49 @@ def layout_arm(pkg, pipe, s, reps=3):
 
 
 JOINT_VARS = 4
+
+
+def graph_arm(pkg, pipe, s, reps=3):
+    """The Voronoi site graph of the last step's decomposition, then the geodesic distances
+    (and the ratio ||x_i - x_j|| / gd) among all sites of its largest component.  The build
+    reads the labels and bands once (5 B per voxel) plus their +x/+y/+z neighbours."""
+    L = pipe.last
+    band = L["band"]
+    cell = L["cell"]
+    sp = L["site_pos"]
+    g = pkg.site_graph(cell, band, sp, L["n_sites"], ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        g = pkg.site_graph(cell, band, sp, L["n_sites"], ws=pipe.ws, status=pipe.status)
+    e1.record(s)
+    torch.cuda.synchronize()
+    pkg.check_status(pipe.status, "site graph")
+    build_ms = e0.elapsed_time(e1) / reps
+    off = L["comp_site_off"][:int(L["n_comp"].item()) + 1].cpu().numpy()
+    c = int((off[1:] - off[:-1]).argmax())
+    s0, s1 = int(off[c]), int(off[c + 1])
+    k = s1 - s0
+    nz, ny, nx = cell.shape
+    dist, ratio = pkg.site_geodesics(g, sp, (nx, ny, nz), s0, s1, c_far=2.0, ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    e0.record(s)
+    dist, ratio = pkg.site_geodesics(g, sp, (nx, ny, nz), s0, s1, c_far=2.0, ws=pipe.ws, status=pipe.status)
+    e1.record(s)
+    torch.cuda.synchronize()
+    pkg.check_status(pipe.status, "site geodesics")
+    geo_ms = e0.elapsed_time(e1)
+    n = cell.numel()
+    gbs = n * 5 / (build_ms * 1e-3) / 1e9
+    pk = peaks()
+    arcs = int(g["off"][s1].item() - g["off"][s0].item())
+    return dict(build_ms=build_ms, edges=int(g["n_edges"].item()), build_algorithmic_gbs=gbs,
+                build_frac=gbs / pk["hbm"], largest_component_sites=k, largest_component_arcs=arcs,
+                apsp_ms=geo_ms, apsp_pairs=k * k, apsp_arcs_scanned_lower_bound=k * arcs,
+                what="site graph (face-adjacent cells, integer Euclidean weights), then geodesic distances and "
+                     "||x_i - x_j|| / gd between all sites of the largest component")
 
 
 def joint_arm(pkg, pipe, lay, s, reps=3):
@@ -665,7 +709,7 @@ def main():
             phases_ms=r["phase"], cvt_gvoxel_iters_per_s=n * N_ITERS / (r["cvt_ms"] * 1e-3) / 1e9,
             moved_per_iter=r["trace"][:, 0].tolist(), clocks=r["clk"], e2e=r["e2e"],
             gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu,
-            layout=r["layout"], forms=forms, precision=precision)
+            layout=r["layout"], graph=r["graph"], forms=forms, precision=precision)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -211,19 +211,27 @@ constexpr int kSThreads = 256;
 constexpr unsigned kSInf = 0xFFFFFFFFu;
 
 // One CTA per source: Bellman-Ford over frontier bitmaps within [s0, s1).  Arcs that leave
-// the range are reported (the range must be closed under adjacency).  At most k rounds.
+// the range are reported (the range must be closed under adjacency).  At most k rounds.  With
+// kShared the distance row and both bitmaps live in shared memory (ranges up to kSharedMax
+// sites) and the row is copied out at the end; otherwise they live in global memory.
+constexpr int kSharedMax = 20000;
+
+template <bool kShared>
 __global__ void __launch_bounds__(kSThreads) graph_sssp_kernel(const int64_t *__restrict__ off,
                                                                 const int32_t *__restrict__ adj,
                                                                 const uint32_t *__restrict__ w, int32_t s0,
                                                                 int32_t s1, uint32_t *dist, uint32_t *fa,
                                                                 uint32_t *fb, const int32_t *__restrict__ site_pos,
                                                                 Dims d, float c_far, float *ratio, int32_t *status) {
+    extern __shared__ uint32_t dyn[];
     __shared__ int any_s;
     const int k = s1 - s0;
     const int nw = (k + 31) / 32;
-    uint32_t *cur = fa + (int64_t)blockIdx.x * nw, *nxt = fb + (int64_t)blockIdx.x * nw;
+    uint32_t *cur = kShared ? dyn + k : fa + (int64_t)blockIdx.x * nw;
+    uint32_t *nxt = kShared ? dyn + k + nw : fb + (int64_t)blockIdx.x * nw;
     for (int src = blockIdx.x; src < k; src += gridDim.x) {
-        uint32_t *D = dist + (int64_t)src * k;
+        uint32_t *row = dist + (int64_t)src * k;
+        uint32_t *D = kShared ? dyn : row;
         for (int i = threadIdx.x; i < k; i += kSThreads) D[i] = i == src ? 0u : kSInf;
         for (int i = threadIdx.x; i < nw; i += kSThreads) {
             cur[i] = i == (src >> 5) ? (1u << (src & 31)) : 0u;
@@ -266,8 +274,10 @@ __global__ void __launch_bounds__(kSThreads) graph_sssp_kernel(const int64_t *__
             for (int i = threadIdx.x; i < nw; i += kSThreads) nxt[i] = 0u;
             __syncthreads();
             if (!more) break;
-            if (round == k) set_status(status, LSRVT_ERR_TIMEOUT);
+            if (round == k && threadIdx.x == 0) set_status(status, LSRVT_ERR_TIMEOUT);
         }
+        if (kShared)
+            for (int i = threadIdx.x; i < k; i += kSThreads) row[i] = D[i];
         if (ratio) {
             const int32_t ps = site_pos[s0 + src];
             const int sx = ps % d.nx, sy = (ps / d.nx) % d.ny, sz = ps / (d.nx * d.ny);
@@ -367,7 +377,14 @@ extern "C" lsrvt_status lsrvt_site_geodesics(const int64_t *adj_off, const int32
     const int64_t nw = (k + 31) / 32;
     uint32_t *fa = reinterpret_cast<uint32_t *>(ws), *fb = fa + (int64_t)grid * nw;
     const Dims d{dd.nx > 0 ? dd.nx : 1, dd.ny > 0 ? dd.ny : 1, dd.nz > 0 ? dd.nz : 1};
-    graph_sssp_kernel<<<grid, kSThreads, 0, s>>>(adj_off, adj, adj_w, s0, s1, dist, fa, fb, site_pos, d, c_far, ratio,
-                                                 status_dev);
+    if (k <= kSharedMax) {
+        const size_t smem = (size_t)(k + 2 * nw) * sizeof(uint32_t);
+        cudaFuncSetAttribute(graph_sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        graph_sssp_kernel<true><<<grid, kSThreads, smem, s>>>(adj_off, adj, adj_w, s0, s1, dist, fa, fb, site_pos, d,
+                                                              c_far, ratio, status_dev);
+    } else {
+        graph_sssp_kernel<false><<<grid, kSThreads, 0, s>>>(adj_off, adj, adj_w, s0, s1, dist, fa, fb, site_pos, d,
+                                                               c_far, ratio, status_dev);
+    }
     return launch_status();
 }
