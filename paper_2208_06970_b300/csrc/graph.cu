@@ -214,7 +214,7 @@ constexpr unsigned kSInf = 0xFFFFFFFFu;
 // the range are reported (the range must be closed under adjacency).  At most k rounds.  With
 // kShared the distance row and both bitmaps live in shared memory (ranges up to kSharedMax
 // sites) and the row is copied out at the end; otherwise they live in global memory.
-constexpr int kSharedMax = 20000;
+constexpr int kSharedMax = 12000;  // distance row + frontier list + bitmaps: 8 k + k / 4 bytes
 
 template <bool kShared>
 __global__ void __launch_bounds__(kSThreads) graph_sssp_kernel(const int64_t *__restrict__ off,
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kSThreads) graph_sssp_kernel(const int64_t *__
                                                                 uint32_t *fb, const int32_t *__restrict__ site_pos,
                                                                 Dims d, float c_far, float *ratio, int32_t *status) {
     extern __shared__ uint32_t dyn[];
-    __shared__ int any_s;
+    __shared__ int any_s, nlist_s;
     const int k = s1 - s0;
     const int nw = (k + 31) / 32;
     uint32_t *cur = kShared ? dyn + k : fa + (int64_t)blockIdx.x * nw;
@@ -241,28 +241,52 @@ __global__ void __launch_bounds__(kSThreads) graph_sssp_kernel(const int64_t *__
         for (int round = 0; round <= k; ++round) {
             if (threadIdx.x == 0) any_s = 0;
             __syncthreads();
-            for (int wi = threadIdx.x; wi < nw; wi += kSThreads) {
-                uint32_t bits = cur[wi];
-                while (bits) {
-                    const int u = wi * 32 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint32_t du = atomicAdd(&D[u], 0u);  // the latest value
-                    const int64_t e0 = off[s0 + u], e1 = off[s0 + u + 1];
-                    for (int64_t e = e0; e < e1; ++e) {
-                        const int t = adj[e] - s0;
-                        if (t < 0 || t >= k) {
-                            set_status(status, LSRVT_ERR_INVALID_ARG);
-                            continue;
-                        }
-                        const unsigned long long nd = (unsigned long long)du + w[e];
-                        if (nd >= kSInf) {
-                            set_status(status, LSRVT_ERR_OVERFLOW);
-                            continue;
-                        }
-                        if ((uint32_t)nd < atomicMin(&D[t], (uint32_t)nd)) {
-                            atomicOr(&nxt[t >> 5], 1u << (t & 31));
-                            any_s = 1;
-                        }
+            // relax the arcs of frontier node u (the latest distance of u is read atomically)
+            auto relax = [&](int u) {
+                const uint32_t du = atomicAdd(&D[u], 0u);
+                const int64_t e0 = off[s0 + u], e1 = off[s0 + u + 1];
+                for (int64_t e = e0; e < e1; ++e) {
+                    const int t = adj[e] - s0;
+                    if (t < 0 || t >= k) {
+                        set_status(status, LSRVT_ERR_INVALID_ARG);
+                        continue;
+                    }
+                    const unsigned long long nd = (unsigned long long)du + w[e];
+                    if (nd >= kSInf) {
+                        set_status(status, LSRVT_ERR_OVERFLOW);
+                        continue;
+                    }
+                    if ((uint32_t)nd < atomicMin(&D[t], (uint32_t)nd)) {
+                        atomicOr(&nxt[t >> 5], 1u << (t & 31));
+                        any_s = 1;
+                    }
+                }
+            };
+            if (kShared) {
+                // the frontier as a list, so every thread takes whole nodes (frontier bits cluster
+                // in a few words: site ids are ordered in space)
+                int *list = reinterpret_cast<int *>(dyn + k + 2 * nw);
+                if (threadIdx.x == 0) nlist_s = 0;
+                __syncthreads();
+                for (int wi = threadIdx.x; wi < nw; wi += kSThreads) {
+                    uint32_t bits = cur[wi];
+                    if (!bits) continue;
+                    int at = atomicAdd(&nlist_s, __popc(bits));
+                    while (bits) {
+                        list[at++] = wi * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                    }
+                }
+                __syncthreads();
+                const int nl = nlist_s;
+                for (int li = threadIdx.x; li < nl; li += kSThreads) relax(list[li]);
+            } else {
+                for (int wi = threadIdx.x; wi < nw; wi += kSThreads) {
+                    uint32_t bits = cur[wi];
+                    while (bits) {
+                        const int u = wi * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        relax(u);
                     }
                 }
             }
@@ -378,7 +402,7 @@ extern "C" lsrvt_status lsrvt_site_geodesics(const int64_t *adj_off, const int32
     uint32_t *fa = reinterpret_cast<uint32_t *>(ws), *fb = fa + (int64_t)grid * nw;
     const Dims d{dd.nx > 0 ? dd.nx : 1, dd.ny > 0 ? dd.ny : 1, dd.nz > 0 ? dd.nz : 1};
     if (k <= kSharedMax) {
-        const size_t smem = (size_t)(k + 2 * nw) * sizeof(uint32_t);
+        const size_t smem = (size_t)(2 * k + 2 * nw) * sizeof(uint32_t);
         cudaFuncSetAttribute(graph_sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         graph_sssp_kernel<true><<<grid, kSThreads, smem, s>>>(adj_off, adj, adj_w, s0, s1, dist, fa, fb, site_pos, d,
                                                               c_far, ratio, status_dev);
