@@ -105,9 +105,10 @@ __device__ __forceinline__ int64_t n_live(const int32_t *n_dev, int32_t cap) {
 // work items: one per range, or one per kJChunk positions of a long range; long ranges get an
 // accumulator slot
 __global__ void joint_items_kernel(const int64_t *__restrict__ off, const int32_t *n_dev, int32_t cap,
-                                   int64_t *items, int64_t *slots) {
+                                   int64_t *items, int64_t *slots, int64_t *n_scan) {
     const int64_t R = n_live(n_dev, cap);
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < cap; r += (int64_t)gridDim.x * blockDim.x) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_scan = R + 1;  // the scans cover the live ranges only
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= R; r += (int64_t)gridDim.x * blockDim.x) {
         int64_t nch = 0, lng = 0;
         if (r < R) {
             const int64_t L = off[r + 1] - off[r];
@@ -116,6 +117,24 @@ __global__ void joint_items_kernel(const int64_t *__restrict__ off, const int32_
         }
         items[r] = nch;
         slots[r] = lng;
+    }
+}
+
+// item -> range, one entry per work item, so the moment kernels read their range with one load
+// (the searches run here, all independent)
+__global__ void joint_item_range_kernel(const int64_t *__restrict__ item_off, const int32_t *n_dev, int32_t cap,
+                                        int32_t *item_range) {
+    const int64_t R = n_live(n_dev, cap);
+    const int64_t nitems = R > 0 ? item_off[R] : 0;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = R;  // last r with item_off[r] <= it
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= it) lo = mid;
+            else hi = mid;
+        }
+        item_range[it] = (int32_t)lo;
     }
 }
 
@@ -195,6 +214,7 @@ template <int QN>
 __global__ void __launch_bounds__(32 * kJWarps) joint_ranges_kernel(JVars V, const int64_t *__restrict__ off,
                                                                     const int32_t *n_dev, int32_t cap,
                                                                     const int64_t *__restrict__ item_off,
+                                                                    const int32_t *__restrict__ item_range,
                                                                     const int64_t *__restrict__ slot_off,
                                                                     double *acc, JointTables T, lsrvt_joint out) {
     __shared__ JointWarpSmem sm[kJWarps];
@@ -212,13 +232,7 @@ __global__ void __launch_bounds__(32 * kJWarps) joint_ranges_kernel(JVars V, con
     float(*z)[kJZ] = sm[w].z;
     for (int64_t it = (int64_t)blockIdx.x * kJWarps + w; it < nitems; it += (int64_t)gridDim.x * kJWarps) {
         // the range of this item: last r with item_off[r] <= it
-        int64_t lo = 0, hi = R;
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (item_off[mid] <= it) lo = mid;
-            else hi = mid;
-        }
-        const int64_t r = lo, chunk = it - item_off[r];
+        const int64_t r = item_range[it], chunk = it - item_off[r];
         const int64_t beg = off[r], end = off[r + 1];
         const int64_t pb = beg + chunk * kJChunk, pe = min(end, pb + kJChunk);
         const bool single = end - beg <= kJChunk;
@@ -275,6 +289,125 @@ __global__ void __launch_bounds__(32 * kJWarps) joint_ranges_kernel(JVars V, con
 #pragma unroll
             for (int q = 0; q < QN; ++q)
                 if (lane + 32 * q < E) atomicAdd(A + lane + 32 * q, ad[q]);
+        }
+    }
+}
+
+// m <= 4: a lane per voxel with every sum in registers (E <= 69), no shared staging; each lane
+// sums its <= 32 voxels of the item in FP32, a butterfly reduction gives the warp's sums, FP64
+// from there.  The sums come in the table's order (orders 1, 2, 3, 4; lexicographic tuples).
+template <int M>
+struct JSmall {
+    static constexpr int T2 = M * (M + 1) / 2;
+    static constexpr int T3 = M * (M + 1) * (M + 2) / 6;
+    static constexpr int T4 = M * (M + 1) * (M + 2) * (M + 3) / 24;
+    static constexpr int E = M + T2 + T3 + T4;
+};
+
+template <int M>
+__device__ __forceinline__ void joint_accumulate(const float (&d)[M], float (&acc)[JSmall<M>::E]) {
+    float P[JSmall<M>::T2];
+    int e = 0, t = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) acc[e++] += d[i];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int j = i; j < M; ++j) {
+            P[t] = d[i] * d[j];
+            acc[e++] += P[t++];
+        }
+    // P index of (j, k), j <= k: position in the lexicographic pair list
+#define LSRVT_PIDX(a, b) ((a) * M - ((a) * ((a) - 1)) / 2 + ((b) - (a)))
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int j = i; j < M; ++j)
+#pragma unroll
+            for (int k = j; k < M; ++k) {
+                acc[e] = fmaf(d[i], P[LSRVT_PIDX(j, k)], acc[e]);
+                ++e;
+            }
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int j = i; j < M; ++j)
+#pragma unroll
+            for (int k = j; k < M; ++k)
+#pragma unroll
+                for (int l = k; l < M; ++l) {
+                    acc[e] = fmaf(P[LSRVT_PIDX(i, j)], P[LSRVT_PIDX(k, l)], acc[e]);
+                    ++e;
+                }
+#undef LSRVT_PIDX
+}
+
+constexpr int kJRegWarps = 4;  // 128-thread CTAs: the sums take up to ~140 registers at m = 4
+
+template <int M>
+__global__ void __launch_bounds__(32 * kJRegWarps) joint_ranges_reg_kernel(JVars V, const int64_t *__restrict__ off,
+                                                                        const int32_t *n_dev, int32_t cap,
+                                                                        const int64_t *__restrict__ item_off,
+                                                                        const int32_t *__restrict__ item_range,
+                                                                        const int64_t *__restrict__ slot_off,
+                                                                        double *acc_g, JointTables T, lsrvt_joint out) {
+    constexpr int E = JSmall<M>::E;
+    __shared__ double S[kJRegWarps][JSmall<M>::E];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t R = n_live(n_dev, cap);
+    const int64_t nitems = R > 0 ? item_off[R] : 0;
+    for (int64_t it = (int64_t)blockIdx.x * kJRegWarps + w; it < nitems; it += (int64_t)gridDim.x * kJRegWarps) {
+        const int64_t r = item_range[it], chunk = it - item_off[r];
+        const int64_t beg = off[r], end = off[r + 1];
+        const int64_t pb = beg + chunk * kJChunk, pe = min(end, pb + kJChunk);
+        float c[kJMax];
+        range_shift(V, M, beg, end, lane, c);
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        // U voxels per lane and step, the next step's values loaded while these are accumulated
+        constexpr int U = M <= 2 ? 4 : 2;
+        float xn[U][M];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const int64_t q = pb + lane + 32 * u;
+                xn[u][i] = q < pe ? __ldcs(V.p[i] + q) : 0.f;
+            }
+        for (int64_t p = pb + lane; p < pe; p += 32 * U) {
+            float x[U][M];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    x[u][i] = xn[u][i];
+                    const int64_t q = p + 32 * (U + u);
+                    xn[u][i] = q < pe ? __ldcs(V.p[i] + q) : 0.f;
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (p + 32 * u >= pe) break;
+                float d[M];
+#pragma unroll
+                for (int i = 0; i < M; ++i) d[i] = x[u][i] - c[i];
+                joint_accumulate<M>(d, acc);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = warp_sum(acc[e]);
+        if (end - beg <= kJChunk) {
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((e & 31) == lane) S[w][e] = (double)acc[e];
+            __syncwarp();
+            joint_finalize(T, lane, end - beg, c, S[w], r, out);
+            __syncwarp();
+        } else {
+            double *A = acc_g + slot_off[r] * (int64_t)E;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((e & 31) == lane) atomicAdd(A + e, (double)acc[e]);
         }
     }
 }
@@ -393,10 +526,10 @@ __device__ __forceinline__ int64_t child_begin(const int32_t *off32, const int64
 // blocks per parent (at least one, so every parent gets a record) and, for parents with more
 // than one block, partial-record rows
 __global__ void joint_merge_blocks_kernel(const int32_t *off32, const int64_t *off64, const int32_t *n_parent_dev,
-                                          int32_t n_parent_max, int64_t *nblk, int64_t *npart) {
+                                          int32_t n_parent_max, int64_t *nblk, int64_t *npart, int64_t *n_scan) {
     const int64_t P = n_live(n_parent_dev, n_parent_max);
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_parent_max;
-         p += (int64_t)gridDim.x * blockDim.x) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_scan = P + 1;  // the scans cover the live parents only
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= P; p += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = 0;
         if (p < P) {
             const int64_t nc = child_begin(off32, off64, p + 1) - child_begin(off32, off64, p);
@@ -489,7 +622,8 @@ __global__ void joint_volume_offsets_kernel(int64_t *off, int32_t n) {
 }
 
 struct JointWs {
-    int64_t *items, *slots;
+    int64_t *items, *slots, *n_scan;
+    int32_t *item_range;
     void *scan_items, *scan_slots;
     double *acc;
 };
@@ -500,8 +634,11 @@ JointWs carve_joint(void *ws, size_t bytes, int32_t max_ranges, int64_t n_positi
     const int64_t R = (int64_t)max_ranges + 1;
     w.items = c.take<int64_t>(R);
     w.slots = c.take<int64_t>(R);
+    w.n_scan = c.take<int64_t>(1);
     w.scan_items = c.take<char>(scan_temp_bytes(R));
     w.scan_slots = c.take<char>(scan_temp_bytes(R));
+    // items: one per range plus one per extra 1024-position chunk of a long range
+    w.item_range = c.take<int32_t>(R + n_positions / kJChunk + 1);
     // long ranges hold more than kJChunk positions each: at most n_positions / kJChunk of them
     w.acc = c.take<double>((n_positions / kJChunk + 1) * (int64_t)E);
     *need = c.used;
@@ -515,7 +652,7 @@ bool joint_ok(lsrvt_joint j) { return j.count && j.mean && j.m2 && j.m3 && j.m4;
 // partial rows are fewer than 2 * children / kJMergeBlock + 1 (the levels run one after another
 // and reuse the scratch)
 struct JointMergeWs {
-    int64_t *nblk, *npart;
+    int64_t *nblk, *npart, *n_scan;
     void *scan;
     lsrvt_joint part;
     int64_t *band_off, *vol_off;
@@ -530,6 +667,7 @@ JointMergeWs carve_joint_merge(void *ws, size_t bytes, int32_t max_children, int
     const int mm = m < 1 ? 1 : (m > kJMax ? kJMax : m);
     w.nblk = c.take<int64_t>(P);
     w.npart = c.take<int64_t>(P);
+    w.n_scan = c.take<int64_t>(1);
     w.scan = c.take<char>(scan_temp_bytes(P));
     w.part.count = c.take<int64_t>(NB);
     w.part.mean = c.take<double>(NB * mm);
@@ -546,9 +684,9 @@ void joint_merge_level(lsrvt_joint child, const int32_t *off32, const int64_t *o
                        int32_t n_parent_max, const JointTables &T, lsrvt_joint parent, JointMergeWs &w, int sms,
                        cudaStream_t s) {
     joint_merge_blocks_kernel<<<grid_for((int64_t)n_parent_max + 1, 256, sms * 4), 256, 0, s>>>(
-        off32, off64, n_parent_dev, n_parent_max, w.nblk, w.npart);
-    exclusive_scan_i64(w.nblk, (int64_t)n_parent_max + 1, nullptr, w.scan, s);
-    exclusive_scan_i64(w.npart, (int64_t)n_parent_max + 1, nullptr, w.scan, s);
+        off32, off64, n_parent_dev, n_parent_max, w.nblk, w.npart, w.n_scan);
+    exclusive_scan_i64_dev(w.nblk, (int64_t)n_parent_max + 1, w.n_scan, nullptr, w.scan, s);
+    exclusive_scan_i64_dev(w.npart, (int64_t)n_parent_max + 1, w.n_scan, nullptr, w.scan, s);
     joint_merge_stage1_kernel<<<sms * 4, 32 * kJWarps, 0, s>>>(child, off32, off64, n_parent_dev, n_parent_max,
                                                                w.nblk, w.npart, T, w.part, parent);
     joint_merge_stage2_kernel<<<grid_for(n_parent_max, kJWarps, sms * 4), 32 * kJWarps, 0, s>>>(
@@ -596,14 +734,28 @@ extern "C" lsrvt_status lsrvt_joint_moments(const float *const *values_host, int
     cudaStream_t s = as_stream(stream);
     const int sms = stream_sms(s);
     joint_items_kernel<<<grid_for(max_ranges, 256, sms * 4), 256, 0, s>>>(range_off, n_ranges_dev, max_ranges,
-                                                                           w.items, w.slots);
-    exclusive_scan_i64(w.items, (int64_t)max_ranges + 1, nullptr, w.scan_items, s);
-    exclusive_scan_i64(w.slots, (int64_t)max_ranges + 1, nullptr, w.scan_slots, s);
+                                                                           w.items, w.slots, w.n_scan);
+    exclusive_scan_i64_dev(w.items, (int64_t)max_ranges + 1, w.n_scan, nullptr, w.scan_items, s);
+    exclusive_scan_i64_dev(w.slots, (int64_t)max_ranges + 1, w.n_scan, nullptr, w.scan_slots, s);
     joint_zero_kernel<<<sms * 4, 256, 0, s>>>(w.acc, w.slots, n_ranges_dev, max_ranges, T.E);
+    joint_item_range_kernel<<<sms * 8, 256, 0, s>>>(w.items, n_ranges_dev, max_ranges, w.item_range);
+    if (m <= 4) {
+#define LSRVT_JOINT_REG(M_)                                                                                      \
+    joint_ranges_reg_kernel<M_><<<sms * 8, 32 * kJRegWarps, 0, s>>>(V, range_off, n_ranges_dev, max_ranges,    \
+                                                                    w.items, w.item_range, w.slots, w.acc, T, out)
+        if (m == 1) LSRVT_JOINT_REG(1);
+        else if (m == 2) LSRVT_JOINT_REG(2);
+        else if (m == 3) LSRVT_JOINT_REG(3);
+        else LSRVT_JOINT_REG(4);
+#undef LSRVT_JOINT_REG
+        joint_long_finalize_kernel<<<sms * 4, 32 * kJWarps, 0, s>>>(V, range_off, n_ranges_dev, max_ranges, w.slots,
+                                                                    w.acc, T, out);
+        return launch_status();
+    }
     const int qn = (T.E + 31) / 32;
 #define LSRVT_JOINT_LAUNCH(Q)                                                                                \
     joint_ranges_kernel<Q><<<sms * 4, 32 * kJWarps, 0, s>>>(V, range_off, n_ranges_dev, max_ranges, w.items, \
-                                                            w.slots, w.acc, T, out)
+                                                            w.item_range, w.slots, w.acc, T, out)
     if (qn <= 1) LSRVT_JOINT_LAUNCH(1);
     else if (qn <= 2) LSRVT_JOINT_LAUNCH(2);
     else if (qn <= 3) LSRVT_JOINT_LAUNCH(3);
