@@ -150,23 +150,27 @@ __global__ void graph_edges_total_kernel(const int64_t *n_edges, int64_t *n_arcs
 
 // CSR offsets (first arc with source >= s) and arc weights
 __global__ void graph_csr_kernel(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
-                                 const int64_t *n_arcs_dev, const int32_t *__restrict__ site_pos, Dims d, int32_t ns,
-                                 int32_t max_sites, int64_t max_arcs, int64_t *off, int32_t *adj, uint32_t *w,
-                                 int32_t *status) {
+                                 const int64_t *n_arcs_dev, const int32_t *__restrict__ site_pos, Dims d,
+                                 const int32_t *n_sites_dev, int32_t max_sites, int64_t max_arcs, int64_t *off,
+                                 int32_t *adj, uint32_t *w, int32_t *status) {
+    const int32_t ns = min(max(*n_sites_dev, 0), max_sites);  // rows past the live sites are empty
     const int64_t n_all = *n_arcs_dev;
     if (n_all > max_arcs && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, LSRVT_ERR_CAPACITY);
     const int64_t n = n_all < max_arcs ? n_all : max_arcs;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t s = t0; s <= max_sites; s += stride) {
+        if (s > ns) {
+            off[s] = n;
+            continue;
+        }
         int64_t lo = 0, hi = n;
-        const uint32_t key = (uint32_t)min((int64_t)s, (int64_t)ns);
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (src[mid] < key) lo = mid + 1;
+            if (src[mid] < (uint32_t)s) lo = mid + 1;
             else hi = mid;
         }
-        off[s] = s <= ns ? lo : n;
+        off[s] = lo;
     }
     for (int64_t i = t0; i < n; i += stride) {
         const int32_t a = (int32_t)src[i], b = (int32_t)dst[i];
@@ -380,7 +384,7 @@ extern "C" lsrvt_status lsrvt_site_graph(const int32_t *cell, const uint8_t *ban
     radix_sort_pairs(w.dst, w.src, 2 * cap, w.n_arcs32, bits, w.radix, s);
     radix_sort_pairs(w.src, w.dst, 2 * cap, w.n_arcs32, bits, w.radix, s);
     // the CSR itself: offsets over max_sites + 1 rows, arcs up to max_arcs
-    graph_csr_kernel<<<sms * 8, 256, 0, s>>>(w.src, w.dst, w.n_arcs, site_pos, d, max_sites, max_sites, max_arcs,
+    graph_csr_kernel<<<sms * 8, 256, 0, s>>>(w.src, w.dst, w.n_arcs, site_pos, d, n_sites_dev, max_sites, max_arcs,
                                              adj_off, adj, adj_w, status_dev);
     return launch_status();
 }
