@@ -70,6 +70,13 @@ __global__ void __launch_bounds__(BV) ccl_brick_kernel(const uint8_t *__restrict
     sb[t] = b;
     lab[t] = t;
     __syncthreads();
+    // a brick inside the volume whose voxels all share one band is one component rooted at its
+    // first voxel (what the unions below reach, smallest index first): no union-find needed
+    if (__syncthreads_and(inb && b != kInvalidBand && b == sb[0])) {
+        const int64_t rg = (blockIdx.x * BX) + (int64_t)d.nx * ((blockIdx.y * BY) + (int64_t)d.ny * (blockIdx.z * BZ));
+        L[g] = (int32_t)rg;
+        return;
+    }
     if (b != kInvalidBand) {
         if (lx > 0 && sb[t - 1] == b) smem_union(lab, t, t - 1);
         if (ly > 0 && sb[t - BX] == b) smem_union(lab, t, t - BX);

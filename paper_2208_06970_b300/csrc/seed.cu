@@ -54,7 +54,11 @@ __device__ int load_sort_block(const int32_t *__restrict__ comp, Dims d, BlockGe
         }
         keys[i] = k;
     }
-    block_bitonic_sort(keys, npow2);
+    __syncthreads();
+    // a block inside one component (most of them) is already in (component, index) order
+    bool ordered = true;
+    for (int i = threadIdx.x; i + 1 < npow2; i += blockDim.x) ordered &= keys[i] <= keys[i + 1];
+    if (!__syncthreads_and(ordered)) block_bitonic_sort(keys, npow2);
     return npow2;
 }
 
