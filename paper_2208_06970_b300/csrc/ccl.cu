@@ -58,7 +58,10 @@ __device__ __forceinline__ int32_t gfind(const int32_t *L, int32_t a) {
     return a;
 }
 
-__global__ void __launch_bounds__(BV) ccl_brick_kernel(const uint8_t *__restrict__ band, Dims d, int32_t *L) {
+constexpr uint8_t kMixedBrick = 0xFE;  // per-brick band summary: the band of a one-band brick, else this
+
+__global__ void __launch_bounds__(BV) ccl_brick_kernel(const uint8_t *__restrict__ band, Dims d, int32_t *L,
+                                                       uint8_t *ub) {
     __shared__ uint8_t sb[BV];
     __shared__ int lab[BV];
     int t = threadIdx.x;
@@ -72,7 +75,10 @@ __global__ void __launch_bounds__(BV) ccl_brick_kernel(const uint8_t *__restrict
     __syncthreads();
     // a brick inside the volume whose voxels all share one band is one component rooted at its
     // first voxel (what the unions below reach, smallest index first): no union-find needed
-    if (__syncthreads_and(inb && b != kInvalidBand && b == sb[0])) {
+    const bool one_band = __syncthreads_and(inb && b != kInvalidBand && b == sb[0]);
+    if (t == 0)
+        ub[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = one_band ? b : kMixedBrick;
+    if (one_band) {
         const int64_t rg = (blockIdx.x * BX) + (int64_t)d.nx * ((blockIdx.y * BY) + (int64_t)d.ny * (blockIdx.z * BZ));
         L[g] = (int32_t)rg;
         return;
@@ -108,8 +114,12 @@ __device__ void gunion(int32_t *L, int32_t a, int32_t b, int32_t *status) {
     set_status(status, LSRVT_ERR_TIMEOUT);
 }
 
-__global__ void ccl_face_kernel(const uint8_t *__restrict__ band, Dims d, int32_t *L, int32_t *status) {
+// Unions across brick faces.  Two neighbouring one-band bricks of the same band are each one
+// component, so one voxel pair of their face (the face's first) joins them and the others skip.
+__global__ void ccl_face_kernel(const uint8_t *__restrict__ band, Dims d, const uint8_t *__restrict__ ub, int32_t *L,
+                                int32_t *status) {
     int64_t n = d.n();
+    const int nbx = (d.nx + BX - 1) / BX, nby = (d.ny + BY - 1) / BY;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t x = (int32_t)(v % d.nx);
         int64_t r = v / d.nx;
@@ -118,9 +128,20 @@ __global__ void ccl_face_kernel(const uint8_t *__restrict__ band, Dims d, int32_
         if (!(fx || fy || fz)) continue;
         uint8_t b = band[v];
         if (b == kInvalidBand) continue;
-        if (fx && band[v - 1] == b) gunion(L, (int32_t)v, (int32_t)(v - 1), status);
-        if (fy && band[v - d.nx] == b) gunion(L, (int32_t)v, (int32_t)(v - d.nx), status);
-        if (fz && band[v - (int64_t)d.nx * d.ny] == b) gunion(L, (int32_t)v, (int32_t)(v - (int64_t)d.nx * d.ny), status);
+        const int bx = x / BX, by = y / BY, bz = z / BZ;
+        const uint8_t u0 = __ldg(ub + bx + (int64_t)nbx * (by + (int64_t)nby * bz));
+        // same one-band brick on the other side: only the face's first voxel pair unites them
+        auto skip = [&](int ox, int oy, int oz, bool first) {
+            if (u0 == kMixedBrick) return false;
+            const uint8_t u1 = __ldg(ub + (bx - ox) + (int64_t)nbx * ((by - oy) + (int64_t)nby * (bz - oz)));
+            return u1 == u0 && !first;
+        };
+        if (fx && band[v - 1] == b && !skip(1, 0, 0, (y % BY) == 0 && (z % BZ) == 0))
+            gunion(L, (int32_t)v, (int32_t)(v - 1), status);
+        if (fy && band[v - d.nx] == b && !skip(0, 1, 0, (x % BX) == 0 && (z % BZ) == 0))
+            gunion(L, (int32_t)v, (int32_t)(v - d.nx), status);
+        if (fz && band[v - (int64_t)d.nx * d.ny] == b && !skip(0, 0, 1, (x % BX) == 0 && (y % BY) == 0))
+            gunion(L, (int32_t)v, (int32_t)(v - (int64_t)d.nx * d.ny), status);
     }
 }
 
@@ -242,6 +263,7 @@ __global__ void ccl_count_out_kernel(const int64_t *total, int32_t *n_comp_dev, 
 
 struct CclWs {
     int32_t *L;
+    uint8_t *ub;  // per brick: its band if it holds one band only, else kMixedBrick
     int64_t *hist;
     int64_t *total;
     void *scan;
@@ -253,6 +275,7 @@ CclWs carve_ccl(void *ws, size_t bytes, Dims d, size_t *need) {
     int64_t nchunks = (n + kChunk - 1) / kChunk;
     CclWs w;
     w.L = c.take<int32_t>(n);
+    w.ub = c.take<uint8_t>((int64_t)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY) * ((d.nz + BZ - 1) / BZ));
     w.hist = c.take<int64_t>(nchunks * kBands);
     w.total = c.take<int64_t>(1);
     w.scan = c.take<char>(scan_temp_bytes(nchunks * kBands));
@@ -287,8 +310,8 @@ extern "C" lsrvt_status lsrvt_label_components(const uint8_t *band, lsrvt_dims d
     int64_t n = d.n();
     int64_t nchunks = (n + kChunk - 1) / kChunk;
     dim3 bgrid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
-    ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L);
-    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.L, status_dev);
+    ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L, w.ub);
+    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.ub, w.L, status_dev);
     ccl_compress_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.L, n);
     int warps = 8;
     int cgrid = (int)((nchunks + warps - 1) / warps);
@@ -363,8 +386,8 @@ extern "C" lsrvt_status lsrvt_label_components_static(const uint8_t *band, lsrvt
     int64_t n = d.n();
     int64_t nchunks = (n + kChunk - 1) / kChunk;
     dim3 bgrid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
-    ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L);
-    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.L, status_dev);
+    ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L, w.ub);
+    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.ub, w.L, status_dev);
     ccl_compress_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.L, n);
     int warps = 8;
     int cgrid = (int)((nchunks + warps - 1) / warps);
