@@ -590,7 +590,8 @@ def profile_step(args):
 
 def profile_layout(args):
     """One step of the workload, then two structured layouts of it, each followed by the joint
-    moments of its cells and their merge (ncu target)."""
+    moments of its cells and their merge, then the site graph and the geodesics of the largest
+    component (ncu target)."""
     import paper_2208_06970_b300 as pkg
     import workloads
     from paper_2208_06970_b300 import build
@@ -609,9 +610,15 @@ def profile_layout(args):
                                L["site_pos"].numel(), ws=pipe.ws)
         pkg.merge_joint_hierarchy(jm, L["n_sites"], L["comp_site_off"], L["comp_band"], L["n_comp"], pipe.max_comp,
                                   pipe.n_bands, ws=pipe.ws)
+    g = pkg.site_graph(L["cell"], L["band"], L["site_pos"], L["n_sites"], ws=pipe.ws, status=pipe.status)
+    off = L["comp_site_off"][:int(L["n_comp"].item()) + 1].cpu().numpy()
+    c = int((off[1:] - off[:-1]).argmax())
+    nz, ny, nx = L["cell"].shape
+    pkg.site_geodesics(g, L["site_pos"], (nx, ny, nz), int(off[c]), int(off[c + 1]), c_far=2.0, ws=pipe.ws,
+                       status=pipe.status)
     torch.cuda.synchronize()
     pkg.check_status(pipe.status, "profile layout")
-    print("profile layout ok: %d voxels" % int(out["n_kept"].item()))
+    print("profile layout ok: %d voxels, %d graph edges" % (int(out["n_kept"].item()), int(g["n_edges"].item())))
 
 
 def profile_precision(args):
