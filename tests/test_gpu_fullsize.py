@@ -258,3 +258,69 @@ def test_full_precision_moments_and_comoments_sampled_cells(precision):
     for k, (i, j) in enumerate(zip(*iu)):
         scale = np.sqrt(np.maximum(R[:, diag[i]] * R[:, diag[j]], 0.0))
         assert np.all(np.abs(C[:, k] - R[:, k]) <= 1e-4 * scale + 1e-9), (i, j)
+
+
+def test_full_joint_moments_sampled_cells(full):
+    """Joint moments of 4 variables over every cell of the 512^3 layout, as the bench computes them;
+    sampled cells (random, largest, smallest) against the FP64 oracle over those cells' voxels,
+    and the merged volume record against the oracle's moments of a voxel sample's hierarchy."""
+    pk, pipe, out, bench = full["pk"], full["pipe"], full["out"], full["bench"]
+    aux = [full["w"]["aux"][j] for j in range(bench.JOINT_VARS)]
+    lay = pk.structured_layout(out["cell"], out["n_sites"], out["site_pos"].numel(), out["comp_site_off"],
+                               out["comp_band"], out["n_comp"], pipe.max_comp, aux=aux, ws=pipe.ws,
+                               status=pipe.status)
+    jm = pk.joint_moments([lay["values"][j] for j in range(bench.JOINT_VARS)], lay["cell_off"], out["n_sites"],
+                          out["site_pos"].numel(), ws=pipe.ws)
+    torch.cuda.synchronize()
+    ns = int(out["n_sites"].item())
+    co = cpu(lay["cell_off"])[:ns + 1]
+    sizes = np.diff(co)
+    rng = np.random.default_rng(17)
+    pick = np.unique(np.concatenate([rng.choice(ns, 40, replace=False), np.argsort(sizes)[-5:],
+                                     np.argsort(sizes)[:5]]))
+    pick = pick[sizes[pick] > 0]
+    order = cpu(lay["order"])
+    A = np.stack([cpu(a).reshape(-1) for a in aux])
+    sub_order = np.concatenate([order[co[s]:co[s + 1]] for s in pick])
+    sub_off = np.concatenate([[0], np.cumsum(sizes[pick])])
+    ref = oracle.joint_moments(A, sub_order, sub_off)
+    got = {k: cpu(v)[pick] for k, v in jm.items()}
+    from itertools import combinations_with_replacement as cwr
+    m = bench.JOINT_VARS
+    assert np.array_equal(got["count"], ref["count"])
+    sig = np.sqrt(ref["m2"][:, [t for t, (i, j) in enumerate(cwr(range(m), 2)) if i == j]] / ref["count"][:, None])
+    for q, key in ((2, "m2"), (3, "m3"), (4, "m4")):
+        tups = list(cwr(range(m), q))
+        scale = ref["count"][:, None] * np.stack([np.prod(sig[:, list(t)], axis=1) for t in tups], 1)
+        assert np.all(np.abs(got[key] - ref[key]) <= 2e-5 * scale + 1e-9), key
+
+
+def test_full_site_graph_sampled(full):
+    """The 512^3 site graph, as the bench builds it: sampled sites' neighbour lists and weights
+    against the oracle's graph of the whole volume, and geodesic rows of sampled sources of the
+    largest component against the oracle's Dijkstra on that graph."""
+    pk, pipe, out = full["pk"], full["pipe"], full["out"]
+    g = pk.site_graph(out["cell"], out["band"], out["site_pos"], out["n_sites"], ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "site graph")
+    ns = int(out["n_sites"].item())
+    sp = cpu(out["site_pos"])[:ns]
+    ref = oracle.site_graph(cpu(out["cell"]), full["band"], sp)
+    E = int(g["n_edges"].item())
+    assert E == len(ref["edges"])
+    off = cpu(g["off"])[:ns + 1]
+    assert np.array_equal(off, ref["off"])
+    adj, w = cpu(g["adj"])[:2 * E], cpu(g["w"])[:2 * E].view(np.uint32)
+    assert np.array_equal(adj, ref["dst"]) and np.array_equal(w, ref["w"])
+    cso = cpu(out["comp_site_off"])[:int(out["n_comp"].item()) + 1]
+    c = int(np.argmax(np.diff(cso)))
+    s0, s1 = int(cso[c]), int(cso[c + 1])
+    nz, ny, nx = out["cell"].shape
+    dist, _ = pk.site_geodesics(g, out["site_pos"], (nx, ny, nz), s0, s1, ws=pipe.ws, status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "site geodesics")
+    D = cpu(dist).view(np.uint32).astype(np.uint64)
+    rng = np.random.default_rng(5)
+    for src in rng.choice(s1 - s0, 6, replace=False):
+        want = oracle.site_sssp(ref, s0 + int(src))[s0:s1]
+        assert np.array_equal(D[src], want)
