@@ -104,6 +104,28 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(sm))
 
 
+# --------------------------------------------------------------------------- replicas
+# The path shards into independent volumes (blocks): under torchrun each rank decomposes its own
+# volume (weak scaling), no data crosses ranks; only the step time is combined.
+def rank_seed(rank):
+    """Workload seed of a rank: every replica gets its own volume."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(ms, world, device):
+    """The step time of the job: the slowest rank's (every rank gets the result)."""
+    if world > 1:
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def job_value(world, voxels_per_rank, iters, ms):
+    """Whole-job throughput: the voxel-iterations of all ranks over the slowest rank's time."""
+    return world * voxels_per_rank * iters / (ms * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------- GPU arm
 class Pipeline:
     """The hot path with buffers and workspaces allocated once (all compute in liblsrvt)."""
@@ -174,7 +196,7 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     side = args.side
-    w = workloads.flame_workload(side=side, seed=2 + 1000 * rank, device=dev, n_aux=N_AUX, n_iters=N_ITERS)
+    w = workloads.flame_workload(side=side, seed=rank_seed(rank), device=dev, n_aux=N_AUX, n_iters=N_ITERS)
     field, aux, iso = w["field"], w["aux"], w["iso"]
     n = field.numel()
     pipe = Pipeline(pkg, field, [aux[j] for j in range(N_AUX)], iso)
@@ -212,10 +234,7 @@ def gpu_arm(args, rank, world, local_rank):
     for a, b in zip(marks_done[:-1], marks_done[1:]):
         phase[b[0]] = a[1].elapsed_time(b[1])
     pkg.check_status(pipe.status, "timed")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
 
     # ---- dominant kernels: one Lloyd iteration (tessellation + geodesically weighted update),
     # timed with CUDA events as cvt_iterate(k) - cvt_iterate(0) from the same sites
@@ -681,7 +700,7 @@ def main():
     r = gpu_arm(args, rank, world, local_rank)
     if rank == 0:
         n = r["n"]
-        value = world * n * N_ITERS / (r["ms"] * 1e-3) / 1e9
+        value = job_value(world, n, N_ITERS, r["ms"])
         forms = None
         if not args.no_forms and world == 1:
             forms = forms_arm(args, torch.device("cuda", local_rank))
