@@ -550,7 +550,8 @@ def precision_setup(pkg, side, dev, m=32):
     sp, sc, off, ns = pkg.seed(comp, None, nc, mc, 512, 16, 4, ws=ws, status=st)
     cell, _, _ = pkg.cvt_iterate(band, None, sp, ns, 10, want_dist=False, want_trace=False, ws=ws, status=st)
     del f, band, comp
-    return dict(side=side, m=m, n=n, cell=cell, aux=aux, auxl=[aux[j] for j in range(m)], sp=sp, ns=ns, ws=ws, st=st)
+    return dict(side=side, m=m, n=n, cell=cell, aux=aux, auxl=[aux[j] for j in range(m)], sp=sp, ns=ns, ws=ws, st=st,
+                off=off, cb=cb, nc=nc, mc=mc)
 
 
 def precision_arm(args, dev):
@@ -580,10 +581,32 @@ def precision_arm(args, dev):
     both = timed(lambda: pkg.aggregate(cell, auxl, sp, ns, None, None, 0, cov=True, ws=ws, status=st))
     pkg.check_status(st, "precision form")
     gb = n * 4 * (1 + m) / 1e9
+    # the same statistics on the structured layout: every cell a contiguous run of a 32 x 4 x N/128
+    # pseudo-volume (per-position cells from the layout), so the co-moments read contiguous runs
+    # instead of gathering each cell's voxels from the volume
+    on_layout = None
+    if n % 128 == 0:
+        rows = sp.numel()
+        lay = pkg.structured_layout(cell, ns, rows, P["off"], P["cb"], P["nc"], P["mc"], aux=auxl, ws=ws, status=st,
+                                    want_cells=True)
+        t_lay = timed(lambda: pkg.structured_layout(cell, ns, rows, P["off"], P["cb"], P["nc"], P["mc"], aux=auxl,
+                                                    ws=ws, status=st, out=lay, want_cells=True))
+        r = int(lay["n_kept"].item())
+        shape = (n // 128, 4, 32)
+        lcell = lay["cell_pos"].view(shape)
+        lvals = [lay["values"][j].view(shape) for j in range(m)]
+        lsite = torch.clamp(lay["cell_off"][:rows], max=max(r - 1, 0)).to(torch.int32).contiguous()
+        lmom = timed(lambda: pkg.aggregate(lcell, lvals, lsite, ns, None, None, 0, ws=ws, status=st))
+        lboth = timed(lambda: pkg.aggregate(lcell, lvals, lsite, ns, None, None, 0, cov=True, ws=ws, status=st))
+        pkg.check_status(st, "precision form on the layout")
+        on_layout = dict(layout_ms=t_lay, moments_ms=lmom, comoments_ms=lboth - lmom,
+                         comoments_gbs=gb / ((lboth - lmom) * 1e-3), total_ms=t_lay + lboth,
+                         volume_form_total_ms=both)
+        del lay, lcell, lvals, lsite
     res = dict(workload="blobs %d^3, 4 isovalues, 1 site/512 voxels, 10 Lloyd iters, %d correlated aux vars" % (side, m),
                voxels=n, sites=int(ns.item()), moments_ms=mom, moments_gbs=gb / (mom * 1e-3),
                comoments_ms=both - mom, comoments_gbs=gb / ((both - mom) * 1e-3),
-               comoments_flop_per_voxel=3 * 2 * 32 * 32,
+               comoments_flop_per_voxel=3 * 2 * 32 * 32, on_layout=on_layout,
                precision="moments: float-float sums per brick, FP64 finalise; co-moments: BF16 hi+lo split, "
                          "hi.hi + hi.lo + lo.hi on tcgen05 (FP32 accumulate), FP64 finalise")
     del P, auxl, cell

@@ -271,7 +271,10 @@ lsrvt_status lsrvt_merge_hierarchy(lsrvt_stats cells, const int32_t *n_sites_dev
  *   [cell_off[s], cell_off[s+1]), component c [comp_off[c], comp_off[c+1]); entries
  *   <= *n_sites_dev / *n_comp_dev written;
  *   band_off [257] int64 (out): band b occupies [band_off[b], band_off[b+1]);
- *   n_kept_dev [1] int64 (out): number of voxels in the layout.
+ *   n_kept_dev [1] int64 (out): number of voxels in the layout;
+ *   cell_out [N] int32 (out, nullable): the cell of each layout position, -1 past the kept
+ *   voxels -- a label array in layout order, so the statistics steps can run on the layout
+ *   (every cell then a contiguous run of positions).
  * Deterministic (stable sort).  Errors: INVALID_ARG synchronously (dims, NULL, cell not
  * 16-byte aligned, n_aux), and in status_dev when a cell id has no site or the numbering is
  * not hierarchical. */
@@ -280,8 +283,8 @@ lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims d, const in
                                      const int32_t *n_comp_dev, int32_t max_comp, const uint32_t *band_mask_host,
                                      const float *const *aux_host, int32_t n_aux, float *const *values_host,
                                      int32_t *order, int64_t *cell_off, int64_t *comp_off, int64_t *band_off,
-                                     int64_t *n_kept_dev, void *ws, size_t ws_bytes, int32_t *status_dev,
-                                     void *stream);
+                                     int64_t *n_kept_dev, int32_t *cell_out, void *ws, size_t ws_bytes,
+                                     int32_t *status_dev, void *stream);
 
 /* Joint central moments of orders 2..4 of m (1..8) variables over contiguous ranges of
  * voxel records: cells, components or bands of a structured layout (the joint-plot section

@@ -83,7 +83,8 @@ def lib():
         L.lsrvt_merge_hierarchy.argtypes = [Stats, P, i32, i32, i32, u32, P, P, P, i32, i32, Stats, Stats, Stats, P,
                                             sz, P]
         L.lsrvt_set_stream_share.argtypes = [P, i32]
-        L.lsrvt_structured_layout.argtypes = [P, Dims, P, i32, P, P, P, i32, P, P, i32, P, P, P, P, P, P, P, sz, P, P]
+        L.lsrvt_structured_layout.argtypes = [P, Dims, P, i32, P, P, P, i32, P, P, i32, P, P, P, P, P, P, P, P, sz, P,
+                                              P]
         L.lsrvt_joint_moments.argtypes = [P, i32, i64, P, P, i32, Joint, P, sz, P]
         L.lsrvt_merge_joint_hierarchy.argtypes = [Joint, P, i32, i32, P, P, P, i32, i32, Joint, Joint, Joint, P, sz, P]
         L.lsrvt_site_graph.argtypes = [P, P, Dims, P, P, i32, P, P, P, i64, P, P, sz, P, P]
@@ -365,13 +366,14 @@ def merge_hierarchy(cells, n_sites_dev, comp_site_off, comp_band, n_comp_dev, ma
 
 
 def structured_layout(cell, n_sites_dev, max_sites, comp_site_off, comp_band, n_comp_dev, max_comp, aux=(),
-                      bands=None, ws=None, status=None, out=None):
+                      bands=None, ws=None, status=None, out=None, want_cells=False):
     """Structured hierarchical layout (Sec. 3.2 "Data Reduction and Structured Data Layout"):
     the voxels of the kept bands (`bands`: iterable of band ids, None = all) ordered by
     (band, component, cell, linear index), with offsets per cell / component / band and the
     variables gathered in the same order.  Returns a dict of device tensors: order [N] int32
     and values (m, N) float32 (first n_kept entries valid), cell_off [max_sites+1],
-    comp_off [max_comp+1], band_off [257] int64, n_kept [1] int64."""
+    comp_off [max_comp+1], band_off [257] int64, n_kept [1] int64; with want_cells also
+    cell_pos [N] int32, the cell of each layout position (-1 past n_kept)."""
     aux = [a.contiguous() for a in aux]
     _require_cuda(cell, comp_site_off, comp_band, *aux)
     dev = cell.device
@@ -386,6 +388,8 @@ def structured_layout(cell, n_sites_dev, max_sites, comp_site_off, comp_band, n_
                    comp_off=torch.empty(max_comp + 1, dtype=torch.int64, device=dev),
                    band_off=torch.empty(257, dtype=torch.int64, device=dev),
                    n_kept=torch.empty(1, dtype=torch.int64, device=dev))
+    if want_cells and out.get("cell_pos") is None:
+        out["cell_pos"] = torch.empty(n, dtype=torch.int32, device=dev)
     mask = None
     if bands is not None:
         words = [0] * 8
@@ -401,7 +405,8 @@ def structured_layout(cell, n_sites_dev, max_sites, comp_site_off, comp_band, n_
                                          C.cast(mask, C.c_void_p) if mask is not None else None,
                                          C.cast(ins, C.c_void_p), m, C.cast(outs, C.c_void_p), _ptr(out["order"]),
                                          _ptr(out["cell_off"]), _ptr(out["comp_off"]), _ptr(out["band_off"]),
-                                         _ptr(out["n_kept"]), _ptr(buf), buf.numel(), _ptr(status), _stream()),
+                                         _ptr(out["n_kept"]), _ptr(out.get("cell_pos") if want_cells else None),
+                                         _ptr(buf), buf.numel(), _ptr(status), _stream()),
            "lsrvt_structured_layout")
     return out
 

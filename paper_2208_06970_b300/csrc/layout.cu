@@ -130,6 +130,7 @@ struct TileArgs {
     int32_t *slot_cnt;         // group: pair voxel counts, same slots
     const int32_t *pstart;     // scatter: layout start of each pair (by pair index)
     int32_t *order;            // scatter
+    int32_t *cell_out;         // scatter (nullable): the cell of each layout position
     VarIn in;                  // scatter
     VarOut out;                // scatter
     int m;
@@ -232,7 +233,10 @@ __global__ void __launch_bounds__(kTileThreads) layout_tile_kernel(TileArgs a) {
                 const int i = r * kTileThreads + tid;
                 const uint16_t sid = sm.segid[i];
                 pos[r] = (base + i < a.n && sid != kNoSeg) ? sm.seg_base[sid] + (i - sm.seg_start[sid]) : -1;
-                if (pos[r] >= 0) a.order[pos[r]] = (int32_t)(base + i);
+                if (pos[r] >= 0) {
+                    a.order[pos[r]] = (int32_t)(base + i);
+                    if (a.cell_out) a.cell_out[pos[r]] = __ldg(a.cell + base + i);
+                }
             }
             // four variables at a time: 32 independent loads in flight per thread
             for (int j0 = 0; j0 < a.m; j0 += 4) {
@@ -279,6 +283,13 @@ __global__ void layout_compact_pairs_kernel(const uint32_t *__restrict__ slot_ke
 }
 
 // the number of pairs: the exclusive scan's entry at ntiles
+// positions past the kept voxels: no cell (so the per-position cells form a complete label array)
+__global__ void layout_cell_tail_kernel(const int64_t *n_kept, int64_t n, int32_t *cell_out) {
+    for (int64_t p = *n_kept + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        cell_out[p] = -1;
+}
+
 __global__ void layout_pairs_total_kernel(const int64_t *tile_off, int64_t ntiles, int64_t *np64, int32_t *np32) {
     *np64 = tile_off[ntiles];
     *np32 = (int32_t)tile_off[ntiles];
@@ -404,8 +415,8 @@ extern "C" lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims 
                                                 const uint32_t *band_mask_host, const float *const *aux_host,
                                                 int32_t n_aux, float *const *values_host, int32_t *order,
                                                 int64_t *cell_off, int64_t *comp_off, int64_t *band_off,
-                                                int64_t *n_kept_dev, void *ws, size_t ws_bytes, int32_t *status_dev,
-                                                void *stream) {
+                                                int64_t *n_kept_dev, int32_t *cell_out, void *ws, size_t ws_bytes,
+                                                int32_t *status_dev, void *stream) {
     if (!dims_ok(dd) || !cell || !n_sites_dev || max_sites < 1 || !comp_site_off || !comp_band || !n_comp_dev ||
         max_comp < 0 || n_aux < 0 || n_aux > kLayMaxVars || (n_aux > 0 && (!aux_host || !values_host)) || !order ||
         !cell_off || !comp_off || !band_off || !n_kept_dev)
@@ -440,6 +451,7 @@ extern "C" lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims 
     a.slot_cnt = w.slot_cnt;
     a.pstart = w.pstart;
     a.order = order;
+    a.cell_out = cell_out;
     a.m = n_aux;
     a.status = status_dev;
     const int tgrid = (int)(ntiles < sms * 5 ? ntiles : sms * 5);
@@ -459,5 +471,6 @@ extern "C" lsrvt_status lsrvt_structured_layout(const int32_t *cell, lsrvt_dims 
         w.pkey, w.cs, w.np64, n_kept_dev, n_sites_dev, max_sites, comp_site_off, comp_band, n_comp_dev, max_comp,
         cell_off, comp_off, band_off);
     layout_tile_kernel<kScatter><<<tgrid, kTileThreads, 0, s>>>(a);
+    if (cell_out) layout_cell_tail_kernel<<<sms * 4, 256, 0, s>>>(n_kept_dev, n, cell_out);
     return launch_status();
 }

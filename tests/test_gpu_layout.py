@@ -37,6 +37,20 @@ def _case(dims, seed, P=200, n_iters=1, iso=(0.3, 0.6), nan_every=0):
     return cell, sc, off, cb
 
 
+def _sites(cell, ns):
+    # one voxel of each cell (its first in linear order): a valid shift voxel for the statistics
+    flat = cell.ravel()
+    first = np.full(ns, 0, np.int32)
+    idx = np.nonzero(flat >= 0)[0]
+    c = flat[idx]
+    seen = np.zeros(ns, bool)
+    for v, s in zip(idx, c):
+        if not seen[s]:
+            seen[s] = True
+            first[s] = v
+    return first
+
+
 def _gpu_layout(pk, cell, off, cb, aux, bands, slack=0, status=None):
     ns, nc = int(off[-1]), len(cb)
     st = pk.new_status() if status is None else status
@@ -142,3 +156,53 @@ def test_layout_store_roundtrip(pk, tmp_path):
         lo, hi = ref["comp_off"][c], ref["comp_off"][c + 1]
         assert np.array_equal(coords, ref["order"][lo:hi])
         assert np.array_equal(vals, ref["values"][:, lo:hi])
+
+
+def test_statistics_on_layout_order(pk):
+    # the statistics steps run on the layout (cells as contiguous runs of a 32 x 4 x N/128
+    # pseudo-volume, per-position cells from the layout) give the volume form's results: counts,
+    # min, max and histograms bit for bit, moments within the moment bar, co-moments within theirs
+    dims = (64, 32, 24)  # N = 49152, a multiple of 128
+    cell, sc, off, cb = _case(dims, 17, P=120)
+    m = 6
+    aux = workloads.correlated_aux(dims, m, 17, "cpu")[0].numpy()
+    ns, nc = int(off[-1]), len(cb)
+    st = pk.new_status()
+    gcell = torch.from_numpy(cell).cuda()
+    gaux = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in aux]
+    lay = pk.structured_layout(gcell, torch.tensor([ns], dtype=torch.int32, device="cuda"), ns,
+                               torch.from_numpy(off).cuda(), torch.from_numpy(cb).cuda(),
+                               torch.tensor([nc], dtype=torch.int32, device="cuda"), nc, aux=gaux, status=st,
+                               want_cells=True)
+    pk.check_status(st, "layout")
+    N = cell.size
+    r = int(lay["n_kept"].item())
+    cpos = cpu(lay["cell_pos"])
+    assert np.array_equal(cpos[:r], cell.ravel()[cpu(lay["order"])[:r]]) and np.all(cpos[r:] == -1)
+    shape = (N // 128, 4, 32)
+    lcell = lay["cell_pos"].view(shape)
+    lvals = [lay["values"][j].view(shape) for j in range(m)]
+    # shift voxel of each cell: its first layout position
+    lsite = torch.clamp(lay["cell_off"][:ns], max=max(r - 1, 0)).to(torch.int32).contiguous()
+    ns_t = torch.tensor([ns], dtype=torch.int32, device="cuda")
+    lo, scale = pk.aux_range(gcell, gaux, 16, st)
+    vol = pk.aggregate(gcell, gaux, torch.from_numpy(_sites(cell, ns)).cuda(), ns_t, lo, scale, 16, cov=True,
+                       status=st)
+    got = pk.aggregate(lcell, lvals, lsite, ns_t, lo, scale, 16, cov=True, status=st)
+    pk.check_status(st, "statistics")
+    for k in ("count", "min", "max", "hist"):
+        assert torch.equal(got[k][:ns], vol[k][:ns]), k
+    ref = oracle.aggregate(cell, aux, ns, cpu(lo), cpu(scale), 16, cov=True)
+    gm, gm2 = cpu(got["mean"])[:ns], cpu(got["m2"])[:ns]
+    cnt = ref["count"][:, None]
+    ex2 = ref["m2"] / np.maximum(cnt, 1) + ref["mean"] ** 2
+    assert np.all(np.abs(gm - ref["mean"]) <= 1e-6 * np.maximum(np.abs(ref["mean"]), 1e-6 * ex2) + 1e-12)
+    assert np.all(np.abs(gm2 / np.maximum(cnt, 1) - ref["m2"] / np.maximum(cnt, 1))
+                  <= 1e-6 * np.maximum(ref["m2"] / np.maximum(cnt, 1), 1e-6 * ex2) + 1e-12)
+    from itertools import combinations_with_replacement as cwr
+    di = [t for t, (i, j) in enumerate(cwr(range(m), 2)) if i == j]
+    R = ref["comom"]
+    C = cpu(got["comom"])[:ns]
+    for t, (i, j) in enumerate(cwr(range(m), 2)):
+        bound = 1e-4 * np.sqrt(np.maximum(R[:, di[i]] * R[:, di[j]], 0)) + 1e-9
+        assert np.all(np.abs(C[:, t] - R[:, t]) <= bound), (i, j)
