@@ -35,9 +35,9 @@ def _rank_main(rank, world, port, out):
 def test_two_replicas_combine_the_slowest_time():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    ctx = mp.get_context("spawn")  # never fork (a forked child of a CUDA process can hang)
+    mgr = ctx.Manager()
     out = mgr.dict()
-    ctx = mp.get_context("spawn")
     procs = [ctx.Process(target=_rank_main, args=(r, world, port, out)) for r in range(world)]
     for p in procs:
         p.start()
