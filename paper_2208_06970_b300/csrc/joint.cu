@@ -4,13 +4,18 @@
 // cokurtosis of the raw data; Sec. 3.3 merges summaries over cells, components and bands.
 //
 // Regions are contiguous ranges of a structured layout (lsrvt_structured_layout): the variables
-// of a cell, component or band are one coalesced stream.  A warp takes a range (or a chunk of a
-// long one), stages 32 voxels' vectors z = (1, d_i, d_i d_j) in shared memory (d = x - c, c the
-// mean of the range's first 32 voxels: a shift close to the range's mean, the same for all its
-// chunks, which keeps the shift corrections below small) and accumulates the raw sums
+// of a cell, component or band are one coalesced stream.  Work items are ranges, or chunks of
+// 1024 positions of long ones; d = x - c with c the mean of the range's first 32 voxels (a shift
+// close to the range's mean, the same for all its chunks, which keeps the shift corrections
+// below small).  The raw sums
 //   S1_i = sum d_i, S2_ij = sum d_i d_j, S3_ijk = sum d_i (d_j d_k), S4_ijkl = sum (d_i d_j)(d_k d_l)
-// as products of two z entries, the entries dealt out to the lanes; FP32 partials go to FP64
-// every 32 voxels.  The central moments follow exactly (in FP64) from the shift formulas:
+// are accumulated in one of two ways:
+//   m <= 4 -- a lane per voxel with all sums (at most 69) in registers, FP32 over the lane's
+//             <= 32 voxels of the item, then a butterfly reduction across the warp;
+//   m <= 8 -- 32 voxels' vectors z = (1, d_i, d_i d_j) staged in shared memory and the sums, as
+//             products of two z entries, dealt out to the lanes; FP32 partials go to FP64 every
+//             32 voxels.
+// The central moments follow exactly (in FP64) from the shift formulas:
 //   e = S1 / n, M2 = S2 - n e e, M3 = S3 - sum_3 e S2 + 2 n e e e,
 //   M4 = S4 - sum_4 e S3 + sum_6 e e S2 - 3 n e e e e.
 // Merges combine records pairwise (Pebay 2008), children in id order, in FP64.
