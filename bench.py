@@ -521,17 +521,19 @@ def forms_arm(args, dev):
         jobs.append(dict(field=f, iso=r["iso"], voxels_per_site=r["voxels_per_site"], n_iters=r["n_iters"], aux=aux,
                          gamma=0, strat_block=16, rng_seed=r["seed"], n_bins=32))
         r["bytes"] = runtime.job_bytes(jobs[-1])
+        r["work"] = int(np.prod(r["dims"])) * r["n_iters"]  # voxel-iterations: the admission estimate
     for k, r in enumerate(reqs):
         r["k"] = k
     summ = {}
-    for name, slots in (("plain", 1), ("served", args.slots)):
-        srv = runtime.Server(n_slots=slots, hbm_budget=args.hbm_budget << 30, device=dev)
+    for name, slots, policy in (("plain", 1, "fifo"), ("served", args.slots, "fifo"), ("served_sjf", args.slots, "sjf")):
+        srv = runtime.Server(n_slots=slots, hbm_budget=args.hbm_budget << 30, device=dev, policy=policy)
         srv.serve([dict(arrival=0.0, k=0, bytes=reqs[0]["bytes"])], lambda r: jobs[r["k"]])  # warm-up
         torch.cuda.synchronize()
         recs = srv.serve(reqs, lambda r: jobs[r["k"]])
         summ[name] = runtime.latency_summary(recs)
     out["served"] = dict(requests=len(reqs), rate_per_s=50.0, sides="64..%d" % args.serve_hi, slots=args.slots,
-                         hbm_budget_gib=args.hbm_budget, plain=summ["plain"], served=summ["served"])
+                         hbm_budget_gib=args.hbm_budget, plain=summ["plain"], served=summ["served"],
+                         served_sjf=summ["served_sjf"])
     return out
 
 

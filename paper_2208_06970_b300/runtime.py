@@ -151,23 +151,50 @@ class GraphBatch:
             check_status(out["status"], "block %d" % k)
 
 
-class Server:
-    """Continuous batching: requests are admitted in arrival order whenever a slot is free and
-    their estimated device bytes fit in the remaining HBM budget; admitted requests run
-    concurrently on the slots' streams.  Latency = completion - arrival (host clock)."""
+def pick_next(pending, requests, now, used, budget, active, policy="fifo"):
+    """Admission choice of the server.  pending: indices not yet admitted, in arrival order.
+    A request is eligible once it has arrived and its estimated device bytes fit in the budget
+    left (any request fits when nothing runs, so the server always progresses).  'fifo' admits
+    the earliest arrival and waits for it when it does not fit yet; 'sjf' admits the eligible
+    request with the least work (requests[i]['work'], else its bytes), earliest arrival first on
+    ties.  Returns the chosen index or None."""
+    def fits(i):
+        return used + (requests[i].get("bytes") or 0) <= budget or active == 0
 
-    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda", share=None):
+    arrived = [i for i in pending if requests[i]["arrival"] <= now]
+    if not arrived:
+        return None
+    if policy == "fifo":
+        return arrived[0] if fits(arrived[0]) else None
+    if policy == "sjf":
+        ok = [i for i in arrived if fits(i)]
+        if not ok:
+            return None
+        return min(ok, key=lambda i: (requests[i].get("work", requests[i].get("bytes") or 0), requests[i]["arrival"]))
+    raise ValueError("unknown admission policy %r" % (policy,))
+
+
+class Server:
+    """Continuous batching: requests are admitted whenever a slot is free and their estimated
+    device bytes fit in the remaining HBM budget -- in arrival order ('fifo') or smallest work
+    first among those that have arrived ('sjf'); admitted requests run concurrently on the
+    slots' streams.  Latency = completion - arrival (host clock)."""
+
+    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda", share=None, policy="fifo"):
         share = default_share(n_slots) if share is None else share
         self.slots = [Slot(device, share) for _ in range(n_slots)]
         self.budget = int(hbm_budget)
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("unknown admission policy %r" % (policy,))
+        self.policy = policy
 
     def serve(self, requests, make_job, keep_outputs=False):
         """requests: list of dicts with 'arrival' (seconds from start); make_job(req) builds the
         job (device tensors) when the request is admitted.  Returns one record per request."""
-        order = sorted(range(len(requests)), key=lambda i: requests[i]["arrival"])
+        pending = sorted(range(len(requests)), key=lambda i: requests[i]["arrival"])
         records = [None] * len(requests)
         cv = threading.Condition()
-        state = dict(used=0, next=0, free=list(range(len(self.slots))), active=0, error=None)
+        state = dict(used=0, active=0, error=None)
         t0 = time.perf_counter()
 
         def admit_loop(slot_id):
@@ -175,18 +202,17 @@ class Server:
             while True:
                 with cv:
                     while True:
-                        if state["error"] is not None or state["next"] >= len(order):
+                        if state["error"] is not None or not pending:
                             return
-                        i = order[state["next"]]
                         now = time.perf_counter() - t0
-                        wait = requests[i]["arrival"] - now
-                        need = requests[i].get("bytes") or 0
-                        fits = state["used"] + need <= self.budget or state["active"] == 0
-                        if wait <= 0 and fits:
-                            state["next"] += 1
+                        i = pick_next(pending, requests, now, state["used"], self.budget, state["active"], self.policy)
+                        if i is not None:
+                            pending.remove(i)
+                            need = requests[i].get("bytes") or 0
                             state["used"] += need
                             state["active"] += 1
                             break
+                        wait = requests[pending[0]]["arrival"] - now
                         cv.wait(timeout=max(min(wait, 0.05), 0.0005) if wait > 0 else 0.01)
                 try:
                     admitted = time.perf_counter() - t0

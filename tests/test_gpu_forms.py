@@ -79,13 +79,15 @@ def test_autotuner_picks_a_schedule_without_changing_results(pk):
     assert best in times and len(times) == 3 and all(t > 0 for t in times.values())
 
 
-def test_served_requests_equal_alone(pk):
+@pytest.mark.parametrize("policy", ["fifo", "sjf"])
+def test_served_requests_equal_alone(pk, policy):
     from paper_2208_06970_b300 import runtime
     jobs = _jobs(8, 24, 64, 5)
-    reqs = [dict(arrival=0.02 * i, k=i, bytes=runtime.job_bytes(j)) for i, j in enumerate(jobs)]
+    reqs = [dict(arrival=0.02 * i, k=i, bytes=runtime.job_bytes(j), work=j["field"].numel() * j["n_iters"])
+            for i, j in enumerate(jobs)]
     # a budget of about two requests forces admission to wait for memory
     budget = 2 * max(r["bytes"] for r in reqs)
-    srv = runtime.Server(n_slots=3, hbm_budget=budget)
+    srv = runtime.Server(n_slots=3, hbm_budget=budget, policy=policy)
     recs = srv.serve(reqs, lambda r: jobs[r["k"]], keep_outputs=True)
     assert all(r is not None for r in recs)
     assert all(r["finished"] >= r["arrival"] for r in recs)
