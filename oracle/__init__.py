@@ -19,6 +19,10 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                       L-infinity BFS bounds
   update/cvt_iterate  independent closed-form Lloyd on a box; LOS hand cases;
                       invariants (sites stay in their component)
+  anyangle_assign     single site in a convex region: ceil(2^16 |x_v - x_s|) closed form;
+                      1-D line: nearest-site distances; bounds ceil-Euclidean <= d <= chamfer
+                      geodesic (assign) and d >= brute-force visibility-graph shortest path;
+                      src chains consistent and ending at the voxel's own site
   aggregate           numpy per-cell statistics (np.var/np.cov definitions)
   merge               direct per-component / per-band statistics
   joint_moments       numpy einsum per region; shift invariance; symmetric data (odd
@@ -36,7 +40,7 @@ from . import build as _build
 _lib = None
 
 ERRORS = {0: "ok", -1: "invalid argument", -2: "isovalues not strictly increasing", -3: "capacity",
-          -4: "out of memory", -5: "distance overflow", -6: "non-finite value"}
+          -4: "out of memory", -5: "distance overflow", -6: "non-finite value", -7: "round limit reached"}
 
 
 class OracleError(RuntimeError):
@@ -61,8 +65,11 @@ def lib():
         L.orc_assign.argtypes = [P, i32, i32, i32, P, i32, P, P]
         L.orc_los.argtypes = [P, i32, i32, i32, i32, i32]
         L.orc_update.argtypes = [P, P, i32, i32, i32, P, P, P, i32, P, P, P, P, P, P]
+        L.orc_update_src.argtypes = [P, P, i32, i32, i32, P, P, P, P, i32, P, P, P, P, P, P]
         L.orc_update_selected.argtypes = [P, P, i32, i32, i32, P, P, P, i32, P, P, P]
         L.orc_cvt_iterate.argtypes = [P, P, i32, i32, i32, P, i32, i32, P, P, P]
+        L.orc_anyangle_assign.argtypes = [P, i32, i32, i32, P, i32, i32, P, P, P, P]
+        L.orc_cvt_iterate_anyangle.argtypes = [P, P, i32, i32, i32, P, i32, i32, i32, P, P, P, P, P]
         L.orc_aux_range.argtypes = [P, P, i32, i64, i32, P, P, P]
         L.orc_aggregate.argtypes = [P, P, i32, i64, i32, P, P, i32, i32, P, P, P, P, P, P, P]
         L.orc_merge.argtypes = [i32, P, i32, i32, i32, i32] + [P] * 7 + [P] * 7
@@ -173,8 +180,11 @@ def los(band, v, s):
     return bool(lib().orc_los(_p(band), nx, ny, nz, int(v), int(s)))
 
 
-def update(band, q, cell, dist, site_pos, diagnostics=False):
-    """Geodesically weighted site update (Eq. 2).  Returns (new_pos, (moved, sumsq)[, diag])."""
+def update(band, q, cell, dist, site_pos, diagnostics=False, src=None):
+    """Geodesically weighted site update (Eq. 2).  Returns (new_pos, (moved, sumsq)[, diag]).
+
+    With `src` (the source map of the any-angle tessellation) phi follows src chains instead
+    of the chamfer parents."""
     band = np.ascontiguousarray(band, dtype=np.uint8)
     nx, ny, nz = _dims(band)
     if q is not None:
@@ -192,8 +202,13 @@ def update(band, q, cell, dist, site_pos, diagnostics=False):
         sums = np.empty((max(S, 1), 4), np.int64)
     else:
         parent = losv = phi = sums = None
-    _check(lib().orc_update(_p(band), _p(q), nx, ny, nz, _p(cell), _p(dist), _p(site_pos), S, _p(new_pos),
-                            _p(stats), _p(parent), _p(losv), _p(phi), _p(sums)), "update")
+    if src is None:
+        _check(lib().orc_update(_p(band), _p(q), nx, ny, nz, _p(cell), _p(dist), _p(site_pos), S, _p(new_pos),
+                                _p(stats), _p(parent), _p(losv), _p(phi), _p(sums)), "update")
+    else:
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        _check(lib().orc_update_src(_p(band), _p(q), nx, ny, nz, _p(cell), _p(dist), _p(src), _p(site_pos), S,
+                                    _p(new_pos), _p(stats), _p(parent), _p(losv), _p(phi), _p(sums)), "update_src")
     out = (new_pos[:S].copy(), (int(stats[0]), int(stats[1])))
     if diagnostics:
         return out + (dict(parent=parent, los=losv.astype(bool), phi=phi, sums=sums[:S]),)
@@ -237,6 +252,41 @@ def cvt_iterate(band, q, site_pos, n_iters):
     _check(lib().orc_cvt_iterate(_p(band), _p(q), nx, ny, nz, _p(sp), len(sp), int(n_iters), _p(cell), _p(dist),
                                  _p(trace)), "cvt_iterate")
     return sp, cell, dist, trace[:n_iters]
+
+
+def anyangle_assign(band, site_pos, max_rounds=1 << 16):
+    """Any-angle restricted geodesic Voronoi tessellation (Sec. 3.2 region growing with
+    src(w) shortcuts, synchronous rounds).  Returns (cell, dist, src, rounds)."""
+    band = np.ascontiguousarray(band, dtype=np.uint8)
+    site_pos = np.ascontiguousarray(site_pos, dtype=np.int32)
+    nx, ny, nz = _dims(band)
+    cell = np.empty(band.shape, np.int32)
+    dist = np.empty(band.shape, np.uint32)
+    src = np.empty(band.shape, np.int32)
+    rounds = np.zeros(1, np.int32)
+    _check(lib().orc_anyangle_assign(_p(band), nx, ny, nz, _p(site_pos), len(site_pos), int(max_rounds), _p(cell),
+                                     _p(dist), _p(src), _p(rounds)), "anyangle_assign")
+    return cell, dist, src, int(rounds[0])
+
+
+def cvt_iterate_anyangle(band, q, site_pos, n_iters, max_rounds=1 << 16):
+    """Algorithm 1 with the any-angle tessellation; the Eq. 2 update follows src chains.
+
+    Returns (site_pos, cell, dist, src, trace[n_iters, 2], rounds[n_iters + 1])."""
+    band = np.ascontiguousarray(band, dtype=np.uint8)
+    nx, ny, nz = _dims(band)
+    if q is not None:
+        q = np.ascontiguousarray(q, dtype=np.uint16)
+    sp = np.array(site_pos, dtype=np.int32, copy=True)
+    cell = np.empty(band.shape, np.int32)
+    dist = np.empty(band.shape, np.uint32)
+    src = np.empty(band.shape, np.int32)
+    trace = np.zeros((max(n_iters, 1), 2), np.int64)
+    rounds = np.zeros(n_iters + 1, np.int32)
+    _check(lib().orc_cvt_iterate_anyangle(_p(band), _p(q), nx, ny, nz, _p(sp), len(sp), int(n_iters),
+                                          int(max_rounds), _p(cell), _p(dist), _p(src), _p(trace), _p(rounds)),
+           "cvt_iterate_anyangle")
+    return sp, cell, dist, src, trace[:n_iters], rounds
 
 
 def aux_range(cell, aux, n_bins):

@@ -31,6 +31,7 @@
 #define ORC_ENOMEM -4
 #define ORC_EOVERFLOW -5
 #define ORC_ENONFINITE -6
+#define ORC_ETIMEOUT -7
 
 #define INVALID_BAND 0xFF
 
@@ -591,7 +592,7 @@ int orc_los(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
 /* size replay check a sample of cells.                                       */
 static int update_impl(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
                        const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
-                       const uint8_t *site_sel, int32_t *new_pos, int64_t *stats,
+                       const uint8_t *site_sel, const int32_t *src_in, int32_t *new_pos, int64_t *stats,
                        int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
 {
     int64_t n = (int64_t)nx * ny * nz;
@@ -608,7 +609,11 @@ static int update_impl(const uint8_t *band, const uint16_t *q, int32_t nx, int32
         if (site_sel && !site_sel[s]) continue;
         int32_t x = (int32_t)(v % nx), y = (int32_t)((v / nx) % ny), z = (int32_t)(v / ((int64_t)nx * ny));
         if (dist[v] == 0) { parent[v] = (int32_t)v; }
-        else {
+        else if (src_in) {
+            /* any-angle paths: the path's next node is the voxel's source */
+            parent[v] = src_in[v];
+            if (parent[v] < 0 || parent[v] >= n || cell[parent[v]] != s) { rc = ORC_EINVAL; goto done; }
+        } else {
             for (int dz = -1; dz <= 1 && parent[v] < 0; ++dz)
                 for (int dy = -1; dy <= 1 && parent[v] < 0; ++dy)
                     for (int dx = -1; dx <= 1 && parent[v] < 0; ++dx) {
@@ -674,7 +679,20 @@ int orc_update(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, i
                int32_t *new_pos, int64_t *stats,
                int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
 {
-    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, NULL, new_pos, stats,
+    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, NULL, NULL, new_pos, stats,
+                       parent_out, los_out, phi_out, sums_out);
+}
+
+/* The same update with the any-angle path representation: a voxel's next path */
+/* node is its source src[v] (from orc_anyangle_assign) instead of the chamfer */
+/* parent, so phi(v) = v if los(v, site(v)) else phi(src(v)).                  */
+int orc_update_src(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+                   const int32_t *cell, const uint32_t *dist, const int32_t *src, const int32_t *site_pos,
+                   int32_t n_sites, int32_t *new_pos, int64_t *stats,
+                   int32_t *parent_out, uint8_t *los_out, int32_t *phi_out, int64_t *sums_out)
+{
+    if (!src) return ORC_EINVAL;
+    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, NULL, src, new_pos, stats,
                        parent_out, los_out, phi_out, sums_out);
 }
 
@@ -685,7 +703,7 @@ int orc_update_selected(const uint8_t *band, const uint16_t *q, int32_t nx, int3
                         const uint8_t *site_sel, int32_t *new_pos, int64_t *sums_out)
 {
     int64_t stats[2];
-    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, site_sel, new_pos, stats,
+    return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, site_sel, NULL, new_pos, stats,
                        NULL, NULL, NULL, sums_out);
 }
 
@@ -712,6 +730,155 @@ int orc_cvt_iterate(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t 
         if (trace) { trace[2 * it] = st[0]; trace[2 * it + 1] = st[1]; }
     }
     rc = orc_assign(band, nx, ny, nz, site_pos, n_sites, cell, dist);
+done:
+    free(np);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Any-angle restricted geodesic Voronoi tessellation, Sec. 3.2 "Discrete     */
+/* Restricted Geodesic Voronoi Tessellation".  Region growing: each voxel v   */
+/* polls its neighbours w and weighs two paths, (v, P_w) of length            */
+/* |x_v - x_w| + d[w] and the shortcut (v, P_src(w)) of length                */
+/* |x_v - x_src(w)| + d[src(w)]; the shortcut only when the ray from v to     */
+/* src(w) stays in the band.  Updates take effect in the next invocation      */
+/* (synchronous rounds: round r+1 reads only the state of round r), and the   */
+/* rounds repeat until one changes nothing.                                   */
+/* Readings:                                                                  */
+/*  - a length |x_a - x_b| is ceil(2^16 |x_a - x_b|) (16.16 fixed point, an   */
+/*    integer), so path lengths are exact sums;                               */
+/*  - v polls the 26-neighbours it has an edge with (the box they span lies   */
+/*    in v's band, as for the chamfer metric); the ray is the 6-connected     */
+/*    traversal walked from v (orc_los);                                      */
+/*  - v also re-evaluates its own path (v, P_src(v)) with the current          */
+/*    d[src(v)], so at the fixed point d[v] = |x_v - x_src(v)| + d[src(v)]    */
+/*    holds everywhere and every src chain ends at the voxel's own site;     */
+/*  - v's new state is the lexicographic minimum of (length, site, d[src],    */
+/*    src) over these candidates: equal lengths go to the lower site id, then */
+/*    to the source nearer its site (the longer straight segment), then to   */
+/*    the lower voxel index.  The re-evaluated own path is never worse than   */
+/*    the previous state, so states only decrease and the rounds end.         */
+/* Sites start at (0, s, 0, p_s) (the lowest id on a shared voxel), every     */
+/* other voxel unreached.  Unreached / invalid voxels: cell -1, dist          */
+/* 0xFFFFFFFF, src -1.  *rounds = rounds run, the last (unchanged) included.  */
+/* ------------------------------------------------------------------------- */
+typedef struct { uint64_t d; int32_t s; uint64_t dp; int32_t p; } aa_cand;
+
+uint32_t orc_site_weight(int32_t dx, int32_t dy, int32_t dz);
+
+static int aa_less(const aa_cand *a, const aa_cand *b)
+{
+    if (a->d != b->d) return a->d < b->d;
+    if (a->s != b->s) return a->s < b->s;
+    if (a->dp != b->dp) return a->dp < b->dp;
+    return a->p < b->p;
+}
+
+/* ceil(2^16 |x_a - x_b|); UINT64_MAX beyond the 32-bit distance range */
+static uint64_t seg_length(int32_t nx, int32_t ny, int64_t a, int64_t b)
+{
+    int64_t dx = a % nx - b % nx, dy = (a / nx) % ny - (b / nx) % ny, dz = a / ((int64_t)nx * ny) - b / ((int64_t)nx * ny);
+    if ((uint64_t)(dx * dx + dy * dy + dz * dz) >= ((uint64_t)1 << 32)) return UINT64_MAX;
+    return orc_site_weight((int32_t)dx, (int32_t)dy, (int32_t)dz);
+}
+
+int orc_anyangle_assign(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
+                        const int32_t *site_pos, int32_t n_sites, int32_t max_rounds,
+                        int32_t *cell, uint32_t *dist, int32_t *src, int32_t *rounds)
+{
+    const uint32_t INF = 0xFFFFFFFFu;
+    int64_t n = (int64_t)nx * ny * nz;
+    uint32_t *D[2];
+    int32_t *S[2], *Q[2];
+    D[0] = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n); D[1] = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    S[0] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n); S[1] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    Q[0] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n); Q[1] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int rc = ORC_OK, cur = 0;
+    int32_t r = 0;
+    if (!D[0] || !D[1] || !S[0] || !S[1] || !Q[0] || !Q[1]) { rc = ORC_ENOMEM; goto done; }
+    for (int64_t v = 0; v < n; ++v) { D[0][v] = INF; S[0][v] = -1; Q[0][v] = -1; }
+    for (int32_t s = 0; s < n_sites; ++s) {
+        int32_t p = site_pos[s];
+        if (p < 0 || p >= n || band[p] == INVALID_BAND) { rc = ORC_EINVAL; goto done; }
+        if (D[0][p] == 0) continue; /* a lower id holds this voxel */
+        D[0][p] = 0; S[0][p] = s; Q[0][p] = p;
+    }
+    for (;;) {
+        if (r >= max_rounds) { rc = ORC_ETIMEOUT; goto done; }
+        ++r;
+        const uint32_t *d0 = D[cur];
+        const int32_t *s0 = S[cur], *q0 = Q[cur];
+        uint32_t *d1 = D[cur ^ 1];
+        int32_t *s1 = S[cur ^ 1], *q1 = Q[cur ^ 1];
+        int changed = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            aa_cand best = {UINT64_MAX, INT32_MAX, UINT64_MAX, INT32_MAX};
+            if (band[v] != INVALID_BAND) {
+                int32_t x = (int32_t)(v % nx), y = (int32_t)((v / nx) % ny), z = (int32_t)(v / ((int64_t)nx * ny));
+                /* own path, re-evaluated */
+                int32_t u = q0[v];
+                if (u >= 0) {
+                    uint64_t L = u == v ? 0 : seg_length(nx, ny, v, u);
+                    if (L != UINT64_MAX) { aa_cand c = {d0[u] + L, s0[u], d0[u], u}; best = c; }
+                }
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dx && !dy && !dz) continue;
+                            if (!has_edge(band, nx, ny, nz, x, y, z, dx, dy, dz)) continue;
+                            int64_t w = (x + dx) + (int64_t)nx * ((y + dy) + (int64_t)ny * (z + dz));
+                            if (d0[w] == INF) continue;
+                            /* (v, P_w) */
+                            aa_cand c = {(uint64_t)d0[w] + edge_weight(dx, dy, dz), s0[w], d0[w], (int32_t)w};
+                            if (aa_less(&c, &best)) best = c;
+                            /* (v, P_src(w)): a shortcut that cannot win needs no ray cast */
+                            int32_t t = q0[w];
+                            if (t < 0 || t == w || t == v) continue;
+                            uint64_t L = seg_length(nx, ny, v, t);
+                            if (L == UINT64_MAX) continue;
+                            aa_cand c2 = {(uint64_t)d0[t] + L, s0[t], d0[t], t};
+                            if (aa_less(&c2, &best) && orc_los(band, nx, ny, nz, (int32_t)v, t)) best = c2;
+                        }
+            }
+            if (best.d != UINT64_MAX && best.d > 0xFFFFFFFEull) { rc = ORC_EOVERFLOW; goto done; }
+            uint32_t nd = best.d == UINT64_MAX ? INF : (uint32_t)best.d;
+            int32_t ns = best.d == UINT64_MAX ? -1 : best.s, np = best.d == UINT64_MAX ? -1 : best.p;
+            if (nd != d0[v] || ns != s0[v] || np != q0[v]) changed = 1;
+            d1[v] = nd; s1[v] = ns; q1[v] = np;
+        }
+        cur ^= 1;
+        if (!changed) break;
+    }
+    for (int64_t v = 0; v < n; ++v) { cell[v] = S[cur][v]; dist[v] = D[cur][v]; if (src) src[v] = Q[cur][v]; }
+    if (rounds) *rounds = r;
+done:
+    free(D[0]); free(D[1]); free(S[0]); free(S[1]); free(Q[0]); free(Q[1]);
+    return rc;
+}
+
+/* Algorithm 1 with the any-angle tessellation: n_iters x (tessellation, Eq. 2  */
+/* update with phi following the src chain), then a final tessellation.       */
+/* rounds[it] = synchronous rounds of tessellation it (n_iters + 1 entries).   */
+int orc_cvt_iterate_anyangle(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
+                             int32_t *site_pos, int32_t n_sites, int32_t n_iters, int32_t max_rounds,
+                             int32_t *cell, uint32_t *dist, int32_t *src, int64_t *trace, int32_t *rounds)
+{
+    if (!src) return ORC_EINVAL;
+    int32_t *np = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_sites > 0 ? n_sites : 1));
+    if (!np) return ORC_ENOMEM;
+    int rc = ORC_OK;
+    for (int32_t it = 0; it < n_iters; ++it) {
+        rc = orc_anyangle_assign(band, nx, ny, nz, site_pos, n_sites, max_rounds, cell, dist, src,
+                                 rounds ? rounds + it : NULL);
+        if (rc) goto done;
+        int64_t st[2];
+        rc = orc_update_src(band, q, nx, ny, nz, cell, dist, src, site_pos, n_sites, np, st, 0, 0, 0, 0);
+        if (rc) goto done;
+        memcpy(site_pos, np, sizeof(int32_t) * (size_t)n_sites);
+        if (trace) { trace[2 * it] = st[0]; trace[2 * it + 1] = st[1]; }
+    }
+    rc = orc_anyangle_assign(band, nx, ny, nz, site_pos, n_sites, max_rounds, cell, dist, src,
+                             rounds ? rounds + n_iters : NULL);
 done:
     free(np);
     return rc;
