@@ -295,10 +295,12 @@ def gpu_arm(args, rank, world, local_rank):
     del h_aux, bufs
     layout = layout_arm(pkg, pipe, s)
     graph = graph_arm(pkg, pipe, s)
+    anyangle = anyangle_arm(pkg, pipe, s)
     res = dict(ms=ms, phase=phase, clk=clk, n_sites=n_sites, n_comp=n_comp, trace=trace, t_assign=t_assign,
                t_iter=t_iter,
                achieved=achieved, peak=pk, stats_gbs=stats_gbs, cvt_ms=cvt_ms, launches=launches_per_step,
-               kernels=kernel_names, e2e=e2e, n=n, field=field, aux=aux, iso=iso, layout=layout, graph=graph)
+               kernels=kernel_names, e2e=e2e, n=n, field=field, aux=aux, iso=iso, layout=layout, graph=graph,
+               anyangle=anyangle)
     return res
 
 
@@ -382,6 +384,54 @@ def graph_arm(pkg, pipe, s, reps=3):
                 apsp_ms=geo_ms, apsp_pairs=k * k, apsp_arcs_scanned_lower_bound=k * arcs,
                 what="site graph (face-adjacent cells, integer Euclidean weights), then geodesic distances and "
                      "||x_i - x_j|| / gd between all sites of the largest component")
+
+
+def anyangle_arm(pkg, pipe, s):
+    """The any-angle tessellation of Sec. 3.2 (region growing with src(w) shortcuts in
+    synchronous rounds) of the last step's final sites, beside the chamfer tessellation of the
+    same sites.  Algorithmic bytes per voxel and round: band 1 + edge mask 4 + key 8 + source 4
+    read, key and source 12 written (neighbour states come from cache): 29 B."""
+    L = pipe.last
+    band, ns = L["band"], L["n_sites"]
+    n = band.numel()
+
+    def any_angle():
+        sp = L["site_pos"].clone()
+        return pkg.cvt_iterate_anyangle(band, None, sp, ns, 0, want_trace=False, ws=pipe.ws, status=pipe.status)
+
+    def chamfer():
+        sp = L["site_pos"].clone()
+        return pkg.cvt_iterate(band, None, sp, ns, 0, want_trace=False, ws=pipe.ws, status=pipe.status)
+    any_angle()
+    chamfer()
+    torch.cuda.synchronize()
+    pkg.check_status(pipe.status, "any-angle tessellation")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    cell_a, dist_a, src_a, _, rounds = any_angle()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    e0.record(s)
+    cell_c, dist_c, _ = chamfer()
+    e1.record(s)
+    torch.cuda.synchronize()
+    pkg.check_status(pipe.status, "any-angle tessellation")
+    chamfer_ms = e0.elapsed_time(e1)
+    reached = cell_c >= 0
+    da = dist_a.to(torch.int64) & 0xFFFFFFFF
+    dc = dist_c.to(torch.int64) & 0xFFFFFFFF
+    r = int(rounds[0])
+    gbs = n * 29 / (ms / r * 1e-3) / 1e9
+    pk = peaks()
+    return dict(ms=ms, rounds=r, ms_per_round=ms / r, algorithmic_bytes_per_voxel_round=29,
+                algorithmic_gbs=gbs, frac=gbs / pk["hbm"], peak_source=pk["src"], chamfer_ms=chamfer_ms,
+                same_cell_frac=float((cell_a == cell_c)[reached].float().mean().item()),
+                shorter_frac=float((da < dc)[reached].float().mean().item()),
+                length_ratio_mean=float((da[reached].double() / dc[reached].clamp(min=1).double()).mean().item()),
+                what="any-angle tessellation (src(w) shortcuts with ray casts, synchronous rounds) of the final "
+                     "sites; chamfer tessellation of the same sites for comparison")
 
 
 def joint_arm(pkg, pipe, lay, s, reps=3):
@@ -760,7 +810,7 @@ def main():
             phases_ms=r["phase"], cvt_gvoxel_iters_per_s=n * N_ITERS / (r["cvt_ms"] * 1e-3) / 1e9,
             moved_per_iter=r["trace"][:, 0].tolist(), clocks=r["clk"], e2e=r["e2e"],
             gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu,
-            layout=r["layout"], graph=r["graph"], forms=forms, precision=precision)
+            layout=r["layout"], graph=r["graph"], anyangle=r["anyangle"], forms=forms, precision=precision)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

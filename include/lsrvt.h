@@ -64,7 +64,8 @@ typedef enum {
     LSRVT_STEP_MERGE = 6,
     LSRVT_STEP_LAYOUT = 7,
     LSRVT_STEP_JOINT = 8, /* max_sites = range capacity, max_comp, n_aux = variables; dims: positions */
-    LSRVT_STEP_GRAPH = 9  /* site graph of a volume of dims d */
+    LSRVT_STEP_GRAPH = 9, /* site graph of a volume of dims d */
+    LSRVT_STEP_CVT_ANYANGLE = 10 /* max_sites; n_aux = max_rounds of the any-angle tessellation */
 } lsrvt_step;
 
 /* Seeding parameters (Sec. 3.2 "Stratified Random Initial Site Distribution", Eq. nc;
@@ -213,6 +214,32 @@ lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q, lsrvt_dim
                                const int32_t *n_sites_dev, int32_t max_sites, int32_t n_iters, int32_t *cell,
                                uint32_t *dist, int64_t *iter_trace, void *ws, size_t ws_bytes,
                                int32_t *status_dev, void *stream);
+
+/* Lloyd iterations with the any-angle tessellation of Sec. 3.2 ("Discrete Restricted Geodesic
+ * Voronoi Tessellation": region growing where each voxel v polls its neighbours w and weighs
+ * the paths (v, P_w), of length |x_v - x_w| + d[w], and (v, P_src(w)), of length
+ * |x_v - x_src(w)| + d[src(w)], the latter only when the ray v -> src(w) stays in the band;
+ * updates take effect in the next round).  Algorithm 1 as lsrvt_cvt_iterate otherwise.
+ *  Rounds are synchronous (round r+1 reads only round r), so the labels do not depend on the
+ *   schedule.  v polls the 26-neighbours it has an edge with (spanned box in its band) and
+ *   also re-evaluates its own path (v, P_src(v)); its new state is the lexicographic minimum
+ *   of (length, site, d[src], src) over these candidates.  Lengths are ceil(2^16 |.|)
+ *   integers; the ray is the 6-connected traversal of lsrvt_cvt_iterate's update walked from
+ *   v.  At the fixed point d[v] = |x_v - x_src(v)| + d[src(v)] and src chains end at v's site.
+ *  Update (Eq. 2): phi(v) = v if v sees its site, else phi(src(v)); target and move as in
+ *   lsrvt_cvt_iterate.
+ *   band, q, site_pos, n_sites_dev, cell, dist, iter_trace as lsrvt_cvt_iterate (dist: the
+ *   any-angle length); src [N] int32 (out, optional: the source of each voxel's path, -1 for
+ *   NaN or unreached voxels); rounds_host [n_iters + 1] int32 (HOST, out, optional: the
+ *   rounds of each tessellation, the last one, which changed nothing, included).
+ *  max_rounds (>= 1) bounds the rounds of one tessellation: TIMEOUT in status_dev past it.
+ *  The call synchronises the stream once per 8 rounds to read the change flags.
+ *  Workspace: lsrvt_workspace_bytes(LSRVT_STEP_CVT_ANYANGLE, d, 0, max_sites, max_rounds). */
+lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const uint16_t *q, lsrvt_dims d, int32_t *site_pos,
+                                        const int32_t *n_sites_dev, int32_t max_sites, int32_t n_iters,
+                                        int32_t max_rounds, int32_t *cell, uint32_t *dist, int32_t *src,
+                                        int64_t *iter_trace, int32_t *rounds_host, void *ws, size_t ws_bytes,
+                                        int32_t *status_dev, void *stream);
 
 /* Per-variable histogram range: lo_j = min, scale_j = float(n_bins) / (max - min) (0 if
  * max == min) over voxels with cell >= 0 (Sec. 3.3 "Aggregation": histograms).

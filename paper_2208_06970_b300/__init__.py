@@ -26,7 +26,8 @@ LIB_PATH = os.path.join(HERE, "liblsrvt.so")
 STATUS = {0: "ok", 1: "invalid argument", 2: "isovalues not strictly increasing", 3: "capacity exceeded",
           4: "non-finite input value", 5: "device loop limit reached", 6: "geodesic distance overflow",
           7: "CUDA launch failure", 8: "workspace missing, misaligned or too small"}
-STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7, joint=8, graph=9)
+STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6, layout=7, joint=8, graph=9,
+            cvt_anyangle=10)
 STATS_HIST = 1
 STATS_COV = 2
 
@@ -78,6 +79,7 @@ def lib():
         L.lsrvt_saliency_grad.argtypes = [P, Dims, i32, P, P, sz, P]
         L.lsrvt_seed.argtypes = [P, P, Dims, P, i32, SeedParams, P, P, P, i32, P, P, sz, P, P]
         L.lsrvt_cvt_iterate.argtypes = [P, P, Dims, P, P, i32, i32, P, P, P, P, sz, P, P]
+        L.lsrvt_cvt_iterate_anyangle.argtypes = [P, P, Dims, P, P, i32, i32, i32, P, P, P, P, P, P, sz, P, P]
         L.lsrvt_aux_range.argtypes = [P, P, i32, Dims, i32, P, P, P, P]
         L.lsrvt_aggregate.argtypes = [P, P, i32, Dims, P, P, i32, u32, P, P, i32, Stats, P, sz, P, P]
         L.lsrvt_merge_hierarchy.argtypes = [Stats, P, i32, i32, i32, u32, P, P, P, i32, i32, Stats, Stats, Stats, P,
@@ -91,8 +93,8 @@ def lib():
         L.lsrvt_site_geodesics.argtypes = [P, P, P, P, Dims, i32, i32, P, P, C.c_float, P, sz, P, P]
         for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
                      "lsrvt_saliency_grad", "lsrvt_seed",
-                     "lsrvt_cvt_iterate", "lsrvt_aux_range", "lsrvt_aggregate", "lsrvt_merge_hierarchy",
-                     "lsrvt_set_stream_share", "lsrvt_structured_layout", "lsrvt_joint_moments",
+                     "lsrvt_cvt_iterate", "lsrvt_cvt_iterate_anyangle", "lsrvt_aux_range", "lsrvt_aggregate",
+                     "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout", "lsrvt_joint_moments",
                      "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -101,7 +103,7 @@ def lib():
 
 def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
-            "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_aux_range",
+            "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_cvt_iterate_anyangle", "lsrvt_aux_range",
             "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout",
             "lsrvt_joint_moments", "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics"]
 
@@ -284,6 +286,31 @@ def cvt_iterate(band, q, site_pos, n_sites_dev, n_iters, want_dist=True, want_tr
                                    _ptr(trace), _ptr(buf), buf.numel(), _ptr(status), _stream()),
            "lsrvt_cvt_iterate")
     return cell, (dist if want_dist else None), (trace[:n_iters] if want_trace else None)
+
+
+def cvt_iterate_anyangle(band, q, site_pos, n_sites_dev, n_iters, max_rounds=1 << 16, want_dist=True,
+                         want_src=True, want_trace=True, ws=None, status=None):
+    """Algorithm 1 with the any-angle tessellation of Sec. 3.2 (region growing with src(w)
+    shortcuts in synchronous rounds); the Eq. 2 update follows src chains.  site_pos is
+    updated in place.  Returns (cell, dist or None, src or None, trace or None, rounds) with
+    rounds[n_iters + 1] the rounds of each tessellation."""
+    _require_cuda(band, q, site_pos)
+    dev = band.device
+    max_sites = site_pos.numel()
+    cell = torch.empty(band.shape, dtype=torch.int32, device=dev)
+    dist = torch.empty(band.shape, dtype=torch.int32, device=dev) if want_dist else None
+    src = torch.empty(band.shape, dtype=torch.int32, device=dev) if want_src else None
+    trace = torch.zeros((max(n_iters, 1), 2), dtype=torch.int64, device=dev) if want_trace else None
+    rounds = np.zeros(n_iters + 1, np.int32)
+    ws = ws or Workspace(dev)
+    status = new_status(dev) if status is None else status
+    buf = ws.get(workspace_bytes("cvt_anyangle", _dims(band), max_sites=max_sites, n_aux=max_rounds))
+    _check(lib().lsrvt_cvt_iterate_anyangle(_ptr(band), _ptr(q), _dims(band), _ptr(site_pos), _ptr(n_sites_dev),
+                                            max_sites, int(n_iters), int(max_rounds), _ptr(cell), _ptr(dist),
+                                            _ptr(src), _ptr(trace), rounds.ctypes.data_as(C.c_void_p), _ptr(buf),
+                                            buf.numel(), _ptr(status), _stream()),
+           "lsrvt_cvt_iterate_anyangle")
+    return cell, dist, src, (trace[:n_iters] if want_trace else None), rounds
 
 
 def _aux_ptrs(aux):

@@ -13,6 +13,7 @@ size_t saliency_workspace(Dims d);
 size_t seed_workspace(Dims d, int32_t sb, int32_t max_comp, int64_t max_rec);
 int64_t seed_default_strata(Dims d, int32_t sb, int32_t max_comp);
 size_t cvt_workspace(Dims d, int32_t max_sites);
+size_t cvt_anyangle_workspace(Dims d, int32_t max_sites, int32_t max_rounds);
 size_t aggregate_workspace(Dims d, int32_t max_sites, int32_t m);
 size_t merge_workspace(int32_t max_sites, int32_t max_comp, int32_t n_bands, int32_t m);
 size_t layout_workspace(Dims d, int32_t max_sites);
@@ -144,6 +145,7 @@ extern "C" size_t lsrvt_workspace_bytes(lsrvt_step step, lsrvt_dims dd, int32_t 
         case LSRVT_STEP_MERGE: return merge_workspace(max_sites, max_comp, 255, n_aux);
         case LSRVT_STEP_LAYOUT: return layout_workspace(d, max_sites > 0 ? max_sites : 1);
         case LSRVT_STEP_GRAPH: return graph_workspace(d);
+        case LSRVT_STEP_CVT_ANYANGLE: return cvt_anyangle_workspace(d, max_sites, n_aux > 0 ? n_aux : 1);
         case LSRVT_STEP_JOINT: {
             // the moments over max_sites ranges of d.n() positions, and the merge of max_sites cell
             // records into max_comp components (n_aux = the variable count)

@@ -22,6 +22,7 @@
 // and are resolved in a second pass by walking parents to the first LOS voxel (phi).  A
 // per-site pass rounds the centroid half up and walks the site toward it, stopping before
 // it would leave its band.
+#include <climits>
 #include <cstdio>
 
 #include "common.cuh"
@@ -1468,8 +1469,10 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
     const uint8_t *__restrict__ band, const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
     const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
     uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const int32_t *__restrict__ plist,
-    const int32_t *n_plist, bool small_coords) {
-    const int32_t cnt = *n_plist;
+    const int32_t *n_plist, bool small_coords, const int32_t *__restrict__ src) {
+    // plist == nullptr: every voxel (N < 2^31); src != nullptr: the path's next node is the
+    // voxel's source (any-angle tessellation) instead of the chamfer parent
+    const int32_t cnt = plist ? *n_plist : (int32_t)d.n();
     // whole warps step through the list together (the warp-level reductions below need them)
     for (int32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < cnt; base += gridDim.x * blockDim.x) {
         const int32_t i = base + (threadIdx.x & 31);
@@ -1479,7 +1482,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
             atomicAdd(&g_phase[4], (unsigned long long)min(32, cnt - base));
         }
 #endif
-        const int64_t v = i < cnt ? __ldg(plist + i) : -1;
+        const int64_t v = i < cnt ? (plist ? __ldg(plist + i) : i) : -1;
         const int64_t wv = v >> 5;
         bool los = false;
         int32_t s = -1;
@@ -1508,8 +1511,8 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
                 if (!los) {
                     // parent: first neighbour in (dz,dy,dx) order with an edge, same site and D(u)+w = D(v)
                     uint8_t b = band[v];
-                    int32_t parent = -1;
-                    for (int o = 0; o < 27 && parent < 0; ++o) {
+                    int32_t parent = src ? __ldg(src + v) : -1;
+                    for (int o = 0; o < 27 && parent < 0 && !src; ++o) {
                         if (o == 13) continue;
                         int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
                         int ux = x + dx, uy = y + dy, uz = z + dz;
@@ -1703,6 +1706,157 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     return w;
 }
 
+// ---------------------------------------------------------------- any-angle tessellation
+// Sec. 3.2 region growing: each voxel v polls the neighbours w it has an edge with and weighs
+// the paths (v, P_w), length |x_v - x_w| + d[w], and (v, P_src(w)), length |x_v - x_src(w)| +
+// d[src(w)], the latter only when the traversal v -> src(w) stays in v's band; v also
+// re-evaluates its own path (v, P_src(v)) with the current d[src(v)].  Updates take effect in
+// the next round (synchronous rounds, double-buffered state), so the result does not depend
+// on thread order.  The new state is the lexicographic minimum of (length, site, d[src], src);
+// the re-evaluated own path is never worse than the old state, so states only decrease and
+// the rounds end.  Lengths are ceil(2^16 |.|) integers, so sums are exact.
+// State: key (length << 32 | site) and src (voxel index, -1 unreached).
+
+// ceil(2^16 sqrt(D)) for 0 < D < 2^32: a rounded square root brought to the exact integer by
+// comparing squares (the result r is the least with r^2 >= 2^32 D; r < 2^32, so r^2 fits).
+__device__ __forceinline__ unsigned long long ceil_q16_length(unsigned long long D) {
+    const unsigned long long v = D << 32;
+    unsigned long long r = D < (1ull << 16) ? (unsigned long long)(__fsqrt_rn((float)D) * 65536.0f)
+                                            : (unsigned long long)(__dsqrt_rn((double)D) * 65536.0);
+    while (r * r < v) ++r;
+    while (r > 1 && (r - 1) * (r - 1) >= v) --r;
+    return r;
+}
+
+__device__ __forceinline__ bool aa_less(unsigned long long ka, uint32_t dpa, int32_t pa, unsigned long long kb,
+                                        uint32_t dpb, int32_t pb) {
+    if (ka != kb) return ka < kb;
+    if (dpa != dpb) return dpa < dpb;
+    return pa < pb;
+}
+
+__global__ void aa_timeout_kernel(int32_t *status) { set_status(status, LSRVT_ERR_TIMEOUT); }
+
+__global__ void aa_init_kernel(int64_t n, unsigned long long *k0, int32_t *p0, unsigned long long *k1, int32_t *p1) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        k0[v] = kInfKey;
+        k1[v] = kInfKey;
+        p0[v] = -1;
+        p1[v] = -1;
+    }
+}
+
+// sites at distance 0, the lowest id on a shared voxel
+__global__ void aa_sites_kernel(const uint8_t *__restrict__ band, Dims d, const int32_t *__restrict__ site_pos,
+                                const int32_t *n_sites_dev, int32_t max_sites, unsigned long long *k0, int32_t *p0,
+                                int32_t *status) {
+    const int32_t ns = min(*n_sites_dev, max_sites);
+    const int64_t n = d.n();
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
+        const int32_t p = site_pos[s];
+        if (p < 0 || p >= n || band[p] == kInvalidBand) {
+            set_status(status, LSRVT_ERR_INVALID_ARG);
+            continue;
+        }
+        atomicMin(&k0[p], (unsigned long long)(uint32_t)s);
+        p0[p] = p;
+    }
+}
+
+// One synchronous round r: reads (k0, p0), writes (k1, p1); flags[r] = 1 if any state
+// changed.  A round after one that changed nothing returns at once (both buffers then hold
+// the fixed point).
+__global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict__ band,
+                                                       const uint8_t *__restrict__ clr,
+                                                       const uint32_t *__restrict__ emask, Dims d,
+                                                       const unsigned long long *__restrict__ k0,
+                                                       const int32_t *__restrict__ p0, unsigned long long *k1,
+                                                       int32_t *p1, uint32_t *flags, int32_t round, int32_t *status) {
+    if (round > 0 && __ldcg(flags + round - 1) == 0) return;
+    const int64_t n = d.n();
+    const int64_t sxy = (int64_t)d.nx * d.ny;
+    bool changed = false;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t b = band[v];
+        if (b == kInvalidBand) continue;  // unreached in both buffers since the init
+        int x, y, z;
+        decode_voxel((uint32_t)v, d, x, y, z);
+        const unsigned long long kv = k0[v];
+        const int32_t pv = p0[v];
+        unsigned long long bk = kInfKey;
+        uint32_t bdp = kInf32;
+        int32_t bp = INT32_MAX;
+        // a candidate through source t (t != v): (d[t] + |x_v - x_t|, site(t), d[t], t)
+        auto through = [&](int32_t t, unsigned long long &ck, uint32_t &cdp) -> bool {
+            const unsigned long long kt = k0[t];
+            if (kt == kInfKey) return false;
+            int tx, ty, tz;
+            decode_voxel((uint32_t)t, d, tx, ty, tz);
+            const long long dx = x - tx, dy = y - ty, dz = z - tz;
+            const unsigned long long D = (unsigned long long)(dx * dx + dy * dy + dz * dz);
+            if (D >= (1ull << 32)) return false;
+            const unsigned long long tot = (kt >> 32) + ceil_q16_length(D);
+            if (tot > 0xFFFFFFFEull) {
+                set_status(status, LSRVT_ERR_OVERFLOW);
+                return false;
+            }
+            ck = (tot << 32) | (kt & 0xFFFFFFFFull);
+            cdp = (uint32_t)(kt >> 32);
+            return true;
+        };
+        if (pv == v) {  // a site keeps (0, s, 0, v)
+            bk = kv;
+            bdp = 0;
+            bp = pv;
+        } else if (pv >= 0) {
+            unsigned long long ck;
+            uint32_t cdp;
+            if (through(pv, ck, cdp)) { bk = ck; bdp = cdp; bp = pv; }
+        }
+        const uint32_t em = emask[v];
+        int32_t rejected = -1;
+        for (int o = 0; o < 27; ++o) {
+            if (!((em >> o) & 1u)) continue;
+            const int64_t w = v + (o % 3 - 1) + d.nx * (int64_t)((o / 3) % 3 - 1) + sxy * (o / 9 - 1);
+            const unsigned long long kw = k0[w];
+            if (kw == kInfKey) continue;
+            {
+                const unsigned long long tot = (kw >> 32) + weight_of(o);
+                if (tot > 0xFFFFFFFEull) {
+                    set_status(status, LSRVT_ERR_OVERFLOW);
+                } else {
+                    const unsigned long long ck = (tot << 32) | (kw & 0xFFFFFFFFull);
+                    if (aa_less(ck, (uint32_t)(kw >> 32), (int32_t)w, bk, bdp, bp)) {
+                        bk = ck;
+                        bdp = (uint32_t)(kw >> 32);
+                        bp = (int32_t)w;
+                    }
+                }
+            }
+            const int32_t t = p0[w];
+            if (t < 0 || t == w || t == v || t == rejected) continue;
+            unsigned long long ck;
+            uint32_t cdp;
+            if (!through(t, ck, cdp) || !aa_less(ck, cdp, t, bk, bdp, bp)) continue;  // cannot win: no ray
+            int tx, ty, tz;
+            decode_voxel((uint32_t)t, d, tx, ty, tz);
+            const int cs = band[t] == b ? __ldg(clr + t) : 0;
+            if (los_clear(band, clr, d, x, y, z, tx, ty, tz, cs)) {
+                bk = ck;
+                bdp = cdp;
+                bp = t;
+            } else {
+                rejected = t;
+            }
+        }
+        const int32_t np = bk == kInfKey ? -1 : bp;
+        k1[v] = bk;
+        p1[v] = np;
+        changed |= (bk != kv) || (np != pv);
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) flags[round] = 1u;
+}
+
 constexpr int kMaxRounds = 1 << 16;
 
 }  // namespace
@@ -1710,6 +1864,52 @@ constexpr int kMaxRounds = 1 << 16;
 size_t cvt_workspace(Dims d, int32_t max_sites) {
     size_t need;
     carve_cvt(nullptr, 0, d, max_sites, &need);
+    return need;
+}
+
+namespace {
+
+struct AaWs {
+    unsigned long long *key[2];
+    int32_t *src[2];
+    uint8_t *clr;
+    uint32_t *emask;
+    uint32_t *planes;
+    uint32_t *los_bits;
+    int32_t *par;
+    int32_t *nonlos;
+    int32_t *counters;  // [0] n_nonlos
+    unsigned long long *sums;
+    uint32_t *flags;  // one per round
+};
+
+AaWs carve_aa(void *ws, size_t bytes, Dims d, int32_t max_sites, int32_t max_rounds, size_t *need) {
+    Carver c(ws, bytes);
+    const int64_t n = d.n();
+    AaWs w;
+    w.key[0] = c.take<unsigned long long>(n);
+    w.key[1] = c.take<unsigned long long>(n);
+    w.src[0] = c.take<int32_t>(n);
+    w.src[1] = c.take<int32_t>(n);
+    w.clr = c.take<uint8_t>(n);
+    w.emask = c.take<uint32_t>(n);
+    BitGeom bgm{(d.nx + 31) / 32};
+    w.planes = c.take<uint32_t>(bgm.words(d) * kClearLevels);
+    w.los_bits = c.take<uint32_t>((n + 31) / 32);
+    w.par = c.take<int32_t>(n);
+    w.nonlos = c.take<int32_t>(n);
+    w.counters = c.take<int32_t>(8);
+    w.sums = c.take<unsigned long long>((int64_t)max_sites * 4 + 4);
+    w.flags = c.take<uint32_t>(max_rounds > 0 ? max_rounds : 1);
+    *need = c.used;
+    return w;
+}
+
+}  // namespace
+
+size_t cvt_anyangle_workspace(Dims d, int32_t max_sites, int32_t max_rounds) {
+    size_t need;
+    carve_aa(nullptr, 0, d, max_sites, max_rounds, &need);
     return need;
 }
 
@@ -1853,7 +2053,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, up);
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
-                                                   w.nonlos, w.counters, w.plist, w.counters + 5, small);
+                                                   w.nonlos, w.counters, w.plist, w.counters + 5, small, nullptr);
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
@@ -1895,5 +2095,100 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         cudaMemcpyToSymbol(g_phase, z, sizeof(z));
     }
 #endif
+    return launch_status();
+}
+
+namespace {
+
+// One any-angle tessellation: synchronous rounds from the sites until a round changes
+// nothing (the fixed point is then in both buffers).  The host reads the change flags once
+// per chunk of rounds; rounds launched after convergence return at once.
+lsrvt_status aa_assignment(const uint8_t *band, Dims d, const int32_t *site_pos, const int32_t *n_sites_dev,
+                           int32_t max_sites, int32_t max_rounds, AaWs &w, int32_t *status, cudaStream_t s,
+                           int32_t *rounds_out) {
+    const int64_t n = d.n();
+    const int sms = stream_sms(s);
+    aa_init_kernel<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(n, w.key[0], w.src[0], w.key[1], w.src[1]);
+    aa_sites_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(band, d, site_pos, n_sites_dev, max_sites,
+                                                                      w.key[0], w.src[0], status);
+    cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (size_t)max_rounds, s);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aa_round_kernel, 256, 0);
+    if (nb < 1) nb = 1;
+    const int grid = grid_for(n, 256, sms * nb);
+    constexpr int kChunk = 8;
+    uint32_t h[kChunk];
+    int32_t r = 0, done = -1;
+    while (r < max_rounds && done < 0) {
+        const int32_t r0 = r, r1 = r + kChunk < max_rounds ? r + kChunk : max_rounds;
+        for (; r < r1; ++r)
+            aa_round_kernel<<<grid, 256, 0, s>>>(band, w.clr, w.emask, d, w.key[r & 1], w.src[r & 1],
+                                                 w.key[(r + 1) & 1], w.src[(r + 1) & 1], w.flags, r, status);
+        if (cudaMemcpyAsync(h, w.flags + r0, sizeof(uint32_t) * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return LSRVT_ERR_CUDA;
+        for (int32_t j = 0; j < r1 - r0; ++j)
+            if (h[j] == 0) { done = r0 + j + 1; break; }
+    }
+    if (done < 0) {
+        aa_timeout_kernel<<<1, 1, 0, s>>>(status);
+        done = max_rounds;
+    }
+    if (rounds_out) *rounds_out = done;
+    return launch_status();
+}
+
+}  // namespace
+
+extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const uint16_t *q, lsrvt_dims dd,
+                                                   int32_t *site_pos, const int32_t *n_sites_dev, int32_t max_sites,
+                                                   int32_t n_iters, int32_t max_rounds, int32_t *cell, uint32_t *dist,
+                                                   int32_t *src, int64_t *iter_trace, int32_t *rounds_host, void *ws,
+                                                   size_t ws_bytes, int32_t *status_dev, void *stream) {
+    if (!dims_ok(dd) || !band || !site_pos || !n_sites_dev || max_sites < 0 || n_iters < 0 || max_rounds < 1 ||
+        !cell)
+        return LSRVT_ERR_INVALID_ARG;
+    Dims d{dd.nx, dd.ny, dd.nz};
+    size_t need;
+    AaWs w = carve_aa(ws, ws_bytes, d, max_sites, max_rounds, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return LSRVT_ERR_WORKSPACE;
+    cudaStream_t s = as_stream(stream);
+    const int64_t n = d.n();
+    const int sms = stream_sms(s);
+    if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * 2 * n_iters, s);
+    const bool small = d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048;
+    {
+        BitGeom bgm{(d.nx + 31) / 32};
+        int64_t nw = bgm.words(d);
+        clear_init_kernel<<<grid_for(nw * 32, 256, kSMs * 16), 256, 0, s>>>(band, d, bgm, w.planes);
+        for (int k = 1; k < kClearLevels; ++k)
+            clear_erode_kernel<<<grid_for(nw, 256, kSMs * 16), 256, 0, s>>>(w.planes + (int64_t)(k - 1) * nw, d, bgm,
+                                                                          w.planes + (int64_t)k * nw);
+        clear_count_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.planes, d, bgm, kClearLevels, w.clr);
+        edge_mask_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.emask);
+    }
+    const int vgrid = grid_for((n + 31) / 32 * 32, 256, sms * 16);
+    const int64_t nwords = (n + 31) / 32;
+    for (int32_t it = 0; it < n_iters; ++it) {
+        lsrvt_status st = aa_assignment(band, d, site_pos, n_sites_dev, max_sites, max_rounds, w, status_dev, s,
+                                        rounds_host ? rounds_host + it : nullptr);
+        if (st != LSRVT_OK) return st;
+        cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
+        cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
+        cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
+        update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key[0], site_pos, w.clr, w.sums, w.los_bits, w.par,
+                                                   w.nonlos, w.counters, nullptr, nullptr, small, w.src[0]);
+        update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key[0], w.los_bits, w.par, w.nonlos, w.counters, w.sums,
+                                                      status_dev);
+        move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
+            band, d, site_pos, n_sites_dev, max_sites, w.sums,
+            iter_trace ? (unsigned long long *)(iter_trace + 2 * it) : nullptr);
+    }
+    lsrvt_status st = aa_assignment(band, d, site_pos, n_sites_dev, max_sites, max_rounds, w, status_dev, s,
+                                    rounds_host ? rounds_host + n_iters : nullptr);
+    if (st != LSRVT_OK) return st;
+    emit_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.key[0], n, cell, dist);
+    if (src) cudaMemcpyAsync(src, w.src[0], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
     return launch_status();
 }
