@@ -685,7 +685,7 @@ def profile_step(args):
 def profile_layout(args):
     """One step of the workload, then two structured layouts of it, each followed by the joint
     moments of its cells and their merge, then the site graph and the geodesics of the largest
-    component (ncu target)."""
+    component, then the any-angle tessellation of the final sites (ncu target)."""
     import paper_2208_06970_b300 as pkg
     import workloads
     from paper_2208_06970_b300 import build
@@ -711,8 +711,16 @@ def profile_layout(args):
     pkg.site_geodesics(g, L["site_pos"], (nx, ny, nz), int(off[c]), int(off[c + 1]), c_far=2.0, ws=pipe.ws,
                        status=pipe.status)
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    aa = pkg.cvt_iterate_anyangle(L["band"], None, L["site_pos"].clone(), L["n_sites"], 0, want_trace=False,
+                                  ws=pipe.ws, status=pipe.status)
+    e1.record()
+    torch.cuda.synchronize()
     pkg.check_status(pipe.status, "profile layout")
-    print("profile layout ok: %d voxels, %d graph edges" % (int(out["n_kept"].item()), int(g["n_edges"].item())))
+    print("profile layout ok: %d voxels, %d graph edges, any-angle %d rounds in %.1f ms"
+          % (int(out["n_kept"].item()), int(g["n_edges"].item()), int(aa[4][0]), e0.elapsed_time(e1)))
 
 
 def profile_precision(args):

@@ -1746,10 +1746,10 @@ __global__ void aa_init_kernel(int64_t n, unsigned long long *k0, int32_t *p0, u
     }
 }
 
-// sites at distance 0, the lowest id on a shared voxel
+// sites at distance 0, the lowest id on a shared voxel, in both state buffers
 __global__ void aa_sites_kernel(const uint8_t *__restrict__ band, Dims d, const int32_t *__restrict__ site_pos,
                                 const int32_t *n_sites_dev, int32_t max_sites, unsigned long long *k0, int32_t *p0,
-                                int32_t *status) {
+                                unsigned long long *k1, int32_t *p1, int32_t *status) {
     const int32_t ns = min(*n_sites_dev, max_sites);
     const int64_t n = d.n();
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
@@ -1759,102 +1759,137 @@ __global__ void aa_sites_kernel(const uint8_t *__restrict__ band, Dims d, const 
             continue;
         }
         atomicMin(&k0[p], (unsigned long long)(uint32_t)s);
+        atomicMin(&k1[p], (unsigned long long)(uint32_t)s);
         p0[p] = p;
+        p1[p] = p;
     }
 }
 
-// One synchronous round r: reads (k0, p0), writes (k1, p1); flags[r] = 1 if any state
-// changed.  A round after one that changed nothing returns at once (both buffers then hold
-// the fixed point).
+__device__ __forceinline__ bool test_bit(const uint32_t *__restrict__ bits, int64_t i) {
+    return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+// One synchronous round r: reads (k0, p0), writes (k1, p1); c1 receives the voxels whose
+// state changed (one bitmap word per warp of 32 consecutive voxels) and flags[r] = 1 if any
+// did.  A voxel whose inputs -- its own state, its source's, and the states of its edge
+// neighbours and of their sources -- did not change in round r-1 (c0) gets the candidates of
+// round r-1 again, so its state stays; it is skipped and not written, since both buffers
+// already hold that state (the sites start in both buffers, and every evaluated voxel is
+// written, so a voxel unchanged in the round that last evaluated it is equal in both).  A round after one that
+// changed nothing returns at once (both buffers then hold the fixed point).
 __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict__ band,
                                                        const uint8_t *__restrict__ clr,
                                                        const uint32_t *__restrict__ emask, Dims d,
                                                        const unsigned long long *__restrict__ k0,
                                                        const int32_t *__restrict__ p0, unsigned long long *k1,
-                                                       int32_t *p1, uint32_t *flags, int32_t round, int32_t *status) {
+                                                       int32_t *p1, const uint32_t *__restrict__ c0, uint32_t *c1,
+                                                       uint32_t *flags, int32_t round, int32_t *status) {
     if (round > 0 && __ldcg(flags + round - 1) == 0) return;
     const int64_t n = d.n();
+    const int64_t nwords = (n + 31) >> 5;
     const int64_t sxy = (int64_t)d.nx * d.ny;
-    bool changed = false;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const uint8_t b = band[v];
-        if (b == kInvalidBand) continue;  // unreached in both buffers since the init
-        int x, y, z;
-        decode_voxel((uint32_t)v, d, x, y, z);
-        const unsigned long long kv = k0[v];
-        const int32_t pv = p0[v];
-        unsigned long long bk = kInfKey;
-        uint32_t bdp = kInf32;
-        int32_t bp = INT32_MAX;
-        // a candidate through source t (t != v): (d[t] + |x_v - x_t|, site(t), d[t], t)
-        auto through = [&](int32_t t, unsigned long long &ck, uint32_t &cdp) -> bool {
-            const unsigned long long kt = k0[t];
-            if (kt == kInfKey) return false;
-            int tx, ty, tz;
-            decode_voxel((uint32_t)t, d, tx, ty, tz);
-            const long long dx = x - tx, dy = y - ty, dz = z - tz;
-            const unsigned long long D = (unsigned long long)(dx * dx + dy * dy + dz * dz);
-            if (D >= (1ull << 32)) return false;
-            const unsigned long long tot = (kt >> 32) + ceil_q16_length(D);
-            if (tot > 0xFFFFFFFEull) {
-                set_status(status, LSRVT_ERR_OVERFLOW);
-                return false;
+    const int lane = threadIdx.x & 31;
+    bool any = false;
+    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nwords;
+         wi += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t v = wi * 32 + lane;
+        bool changed = false;
+        const uint8_t b = v < n ? band[v] : kInvalidBand;
+        if (b != kInvalidBand) {  // NaN voxels stay unreached in both buffers
+            const uint32_t em = emask[v];
+            const int32_t pv = p0[v];
+            bool active = round == 0 || test_bit(c0, v) || (pv >= 0 && test_bit(c0, pv));
+            for (int o = 0; o < 27 && !active; ++o) {
+                if (!((em >> o) & 1u)) continue;
+                const int64_t w = v + (o % 3 - 1) + d.nx * (int64_t)((o / 3) % 3 - 1) + sxy * (o / 9 - 1);
+                const int32_t t = p0[w];
+                active = test_bit(c0, w) || (t >= 0 && test_bit(c0, t));
             }
-            ck = (tot << 32) | (kt & 0xFFFFFFFFull);
-            cdp = (uint32_t)(kt >> 32);
-            return true;
-        };
-        if (pv == v) {  // a site keeps (0, s, 0, v)
-            bk = kv;
-            bdp = 0;
-            bp = pv;
-        } else if (pv >= 0) {
-            unsigned long long ck;
-            uint32_t cdp;
-            if (through(pv, ck, cdp)) { bk = ck; bdp = cdp; bp = pv; }
-        }
-        const uint32_t em = emask[v];
-        int32_t rejected = -1;
-        for (int o = 0; o < 27; ++o) {
-            if (!((em >> o) & 1u)) continue;
-            const int64_t w = v + (o % 3 - 1) + d.nx * (int64_t)((o / 3) % 3 - 1) + sxy * (o / 9 - 1);
-            const unsigned long long kw = k0[w];
-            if (kw == kInfKey) continue;
-            {
-                const unsigned long long tot = (kw >> 32) + weight_of(o);
-                if (tot > 0xFFFFFFFEull) {
-                    set_status(status, LSRVT_ERR_OVERFLOW);
-                } else {
-                    const unsigned long long ck = (tot << 32) | (kw & 0xFFFFFFFFull);
-                    if (aa_less(ck, (uint32_t)(kw >> 32), (int32_t)w, bk, bdp, bp)) {
+            if (active) {
+                int x, y, z;
+                decode_voxel((uint32_t)v, d, x, y, z);
+                const unsigned long long kv = k0[v];
+                unsigned long long bk = kInfKey;
+                uint32_t bdp = kInf32;
+                int32_t bp = INT32_MAX;
+                // a candidate through source t (t != v): (d[t] + |x_v - x_t|, site(t), d[t], t)
+                auto through = [&](int32_t t, unsigned long long &ck, uint32_t &cdp) -> bool {
+                    const unsigned long long kt = k0[t];
+                    if (kt == kInfKey) return false;
+                    int tx, ty, tz;
+                    decode_voxel((uint32_t)t, d, tx, ty, tz);
+                    const long long dx = x - tx, dy = y - ty, dz = z - tz;
+                    const unsigned long long D = (unsigned long long)(dx * dx + dy * dy + dz * dz);
+                    if (D >= (1ull << 32)) return false;
+                    const unsigned long long tot = (kt >> 32) + ceil_q16_length(D);
+                    if (tot > 0xFFFFFFFEull) {
+                        set_status(status, LSRVT_ERR_OVERFLOW);
+                        return false;
+                    }
+                    ck = (tot << 32) | (kt & 0xFFFFFFFFull);
+                    cdp = (uint32_t)(kt >> 32);
+                    return true;
+                };
+                if (pv == v) {  // a site keeps (0, s, 0, v)
+                    bk = kv;
+                    bdp = 0;
+                    bp = pv;
+                } else if (pv >= 0) {
+                    unsigned long long ck;
+                    uint32_t cdp;
+                    if (through(pv, ck, cdp)) { bk = ck; bdp = cdp; bp = pv; }
+                }
+                // a source already weighed (the own one, the last one, the last rejected) gives
+                // the same candidate again, which cannot beat the best so far
+                int32_t last = pv, rejected = -1;
+                for (int o = 0; o < 27; ++o) {
+                    if (!((em >> o) & 1u)) continue;
+                    const int64_t w = v + (o % 3 - 1) + d.nx * (int64_t)((o / 3) % 3 - 1) + sxy * (o / 9 - 1);
+                    const unsigned long long kw = k0[w];
+                    if (kw == kInfKey) continue;
+                    {
+                        const unsigned long long tot = (kw >> 32) + weight_of(o);
+                        if (tot > 0xFFFFFFFEull) {
+                            set_status(status, LSRVT_ERR_OVERFLOW);
+                        } else {
+                            const unsigned long long ck = (tot << 32) | (kw & 0xFFFFFFFFull);
+                            if (aa_less(ck, (uint32_t)(kw >> 32), (int32_t)w, bk, bdp, bp)) {
+                                bk = ck;
+                                bdp = (uint32_t)(kw >> 32);
+                                bp = (int32_t)w;
+                            }
+                        }
+                    }
+                    const int32_t t = p0[w];
+                    if (t < 0 || t == w || t == v || t == last || t == pv || t == rejected) continue;
+                    last = t;
+                    unsigned long long ck;
+                    uint32_t cdp;
+                    if (!through(t, ck, cdp) || !aa_less(ck, cdp, t, bk, bdp, bp)) continue;  // cannot win: no ray
+                    int tx, ty, tz;
+                    decode_voxel((uint32_t)t, d, tx, ty, tz);
+                    const int cs = band[t] == b ? __ldg(clr + t) : 0;
+                    if (los_clear(band, clr, d, x, y, z, tx, ty, tz, cs)) {
                         bk = ck;
-                        bdp = (uint32_t)(kw >> 32);
-                        bp = (int32_t)w;
+                        bdp = cdp;
+                        bp = t;
+                    } else {
+                        rejected = t;
                     }
                 }
-            }
-            const int32_t t = p0[w];
-            if (t < 0 || t == w || t == v || t == rejected) continue;
-            unsigned long long ck;
-            uint32_t cdp;
-            if (!through(t, ck, cdp) || !aa_less(ck, cdp, t, bk, bdp, bp)) continue;  // cannot win: no ray
-            int tx, ty, tz;
-            decode_voxel((uint32_t)t, d, tx, ty, tz);
-            const int cs = band[t] == b ? __ldg(clr + t) : 0;
-            if (los_clear(band, clr, d, x, y, z, tx, ty, tz, cs)) {
-                bk = ck;
-                bdp = cdp;
-                bp = t;
-            } else {
-                rejected = t;
+                const int32_t np = bk == kInfKey ? -1 : bp;
+                changed = (bk != kv) || (np != pv);
+                // written even when unchanged: the other buffer may still hold the state before
+                // the last change
+                k1[v] = bk;
+                p1[v] = np;
             }
         }
-        const int32_t np = bk == kInfKey ? -1 : bp;
-        k1[v] = bk;
-        p1[v] = np;
-        changed |= (bk != kv) || (np != pv);
+        const unsigned bal = __ballot_sync(0xffffffffu, changed);
+        if (lane == 0) c1[wi] = bal;
+        any |= bal != 0u;
     }
-    if (__syncthreads_or(changed) && threadIdx.x == 0) flags[round] = 1u;
+    if (__syncthreads_or(any) && threadIdx.x == 0) flags[round] = 1u;
 }
 
 constexpr int kMaxRounds = 1 << 16;
@@ -1881,6 +1916,7 @@ struct AaWs {
     int32_t *counters;  // [0] n_nonlos
     unsigned long long *sums;
     uint32_t *flags;  // one per round
+    uint32_t *chg[2];  // voxels changed in the last round, ping-pong
 };
 
 AaWs carve_aa(void *ws, size_t bytes, Dims d, int32_t max_sites, int32_t max_rounds, size_t *need) {
@@ -1901,6 +1937,8 @@ AaWs carve_aa(void *ws, size_t bytes, Dims d, int32_t max_sites, int32_t max_rou
     w.counters = c.take<int32_t>(8);
     w.sums = c.take<unsigned long long>((int64_t)max_sites * 4 + 4);
     w.flags = c.take<uint32_t>(max_rounds > 0 ? max_rounds : 1);
+    w.chg[0] = c.take<uint32_t>((n + 31) / 32);
+    w.chg[1] = c.take<uint32_t>((n + 31) / 32);
     *need = c.used;
     return w;
 }
@@ -2110,12 +2148,13 @@ lsrvt_status aa_assignment(const uint8_t *band, Dims d, const int32_t *site_pos,
     const int sms = stream_sms(s);
     aa_init_kernel<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(n, w.key[0], w.src[0], w.key[1], w.src[1]);
     aa_sites_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(band, d, site_pos, n_sites_dev, max_sites,
-                                                                      w.key[0], w.src[0], status);
+                                                                      w.key[0], w.src[0], w.key[1], w.src[1],
+                                                                      status);
     cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (size_t)max_rounds, s);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aa_round_kernel, 256, 0);
     if (nb < 1) nb = 1;
-    const int grid = grid_for(n, 256, sms * nb);
+    const int grid = grid_for((n + 31) / 32 * 32, 256, sms * nb);
     constexpr int kChunk = 8;
     uint32_t h[kChunk];
     int32_t r = 0, done = -1;
@@ -2123,7 +2162,8 @@ lsrvt_status aa_assignment(const uint8_t *band, Dims d, const int32_t *site_pos,
         const int32_t r0 = r, r1 = r + kChunk < max_rounds ? r + kChunk : max_rounds;
         for (; r < r1; ++r)
             aa_round_kernel<<<grid, 256, 0, s>>>(band, w.clr, w.emask, d, w.key[r & 1], w.src[r & 1],
-                                                 w.key[(r + 1) & 1], w.src[(r + 1) & 1], w.flags, r, status);
+                                                 w.key[(r + 1) & 1], w.src[(r + 1) & 1], w.chg[r & 1],
+                                                 w.chg[(r + 1) & 1], w.flags, r, status);
         if (cudaMemcpyAsync(h, w.flags + r0, sizeof(uint32_t) * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
