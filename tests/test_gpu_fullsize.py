@@ -10,7 +10,10 @@ The oracle cannot rerun 30 Lloyd iterations on 134 M voxels in test time, so:
 - resuming (29 iterations, then 1) gives the 30-iteration sites and labels bit for bit;
 - statistics are compared on a sample of cells (the oracle sees only those voxels), with
   the histogram ranges computed by the oracle over the whole volume;
-- the merge is compared with the oracle's merge of the same per-cell records.
+- the merge is compared with the oracle's merge of the same per-cell records;
+- the any-angle tessellation of the final sites is checked on every voxel by exact properties
+  (chamfer upper bound, straight-segment lower bound, consistent source chains ending at the
+  site, component membership) and on sampled shortcut segments by the oracle's traversal.
 """
 import numpy as np
 import pytest
@@ -324,3 +327,68 @@ def test_full_site_graph_sampled(full):
     for src in rng.choice(s1 - s0, 6, replace=False):
         want = oracle.site_sssp(ref, s0 + int(src))[s0:s1]
         assert np.array_equal(D[src], want)
+
+
+def _ceil_q16(D):
+    """ceil(2^16 sqrt(D)) for an int64 tensor D < 2^20 (exact: a double root, then squares)."""
+    v = D << 32
+    r = torch.floor(torch.sqrt(D.double()) * 65536.0).long()
+    for _ in range(2):
+        r = r + (r * r < v).long()
+        r = r - ((r > 0) & ((r - 1) * (r - 1) >= v)).long()
+    assert bool(((r * r >= v) & ((r == 0) | ((r - 1) * (r - 1) < v))).all())
+    return r
+
+
+def test_full_anyangle_properties(full):
+    """The any-angle tessellation of the final 512^3 sites, run as the bench runs it, checked on
+    every voxel by properties that hold at any size: the reached voxels are the chamfer
+    tessellation's and no length exceeds its geodesic (direct neighbour paths are its edges);
+    no length is below the straight segment to the voxel's site; every source gives exactly the
+    voxel's length (d[v] = d[src] + ceil(2^16 |x_v - x_src|)) and cell, lengths fall along the
+    chain, and d = 0 only on a site's own voxel, so every chain ends at the voxel's site; every
+    cell stays in its site's component; sampled shortcut segments see their source (the oracle's
+    traversal)."""
+    pk, pipe, out = full["pk"], full["pipe"], full["out"]
+    band, ns = out["band"], out["n_sites"]
+    cell, dist, src, _, rounds = pk.cvt_iterate_anyangle(band, None, out["site_pos"].clone(), ns, 0, want_trace=False,
+                                                         ws=pipe.ws, status=pipe.status)
+    cc, cd, _ = pk.cvt_iterate(band, None, out["site_pos"].clone(), ns, 0, want_trace=False, ws=pipe.ws,
+                               status=pipe.status)
+    torch.cuda.synchronize()
+    pk.check_status(pipe.status, "any-angle tessellation")
+    assert 1 < int(rounds[0]) < (1 << 16)
+    nz, ny, nx = band.shape
+    c, s = cell.reshape(-1).long(), src.reshape(-1).long()
+    d = dist.reshape(-1).long() & 0xFFFFFFFF
+    reached = c >= 0
+    assert torch.equal(reached, cc.reshape(-1) >= 0)
+    assert bool((d[reached] <= (cd.reshape(-1).long() & 0xFFFFFFFF)[reached]).all())
+    assert bool((d[reached] < (cd.reshape(-1).long() & 0xFFFFFFFF)[reached]).any())
+    idx = torch.nonzero(reached).squeeze(1)
+    sp = out["site_pos"].long()
+
+    def sq(a, b):
+        ax, ay, az = a % nx, (a // nx) % ny, a // (nx * ny)
+        bx, by, bz = b % nx, (b // nx) % ny, b // (nx * ny)
+        return (ax - bx) ** 2 + (ay - by) ** 2 + (az - bz) ** 2
+    cv = c[idx]
+    assert bool((d[idx] >= _ceil_q16(sq(idx, sp[cv]))).all())
+    t = s[idx]
+    assert bool((t >= 0).all())
+    site_vox = t == idx
+    assert torch.equal(site_vox, d[idx] == 0) and bool((sp[cv[site_vox]] == idx[site_vox]).all())
+    ch = ~site_vox
+    i1, t1 = idx[ch], t[ch]
+    assert torch.equal(c[t1], c[i1])
+    assert torch.equal(d[i1], d[t1] + _ceil_q16(sq(i1, t1)))
+    comp = pk.label_components(band)[0].reshape(-1).long()
+    assert torch.equal(comp[idx], comp[sp[cv]])
+    # shortcut segments (source beyond the 26 neighbours) see their source
+    far = ch.clone()
+    far[ch] = sq(i1, t1) > 3
+    fi = idx[far].cpu().numpy()
+    rng = np.random.default_rng(9)
+    bnp = full["band"]
+    for v in rng.choice(fi, min(2000, len(fi)), replace=False):
+        assert oracle.los(bnp, int(v), int(s[int(v)].item()))
