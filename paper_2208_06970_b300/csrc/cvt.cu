@@ -1799,11 +1799,17 @@ __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict
             const uint32_t em = emask[v];
             const int32_t pv = p0[v];
             bool active = round == 0 || test_bit(c0, v) || (pv >= 0 && test_bit(c0, pv));
-            for (int o = 0; o < 27 && !active; ++o) {
-                if (!((em >> o) & 1u)) continue;
-                const int64_t w = v + (o % 3 - 1) + d.nx * (int64_t)((o / 3) % 3 - 1) + sxy * (o / 9 - 1);
-                const int32_t t = p0[w];
-                active = test_bit(c0, w) || (t >= 0 && test_bit(c0, t));
+            if (!active) {
+                // all 26 tests issued without an early exit, so their loads overlap
+                uint32_t hit = 0u;
+#pragma unroll
+                for (int o = 0; o < 27; ++o) {
+                    if (o == 13 || !((em >> o) & 1u)) continue;
+                    const int64_t w = v + (o % 3 - 1) + d.nx * (int64_t)((o / 3) % 3 - 1) + sxy * (o / 9 - 1);
+                    const int32_t t = __ldg(p0 + w);
+                    hit |= (uint32_t)test_bit(c0, w) | (t >= 0 ? (uint32_t)test_bit(c0, t) : 0u);
+                }
+                active = hit != 0u;
             }
             if (active) {
                 int x, y, z;
