@@ -541,9 +541,15 @@ def _dims_of_nothing():
 
 # --------------------------------------------------------------------------- pipeline
 def decompose(field, iso, voxels_per_site, n_iters, aux=(), gamma=0, strat_block=16, rng_seed=0, n_bins=32,
-              cov=False, max_comp=None, ws=None, check=True):
+              cov=False, max_comp=None, ws=None, check=True, metric="chamfer"):
     """The whole hot path on the current stream: classify -> CCL -> [saliency] -> seed ->
-    Lloyd iterations -> per-cell statistics -> hierarchy merge.  Returns a dict of tensors."""
+    Lloyd iterations -> per-cell statistics -> hierarchy merge.  Returns a dict of tensors.
+
+    metric: "chamfer" (restricted 26-neighbour geodesics, lsrvt_cvt_iterate) or "anyangle"
+    (Sec. 3.2 region growing with src(w) shortcuts, lsrvt_cvt_iterate_anyangle; adds the
+    source map `src` and the round counts `rounds` to the result)."""
+    if metric not in ("chamfer", "anyangle"):
+        raise ValueError("metric must be 'chamfer' or 'anyangle', not %r" % (metric,))
     dev = field.device
     ws = ws or Workspace(dev)
     status = new_status(dev)
@@ -554,9 +560,14 @@ def decompose(field, iso, voxels_per_site, n_iters, aux=(), gamma=0, strat_block
     comp, cb, cs, cf, nc = label_components(band, max_comp, ws, status)
     q = saliency_grad(field, gamma, ws) if gamma else None
     sp, sc, off, ns = seed(comp, q, nc, max_comp, voxels_per_site, strat_block, rng_seed, ws=ws, status=status)
-    cell, dist, trace = cvt_iterate(band, q, sp, ns, n_iters, ws=ws, status=status)
+    extra = {}
+    if metric == "anyangle":
+        cell, dist, src, trace, rounds = cvt_iterate_anyangle(band, q, sp, ns, n_iters, ws=ws, status=status)
+        extra = dict(src=src, rounds=rounds)
+    else:
+        cell, dist, trace = cvt_iterate(band, q, sp, ns, n_iters, ws=ws, status=status)
     out = dict(band=band, comp=comp, comp_band=cb, comp_size=cs, comp_first=cf, n_comp=nc, q=q, site_pos=sp,
-               site_comp=sc, comp_site_off=off, n_sites=ns, cell=cell, dist=dist, trace=trace, status=status)
+               site_comp=sc, comp_site_off=off, n_sites=ns, cell=cell, dist=dist, trace=trace, status=status, **extra)
     if len(aux):
         cells = aggregate(cell, list(aux), sp, ns, n_bins=n_bins, cov=cov, ws=ws, status=status)
         comps, bands, vol = merge_hierarchy(cells, ns, off, cb, nc, max_comp, len(iso) + 1, n_bins, cov, ws)

@@ -61,3 +61,11 @@ def test_argument_errors_return_synchronously(L):
     assert L.lsrvt_saliency_grad(fake, d, 7, fake, fake, 1 << 20, None) == 1
     sp = pkg.SeedParams(512, 17, 0, 0)  # strat_block above 16
     assert L.lsrvt_seed(fake, None, d, fake, 8, sp, fake, fake, fake, 8, fake, fake, 1 << 30, None, None) == 1
+
+
+def test_decompose_rejects_unknown_metric():
+    import pytest
+    import torch
+    import paper_2208_06970_b300 as pkg
+    with pytest.raises(ValueError):
+        pkg.decompose(torch.zeros(2, 2, 2), [0.5], 8, 1, metric="euclid")

@@ -121,3 +121,24 @@ def test_anyangle_round_limit_and_bad_site(pk):
     (cell, dist, src, trace, rounds), spt, st = _gpu(pk, band, None, bad, 0)
     torch.cuda.synchronize()
     assert int(st.item()) == INVALID_ARG
+
+
+def test_decompose_anyangle_chain(pk):
+    # the chained path with the any-angle metric and |grad f| weights: sites, cells, lengths,
+    # sources and per-cell counts equal the oracle's chain
+    w = workloads.blobs_workload(side=40, seed=3)
+    f, aux = w["field"], w["aux"]
+    out = pk.decompose(f.cuda(), w["iso"], 256, 2, aux=[a.cuda() for a in aux], gamma=1, rng_seed=3,
+                       metric="anyangle")
+    torch.cuda.synchronize()
+    band = oracle.classify(f.numpy(), w["iso"])
+    q = oracle.saliency(f.numpy(), 1)
+    comp, cb, cs, cf = oracle.label_components(band)
+    sp, sc, off, nc = oracle.seed(comp, q, len(cb), 256, 16, 3)
+    rsp, rc, rd, rs, rt, rr = oracle.cvt_iterate_anyangle(band, q, sp, 2)
+    ns = int(out["n_sites"].item())
+    assert np.array_equal(cpu(out["site_pos"])[:ns], rsp)
+    assert np.array_equal(cpu(out["cell"]), rc) and np.array_equal(cpu(out["src"]), rs)
+    assert np.array_equal(cpu(out["dist"]).view(np.uint32), rd) and np.array_equal(out["rounds"], rr)
+    ref = oracle.aggregate(rc, aux.numpy(), len(rsp), n_bins=32)
+    assert np.array_equal(cpu(out["cells"]["count"])[:ns], ref["count"])
