@@ -233,7 +233,8 @@ lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q, lsrvt_dim
  *   NaN or unreached voxels); rounds_host [n_iters + 1] int32 (HOST, out, optional: the
  *   rounds of each tessellation, the last one, which changed nothing, included).
  *  max_rounds (>= 1) bounds the rounds of one tessellation: TIMEOUT in status_dev past it.
- *  The call synchronises the stream once per 8 rounds to read the change flags.
+ *  The call synchronises the stream once per 8 rounds to read the change flags, so it cannot
+ *   be captured in a CUDA graph (lsrvt_cvt_iterate can).
  *  Workspace: lsrvt_workspace_bytes(LSRVT_STEP_CVT_ANYANGLE, d, 0, max_sites, max_rounds). */
 lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const uint16_t *q, lsrvt_dims d, int32_t *site_pos,
                                         const int32_t *n_sites_dev, int32_t max_sites, int32_t n_iters,

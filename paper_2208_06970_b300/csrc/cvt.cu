@@ -1154,7 +1154,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             const int cov = brick_tube_in_band(clr, d, lx, ly, lz, hx, hy, hz, c.y, c.z, c.w & 0xFFFFFF);
             const int L2 = max(abs(2 * c.y - lx - hx), max(abs(2 * c.z - ly - hy), abs(2 * (c.w & 0xFFFFFF) - lz - hz)));
             wcov[c2] = cov;
-            // L2 = 0 (a clipped edge brick centred on the site): the walk returns its verdict, 0 or 1
+            // L2 = 0 (a clipped edge brick centred on the site): the walk returns its answer, 0 or 1
             if (cov >= max(L2, 1)) wcert[c2] = 2;
         }
         __syncthreads();
