@@ -1718,7 +1718,9 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
 // State: key (length << 32 | site) and src (voxel index, -1 unreached).
 
 // ceil(2^16 sqrt(D)) for 0 < D < 2^32: a rounded square root brought to the exact integer by
-// comparing squares (the result r is the least with r^2 >= 2^32 D; r < 2^32, so r^2 fits).
+// comparing squares (the result r is the least with r^2 >= 2^32 D).  D = dx^2 + dy^2 + dz^2 is
+// never 2^32 - 1 (7 mod 8: not a sum of three squares), the one value whose r would be 2^32,
+// so r < 2^32 and r^2 fits in 64 bits.
 __device__ __forceinline__ unsigned long long ceil_q16_length(unsigned long long D) {
     const unsigned long long v = D << 32;
     unsigned long long r = D < (1ull << 16) ? (unsigned long long)(__fsqrt_rn((float)D) * 65536.0f)
