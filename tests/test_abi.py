@@ -45,6 +45,11 @@ def test_workspace_queries(L):
     assert w >= 64 ** 3 * 8  # one 64-bit key per voxel at least
     assert pkg.workspace_bytes("label", (0, 4, 4)) == 0  # invalid dims
     assert pkg.workspace_bytes("seed", (512, 512, 512), max_comp=1 << 20) > 0
+    # any-angle: two key + two source buffers, edge masks and clearance at least; one flag per round
+    a1 = pkg.workspace_bytes("cvt_anyangle", (64, 64, 64), max_sites=1000, n_aux=64)
+    a2 = pkg.workspace_bytes("cvt_anyangle", (64, 64, 64), max_sites=1000, n_aux=64 + 4096)
+    assert a1 >= 64 ** 3 * (2 * 8 + 2 * 4 + 4 + 1)
+    assert 4 * 4096 <= a2 - a1 <= 4 * 4096 + 256
 
 
 def test_argument_errors_return_synchronously(L):
@@ -61,6 +66,10 @@ def test_argument_errors_return_synchronously(L):
     assert L.lsrvt_saliency_grad(fake, d, 7, fake, fake, 1 << 20, None) == 1
     sp = pkg.SeedParams(512, 17, 0, 0)  # strat_block above 16
     assert L.lsrvt_seed(fake, None, d, fake, 8, sp, fake, fake, fake, 8, fake, fake, 1 << 30, None, None) == 1
+    aa = L.lsrvt_cvt_iterate_anyangle
+    assert aa(fake, None, d, fake, fake, 8, 1, 0, fake, None, None, None, None, fake, 1 << 30, None, None) == 1
+    assert aa(fake, None, d, None, fake, 8, 1, 16, fake, None, None, None, None, fake, 1 << 30, None, None) == 1
+    assert aa(fake, None, d, fake, fake, 8, 1, 16, fake, None, None, None, None, fake, 64, None, None) == 8
 
 
 def test_decompose_rejects_unknown_metric():
