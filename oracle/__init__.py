@@ -84,6 +84,9 @@ def lib():
         L.orc_site_edges.argtypes = [P, P, i32, i32, i32, i64, P, P]
         L.orc_site_edges.restype = i64
         L.orc_site_sssp.argtypes = [i32, P, P, P, i32, P]
+        L.orc_energy.argtypes = [P, P, P, i64, P]
+        L.orc_energy.restype = None
+        L.orc_lattice_lloyd.argtypes = [i32, i32, i32, P, i32, i32, P]
         _lib = L
     return _lib
 
@@ -181,7 +184,8 @@ def los(band, v, s):
 
 
 def update(band, q, cell, dist, site_pos, diagnostics=False, src=None):
-    """Geodesically weighted site update (Eq. 2).  Returns (new_pos, (moved, sumsq)[, diag]).
+    """Geodesically weighted site update (Eq. 2).  Returns (new_pos, (moved, sumsq, sum_ds_q16)[, diag])
+    with sum_ds_q16 the sum over moved sites of ceil(2^16 |displacement|).
 
     With `src` (the source map of the any-angle tessellation) phi follows src chains instead
     of the chamfer parents."""
@@ -194,7 +198,7 @@ def update(band, q, cell, dist, site_pos, diagnostics=False, src=None):
     site_pos = np.ascontiguousarray(site_pos, dtype=np.int32)
     S = len(site_pos)
     new_pos = np.empty(max(S, 1), np.int32)
-    stats = np.zeros(2, np.int64)
+    stats = np.zeros(3, np.int64)
     if diagnostics:
         parent = np.empty(band.shape, np.int32)
         losv = np.empty(band.shape, np.uint8)
@@ -209,7 +213,7 @@ def update(band, q, cell, dist, site_pos, diagnostics=False, src=None):
         src = np.ascontiguousarray(src, dtype=np.int32)
         _check(lib().orc_update_src(_p(band), _p(q), nx, ny, nz, _p(cell), _p(dist), _p(src), _p(site_pos), S,
                                     _p(new_pos), _p(stats), _p(parent), _p(losv), _p(phi), _p(sums)), "update_src")
-    out = (new_pos[:S].copy(), (int(stats[0]), int(stats[1])))
+    out = (new_pos[:S].copy(), (int(stats[0]), int(stats[1]), int(stats[2])))
     if diagnostics:
         return out + (dict(parent=parent, los=losv.astype(bool), phi=phi, sums=sums[:S]),)
     return out
@@ -240,7 +244,9 @@ def update_selected(band, q, cell, dist, site_pos, sites):
 def cvt_iterate(band, q, site_pos, n_iters):
     """Algorithm 1 after seeding: n_iters x (assign, update) then a final assign.
 
-    Returns (site_pos, cell, dist, trace[n_iters, 2])."""
+    Returns (site_pos, cell, dist, trace[n_iters, TRACE]); a trace row is (sites moved,
+    sum |d|^2, sum ceil(2^16 |d|), energy low 64 bits, energy high 64 bits) -- see
+    trace_columns()."""
     band = np.ascontiguousarray(band, dtype=np.uint8)
     nx, ny, nz = _dims(band)
     if q is not None:
@@ -248,10 +254,45 @@ def cvt_iterate(band, q, site_pos, n_iters):
     sp = np.array(site_pos, dtype=np.int32, copy=True)
     cell = np.empty(band.shape, np.int32)
     dist = np.empty(band.shape, np.uint32)
-    trace = np.zeros((max(n_iters, 1), 2), np.int64)
+    trace = np.zeros((max(n_iters, 1), TRACE), np.int64)
     _check(lib().orc_cvt_iterate(_p(band), _p(q), nx, ny, nz, _p(sp), len(sp), int(n_iters), _p(cell), _p(dist),
                                  _p(trace)), "cvt_iterate")
     return sp, cell, dist, trace[:n_iters]
+
+
+TRACE = 5  # columns of a Lloyd-iteration trace row
+
+
+def trace_columns(trace):
+    """Named columns of a trace [n_iters, TRACE]: moved, sumsq, sum_ds_q16 (int64 arrays),
+    energy (exact Python ints, sum of m_v D(v)^2 in (1/2^16 voxel)^2 units) and mean_ds
+    (float: mean displacement over n sites needs n, so it is left to the caller)."""
+    t = np.asarray(trace, dtype=np.int64)
+    lo = t[:, 3].astype(np.uint64)
+    hi = t[:, 4].astype(np.uint64)
+    energy = [int(h) << 64 | int(l) for l, h in zip(lo, hi)]
+    return dict(moved=t[:, 0], sumsq=t[:, 1], sum_ds_q16=t[:, 2], energy=energy)
+
+
+def energy(q, cell, dist):
+    """CVT energy sum over assigned voxels of m_v D(v)^2 (16.16 distances), an exact int."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    dist = np.ascontiguousarray(dist, dtype=np.uint32)
+    if q is not None:
+        q = np.ascontiguousarray(q, dtype=np.uint16)
+    out = np.zeros(2, np.uint64)
+    lib().orc_energy(_p(q), _p(cell), _p(dist), cell.size, _p(out))
+    return int(out[1]) << 64 | int(out[0])
+
+
+def lattice_lloyd(shape, site_pos, n_iters):
+    """Textbook Euclidean Lloyd on the lattice of a box (nearest site, centroid rounded half
+    up).  shape = (nz, ny, nx).  Returns (site_pos, energy[n_iters + 1])."""
+    nz, ny, nx = shape
+    sp = np.array(site_pos, dtype=np.int32, copy=True)
+    e = np.zeros(n_iters + 1, np.int64)
+    _check(lib().orc_lattice_lloyd(nx, ny, nz, _p(sp), len(sp), int(n_iters), _p(e)), "lattice_lloyd")
+    return sp, e
 
 
 def anyangle_assign(band, site_pos, max_rounds=1 << 16):
@@ -272,7 +313,7 @@ def anyangle_assign(band, site_pos, max_rounds=1 << 16):
 def cvt_iterate_anyangle(band, q, site_pos, n_iters, max_rounds=1 << 16):
     """Algorithm 1 with the any-angle tessellation; the Eq. 2 update follows src chains.
 
-    Returns (site_pos, cell, dist, src, trace[n_iters, 2], rounds[n_iters + 1])."""
+    Returns (site_pos, cell, dist, src, trace[n_iters, TRACE], rounds[n_iters + 1])."""
     band = np.ascontiguousarray(band, dtype=np.uint8)
     nx, ny, nz = _dims(band)
     if q is not None:
@@ -281,7 +322,7 @@ def cvt_iterate_anyangle(band, q, site_pos, n_iters, max_rounds=1 << 16):
     cell = np.empty(band.shape, np.int32)
     dist = np.empty(band.shape, np.uint32)
     src = np.empty(band.shape, np.int32)
-    trace = np.zeros((max(n_iters, 1), 2), np.int64)
+    trace = np.zeros((max(n_iters, 1), TRACE), np.int64)
     rounds = np.zeros(n_iters + 1, np.int32)
     _check(lib().orc_cvt_iterate_anyangle(_p(band), _p(q), nx, ny, nz, _p(sp), len(sp), int(n_iters),
                                           int(max_rounds), _p(cell), _p(dist), _p(src), _p(trace), _p(rounds)),

@@ -582,7 +582,8 @@ int orc_los(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
 /*  move: walk the traversal from the site toward the target and stop at the */
 /*   last voxel of the site's band (move only as far as possible before      */
 /*   crossing the boundary).  Cells with M = 0 do not move.                   */
-/* stats[0] = sites moved, stats[1] = sum of squared displacements.           */
+/* stats[0] = sites moved, stats[1] = sum of squared displacements,          */
+/* stats[2] = sum of ceil(2^16 |displacement|).                                */
 /* parent_out / los_out / phi_out / sums_out are optional (NULL) diagnostics. */
 /* ------------------------------------------------------------------------- */
 /* site_sel (optional, one byte per site): when given, only the voxels of the  */
@@ -590,6 +591,16 @@ int orc_los(const uint8_t *band, int32_t nx, int32_t ny, int32_t nz,
 /* parents, line-of-sight tests and phi never leave the cell, so the selected */
 /* sites get exactly the positions of the full update; this lets one full-    */
 /* size replay check a sample of cells.                                       */
+/* Per-axis target of Eq. 2: the centroid S / M rounded half up, floor((2S + M) / (2M)),   */
+/* for M > 0 and S >= 0 (coordinates are non-negative, so C division is the floor).        */
+static int32_t centroid_round(int64_t S, int64_t M)
+{
+    return (int32_t)((2 * S + M) / (2 * M));
+}
+
+/* ceil(2^16 sqrt(D)) of an integer D (declared here, defined with the site graph).        */
+uint32_t orc_site_weight(int32_t dx, int32_t dy, int32_t dz);
+
 static int update_impl(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
                        const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
                        const uint8_t *site_sel, const int32_t *src_in, int32_t *new_pos, int64_t *stats,
@@ -645,16 +656,16 @@ static int update_impl(const uint8_t *band, const uint16_t *q, int32_t nx, int32
         S[4 * s + 2] += w * pz;
         S[4 * s + 3] += w;
     }
-    int64_t moved = 0, sumsq = 0;
+    int64_t moved = 0, sumsq = 0, sumlen = 0;
     for (int32_t s = 0; s < n_sites; ++s) {
         int32_t p = site_pos[s];
         int32_t x = p % nx, y = (p / nx) % ny, z = p / (nx * ny);
         int64_t M = S[4 * s + 3];
         int32_t nxp = x, nyp = y, nzp = z;
         if (M > 0) {
-            int32_t tx = (int32_t)((2 * S[4 * s + 0] + M) / (2 * M));
-            int32_t ty = (int32_t)((2 * S[4 * s + 1] + M) / (2 * M));
-            int32_t tz = (int32_t)((2 * S[4 * s + 2] + M) / (2 * M));
+            int32_t tx = centroid_round(S[4 * s + 0], M);
+            int32_t ty = centroid_round(S[4 * s + 1], M);
+            int32_t tz = centroid_round(S[4 * s + 2], M);
             walk_traversal(band, nx, ny, x, y, z, tx, ty, tz, band[p], &nxp, &nyp, &nzp);
         }
         new_pos[s] = nxp + nx * (nyp + ny * nzp);
@@ -662,9 +673,11 @@ static int update_impl(const uint8_t *band, const uint16_t *q, int32_t nx, int32
             moved++;
             int64_t ddx = nxp - x, ddy = nyp - y, ddz = nzp - z;
             sumsq += ddx * ddx + ddy * ddy + ddz * ddz;
+            /* d_s = |new - old| in 16.16 fixed point, rounded up (Fig. "convergence": mean d_s) */
+            sumlen += orc_site_weight((int32_t)ddx, (int32_t)ddy, (int32_t)ddz);
         }
     }
-    stats[0] = moved; stats[1] = sumsq;
+    stats[0] = moved; stats[1] = sumsq; stats[2] = sumlen;
     if (parent_out) memcpy(parent_out, parent, sizeof(int32_t) * (size_t)n);
     if (los_out) for (int64_t v = 0; v < n; ++v) los_out[v] = (uint8_t)los[v];
     if (phi_out) memcpy(phi_out, phi, sizeof(int32_t) * (size_t)n);
@@ -702,16 +715,108 @@ int orc_update_selected(const uint8_t *band, const uint16_t *q, int32_t nx, int3
                         const int32_t *cell, const uint32_t *dist, const int32_t *site_pos, int32_t n_sites,
                         const uint8_t *site_sel, int32_t *new_pos, int64_t *sums_out)
 {
-    int64_t stats[2];
+    int64_t stats[3];
     return update_impl(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, site_sel, NULL, new_pos, stats,
                        NULL, NULL, NULL, sums_out);
+}
+
+/* ------------------------------------------------------------------------- */
+/* CVT energy of an assignment, the quantity Lloyd's method lowers:          */
+/* E = sum over assigned voxels of m_v D(v)^2 (Sec. 3.1 "Centroids or Centers */
+/* of Mass": m_v; Eq. 1: D = the tessellation's distance to the voxel's      */
+/* site, 16.16 fixed point), exact in 128 bits: out[0] = low 64 bits,        */
+/* out[1] = high 64 bits.  Recorded per iteration, never used in control.    */
+/* ------------------------------------------------------------------------- */
+void orc_energy(const uint16_t *q, const int32_t *cell, const uint32_t *dist, int64_t n, uint64_t *out)
+{
+    u128 e = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        if (cell[v] < 0) continue;
+        u128 d = dist[v];
+        e += (u128)(q ? q[v] : 1u) * d * d;
+    }
+    out[0] = (uint64_t)e;
+    out[1] = (uint64_t)(e >> 64);
+}
+
+/* One Lloyd iteration's trace record: sites moved, sum of |d|^2, sum of      */
+/* ceil(2^16 |d|) (mean d_s = that / 2^16 / n_sites), and the energy of the  */
+/* iteration's assignment (low, high 64 bits).                                */
+#define ORC_TRACE 5
+
+static void trace_record(int64_t *trace, int32_t it, const int64_t *st, const uint16_t *q, const int32_t *cell,
+                         const uint32_t *dist, int64_t n)
+{
+    uint64_t e[2];
+    orc_energy(q, cell, dist, n, e);
+    int64_t *t = trace + (int64_t)ORC_TRACE * it;
+    t[0] = st[0]; t[1] = st[1]; t[2] = st[2];
+    t[3] = (int64_t)e[0]; t[4] = (int64_t)e[1];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Textbook Lloyd iteration on the integer lattice of a box, Euclidean       */
+/* metric (the CVT setting of Sec. 2 without restriction), used to pin the   */
+/* centroid rounding of Eq. 2 by a theorem: every voxel goes to its nearest  */
+/* site (squared distance, ties to the lowest id), then every site with a    */
+/* non-empty cell moves to its cell's centroid rounded half up per axis --   */
+/* the same centroid_round as the update.  That rounding is a nearest lattice */
+/* point to the centroid, and sum |v - p|^2 over a cell = sum |v - c|^2 +    */
+/* n |c - p|^2, so neither step can raise E = sum |v - site(v)|^2.           */
+/* energy[k], k = 0..n_iters: E of the k-th assignment; site_pos in/out.     */
+/* ------------------------------------------------------------------------- */
+int orc_lattice_lloyd(int32_t nx, int32_t ny, int32_t nz, int32_t *site_pos, int32_t n_sites, int32_t n_iters,
+                      int64_t *energy)
+{
+    int64_t n = (int64_t)nx * ny * nz;
+    if (n <= 0 || n_sites <= 0 || n_iters < 0) return ORC_EINVAL;
+    for (int32_t s = 0; s < n_sites; ++s)
+        if (site_pos[s] < 0 || site_pos[s] >= n) return ORC_EINVAL;
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *S = (int64_t *)malloc(sizeof(int64_t) * 4 * (size_t)n_sites);
+    if (!cell || !S) { free(cell); free(S); return ORC_ENOMEM; }
+    for (int32_t it = 0; it <= n_iters; ++it) {
+        int64_t E = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t x = v % nx, y = (v / nx) % ny, z = v / ((int64_t)nx * ny);
+            int64_t best = -1;
+            int32_t bs = -1;
+            for (int32_t s = 0; s < n_sites; ++s) {
+                int64_t p = site_pos[s];
+                int64_t dx = x - p % nx, dy = y - (p / nx) % ny, dz = z - p / ((int64_t)nx * ny);
+                int64_t d2 = dx * dx + dy * dy + dz * dz;
+                if (bs < 0 || d2 < best) { best = d2; bs = s; }
+            }
+            cell[v] = bs;
+            E += best;
+        }
+        energy[it] = E;
+        if (it == n_iters) break;
+        memset(S, 0, sizeof(int64_t) * 4 * (size_t)n_sites);
+        for (int64_t v = 0; v < n; ++v) {
+            int32_t s = cell[v];
+            S[4 * s + 0] += v % nx;
+            S[4 * s + 1] += (v / nx) % ny;
+            S[4 * s + 2] += v / ((int64_t)nx * ny);
+            S[4 * s + 3] += 1;
+        }
+        for (int32_t s = 0; s < n_sites; ++s) {
+            int64_t M = S[4 * s + 3];
+            if (M == 0) continue;
+            site_pos[s] = centroid_round(S[4 * s + 0], M) +
+                          nx * (centroid_round(S[4 * s + 1], M) + ny * centroid_round(S[4 * s + 2], M));
+        }
+    }
+    free(cell); free(S);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
 /* Algorithm 1 (LRCVT) after seeding: n_iters x (restricted geodesic VT,      */
 /* geodesically weighted update), then a final VT.  The paper loops until    */
 /* converged (mean d_s below a tolerance, Fig. "scaling"/Table 1); here the  */
-/* count is given.  trace[2*it] = sites moved, trace[2*it+1] = sum |dx|^2.    */
+/* count is given.  trace[ORC_TRACE*it ...] = the iteration's record          */
+/* (trace_record: moved, sum |d|^2, sum ceil(2^16 |d|), energy low, high).    */
 /* ------------------------------------------------------------------------- */
 int orc_cvt_iterate(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t ny, int32_t nz,
                     int32_t *site_pos, int32_t n_sites, int32_t n_iters,
@@ -723,11 +828,11 @@ int orc_cvt_iterate(const uint8_t *band, const uint16_t *q, int32_t nx, int32_t 
     for (int32_t it = 0; it < n_iters; ++it) {
         rc = orc_assign(band, nx, ny, nz, site_pos, n_sites, cell, dist);
         if (rc) goto done;
-        int64_t st[2];
+        int64_t st[3];
         rc = orc_update(band, q, nx, ny, nz, cell, dist, site_pos, n_sites, np, st, 0, 0, 0, 0);
         if (rc) goto done;
         memcpy(site_pos, np, sizeof(int32_t) * (size_t)n_sites);
-        if (trace) { trace[2 * it] = st[0]; trace[2 * it + 1] = st[1]; }
+        if (trace) trace_record(trace, it, st, q, cell, dist, (int64_t)nx * ny * nz);
     }
     rc = orc_assign(band, nx, ny, nz, site_pos, n_sites, cell, dist);
 done:
@@ -763,8 +868,6 @@ done:
 /* 0xFFFFFFFF, src -1.  *rounds = rounds run, the last (unchanged) included.  */
 /* ------------------------------------------------------------------------- */
 typedef struct { uint64_t d; int32_t s; uint64_t dp; int32_t p; } aa_cand;
-
-uint32_t orc_site_weight(int32_t dx, int32_t dy, int32_t dz);
 
 static int aa_less(const aa_cand *a, const aa_cand *b)
 {
@@ -871,11 +974,11 @@ int orc_cvt_iterate_anyangle(const uint8_t *band, const uint16_t *q, int32_t nx,
         rc = orc_anyangle_assign(band, nx, ny, nz, site_pos, n_sites, max_rounds, cell, dist, src,
                                  rounds ? rounds + it : NULL);
         if (rc) goto done;
-        int64_t st[2];
+        int64_t st[3];
         rc = orc_update_src(band, q, nx, ny, nz, cell, dist, src, site_pos, n_sites, np, st, 0, 0, 0, 0);
         if (rc) goto done;
         memcpy(site_pos, np, sizeof(int32_t) * (size_t)n_sites);
-        if (trace) { trace[2 * it] = st[0]; trace[2 * it + 1] = st[1]; }
+        if (trace) trace_record(trace, it, st, q, cell, dist, (int64_t)nx * ny * nz);
     }
     rc = orc_anyangle_assign(band, nx, ny, nz, site_pos, n_sites, max_rounds, cell, dist, src,
                              rounds ? rounds + n_iters : NULL);
