@@ -175,6 +175,18 @@ class Pipeline:
         return self.last
 
 
+def convergence_summary(trace, n_sites):
+    """The Lloyd trace of the last step: sites moved, mean d_s (voxels; the paper's
+    convergence measure) and the CVT energy sum q_v D(v)^2 (voxel^2) per iteration, with the
+    number of iterations that raised it (recorded, not asserted: the method does not promise
+    a monotone energy)."""
+    import paper_2208_06970_b300 as pkg
+    t = pkg.trace_summary(trace, n_sites)
+    return dict(moved=t["moved"], mean_ds=[round(v, 5) for v in t["mean_ds"]],
+                energy_voxel2=[float("%.6g" % v) for v in t["energy_voxel2"]],
+                energy_increases=t["energy_increases"])
+
+
 def count_launches(fn):
     """Kernels launched by one call of fn, from the CUDA activity trace (CUPTI via torch.profiler)."""
     from torch.profiler import ProfilerActivity, profile
@@ -816,7 +828,7 @@ def main():
             stats=dict(aggregate_ms=r["phase"].get("aggregate"), algorithmic_gbs=r["stats_gbs"],
                        frac=(r["stats_gbs"] / pk["hbm"]) if r["stats_gbs"] else None),
             phases_ms=r["phase"], cvt_gvoxel_iters_per_s=n * N_ITERS / (r["cvt_ms"] * 1e-3) / 1e9,
-            moved_per_iter=r["trace"][:, 0].tolist(), clocks=r["clk"], e2e=r["e2e"],
+            convergence=convergence_summary(r["trace"], r["n_sites"]), clocks=r["clk"], e2e=r["e2e"],
             gpu_launches=int(r["launches"] * args.steps), launches_per_step=r["launches"], cpu_baseline=cpu,
             layout=r["layout"], graph=r["graph"], anyangle=r["anyangle"], forms=forms, precision=precision)
         print(json.dumps(line), flush=True)

@@ -37,6 +37,9 @@
 extern "C" {
 #endif
 
+/* Columns of a Lloyd-iteration trace record (lsrvt_cvt_iterate, lsrvt_cvt_iterate_anyangle). */
+#define LSRVT_TRACE 5
+
 typedef enum {
     LSRVT_OK = 0,
     LSRVT_ERR_INVALID_ARG = 1, /* bad dims / NULL pointer / parameter out of range       */
@@ -158,8 +161,10 @@ lsrvt_status lsrvt_label_components(const uint8_t *band, lsrvt_dims d, int32_t *
  *  - Scratch lives in a fixed device array inside the library (1.25 MiB, held by every
  *    GPU that loads the library until the process exits); volumes of more than 2^18
  *    voxels (64^3) are rejected with LSRVT_ERR_WORKSPACE and nothing is launched.
- *  - The first call on a device looks up that array's device address (with the device
- *    current); make that first call before any stream capture.
+ *  - Each call made outside stream capture looks up that array's device address on the
+ *    current device (so a device reset, which moves the array, is followed); a call made
+ *    while its stream is being captured uses the address the last uncaptured call on that
+ *    device found.  Make the first call on a device before any stream capture.
  *  - It calls no cudaMalloc, cudaFree or allocating library routine.
  *  - Every call shares the one array: calls that may overlap on the GPU (different streams
  *    without ordering, or several host threads) race and corrupt each other's results;
@@ -208,7 +213,14 @@ lsrvt_status lsrvt_seed(const int32_t *comp, const uint16_t *q, lsrvt_dims d, co
  *   site_pos [max_sites] int32 (in/out), n_sites_dev (in);
  *   cell [N] int32 (out, site id, -1 for NaN voxels); dist [N] uint32 (out, optional:
  *   16.16 geodesic distance to the site, 0xFFFFFFFF for NaN voxels);
- *   iter_trace [n_iters][2] int64 (out, optional: sites moved, sum of squared moves).
+ *   iter_trace [n_iters][LSRVT_TRACE] int64 (out, optional), one record per iteration:
+ *     [0] sites moved, [1] sum of squared moves (voxels^2), [2] sum over moved sites of
+ *     ceil(2^16 |move|) (the paper's convergence measure, Fig. "convergence": mean d_s =
+ *     [2] / 2^16 / n_sites), [3], [4] the CVT energy of the iteration's assignment,
+ *     E = sum over assigned voxels of q_v D(v)^2 with D the 16.16 distance, an exact
+ *     unsigned 128-bit integer: [3] its low 64 bits, [4] its high 64 bits.  Recorded
+ *     only: E is not guaranteed to fall (the geodesic update of Eq. 2 is not Lloyd's
+ *     centroid step), and nothing depends on it.
  * OVERFLOW if a distance reaches 2^32; TIMEOUT if the relaxation exceeds its round limit. */
 lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q, lsrvt_dims d, int32_t *site_pos,
                                const int32_t *n_sites_dev, int32_t max_sites, int32_t n_iters, int32_t *cell,
@@ -232,7 +244,11 @@ lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q, lsrvt_dim
  *   any-angle length); src [N] int32 (out, optional: the source of each voxel's path, -1 for
  *   NaN or unreached voxels); rounds_host [n_iters + 1] int32 (HOST, out, optional: the
  *   rounds of each tessellation, the last one, which changed nothing, included).
- *  max_rounds (>= 1) bounds the rounds of one tessellation: TIMEOUT in status_dev past it.
+ *  max_rounds (>= 1) bounds the rounds of one tessellation.  A tessellation that does not
+ *   settle within it ends the call at once: TIMEOUT goes to status_dev, cell/dist/src receive
+ *   the state of its last round (not converged), no update or further tessellation runs (the
+ *   sites keep their positions from before that tessellation), rounds_host gets max_rounds
+ *   for it and stays untouched after it, and the call returns LSRVT_ERR_TIMEOUT.
  *  The call synchronises the stream once per 8 rounds to read the change flags, so it cannot
  *   be captured in a CUDA graph (lsrvt_cvt_iterate can).
  *  Workspace: lsrvt_workspace_bytes(LSRVT_STEP_CVT_ANYANGLE, d, 0, max_sites, max_rounds). */

@@ -30,6 +30,7 @@ STEP = dict(classify=0, label=1, saliency=2, seed=3, cvt=4, aggregate=5, merge=6
             cvt_anyangle=10)
 STATS_HIST = 1
 STATS_COV = 2
+TRACE = 5  # columns of a Lloyd-iteration trace record (LSRVT_TRACE)
 
 
 class LsrvtError(RuntimeError):
@@ -269,7 +270,8 @@ def cvt_iterate(band, q, site_pos, n_sites_dev, n_iters, want_dist=True, want_tr
                 cell=None, dist=None):
     """Algorithm 1 after seeding: n_iters x (Eq. 1 assignment, Eq. 2 update) + final assignment.
 
-    site_pos is updated in place.  Returns (cell, dist or None, trace[n_iters, 2] or None)."""
+    site_pos is updated in place.  Returns (cell, dist or None, trace[n_iters, TRACE] or None);
+    trace_summary() reads a trace."""
     _require_cuda(band, q, site_pos)
     dev = band.device
     max_sites = site_pos.numel()
@@ -277,7 +279,7 @@ def cvt_iterate(band, q, site_pos, n_sites_dev, n_iters, want_dist=True, want_tr
         cell = torch.empty(band.shape, dtype=torch.int32, device=dev)
     if want_dist and dist is None:
         dist = torch.empty(band.shape, dtype=torch.int32, device=dev)
-    trace = torch.zeros((max(n_iters, 1), 2), dtype=torch.int64, device=dev) if want_trace else None
+    trace = torch.zeros((max(n_iters, 1), TRACE), dtype=torch.int64, device=dev) if want_trace else None
     ws = ws or Workspace(dev)
     status = new_status(dev) if status is None else status
     buf = ws.get(workspace_bytes("cvt", _dims(band), max_sites=max_sites))
@@ -286,6 +288,19 @@ def cvt_iterate(band, q, site_pos, n_sites_dev, n_iters, want_dist=True, want_tr
                                    _ptr(trace), _ptr(buf), buf.numel(), _ptr(status), _stream()),
            "lsrvt_cvt_iterate")
     return cell, (dist if want_dist else None), (trace[:n_iters] if want_trace else None)
+
+
+def trace_summary(trace, n_sites):
+    """Per-iteration figures of a Lloyd trace (host lists): sites moved, mean d_s (the paper's
+    convergence measure, voxels), and the CVT energy sum q_v D(v)^2 of each iteration's
+    assignment (exact ints in (2^-16 voxel)^2 units, and as floats in voxel^2), plus how many
+    iterations raised the energy (recorded, not a guarantee of the method)."""
+    t = trace.cpu().numpy().astype(np.int64) if hasattr(trace, "cpu") else np.asarray(trace, np.int64)
+    energy = [(int(h) & (2 ** 64 - 1)) << 64 | (int(l) & (2 ** 64 - 1)) for l, h in zip(t[:, 3], t[:, 4])]
+    ns = max(int(n_sites), 1)
+    return dict(moved=[int(v) for v in t[:, 0]], mean_ds=[float(v) / 65536.0 / ns for v in t[:, 2]],
+                energy=energy, energy_voxel2=[e / 2.0 ** 32 for e in energy],
+                energy_increases=sum(1 for a, b in zip(energy[:-1], energy[1:]) if b > a))
 
 
 def cvt_iterate_anyangle(band, q, site_pos, n_sites_dev, n_iters, max_rounds=1 << 16, want_dist=True,
@@ -300,7 +315,7 @@ def cvt_iterate_anyangle(band, q, site_pos, n_sites_dev, n_iters, max_rounds=1 <
     cell = torch.empty(band.shape, dtype=torch.int32, device=dev)
     dist = torch.empty(band.shape, dtype=torch.int32, device=dev) if want_dist else None
     src = torch.empty(band.shape, dtype=torch.int32, device=dev) if want_src else None
-    trace = torch.zeros((max(n_iters, 1), 2), dtype=torch.int64, device=dev) if want_trace else None
+    trace = torch.zeros((max(n_iters, 1), TRACE), dtype=torch.int64, device=dev) if want_trace else None
     rounds = np.zeros(n_iters + 1, np.int32)
     ws = ws or Workspace(dev)
     status = new_status(dev) if status is None else status

@@ -347,12 +347,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void *g_static_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device.
-lsrvt_status static_scratch(void **out) {
+// Device address of the scratch array on the current device.  Outside stream capture it is
+// looked up on every call (a device reset re-creates the context and moves the array), and the
+// result is remembered per device; while the stream is being captured the remembered address
+// is used, so the first call on a device must come before any capture.
+lsrvt_status static_scratch(cudaStream_t s, void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LSRVT_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return LSRVT_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_static_ptr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_ccl_static_scratch) != cudaSuccess || !p) return LSRVT_ERR_CUDA;
         g_static_ptr[dev] = p;
@@ -376,13 +381,13 @@ extern "C" lsrvt_status lsrvt_label_components_static(const uint8_t *band, lsrvt
     size_t need;
     carve_ccl(nullptr, 0, d, &need);
     if (need > kStaticScratchBytes) return LSRVT_ERR_WORKSPACE;
+    cudaStream_t s = as_stream(stream);
     void *ws = nullptr;
-    lsrvt_status st = static_scratch(&ws);
+    lsrvt_status st = static_scratch(s, &ws);
     if (st != LSRVT_OK) return st;
     CclWs w = carve_ccl(ws, kStaticScratchBytes, d, &need);
     // Every buffer below is written before it is read, so nothing left by an earlier call
     // needs clearing.
-    cudaStream_t s = as_stream(stream);
     int64_t n = d.n();
     int64_t nchunks = (n + kChunk - 1) / kChunk;
     dim3 bgrid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);

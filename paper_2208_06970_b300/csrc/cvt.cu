@@ -71,6 +71,47 @@ __device__ __forceinline__ void decode_voxel(uint32_t v, Dims d, int &x, int &y,
     y = (int)(r - (uint32_t)z * (uint32_t)d.ny);
 }
 
+// CVT energy sum of m_v D(v)^2 (16.16 distances), exact in 128 bits: each thread keeps its
+// own sum, a warp folds its lanes' sums at the end of the kernel and adds them to the two
+// 64-bit words of the iteration's trace record (low word first, the carry detected from the
+// old value the atomic returns).  A term is below 2^16 * 2^64, the total below 2^111.
+struct EnergyAcc {
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(unsigned w, uint32_t D) {
+        const unsigned long long d2 = (unsigned long long)D * D;
+        const unsigned long long l = d2 * w, h = __umul64hi(d2, (unsigned long long)w);
+        lo += l;
+        hi += h + (lo < l ? 1ull : 0ull);
+    }
+    // every lane of the warp calls this (full-warp shuffles)
+    __device__ __forceinline__ void flush(unsigned long long *out) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+            const unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+            lo += l2;
+            hi += h2 + (lo < l2 ? 1ull : 0ull);
+        }
+        if (out && (threadIdx.x & 31) == 0 && (lo | hi)) {
+            const unsigned long long old = atomicAdd(out, lo);
+            atomicAdd(out + 1, hi + (old + lo < old ? 1ull : 0ull));
+        }
+    }
+};
+
+// ceil(2^16 sqrt(D)) for 0 < D < 2^32: a rounded square root brought to the exact integer by
+// comparing squares (the result r is the least with r^2 >= 2^32 D).  D = dx^2 + dy^2 + dz^2 is
+// never 2^32 - 1 (7 mod 8: not a sum of three squares), the one value whose r would be 2^32,
+// so r < 2^32 and r^2 fits in 64 bits.
+__device__ __forceinline__ unsigned long long ceil_q16_length(unsigned long long D) {
+    const unsigned long long v = D << 32;
+    unsigned long long r = D < (1ull << 16) ? (unsigned long long)(__fsqrt_rn((float)D) * 65536.0f)
+                                            : (unsigned long long)(__dsqrt_rn((double)D) * 65536.0);
+    while (r * r < v) ++r;
+    while (r > 1 && (r - 1) * (r - 1) >= v) --r;
+    return r;
+}
+
 // 26-bit edge mask from the 27-bit "same band" mask S (bit 13 = the voxel itself)
 __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
     uint32_t e = 0;
@@ -785,6 +826,7 @@ struct UpdateOut {
     uint32_t *los_bits;
     int32_t *plist;    // pending voxels, appended per brick
     int32_t *n_plist;
+    unsigned long long *energy;  // the iteration's energy words (trace record), or null
 };
 
 // Voxels whose key needs their own path check (no brick tube covers them), handed from the
@@ -967,6 +1009,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
     __shared__ int wcov[kMaxCand];            // per candidate: tube extent certified (half voxels)
     const int tid = threadIdx.x;
     const int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
+    EnergyAcc eacc;
     for (int64_t brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
         const int bx = (int)(brick % bg.nbx), by = (int)((brick / bg.nbx) % bg.nby),
                   bz = (int)(brick / ((int64_t)bg.nbx * bg.nby));
@@ -1237,6 +1280,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                 // warp-aggregated integer moment sums of the line-of-sight voxels (Eq. 2, phi(v) = v)
                 const int32_t sid = los ? bs.x : -1;
                 const unsigned w = los ? (up.q ? up.q[g] : 1u) : 0u;
+                if (los) eacc.add(w, (uint32_t)(best >> 32));
                 if (up.small_coords) {
                     unsigned m = __match_any_sync(0xffffffffu, sid);
                     unsigned sx = __reduce_add_sync(m, w * (unsigned)x);
@@ -1319,6 +1363,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         }
         __syncthreads();
     }
+    if (up.enabled) eacc.flush(up.energy);
 }
 
 
@@ -1334,6 +1379,7 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
     uint32_t tag, int32_t *list_out, int32_t *n_out, CheckList chk, UpdateOut up) {
     const int32_t cnt = *chk.n;
     const int lane = threadIdx.x & 31;
+    EnergyAcc eacc;
     // whole warps step through the list together (warp-level reductions and appends below)
     for (int32_t bstart = blockIdx.x * blockDim.x; bstart < cnt; bstart += gridDim.x * blockDim.x) {
         const int32_t i = bstart + threadIdx.x;
@@ -1398,6 +1444,13 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
         // warp-aggregated integer moment sums of the line-of-sight voxels (Eq. 2, phi(v) = v)
         const int32_t sid = los ? s : -1;
         const unsigned w = los ? (up.q ? up.q[g] : 1u) : 0u;
+        if (los) {
+            // the key of a checked voxel is its chamfer distance to the site
+            const int32_t p = __ldg(site_pos + s);
+            int px, py, pz;
+            decode_voxel((uint32_t)p, d, px, py, pz);
+            eacc.add(w, (uint32_t)chamfer(px - x, py - y, pz - z));
+        }
         if (up.small_coords) {
             unsigned m = __match_any_sync(0xffffffffu, sid);
             unsigned sx = __reduce_add_sync(m, w * (unsigned)x);
@@ -1424,6 +1477,7 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
         wbase = __shfl_sync(0xffffffffu, wbase, 0);
         if (pend) up.plist[wbase + __popc(pb & lanemask_lt())] = (int32_t)g;
     }
+    if (up.enabled) eacc.flush(up.energy);
 }
 
 // ---------------------------------------------------------------- voxel traversal
@@ -1469,10 +1523,11 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
     const uint8_t *__restrict__ band, const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
     const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
     uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const int32_t *__restrict__ plist,
-    const int32_t *n_plist, bool small_coords, const int32_t *__restrict__ src) {
+    const int32_t *n_plist, bool small_coords, const int32_t *__restrict__ src, unsigned long long *energy) {
     // plist == nullptr: every voxel (N < 2^31); src != nullptr: the path's next node is the
     // voxel's source (any-angle tessellation) instead of the chamfer parent
     const int32_t cnt = plist ? *n_plist : (int32_t)d.n();
+    EnergyAcc eacc;
     // whole warps step through the list together (the warp-level reductions below need them)
     for (int32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < cnt; base += gridDim.x * blockDim.x) {
         const int32_t i = base + (threadIdx.x & 31);
@@ -1548,6 +1603,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
         int32_t grp = los ? s : -1;
         unsigned m = __match_any_sync(0xffffffffu, grp);
         unsigned w = los ? (q ? q[v] : 1u) : 0u;
+        if (los) eacc.add(w, (uint32_t)(key[v] >> 32));
         if (small_coords) {
             unsigned sx = __reduce_add_sync(m, w * (unsigned)x);
             unsigned sy = __reduce_add_sync(m, w * (unsigned)y);
@@ -1566,14 +1622,16 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
             atomicAdd(&sums[4 * (int64_t)s + 3], (unsigned long long)w);
         }
     }
+    eacc.flush(energy);
 }
 
 __global__ void update_nonlos_kernel(const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
                                      const uint32_t *__restrict__ los_bits, const int32_t *__restrict__ par,
                                      const int32_t *__restrict__ nonlos, const int32_t *n_nonlos,
-                                     unsigned long long *sums, int32_t *status) {
+                                     unsigned long long *sums, int32_t *status, unsigned long long *energy) {
     int32_t cnt = *n_nonlos;
     int64_t n = d.n();
+    EnergyAcc eacc;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
         int32_t v = nonlos[i];
         int32_t u = par[v];
@@ -1590,8 +1648,10 @@ __global__ void update_nonlos_kernel(const uint16_t *__restrict__ q, Dims d, con
             set_status(status, LSRVT_ERR_TIMEOUT);
             continue;
         }
-        int32_t s = (int32_t)(uint32_t)key[v];
+        const unsigned long long kv = key[v];
+        int32_t s = (int32_t)(uint32_t)kv;
         unsigned long long w = q ? q[v] : 1u;
+        eacc.add((unsigned)w, (uint32_t)(kv >> 32));
         int ux, uy, uz;
         decode_voxel((uint32_t)u, d, ux, uy, uz);
         atomicAdd(&sums[4 * (int64_t)s + 0], w * (unsigned)ux);
@@ -1599,6 +1659,7 @@ __global__ void update_nonlos_kernel(const uint16_t *__restrict__ q, Dims d, con
         atomicAdd(&sums[4 * (int64_t)s + 2], w * (unsigned)uz);
         atomicAdd(&sums[4 * (int64_t)s + 3], w);
     }
+    eacc.flush(energy);
 }
 
 __global__ void move_sites_kernel(const uint8_t *__restrict__ band, Dims d, int32_t *site_pos, const int32_t *n_sites_dev,
@@ -1624,8 +1685,10 @@ __global__ void move_sites_kernel(const uint8_t *__restrict__ band, Dims d, int3
             site_pos[s] = np;
             long long ddx = ex - x, ddy = ey - y, ddz = ez - z;
             if (trace) {
+                const unsigned long long D2 = (unsigned long long)(ddx * ddx + ddy * ddy + ddz * ddz);
                 atomicAdd(&trace[0], 1ULL);
-                atomicAdd(&trace[1], (unsigned long long)(ddx * ddx + ddy * ddy + ddz * ddz));
+                atomicAdd(&trace[1], D2);
+                atomicAdd(&trace[2], ceil_q16_length(D2));  // d_s in 16.16, rounded up
             }
         }
     }
@@ -1716,19 +1779,6 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
 // the re-evaluated own path is never worse than the old state, so states only decrease and
 // the rounds end.  Lengths are ceil(2^16 |.|) integers, so sums are exact.
 // State: key (length << 32 | site) and src (voxel index, -1 unreached).
-
-// ceil(2^16 sqrt(D)) for 0 < D < 2^32: a rounded square root brought to the exact integer by
-// comparing squares (the result r is the least with r^2 >= 2^32 D).  D = dx^2 + dy^2 + dz^2 is
-// never 2^32 - 1 (7 mod 8: not a sum of three squares), the one value whose r would be 2^32,
-// so r < 2^32 and r^2 fits in 64 bits.
-__device__ __forceinline__ unsigned long long ceil_q16_length(unsigned long long D) {
-    const unsigned long long v = D << 32;
-    unsigned long long r = D < (1ull << 16) ? (unsigned long long)(__fsqrt_rn((float)D) * 65536.0f)
-                                            : (unsigned long long)(__dsqrt_rn((double)D) * 65536.0);
-    while (r * r < v) ++r;
-    while (r > 1 && (r - 1) * (r - 1) >= v) --r;
-    return r;
-}
 
 __device__ __forceinline__ bool aa_less(unsigned long long ka, uint32_t dpa, int32_t pa, unsigned long long kb,
                                         uint32_t dpb, int32_t pb) {
@@ -2069,7 +2119,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     BrickGeom bg{(d.nx + RX - 1) / RX, (d.ny + RY - 1) / RY, (d.nz + RZ - 1) / RZ};
     int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
     cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * nbricks, s);
-    if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * 2 * n_iters, s);
+    if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * LSRVT_TRACE * n_iters, s);
     bool small = d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048;
     {
         BitGeom bgm{(d.nx + 31) / 32};
@@ -2088,10 +2138,12 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     uint32_t tag = 0;
     const int sms = stream_sms(s);
     int vgrid = grid_for((n + 31) / 32 * 32, 256, sms * 16);
-    UpdateOut up{true, small, q, site_pos, w.sums, w.los_bits, w.plist, w.counters + 5};
-    UpdateOut no_up{false, small, q, site_pos, nullptr, nullptr, nullptr, nullptr};
+    UpdateOut up{true, small, q, site_pos, w.sums, w.los_bits, w.plist, w.counters + 5, nullptr};
+    UpdateOut no_up{false, small, q, site_pos, nullptr, nullptr, nullptr, nullptr, nullptr};
     const int64_t nwords = (n + 31) / 32;
     for (int32_t it = 0; it < n_iters; ++it) {
+        unsigned long long *rec = iter_trace ? (unsigned long long *)(iter_trace + (int64_t)LSRVT_TRACE * it) : nullptr;
+        up.energy = rec ? rec + 3 : nullptr;
         cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
         cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
@@ -2099,12 +2151,12 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, up);
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
-                                                   w.nonlos, w.counters, w.plist, w.counters + 5, small, nullptr);
+                                                   w.nonlos, w.counters, w.plist, w.counters + 5, small, nullptr,
+                                                   up.energy);
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
-                                                      status_dev);
-        move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
-            band, d, site_pos, n_sites_dev, max_sites, w.sums,
-            iter_trace ? (unsigned long long *)(iter_trace + 2 * it) : nullptr);
+                                                      status_dev, up.energy);
+        move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
+                                                                            max_sites, w.sums, rec);
     }
     lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, no_up);
     if (st != LSRVT_OK) return st;
@@ -2180,8 +2232,11 @@ lsrvt_status aa_assignment(const uint8_t *band, Dims d, const int32_t *site_pos,
             if (h[j] == 0) { done = r0 + j + 1; break; }
     }
     if (done < 0) {
+        // the host knows the limit was hit: record it and stop the whole call here
         aa_timeout_kernel<<<1, 1, 0, s>>>(status);
-        done = max_rounds;
+        if (rounds_out) *rounds_out = max_rounds;
+        const lsrvt_status ls = launch_status();
+        return ls != LSRVT_OK ? ls : LSRVT_ERR_TIMEOUT;
     }
     if (rounds_out) *rounds_out = done;
     return launch_status();
@@ -2204,7 +2259,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
     cudaStream_t s = as_stream(stream);
     const int64_t n = d.n();
     const int sms = stream_sms(s);
-    if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * 2 * n_iters, s);
+    if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * LSRVT_TRACE * n_iters, s);
     const bool small = d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048;
     {
         BitGeom bgm{(d.nx + 31) / 32};
@@ -2218,23 +2273,35 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
     }
     const int vgrid = grid_for((n + 31) / 32 * 32, 256, sms * 16);
     const int64_t nwords = (n + 31) / 32;
+    // a tessellation that hits the round limit ends the call: its last round's state (in the
+    // buffer that round wrote) is emitted unconverged, no update or further tessellation runs
+    auto stop_at_limit = [&]() {
+        const int b = max_rounds & 1;
+        emit_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.key[b], n, cell, dist);
+        if (src) cudaMemcpyAsync(src, w.src[b], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        const lsrvt_status ls = launch_status();
+        return ls != LSRVT_OK ? ls : LSRVT_ERR_TIMEOUT;
+    };
     for (int32_t it = 0; it < n_iters; ++it) {
         lsrvt_status st = aa_assignment(band, d, site_pos, n_sites_dev, max_sites, max_rounds, w, status_dev, s,
                                         rounds_host ? rounds_host + it : nullptr);
+        if (st == LSRVT_ERR_TIMEOUT) return stop_at_limit();
         if (st != LSRVT_OK) return st;
+        unsigned long long *rec = iter_trace ? (unsigned long long *)(iter_trace + (int64_t)LSRVT_TRACE * it) : nullptr;
         cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
         cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key[0], site_pos, w.clr, w.sums, w.los_bits, w.par,
-                                                   w.nonlos, w.counters, nullptr, nullptr, small, w.src[0]);
+                                                   w.nonlos, w.counters, nullptr, nullptr, small, w.src[0],
+                                                   rec ? rec + 3 : nullptr);
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key[0], w.los_bits, w.par, w.nonlos, w.counters, w.sums,
-                                                      status_dev);
-        move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(
-            band, d, site_pos, n_sites_dev, max_sites, w.sums,
-            iter_trace ? (unsigned long long *)(iter_trace + 2 * it) : nullptr);
+                                                      status_dev, rec ? rec + 3 : nullptr);
+        move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
+                                                                            max_sites, w.sums, rec);
     }
     lsrvt_status st = aa_assignment(band, d, site_pos, n_sites_dev, max_sites, max_rounds, w, status_dev, s,
                                     rounds_host ? rounds_host + n_iters : nullptr);
+    if (st == LSRVT_ERR_TIMEOUT) return stop_at_limit();
     if (st != LSRVT_OK) return st;
     emit_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.key[0], n, cell, dist);
     if (src) cudaMemcpyAsync(src, w.src[0], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);

@@ -78,3 +78,18 @@ def test_decompose_rejects_unknown_metric():
     import paper_2208_06970_b300 as pkg
     with pytest.raises(ValueError):
         pkg.decompose(torch.zeros(2, 2, 2), [0.5], 8, 1, metric="euclid")
+
+
+def test_static_labelling_scratch_covers_its_limit():
+    """The allocation-free labelling accepts every volume of up to 2^18 voxels, so the
+    workspace such a volume needs must fit its built-in scratch (1,310,720 bytes).  The
+    workspace grows with the brick and chunk counts, so long thin shapes are the largest."""
+    import paper_2208_06970_b300 as pkg
+    limit = 1310720
+    worst = 0
+    for dims in ((64, 64, 64), (262144, 1, 1), (1, 1, 262144), (1, 4, 65536), (65536, 4, 1), (1, 262144, 1),
+                 (3, 3, 29127), (2, 2, 65536), (512, 512, 1), (8, 8, 4096), (17, 15, 1028)):
+        n = dims[0] * dims[1] * dims[2]
+        assert n <= 1 << 18
+        worst = max(worst, pkg.workspace_bytes("label", dims))
+    assert 0 < worst <= limit

@@ -51,6 +51,26 @@ def _gpu(pk, band, q, sp, n_iters, slack=0, max_rounds=1 << 16, status=None):
     return out, spt, st
 
 
+def _anyangle_with_rounds(pk, band, spt, n_iters, max_rounds, st, rounds):
+    """lsrvt_cvt_iterate_anyangle through the C ABI with a caller-owned rounds_host array."""
+    import ctypes as C
+    bt = torch.from_numpy(band).cuda()
+    ns = torch.tensor([spt.numel()], dtype=torch.int32, device="cuda")
+    cell = torch.empty(band.shape, dtype=torch.int32, device="cuda")
+    d = pk.Dims(band.shape[2], band.shape[1], band.shape[0])
+    nb = pk.workspace_bytes("cvt_anyangle", d, max_sites=spt.numel(), n_aux=max_rounds)
+    buf = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    rc = pk.lib().lsrvt_cvt_iterate_anyangle(
+        C.c_void_p(bt.data_ptr()), None, d, C.c_void_p(spt.data_ptr()), C.c_void_p(ns.data_ptr()), spt.numel(),
+        n_iters, max_rounds, C.c_void_p(cell.data_ptr()), None, None, None, rounds.ctypes.data_as(C.c_void_p),
+        C.c_void_p(buf.data_ptr()), buf.numel(), C.c_void_p(st.data_ptr()),
+        C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    if rc != 0:
+        raise pk.LsrvtError(rc, "lsrvt_cvt_iterate_anyangle")
+    return cell
+
+
 @pytest.mark.parametrize("dims,P,seed", [((44, 30, 21), 200, 1), ((37, 29, 23), 64, 2), ((64, 64, 64), 512, 3),
                                          ((24, 20, 16), 2, 4), ((33, 1, 40), 16, 5), ((70, 9, 3), 40, 6)])
 def test_anyangle_assignment_parity(pk, dims, P, seed):
@@ -110,9 +130,20 @@ def test_anyangle_degenerate(pk):
 def test_anyangle_round_limit_and_bad_site(pk):
     band, q, sp = _case((44, 30, 21), 1, 200)
     rr = oracle.anyangle_assign(band, sp)[3]
-    (cell, dist, src, trace, rounds), spt, st = _gpu(pk, band, None, sp, 0, max_rounds=rr - 1)
-    torch.cuda.synchronize()
-    assert int(st.item()) == TIMEOUT
+    st = pk.new_status()
+    with pytest.raises(pk.LsrvtError) as e:
+        _gpu(pk, band, None, sp, 0, max_rounds=rr - 1, status=st)
+    assert e.value.code == TIMEOUT and int(st.item()) == TIMEOUT
+    # a Lloyd loop stops at the first tessellation that hits the limit: no update, no
+    # further tessellation, the sites unmoved
+    st = pk.new_status()
+    spt = torch.from_numpy(sp.astype(np.int32)).cuda()
+    rounds = np.full(4, -9, np.int32)
+    with pytest.raises(pk.LsrvtError) as e:
+        _anyangle_with_rounds(pk, band, spt, 3, rr - 1, st, rounds)
+    assert e.value.code == TIMEOUT and int(st.item()) == TIMEOUT
+    assert list(rounds) == [rr - 1, -9, -9, -9]
+    assert np.array_equal(cpu(spt), sp)
     (cell, dist, src, trace, rounds), spt, st = _gpu(pk, band, None, sp, 0, max_rounds=rr)
     pk.check_status(st, "exact round limit")
     nan_voxel = int(np.flatnonzero(band.ravel() == 255)[0])

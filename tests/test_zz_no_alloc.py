@@ -21,14 +21,20 @@ def _volume(seed, shape):
     return torch.from_numpy(band).cuda()
 
 
-def _static_call(pk, band, max_comp):
-    L = pk.lib()
+def _outputs(band, max_comp):
     comp = torch.full(band.shape, -7, dtype=torch.int32, device="cuda")
     cb = torch.zeros(max_comp, dtype=torch.uint8, device="cuda")
     cs = torch.zeros(max_comp, dtype=torch.int64, device="cuda")
     cf = torch.zeros(max_comp, dtype=torch.int32, device="cuda")
     nc = torch.zeros(1, dtype=torch.int32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return comp, cb, cs, cf, nc, st
+
+
+def _static_call(pk, band, max_comp, out=None):
+    """One call through the C ABI into caller-allocated outputs (allocated here unless given)."""
+    L = pk.lib()
+    comp, cb, cs, cf, nc, st = _outputs(band, max_comp) if out is None else out
     p = lambda t: C.c_void_p(t.data_ptr())
     rc = L.lsrvt_label_components_static(p(band), pk._dims(band), p(comp), p(cb), p(cs), p(cf), max_comp, p(nc), p(st),
                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -65,3 +71,25 @@ def test_static_labelling_rejects_large_volumes():
     with pytest.raises(pk.LsrvtError) as e:
         pk.label_components_static(band)
     assert e.value.code == 8
+
+
+def test_static_labelling_allocates_nothing():
+    """The property the entry point exists for: with its outputs in place, a call leaves the
+    caching allocator's counters and the device's free memory exactly as they were."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2208_06970_b300 as pk
+    band = _volume(13, (64, 64, 64))
+    n = band.numel()
+    out = _outputs(band, n)
+    _static_call(pk, band, n, out)  # warm: module load and the address look-up happen here
+    torch.cuda.synchronize()
+    keys = ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.allocated")
+    before = {k: torch.cuda.memory_stats().get(k, 0) for k in keys}
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        _static_call(pk, band, n, out)
+    torch.cuda.synchronize()
+    after = {k: torch.cuda.memory_stats().get(k, 0) for k in keys}
+    assert after == before
+    assert torch.cuda.mem_get_info()[0] == free0
