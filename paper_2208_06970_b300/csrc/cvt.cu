@@ -838,6 +838,23 @@ struct CheckList {
     int32_t *n;
 };
 
+// Warm start of the relaxation.  From the second tessellation of a call on, the key array
+// still holds the previous tessellation's exact keys (d, s), and site s has since moved by
+// msteps[s] face steps, all inside its band (Eq. 2's move walks the 6-connected traversal),
+// so a path of length d + msteps[s] W1 from s's new position reaches the voxel: an upper
+// bound of its new key.  Voxels whose key is not settled by the filter start the relaxation
+// there instead of at +inf, which leaves it far less to do when the sites move little.
+struct WarmStart {
+    bool on;
+    const int32_t *msteps;
+    __device__ __forceinline__ unsigned long long bound(unsigned long long old) const {
+        if (!on || old == kInfKey) return kInfKey;
+        const uint32_t s = (uint32_t)old;
+        const unsigned long long dd = (old >> 32) + (unsigned long long)__ldg(msteps + s) * kWFace;
+        return dd >= kInf32 ? kInfKey : (dd << 32) | s;
+    }
+};
+
 constexpr int kCellGather = 4096;   // shared buffer while searching
 constexpr int kCellList = 2048;     // stored list per coarse cell
 constexpr int kCellThreads = 256;
@@ -996,7 +1013,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                                                             const int4 *__restrict__ fine_cand, unsigned long long *key,
                                                             int32_t *list_out, int32_t *n_out, uint32_t *flags,
                                                             uint32_t *xmask, uint8_t *hasunk, uint32_t tag,
-                                                            UpdateOut up, CheckList chk) {
+                                                            UpdateOut up, CheckList chk, WarmStart warm) {
     __shared__ int4 cs[kMaxCand];
     __shared__ unsigned long long ck[kMaxCand];
     __shared__ unsigned long long Ub[256];
@@ -1217,7 +1234,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             const int bidx = vwin[i];
             const int4 bs = bidx >= 0 ? cs[bidx] : make_int4(0, 0, 0, 0);
             unsigned long long k = kInfKey;
-            bool los = false, pend = false;
+            bool los = false, pend = false, exactv = false;
             cmv[j] = 0;
             if (inb && vb[j] != kInvalidBand) {
                 int status = 0;
@@ -1244,7 +1261,8 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                     }
                 }
                 if (status < 0) {
-                    k = best;
+                    // the path check writes the exact key; until then the warm bound
+                    k = warm.bound(key[g]);
                 } else if (status) {
                     k = best;
                     if (up.enabled) {
@@ -1253,10 +1271,12 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                         pend = !los;
                     }
                 } else {
+                    k = warm.bound(key[g]);
                     unknown = 1;
                     pend = up.enabled;
                 }
                 key[g] = k;
+                exactv = status != 0;
             } else if (inb) {
                 key[g] = k;
             }
@@ -1264,7 +1284,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             {
                 // exact keys never change in the relaxation: one bit per voxel in brick order
                 // (a failed path check clears its bit)
-                const bool exact = !(inb && vb[j] != kInvalidBand) || k != kInfKey;
+                const bool exact = !(inb && vb[j] != kInvalidBand) || exactv;
                 const unsigned xb = __ballot_sync(0xffffffffu, exact);
                 if ((tid & 31) == 0) xmask[brick * 32 + (tid >> 5) + (kRelaxThreads / 32) * j] = xb;
             }
@@ -1418,8 +1438,10 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
                 atomicAdd(&g_path_dbg[10], 1ULL);
 #endif
             }
-            if (status == 0) {
-                key[g] = kInfKey;
+            if (status != 0) {
+                // exact: the chamfer distance to the site (the filter left the warm bound here)
+                key[g] = ((unsigned long long)chamfer(px - x, py - y, pz - z) << 32) | (uint32_t)s;
+            } else {
                 const int64_t brick = x / RX + (int64_t)bg.nbx * (y / RY + (int64_t)bg.nby * (z / RZ));
                 const int li = (x & (RX - 1)) + RX * ((y & (RY - 1)) + RY * (z & (RZ - 1)));
                 atomicAnd(&xmask[brick * 32 + (li >> 5)], ~(1u << (li & 31)));
@@ -1664,12 +1686,13 @@ __global__ void update_nonlos_kernel(const uint16_t *__restrict__ q, Dims d, con
 
 __global__ void move_sites_kernel(const uint8_t *__restrict__ band, Dims d, int32_t *site_pos, const int32_t *n_sites_dev,
                                   int32_t max_sites, const unsigned long long *__restrict__ sums,
-                                  unsigned long long *trace) {
+                                  unsigned long long *trace, int32_t *msteps) {
     int32_t ns = min(*n_sites_dev, max_sites);
     for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
         int32_t p = site_pos[s];
         int x = p % d.nx, y = (p / d.nx) % d.ny, z = p / (d.nx * d.ny);
         long long M = (long long)sums[4 * (int64_t)s + 3];
+        if (msteps) msteps[s] = 0;
         if (M <= 0) continue;
         long long tx = (2 * (long long)sums[4 * (int64_t)s + 0] + M) / (2 * M);
         long long ty = (2 * (long long)sums[4 * (int64_t)s + 1] + M) / (2 * M);
@@ -1684,6 +1707,8 @@ __global__ void move_sites_kernel(const uint8_t *__restrict__ band, Dims d, int3
         if (np != p) {
             site_pos[s] = np;
             long long ddx = ex - x, ddy = ey - y, ddz = ez - z;
+            // the walk's face steps: a path of this many W1 edges joins the old and new position
+            if (msteps) msteps[s] = (int32_t)(llabs(ddx) + llabs(ddy) + llabs(ddz));
             if (trace) {
                 const unsigned long long D2 = (unsigned long long)(ddx * ddx + ddy * ddy + ddz * ddz);
                 atomicAdd(&trace[0], 1ULL);
@@ -1725,6 +1750,7 @@ struct CvtWs {
     int4 *cell_list;
     int32_t *cell_count;
     int32_t *plist;
+    int32_t *msteps;   // per site: face steps of its last move (warm start)
     GridBarrier *bar;
     void *scan;
 };
@@ -1763,6 +1789,7 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.cell_list = c.take<int4>(ncoarse * kCellList);
     w.cell_count = c.take<int32_t>(ncoarse);
     w.plist = c.take<int32_t>(n);
+    w.msteps = c.take<int32_t>((int64_t)max_sites + 1);
     w.bar = c.take<GridBarrier>(1);
     w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
     *need = c.used;
@@ -2018,7 +2045,7 @@ namespace {
 // One tessellation: keys <- restricted geodesic Voronoi assignment of the current sites.
 lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos, const int32_t *n_sites_dev,
                             int32_t max_sites, CvtWs &w, uint32_t &tag, int32_t *status, cudaStream_t s,
-                            UpdateOut up) {
+                            UpdateOut up, bool warm) {
     BrickGeom bg{(d.nx + RX - 1) / RX, (d.ny + RY - 1) / RY, (d.nz + RZ - 1) / RZ};
     int64_t n = d.n();
     int64_t nbricks = (int64_t)bg.nbx * bg.nby * bg.nbz;
@@ -2058,7 +2085,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     int cgrid = (int)(nbricks < (int64_t)sms * nb_cfi ? nbricks : (int64_t)sms * nb_cfi);
     cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
                                                w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, w.xmask,
-                                               w.hasunk, tag, up, chk);
+                                               w.hasunk, tag, up, chk, WarmStart{warm, w.msteps});
     check_paths_kernel<<<sms * 16, 256, 0, s>>>(band, w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
                                                  tag, w.list[0], w.counters + 1, chk, up);
 #ifdef LSRVT_DEBUG
@@ -2148,7 +2175,8 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
         cudaMemsetAsync(w.counters + 5, 0, sizeof(int32_t), s);
-        lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, up);
+        // from the second tessellation on, the keys of the last one bound the new ones
+        lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, up, it > 0);
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
                                                    w.nonlos, w.counters, w.plist, w.counters + 5, small, nullptr,
@@ -2156,9 +2184,10 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev, up.energy);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
-                                                                            max_sites, w.sums, rec);
+                                                                            max_sites, w.sums, rec, w.msteps);
     }
-    lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, no_up);
+    lsrvt_status st = run_assignment(band, d, site_pos, n_sites_dev, max_sites, w, tag, status_dev, s, no_up,
+                                     n_iters > 0);
     if (st != LSRVT_OK) return st;
     emit_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.key, n, cell, dist);
 #ifdef LSRVT_DEBUG
@@ -2297,7 +2326,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key[0], w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev, rec ? rec + 3 : nullptr);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
-                                                                            max_sites, w.sums, rec);
+                                                                            max_sites, w.sums, rec, nullptr);
     }
     lsrvt_status st = aa_assignment(band, d, site_pos, n_sites_dev, max_sites, max_rounds, w, status_dev, s,
                                     rounds_host ? rounds_host + n_iters : nullptr);
