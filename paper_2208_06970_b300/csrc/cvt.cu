@@ -519,6 +519,19 @@ __device__ __forceinline__ unsigned long long udiv_fast(unsigned long long a, un
     return q;
 }
 
+// floor(a / b) for b >= 1 with the float reciprocal of b computed once by the caller
+// (rb = __frcp_rn((float)b), meaningful when b < 2^22): the same bound as udiv_fast, so a walk
+// that divides by the same b at every jump pays for one reciprocal
+__device__ __forceinline__ unsigned long long udiv_rcp(unsigned long long a, unsigned long long b, float rb) {
+    if (((a | b) >> 22) != 0) return udiv(a, b);
+    const unsigned ua = (unsigned)a, ub = (unsigned)b;
+    unsigned q = __float2uint_rz(__fmul_rn((float)ua, rb));
+    const int r = (int)(ua - q * ub);
+    if (r < 0) --q;
+    else if (r >= (int)ub) ++q;
+    return q;
+}
+
 // One shortest chamfer path from v to s (26-connected digital line: the dominant axis i
 // advances every move, the middle axis j after move t has advanced round(t aj / ai)
 // times, the smallest axis k after m middle-axis advances round(m ak / aj) times, so it
@@ -557,6 +570,7 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
     const int oi = 13 + ow[i] * sgn[i], oj = ow[j] * sgn[j], ok = ow[k] * sgn[k];  // edge-mask bit offsets
     const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
     const unsigned long long ai2 = 2ULL * Ai, aj2 = 2ULL * Aj;
+    const float rai2 = __frcp_rn((float)ai2), raj2 = Aj ? __frcp_rn((float)aj2) : 0.0f;
     int mv = 0, jc = 0, kc = 0;
     // error terms: ej = 2 mv aj + ai - 2 ai jc in [0, 2ai); ek = 2 jc ak + aj - 2 aj kc in [0, 2aj)
     long long ej = Ai, ek = Aj;
@@ -564,16 +578,19 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
     if (mv_start > 0) {
         mv = mv_start < Ai ? mv_start : Ai;
         unsigned long long nj = 2ULL * mv * Aj + Ai;
-        jc = (int)udiv_fast(nj, ai2);
+        jc = (int)udiv_rcp(nj, ai2, rai2);
         ej = (long long)(nj - ai2 * jc);
         if (Aj) {
             unsigned long long nk = 2ULL * jc * Ak + Aj;
-            kc = (int)udiv_fast(nk, aj2);
+            kc = (int)udiv_rcp(nk, aj2, raj2);
             ek = (long long)(nk - aj2 * kc);
         }
         g = v0 + si * mv + sj * jc + sk * kc;
     }
     while (mv < Ai) {
+#ifdef LSRVT_DEBUG
+        atomicAdd(&g_path_dbg[2], 1ULL);
+#endif
         // the rest of the path approaches s monotonically on every axis, so once within the
         // site's own clearance ball it stays in band
         int rem = max(Ai - mv, max(Aj - jc, Ak - kc));
@@ -585,11 +602,11 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
             else margin = false;
             int mv2 = mv + step < Ai ? mv + step : Ai;
             unsigned long long nj = 2ULL * mv2 * Aj + Ai;
-            jc = (int)udiv_fast(nj, ai2);
+            jc = (int)udiv_rcp(nj, ai2, rai2);
             ej = (long long)(nj - ai2 * jc);
             if (Aj) {
                 unsigned long long nk = 2ULL * jc * Ak + Aj;
-                kc = (int)udiv_fast(nk, aj2);
+                kc = (int)udiv_rcp(nk, aj2, raj2);
                 ek = (long long)(nk - aj2 * kc);
             }
             mv = mv2;
@@ -769,7 +786,11 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
     unsigned long long T0 = A0 ? P0 : INF, T1 = A1 ? P1 : INF, T2 = A2 ? P2 : INF;
     int64_t g = v0;
     int done = 0;
+    const float ram2 = __frcp_rn((float)(2ULL * Am));
     while (done < total) {
+#ifdef LSRVT_DEBUG
+        atomicAdd(&g_path_dbg[3], 1ULL);
+#endif
         // inside the site's clearance ball the rest of the (monotone) traversal is in band
         if (max(A0 - k0, max(A1 - k1, A2 - k2)) <= cs) return true;
         int c = __ldg(clr + g);
@@ -778,9 +799,9 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
             long long mt = km + c - 1;
             if (mt > Am) mt = Am;
             unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
-            k0 = m == 0 ? (int)mt : (int)udiv_fast(num * A0 + Am, den);
-            k1 = m == 1 ? (int)mt : (int)udiv_fast(num * A1 + Am, den);
-            k2 = m == 2 ? (int)mt : (int)udiv_fast(num * A2 + Am, den);
+            k0 = m == 0 ? (int)mt : (int)udiv_rcp(num * A0 + Am, den, ram2);
+            k1 = m == 1 ? (int)mt : (int)udiv_rcp(num * A1 + Am, den, ram2);
+            k2 = m == 2 ? (int)mt : (int)udiv_rcp(num * A2 + Am, den, ram2);
             T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
             T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
             T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;
@@ -1086,12 +1107,32 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         PHASE_ADD(0);
         const int nc = ncand_s;
         const bool ok_list = nc <= kMaxCand;
+#ifdef LSRVT_DEBUG
+        if (tid == 0) { atomicAdd(&g_phase[0], (unsigned long long)max(nl, 0)); atomicAdd(&g_phase[1], (unsigned long long)nc); atomicAdd(&g_phase[3], 1ULL); }
+#endif
         // fine search box in voxels (used only when !complete)
         const int flx = (bx - FX) * RX, fhx = (bx + FX + 1) * RX - 1;
         const int fly = (by - FY) * RY, fhy = (by + FY + 1) * RY - 1;
         const int flz = (bz - FZ) * RZ, fhz = (bz + FZ + 1) * RZ - 1;
         int npow2 = 1;
-        if (ok_list) {
+        if (ok_list && nc <= kRelaxThreads) {
+            // one key per thread, placed at its rank among the others (keys are distinct): one
+            // barrier instead of the sorting network's log^2 stages
+            unsigned long long e = ~0ULL;
+            if (tid < nc) {
+                const int4 c = cs[tid];
+                unsigned long long cc = chamfer(c.y - (ox + RX / 2), c.z - (oy + RY / 2), (c.w & 0xFFFFFF) - (oz + RZ / 2));
+                if (cc > (1ULL << 36) - 1) cc = (1ULL << 36) - 1;
+                e = ((unsigned long long)(uint32_t)(c.w >> 24) << 56) | (cc << 12) | (unsigned)tid;
+                vbest[tid] = e;  // staging (vbest is written again only in the scan below)
+            }
+            __syncthreads();
+            if (tid < nc) {
+                int r = 0;
+                for (int f = 0; f < nc; ++f) r += vbest[f] < e;
+                ck[r] = e;
+            }
+        } else if (ok_list) {
             while (npow2 < nc) npow2 <<= 1;
             for (int i = tid; i < npow2; i += blockDim.x) {
                 unsigned long long e = ~0ULL;
@@ -1104,6 +1145,9 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                 ck[i] = e;
             }
             if (npow2 > 1) block_bitonic_sort(ck, npow2);
+        }
+        __syncthreads();
+        if (ok_list) {
             for (int b2 = tid; b2 <= 256; b2 += blockDim.x) {
                 int lo2 = 0, hi2 = nc;
                 while (lo2 < hi2) {
@@ -1158,6 +1202,9 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                     if (!any) break;
                     const int4 c = cs[(unsigned)(e & 0xFFF)];
                     const int cz = c.w & 0xFFFFFF;
+#ifdef LSRVT_DEBUG
+                    atomicAdd(&g_phase[10], 1ULL);
+#endif
 #pragma unroll
                     for (int j = 0; j < kVPT; ++j) {
                         if (!act[j]) continue;
@@ -1175,6 +1222,9 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                     for (int t = t0; t < t1; ++t) {
                         const unsigned long long e = ck[t];
                         if (((e >> 12) & ((1ULL << 36) - 1)) > (bestv[j] >> 32) + cvv[j]) break;
+#ifdef LSRVT_DEBUG
+                        atomicAdd(&g_phase[11], 1ULL);
+#endif
                         const int4 c = cs[(unsigned)(e & 0xFFF)];
                         const unsigned long long cd = chamfer(c.y - xv[j], c.z - yv[j], (c.w & 0xFFFFFF) - zv[j]);
                         if (cd >= kInf32) continue;
@@ -2207,9 +2257,12 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         unsigned long long pd[12], pz[12] = {0};
         cudaMemcpyFromSymbol(pd, g_path_dbg, sizeof(pd));
         cudaMemcpyToSymbol(g_path_dbg, pz, sizeof(pz));
+        fprintf(stderr, "walk loop turns: path %llu los %llu\n", pd[2], pd[3]);
         fprintf(stderr, "path checks: from start %llu after tube prefix %llu | status0 %llu status1 %llu status2 %llu "
                 "| sub-box tubes 4x4x4 %llu 8x4x4 %llu 2x2x2 %llu | los upgrades %llu\n", pd[0], pd[1], pd[4], pd[5],
                 pd[6], pd[7], pd[8], pd[9], pd[10]);
+        fprintf(stderr, "cfi bricks %llu coarse-list entries %llu brick candidates %llu | scan steps same-band %llu mixed %llu\n",
+                ph[3], ph[0], ph[1], ph[10], ph[11]);
         fprintf(stderr, "cfi chamfer-evals %llu | update: pending warps %llu pending voxels %llu los-walks true %llu "
                 "nonlos %llu los-cycles %.3g\n", ph[10], ph[2], ph[4], ph[9], ph[7], (double)ph[6]);
         unsigned long long cp[8], cz[8] = {0};
