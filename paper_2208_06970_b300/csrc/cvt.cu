@@ -375,98 +375,132 @@ struct BitGeom {
     __host__ __device__ int64_t words(Dims d) const { return (int64_t)W * d.ny * d.nz; }
 };
 
-__global__ void clear_init_kernel(const uint8_t *__restrict__ band, Dims d, BitGeom bgm, uint32_t *S0) {
-    int64_t nw = bgm.words(d);
-    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < nw;
-         wi += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        int lane = threadIdx.x & 31;
-        int wx = (int)(wi % bgm.W);
-        int64_t row = wi / bgm.W;
-        int y = (int)(row % d.ny), z = (int)(row / d.ny);
-        int x = wx * 32 + lane;
-        bool ok = x >= 1 && x < d.nx - 1 && y >= 1 && y < d.ny - 1 && z >= 1 && z < d.nz - 1;
-        if (ok) {
-            int64_t g = x + (int64_t)d.nx * (y + (int64_t)d.ny * z);
-            uint8_t b = band[g];
-            ok = b != kInvalidBand;
-            for (int dz = -1; dz <= 1 && ok; ++dz)
-                for (int dy = -1; dy <= 1 && ok; ++dy)
-                    for (int dx = -1; dx <= 1 && ok; ++dx)
-                        ok = band[g + dx + (int64_t)d.nx * (dy + (int64_t)d.ny * dz)] == b;
+// The bands of a 32 x 8 x 8 tile plus a one-voxel halo in shared memory (16-bit entries:
+// kOutside marks positions outside the volume, unequal to every band).  From them, per voxel:
+// the 27-bit "same band" mask S (bit 13 the voxel itself); the edge mask (bit o set when the
+// move by offset o = (dz+1) 9 + (dy+1) 3 + (dx+1) spans a box that lies in the band, so a path
+// move costs one word instead of up to seven band bytes); and S_0, the non-boundary bit
+// (a valid voxel whose 26 neighbours all lie in the volume and share its band), packed 32
+// voxels to a word along x.  A warp handles a row of the tile, a lane a voxel.
+constexpr int kTileX = 32, kTileY = 8, kTileZ = 8;
+constexpr int kHX = kTileX + 2, kHY = kTileY + 2, kHZ = kTileZ + 2;
+constexpr uint16_t kOutside = 0x100;
+
+__global__ void __launch_bounds__(256) band_masks_kernel(const uint8_t *__restrict__ band, Dims d, BitGeom bgm,
+                                                         uint32_t *__restrict__ S0, uint32_t *__restrict__ emask) {
+    __shared__ uint16_t t[kHZ][kHY][kHX];
+    const int nty = (d.ny + kTileY - 1) / kTileY, ntz = (d.nz + kTileZ - 1) / kTileZ;
+    const int64_t ntiles = (int64_t)bgm.W * nty * ntz;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int wx = (int)(tile % bgm.W);
+        const int ty = (int)((tile / bgm.W) % nty), tz = (int)(tile / ((int64_t)bgm.W * nty));
+        const int x0 = wx * kTileX - 1, y0 = ty * kTileY - 1, z0 = tz * kTileZ - 1;
+        for (int i = threadIdx.x; i < kHX * kHY * kHZ; i += blockDim.x) {
+            const int hx = i % kHX, hy = (i / kHX) % kHY, hz = i / (kHX * kHY);
+            const int x = x0 + hx, y = y0 + hy, z = z0 + hz;
+            uint16_t v = kOutside;
+            if (x >= 0 && x < d.nx && y >= 0 && y < d.ny && z >= 0 && z < d.nz)
+                v = __ldg(band + x + (int64_t)d.nx * (y + (int64_t)d.ny * z));
+            t[hz][hy][hx] = v;
         }
-        unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (lane == 0) S0[wi] = bal;
+        __syncthreads();
+        for (int r = w; r < kTileY * kTileZ; r += blockDim.x >> 5) {
+            const int ly = r % kTileY, lz = r / kTileY;
+            const int x = x0 + 1 + lane, y = y0 + 1 + ly, z = z0 + 1 + lz;
+            const bool live = x < d.nx && y < d.ny && z < d.nz;
+            const uint16_t b = t[lz + 1][ly + 1][lane + 1];
+            uint32_t S = 0;
+            if (live && b != kInvalidBand) {
+#pragma unroll
+                for (int o = 0; o < 27; ++o) {
+                    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+                    S |= (uint32_t)(t[lz + 1 + dz][ly + 1 + dy][lane + 1 + dx] == b) << o;
+                }
+            }
+            if (live) emask[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)] = S ? edges_from_same(S) : 0u;
+            const unsigned bal = __ballot_sync(0xffffffffu, S == 0x7FFFFFFu);
+            if (lane == 0 && y < d.ny && z < d.nz) S0[wx + (int64_t)bgm.W * (y + (int64_t)d.ny * z)] = bal;
+        }
+        __syncthreads();
     }
 }
 
 // x-erosion of word wx of a row (bits outside the row count as 0)
-__device__ __forceinline__ uint32_t erode_x(const uint32_t *row, int wx, int W) {
-    uint32_t w = row[wx];
-    uint32_t lo = wx > 0 ? row[wx - 1] : 0u, hi = wx + 1 < W ? row[wx + 1] : 0u;
-    uint32_t left = (w << 1) | (lo >> 31);   // bit i <- bit i-1
-    uint32_t right = (w >> 1) | (hi << 31);  // bit i <- bit i+1
+__device__ __forceinline__ uint32_t erode_x3(uint32_t lo, uint32_t w, uint32_t hi) {
+    const uint32_t left = (w << 1) | (lo >> 31);   // bit i <- bit i-1
+    const uint32_t right = (w >> 1) | (hi << 31);  // bit i <- bit i+1
     return w & left & right;
 }
 
-__global__ void clear_erode_kernel(const uint32_t *__restrict__ Sk, Dims d, BitGeom bgm, uint32_t *Sk1) {
-    int64_t nw = bgm.words(d);
-    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < nw; wi += (int64_t)gridDim.x * blockDim.x) {
-        int wx = (int)(wi % bgm.W);
-        int64_t row = wi / bgm.W;
-        int y = (int)(row % d.ny), z = (int)(row / d.ny);
-        uint32_t acc = 0xffffffffu;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                int y2 = y + dy, z2 = z + dz;
-                if (y2 < 0 || y2 >= d.ny || z2 < 0 || z2 >= d.nz) { acc = 0; continue; }
-                acc &= erode_x(Sk + ((int64_t)y2 + (int64_t)d.ny * z2) * bgm.W, wx, bgm.W);
+// S_k+1 = S_k eroded by the 3x3x3 cube (a voxel stays when its whole neighbourhood is in S_k;
+// words and rows outside the volume count as 0).  A CTA loads 6 words x 10 rows x 10 slabs
+// (its 4 x 8 x 8 output words plus a halo) into shared memory.
+constexpr int kEW = 4, kEY = 8, kEZ = 8;
+
+__global__ void __launch_bounds__(256) clear_erode_kernel(const uint32_t *__restrict__ Sk, Dims d, BitGeom bgm,
+                                                          uint32_t *__restrict__ Sk1) {
+    __shared__ uint32_t t[kEZ + 2][kEY + 2][kEW + 2];
+    const int ntx = (bgm.W + kEW - 1) / kEW, nty = (d.ny + kEY - 1) / kEY, ntz = (d.nz + kEZ - 1) / kEZ;
+    const int64_t ntiles = (int64_t)ntx * nty * ntz;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = (int)(tile % ntx), ty = (int)((tile / ntx) % nty), tz = (int)(tile / ((int64_t)ntx * nty));
+        const int w0 = tx * kEW - 1, y0 = ty * kEY - 1, z0 = tz * kEZ - 1;
+        for (int i = threadIdx.x; i < (kEW + 2) * (kEY + 2) * (kEZ + 2); i += blockDim.x) {
+            const int hx = i % (kEW + 2), hy = (i / (kEW + 2)) % (kEY + 2), hz = i / ((kEW + 2) * (kEY + 2));
+            const int wx = w0 + hx, y = y0 + hy, z = z0 + hz;
+            uint32_t v = 0;
+            if (wx >= 0 && wx < bgm.W && y >= 0 && y < d.ny && z >= 0 && z < d.nz)
+                v = Sk[wx + (int64_t)bgm.W * (y + (int64_t)d.ny * z)];
+            t[hz][hy][hx] = v;
+        }
+        __syncthreads();
+        {
+            const int i = threadIdx.x;  // one output word per thread (kEW * kEY * kEZ = 256)
+            const int ox = i % kEW, oy = (i / kEW) % kEY, oz = i / (kEW * kEY);
+            const int wx = w0 + 1 + ox, y = y0 + 1 + oy, z = z0 + 1 + oz;
+            if (wx < bgm.W && y < d.ny && z < d.nz) {
+                uint32_t acc = 0xffffffffu;
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+                        acc &= erode_x3(t[oz + dz][oy + dy][ox], t[oz + dz][oy + dy][ox + 1], t[oz + dz][oy + dy][ox + 2]);
+                Sk1[wx + (int64_t)bgm.W * (y + (int64_t)d.ny * z)] = acc;
             }
-        Sk1[wi] = acc;
+        }
+        __syncthreads();
     }
 }
 
+// c(v) = number of the nested sets S_0 ... S_levels-1 holding v.  A thread per word: the word's
+// planes are added into 6-bit counters held bit-sliced (one word per counter bit), stopping
+// at the first empty plane (the sets are nested), then each voxel's count is read out.
 __global__ void clear_count_kernel(const uint32_t *__restrict__ planes, Dims d, BitGeom bgm, int levels,
                                    uint8_t *__restrict__ clr) {
-    int64_t n = d.n();
-    int64_t nw = bgm.words(d);
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t row32 = (uint32_t)v / (uint32_t)d.nx;  // N < 2^31
-        const int x = (int)((uint32_t)v - row32 * (uint32_t)d.nx);
-        const int64_t row = row32;
-        int64_t wi = row * bgm.W + (x >> 5);
-        uint32_t bit = 1u << (x & 31);
-        int c = 0;
+    const int64_t nw = bgm.words(d);
+    for (int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; wi < nw; wi += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
         for (int k = 0; k < levels; ++k) {
-            if (!(planes[(int64_t)k * nw + wi] & bit)) break;
-            ++c;
+            uint32_t carry = planes[(int64_t)k * nw + wi];
+            if (!carry) break;
+            uint32_t tt;
+            tt = c0 & carry; c0 ^= carry; carry = tt;
+            tt = c1 & carry; c1 ^= carry; carry = tt;
+            tt = c2 & carry; c2 ^= carry; carry = tt;
+            tt = c3 & carry; c3 ^= carry; carry = tt;
+            tt = c4 & carry; c4 ^= carry; carry = tt;
+            c5 ^= carry;
         }
-        clr[v] = (uint8_t)c;
-    }
-}
-
-// Edge masks (once per call, like the clearance): bit o of emask[v] is set when the
-// 26-neighbour move v -> v + offset(o) is an edge, i.e. every voxel of the box it spans
-// is in v's band (o = (dz+1) 9 + (dy+1) 3 + (dx+1)).  Path checks then test one word per
-// move instead of up to seven band bytes.
-__global__ void edge_mask_kernel(const uint8_t *__restrict__ band, Dims d, uint32_t *__restrict__ emask) {
-    int64_t n = d.n();
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int x, y, z;
-        decode_voxel((uint32_t)v, d, x, y, z);
-        const uint8_t b = band[v];
-        uint32_t e = 0;
-        if (b != kInvalidBand) {
-            uint32_t S = 0;
-#pragma unroll
-            for (int o = 0; o < 27; ++o) {
-                const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-                const int ux = x + dx, uy = y + dy, uz = z + dz;
-                if (ux < 0 || ux >= d.nx || uy < 0 || uy >= d.ny || uz < 0 || uz >= d.nz) continue;
-                S |= (uint32_t)(__ldg(band + v + dx + (int64_t)d.nx * (dy + (int64_t)d.ny * dz)) == b) << o;
-            }
-            e = edges_from_same(S);
+        const int wx = (int)(wi % bgm.W);
+        const int64_t row = wi / bgm.W;
+        const int xs = wx * 32, xe = min(xs + 32, d.nx);
+        uint8_t *out = clr + row * d.nx;
+        for (int x = xs; x < xe; ++x) {
+            const int bb = x - xs;
+            out[x] = (uint8_t)(((c0 >> bb) & 1u) | (((c1 >> bb) & 1u) << 1) | (((c2 >> bb) & 1u) << 2) |
+                               (((c3 >> bb) & 1u) << 3) | (((c4 >> bb) & 1u) << 4) | (((c5 >> bb) & 1u) << 5));
         }
-        emask[v] = e;
     }
 }
 
@@ -1778,6 +1812,22 @@ __global__ void emit_kernel(const unsigned long long *__restrict__ key, int64_t 
     }
 }
 
+// Edge masks and the clearance field, once per call (the bands never change during the Lloyd
+// iterations): S_0 and the edge masks from band tiles, kClearLevels - 1 tiled erosions, then
+// the per-voxel count of sets.
+void clearance_and_edges(const uint8_t *band, Dims d, uint32_t *planes, uint8_t *clr, uint32_t *emask,
+                         cudaStream_t s) {
+    BitGeom bgm{(d.nx + 31) / 32};
+    const int64_t nw = bgm.words(d);
+    const int64_t mt = (int64_t)bgm.W * ((d.ny + kTileY - 1) / kTileY) * ((d.nz + kTileZ - 1) / kTileZ);
+    band_masks_kernel<<<(int)(mt < kSMs * 8 ? mt : kSMs * 8), 256, 0, s>>>(band, d, bgm, planes, emask);
+    const int64_t et = (int64_t)((bgm.W + kEW - 1) / kEW) * ((d.ny + kEY - 1) / kEY) * ((d.nz + kEZ - 1) / kEZ);
+    for (int k = 1; k < kClearLevels; ++k)
+        clear_erode_kernel<<<(int)(et < kSMs * 8 ? et : kSMs * 8), 256, 0, s>>>(planes + (int64_t)(k - 1) * nw, d, bgm,
+                                                                                planes + (int64_t)k * nw);
+    clear_count_kernel<<<grid_for(nw, 256, kSMs * 16), 256, 0, s>>>(planes, d, bgm, kClearLevels, clr);
+}
+
 struct CvtWs {
     unsigned long long *key;
     int32_t *par;
@@ -2199,14 +2249,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * LSRVT_TRACE * n_iters, s);
     bool small = d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048;
     {
-        BitGeom bgm{(d.nx + 31) / 32};
-        int64_t nw = bgm.words(d);
-        clear_init_kernel<<<grid_for(nw * 32, 256, kSMs * 16), 256, 0, s>>>(band, d, bgm, w.planes);
-        for (int k = 1; k < kClearLevels; ++k)
-            clear_erode_kernel<<<grid_for(nw, 256, kSMs * 16), 256, 0, s>>>(w.planes + (int64_t)(k - 1) * nw, d, bgm,
-                                                                          w.planes + (int64_t)k * nw);
-        clear_count_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.planes, d, bgm, kClearLevels, w.clr);
-        edge_mask_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.emask);
+        clearance_and_edges(band, d, w.planes, w.clr, w.emask, s);
         CoarseGeom cg{(d.nx + kCoarse - 1) / kCoarse, (d.ny + kCoarse - 1) / kCoarse, (d.nz + kCoarse - 1) / kCoarse};
         int64_t ncoarse = (int64_t)cg.ncx * cg.ncy * cg.ncz;
         cell_bands_kernel<<<(int)(ncoarse < kSMs * 8 ? ncoarse : kSMs * 8), kCellThreads, 0, s>>>(band, d, cg,
@@ -2343,16 +2386,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
     const int sms = stream_sms(s);
     if (iter_trace && n_iters > 0) cudaMemsetAsync(iter_trace, 0, sizeof(int64_t) * LSRVT_TRACE * n_iters, s);
     const bool small = d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048;
-    {
-        BitGeom bgm{(d.nx + 31) / 32};
-        int64_t nw = bgm.words(d);
-        clear_init_kernel<<<grid_for(nw * 32, 256, kSMs * 16), 256, 0, s>>>(band, d, bgm, w.planes);
-        for (int k = 1; k < kClearLevels; ++k)
-            clear_erode_kernel<<<grid_for(nw, 256, kSMs * 16), 256, 0, s>>>(w.planes + (int64_t)(k - 1) * nw, d, bgm,
-                                                                          w.planes + (int64_t)k * nw);
-        clear_count_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.planes, d, bgm, kClearLevels, w.clr);
-        edge_mask_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.emask);
-    }
+    clearance_and_edges(band, d, w.planes, w.clr, w.emask, s);
     const int vgrid = grid_for((n + 31) / 32 * 32, 256, sms * 16);
     const int64_t nwords = (n + 31) / 32;
     // a tessellation that hits the round limit ends the call: its last round's state (in the
