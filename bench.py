@@ -130,14 +130,14 @@ def job_value(world, voxels_per_rank, iters, ms):
 class Pipeline:
     """The hot path with buffers and workspaces allocated once (all compute in liblsrvt)."""
 
-    def __init__(self, pkg, field, aux, iso):
+    def __init__(self, pkg, field, aux, iso, max_comp=None):
         self.pkg = pkg
         self.field = field
         self.aux = list(aux)
         self.iso = iso
         self.dev = field.device
         self.n = field.numel()
-        self.max_comp = pkg.default_max_comp(self.n)
+        self.max_comp = pkg.default_max_comp(self.n) if max_comp is None else int(max_comp)
         self.ws = pkg.Workspace(self.dev)
         self.status = pkg.new_status(self.dev)
         self.n_bands = len(iso) + 1
@@ -208,10 +208,20 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     side = args.side
-    w = workloads.flame_workload(side=side, seed=rank_seed(rank), device=dev, n_aux=N_AUX, n_iters=N_ITERS)
+    w = workloads.flame_workload(side=side, seed=rank_seed(rank), device=dev, n_aux=N_AUX, n_iters=N_ITERS,
+                                 recipe=args.flame_recipe)
     field, aux, iso = w["field"], w["aux"], w["iso"]
     n = field.numel()
-    pipe = Pipeline(pkg, field, [aux[j] for j in range(N_AUX)], iso)
+    # the survey recipe shatters the isobands into more components than the default capacity:
+    # count them once and size the component (and so the site and statistics) capacity to fit
+    max_comp = None
+    if args.flame_recipe == "survey":
+        b0 = pkg.classify(field, iso)
+        nc0 = pkg.label_components(b0, max_comp=n // 4)[4]
+        max_comp = int(nc0.item()) + 1024
+        del b0, nc0
+        torch.cuda.empty_cache()
+    pipe = Pipeline(pkg, field, [aux[j] for j in range(N_AUX)], iso, max_comp=max_comp)
     for _ in range(args.warmup):
         pipe.step()
     torch.cuda.synchronize()
@@ -484,12 +494,49 @@ def joint_arm(pkg, pipe, lay, s, reps=3):
 
 
 # --------------------------------------------------------------------------- oracle arm
+def host_info():
+    """Core count and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return dict(nproc=os.cpu_count(), cpu_model=model)
+
+
+class PinnedCore:
+    """Runs the enclosed (single-threaded) oracle call pinned to one core, then restores the
+    calling thread's affinity.  The core is the highest one the process may use."""
+
+    def __enter__(self):
+        self.old = None
+        self.core = None
+        if hasattr(os, "sched_getaffinity"):
+            self.old = os.sched_getaffinity(0)
+            self.core = max(self.old)
+            os.sched_setaffinity(0, {self.core})
+        return self
+
+    def __exit__(self, *exc):
+        if self.old is not None:
+            os.sched_setaffinity(0, self.old)
+        return False
+
+
 def oracle_sample(field, aux, iso, side=96, iters=2):
-    """The CPU oracle on a side^3 corner of the workload (bounded sample); returns
-    (voxel-iterations per second, seconds, description)."""
+    """The CPU oracle on a side^3 corner of the workload (bounded sample), pinned to one core;
+    returns (voxel-iterations per second, seconds, description)."""
     import oracle
     f = field[:side, :side, :side].contiguous().cpu().numpy()
     a = aux[:, :side, :side, :side].contiguous().cpu().numpy()
+    with PinnedCore():
+        return _oracle_path(oracle, f, a, iso, iters, side)
+
+
+def _oracle_path(oracle, f, a, iso, iters, side):
     t0 = time.perf_counter()
     band = oracle.classify(f, iso)
     comp, cb, cs, cf = oracle.label_components(band)
@@ -501,7 +548,42 @@ def oracle_sample(field, aux, iso, side=96, iters=2):
     oracle.merge_hierarchy(st, sc, cb, len(iso) + 1)
     dt = time.perf_counter() - t0
     vox = f.size
-    return vox * iters / dt / 1e9, dt, "%d^3 corner of the workload, %d Lloyd iterations, full path" % (side, iters)
+    return (vox * iters / dt / 1e9, dt, "%d^3 corner of the workload, %d Lloyd iterations, whole path; "
+            "the metric's value is extrapolated from it (voxel-iterations of the corner / its time)" % (side, iters))
+
+
+def oracle_full_size_stages(field, aux, iso):
+    """The one-pass stages of the path on the whole volume, in the oracle pinned to one core:
+    classification, component labelling, saliency, seeding and the statistics sweep (per-cell
+    moments and histograms of every auxiliary variable; the cells for this timing are the
+    oracle's own components, since a full-size oracle tessellation is out of reach).  The
+    Lloyd loop itself is timed only on the corner sample.  Returns seconds per stage."""
+    import oracle
+    f = field.contiguous().cpu().numpy()
+    out = {}
+    with PinnedCore() as pc:
+        t = time.perf_counter()
+        band = oracle.classify(f, iso)
+        out["classify"] = time.perf_counter() - t
+        t = time.perf_counter()
+        comp, cb, cs, cf = oracle.label_components(band)
+        out["label_components"] = time.perf_counter() - t
+        t = time.perf_counter()
+        q = oracle.saliency(f, 1)
+        out["saliency"] = time.perf_counter() - t
+        t = time.perf_counter()
+        oracle.seed(comp, q, len(cb), VPS, 16, 2)
+        out["seed"] = time.perf_counter() - t
+        del q, band
+        a = aux.contiguous().cpu().numpy()
+        t = time.perf_counter()
+        lo, hi, scale = oracle.aux_range(comp, a, N_BINS)
+        oracle.aggregate(comp, a, len(cb), lo, scale, N_BINS)
+        out["aggregate"] = time.perf_counter() - t
+        core = pc.core
+    del a
+    return dict(seconds=out, core=core, voxels=int(f.size), n_aux=int(aux.shape[0]),
+                note="whole %dx%dx%d volume; statistics over the oracle's components" % tuple(f.shape[::-1]))
 
 
 def reference_arm(args):
@@ -521,7 +603,8 @@ def reference_arm(args):
                 dtype="int32/f32/f64", data="synthetic", impl="reference",
                 config=dict(workload="flame %d^3 (oracle sample %d^3)" % (args.side, args.ref_side),
                             voxels_per_site=VPS, n_iters=N_ITERS, n_aux=N_AUX),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=desc),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=desc, extrapolated=True,
+                                  pinned="one core (sched_setaffinity)", host=host_info()),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -756,9 +839,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lsrvt")
     ap.add_argument("--side", type=int, default=512)
+    ap.add_argument("--flame-recipe", default="resolved", choices=("resolved", "survey"),
+                    help="flame field: resolved front (default) or the survey's eta = 0, 4-voxel front")
     ap.add_argument("--ref-side", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-full", action="store_true", help="skip the full-size oracle stage timings")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / served comparison")
     ap.add_argument("--blocks", type=int, default=64)
     ap.add_argument("--requests", type=int, default=24)
@@ -805,14 +891,19 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             v, dt, desc = oracle_sample(r["field"], r["aux"], r["iso"], side=args.ref_side, iters=args.ref_iters)
-            cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=desc, seconds=dt)
+            cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=desc, seconds=dt, extrapolated=True,
+                       pinned="one core (sched_setaffinity)", host=host_info())
+            if not args.no_oracle_full:
+                cpu["full_size_stages"] = oracle_full_size_stages(r["field"], r["aux"], r["iso"])
         pk = r["peak"]
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=r["ms"], higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="int32/u64 labels, f32 float-float + f64 stats", data="synthetic",
-            config=dict(workload="flame %d^3, 8 isovalues, |grad| weight, 1 site/4096 voxels, %d Lloyd iters, "
-                                 "%d aux vars, %d bins" % (args.side, N_ITERS, N_AUX, N_BINS),
+            config=dict(workload="flame %d^3%s, 8 isovalues, |grad| weight, 1 site/4096 voxels, %d Lloyd iters, "
+                                 "%d aux vars, %d bins" % (args.side, "" if args.flame_recipe == "resolved"
+                                                           else " (survey recipe: eta 0, front width 4)", N_ITERS,
+                                                           N_AUX, N_BINS),
                         voxels=n, sites=r["n_sites"], components=r["n_comp"], parallelism="replicas" if world > 1
                         else "single", l2="inputs larger than L2 (field 512 MiB + aux 8 GiB), no flush"),
             roofline=dict(kernel="one Lloyd iteration: site bins + cell lists + cfi_kernel + relax_persistent_kernel + "

@@ -553,19 +553,6 @@ __device__ __forceinline__ unsigned long long udiv_fast(unsigned long long a, un
     return q;
 }
 
-// floor(a / b) for b >= 1 with the float reciprocal of b computed once by the caller
-// (rb = __frcp_rn((float)b), meaningful when b < 2^22): the same bound as udiv_fast, so a walk
-// that divides by the same b at every jump pays for one reciprocal
-__device__ __forceinline__ unsigned long long udiv_rcp(unsigned long long a, unsigned long long b, float rb) {
-    if (((a | b) >> 22) != 0) return udiv(a, b);
-    const unsigned ua = (unsigned)a, ub = (unsigned)b;
-    unsigned q = __float2uint_rz(__fmul_rn((float)ua, rb));
-    const int r = (int)(ua - q * ub);
-    if (r < 0) --q;
-    else if (r >= (int)ub) ++q;
-    return q;
-}
-
 // One shortest chamfer path from v to s (26-connected digital line: the dominant axis i
 // advances every move, the middle axis j after move t has advanced round(t aj / ai)
 // times, the smallest axis k after m middle-axis advances round(m ak / aj) times, so it
@@ -604,7 +591,6 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
     const int oi = 13 + ow[i] * sgn[i], oj = ow[j] * sgn[j], ok = ow[k] * sgn[k];  // edge-mask bit offsets
     const int64_t v0 = vx + (int64_t)d.nx * vy + sxy * vz;
     const unsigned long long ai2 = 2ULL * Ai, aj2 = 2ULL * Aj;
-    const float rai2 = __frcp_rn((float)ai2), raj2 = Aj ? __frcp_rn((float)aj2) : 0.0f;
     int mv = 0, jc = 0, kc = 0;
     // error terms: ej = 2 mv aj + ai - 2 ai jc in [0, 2ai); ek = 2 jc ak + aj - 2 aj kc in [0, 2aj)
     long long ej = Ai, ek = Aj;
@@ -612,11 +598,11 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
     if (mv_start > 0) {
         mv = mv_start < Ai ? mv_start : Ai;
         unsigned long long nj = 2ULL * mv * Aj + Ai;
-        jc = (int)udiv_rcp(nj, ai2, rai2);
+        jc = (int)udiv_fast(nj, ai2);
         ej = (long long)(nj - ai2 * jc);
         if (Aj) {
             unsigned long long nk = 2ULL * jc * Ak + Aj;
-            kc = (int)udiv_rcp(nk, aj2, raj2);
+            kc = (int)udiv_fast(nk, aj2);
             ek = (long long)(nk - aj2 * kc);
         }
         g = v0 + si * mv + sj * jc + sk * kc;
@@ -636,11 +622,11 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
             else margin = false;
             int mv2 = mv + step < Ai ? mv + step : Ai;
             unsigned long long nj = 2ULL * mv2 * Aj + Ai;
-            jc = (int)udiv_rcp(nj, ai2, rai2);
+            jc = (int)udiv_fast(nj, ai2);
             ej = (long long)(nj - ai2 * jc);
             if (Aj) {
                 unsigned long long nk = 2ULL * jc * Ak + Aj;
-                kc = (int)udiv_rcp(nk, aj2, raj2);
+                kc = (int)udiv_fast(nk, aj2);
                 ek = (long long)(nk - aj2 * kc);
             }
             mv = mv2;
@@ -820,7 +806,6 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
     unsigned long long T0 = A0 ? P0 : INF, T1 = A1 ? P1 : INF, T2 = A2 ? P2 : INF;
     int64_t g = v0;
     int done = 0;
-    const float ram2 = __frcp_rn((float)(2ULL * Am));
     while (done < total) {
 #ifdef LSRVT_DEBUG
         atomicAdd(&g_path_dbg[3], 1ULL);
@@ -833,9 +818,9 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
             long long mt = km + c - 1;
             if (mt > Am) mt = Am;
             unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
-            k0 = m == 0 ? (int)mt : (int)udiv_rcp(num * A0 + Am, den, ram2);
-            k1 = m == 1 ? (int)mt : (int)udiv_rcp(num * A1 + Am, den, ram2);
-            k2 = m == 2 ? (int)mt : (int)udiv_rcp(num * A2 + Am, den, ram2);
+            k0 = m == 0 ? (int)mt : (int)udiv_fast(num * A0 + Am, den);
+            k1 = m == 1 ? (int)mt : (int)udiv_fast(num * A1 + Am, den);
+            k2 = m == 2 ? (int)mt : (int)udiv_fast(num * A2 + Am, den);
             T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
             T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
             T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;

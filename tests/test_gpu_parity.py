@@ -376,3 +376,35 @@ def test_degenerate_volumes_end_to_end(pk, case):
         assert np.array_equal(cpu(got["min"])[:ns], stats["min"]) and np.array_equal(cpu(got["max"])[:ns], stats["max"])
         assert np.array_equal(cpu(got["hist"])[:ns].view(np.uint32), stats["hist"])
         _moment_ok(cpu(got["mean"])[:ns], cpu(got["m2"])[:ns], stats["mean"], stats["m2"], stats["count"])
+
+
+def test_cvt_parity_survey_flame_recipe(pk):
+    """The survey's flame recipe (no dissipation cutoff, 4-voxel front) at 128^3 shatters the
+    thin isobands into ~10^5 components, most of a few voxels: labels, seeds (at least one per
+    component), two Lloyd iterations with |grad f| weights and the final cells, bit for bit."""
+    w = workloads.flame_workload(side=128, seed=2, n_aux=0, recipe="survey")
+    f = w["field"].numpy()
+    band = oracle.classify(f, w["iso"])
+    comp, cb, cs, cf = oracle.label_components(band)
+    assert len(cb) > 100000
+    gband = torch.from_numpy(band).cuda()
+    st = pk.new_status()
+    n = band.size
+    gcomp, gcb, gcs, gcf, gnc = pk.label_components(gband, max_comp=n // 4, status=st)
+    pk.check_status(st, "labels")
+    k = int(gnc.item())
+    assert k == len(cb) and np.array_equal(cpu(gcomp), comp) and np.array_equal(cpu(gcs)[:k], cs)
+    q = oracle.saliency(f, 1)
+    gq = pk.saliency_grad(torch.from_numpy(f).cuda(), 1)
+    assert np.array_equal(cpu(gq).view(np.uint16), q)
+    sp, sc, off, nc = oracle.seed(comp, q, len(cb), 4096, 16, 2)
+    gsp, gsc, goff, gns = pk.seed(gcomp, gq, gnc, n // 4, 4096, 16, 2, status=st)
+    pk.check_status(st, "seeds")
+    ns = int(gns.item())
+    assert ns == len(sp) and np.array_equal(cpu(gsp)[:ns], sp)
+    sp_ref, cell_ref, dist_ref, tr_ref = oracle.cvt_iterate(band, q, sp, 2)
+    cell, dist, tr = pk.cvt_iterate(gband, gq, gsp, gns, 2, status=st)
+    pk.check_status(st, "Lloyd iterations")
+    assert np.array_equal(cpu(gsp)[:ns], sp_ref)
+    assert np.array_equal(cpu(cell), cell_ref) and np.array_equal(cpu(dist).view(np.uint32), dist_ref)
+    assert np.array_equal(cpu(tr), tr_ref)

@@ -14,7 +14,8 @@ Recipes (the five workloads):
   flame   : u = isotropic spectral field with amplitude ~ |k|^(-11/6) (E(k) ~ k^(-5/3))
             and a dissipation-range cutoff exp(-2.6 k eta), eta = 2 voxels, random phases,
             unit std; f = (1 + tanh((x - nx/2 + 24 u) / 8)) / 2, a progress-variable-like
-            front about 16 voxels thick.
+            front about 16 voxels thick.  Recipe "survey": eta = 0 (no cutoff) and tanh
+            width 4, which shatters the thin isobands into very many components.
   corr    : m correlated Gaussian variables x = mu + L z, L L^T = A A^T / m + 0.1 I.
 """
 import math
@@ -94,11 +95,20 @@ def spectral_field(dims, seed, device="cpu", slope=-11.0 / 6.0, eta=2.0):
     return u.to(torch.float32).contiguous()
 
 
-def flame_field(dims, seed, device="cpu", width=8.0):
+FLAME_RECIPES = {
+    # a resolved front: dissipation-range cutoff (eta = 2 voxels), tanh width 8
+    "resolved": dict(eta=2.0, width=8.0),
+    # the survey's recipe as written: pure k^-5/3 amplitudes to the grid scale, tanh width 4;
+    # it breaks the thin isobands into very many small components
+    "survey": dict(eta=0.0, width=4.0),
+}
+
+
+def flame_field(dims, seed, device="cpu", width=8.0, eta=2.0):
     """Progress-variable-like flame front wrinkled by spectral turbulence.  Returns (f, u).
     The tanh width (8 voxels) makes the front about 16 voxels thick, resolved like a DNS flame."""
     nx, ny, nz = dims
-    u = spectral_field(dims, seed, device)
+    u = spectral_field(dims, seed, device, eta=eta)
     x = torch.arange(nx, dtype=torch.float32, device=device).view(1, 1, nx)
     f = 0.5 * (1.0 + torch.tanh((x - nx / 2.0 + 24.0 * u) / width))
     return f.to(torch.float32).contiguous(), u
@@ -141,11 +151,12 @@ def blobs_workload(side=64, seed=1, device="cpu", n_aux=3):
                 aux=torch.stack(aux[:n_aux]) if n_aux else torch.zeros((0,) + f.shape, device=device))
 
 
-def flame_workload(side=512, seed=2, device="cpu", n_aux=16, n_iters=30):
+def flame_workload(side=512, seed=2, device="cpu", n_aux=16, n_iters=30, recipe="resolved"):
     """512^3 spectral-turbulence flame; 8 isovalues i/9; weight |grad f| (gamma 1);
-    4096 voxels per site; 30 Lloyd iterations; 16 aux = (f, u, 14 spectral fields)."""
+    4096 voxels per site; 30 Lloyd iterations; 16 aux = (f, u, 14 spectral fields).
+    recipe: "resolved" (default) or "survey" (see FLAME_RECIPES)."""
     dims = (side, side, side) if np.isscalar(side) else tuple(side)
-    f, u = flame_field(dims, seed, device)
+    f, u = flame_field(dims, seed, device, **FLAME_RECIPES[recipe])
     aux = torch.empty((n_aux,) + f.shape, dtype=torch.float32, device=device)
     if n_aux > 0:
         aux[0] = f
@@ -154,7 +165,7 @@ def flame_workload(side=512, seed=2, device="cpu", n_aux=16, n_iters=30):
     del u
     for j in range(2, n_aux):
         aux[j] = spectral_field(dims, seed * 1000 + j, device)
-    return dict(name="flame%dx%dx%d" % dims, dims=dims, field=f,
+    return dict(name="flame%dx%dx%d%s" % (dims + ("" if recipe == "resolved" else "-" + recipe,)), dims=dims, field=f,
                 iso=(np.arange(1, 9, dtype=np.float32) / np.float32(9.0)).astype(np.float32), gamma=1,
                 voxels_per_site=4096, strat_block=16, rng_seed=seed, n_iters=n_iters, n_bins=32, aux=aux)
 
