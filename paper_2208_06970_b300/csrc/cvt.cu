@@ -787,8 +787,10 @@ __device__ __forceinline__ void shell_cell(int q, int rho, int &dx, int &dy, int
 // dominant axis (all crossings up to that time, ties included, exactly as the stepwise
 // walk takes them).  Over that interval each axis crosses at most c times, so every voxel
 // passed is within L-infinity distance c and in band: no tests are needed.
+// mt_start > 0: the traversal up to the mt_start-th crossing of the dominant axis is known to
+// be in band (a brick tube certified the segment that far with a margin of 2); it starts there.
 __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__restrict__ clr, Dims d, int vx, int vy,
-                          int vz, int sx, int sy, int sz, int cs) {
+                          int vz, int sx, int sy, int sz, int cs, int mt_start = 0) {
     const int A0 = abs(sx - vx), A1 = abs(sy - vy), A2 = abs(sz - vz);
     const int total = A0 + A1 + A2;
     if (total == 0) return true;
@@ -806,6 +808,18 @@ __device__ bool los_clear(const uint8_t *__restrict__ band, const uint8_t *__res
     unsigned long long T0 = A0 ? P0 : INF, T1 = A1 ? P1 : INF, T2 = A2 ? P2 : INF;
     int64_t g = v0;
     int done = 0;
+    if (mt_start > 0) {
+        const long long mt = mt_start < Am ? mt_start : Am;
+        const unsigned long long num = 2ULL * mt - 1, den = 2ULL * Am;
+        k0 = m == 0 ? (int)mt : (int)udiv_fast(num * A0 + Am, den);
+        k1 = m == 1 ? (int)mt : (int)udiv_fast(num * A1 + Am, den);
+        k2 = m == 2 ? (int)mt : (int)udiv_fast(num * A2 + Am, den);
+        T0 = k0 < A0 ? (2ULL * k0 + 1) * P0 : INF;
+        T1 = k1 < A1 ? (2ULL * k1 + 1) * P1 : INF;
+        T2 = k2 < A2 ? (2ULL * k2 + 1) * P2 : INF;
+        g = v0 + st0 * k0 + st1 * k1 + st2 * k2;
+        done = k0 + k1 + k2;
+    }
     while (done < total) {
 #ifdef LSRVT_DEBUG
         atomicAdd(&g_path_dbg[3], 1ULL);
@@ -1501,7 +1515,7 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
 #endif
             // an exact key without the margin certificate: walk Eq. 2's traversal now (the
             // update pass keeps only the voxels without line of sight, for their parents)
-            if (status == 1 && up.enabled && los_clear(band, clr, d, x, y, z, px, py, pz, cs)) {
+            if (status == 1 && up.enabled && los_clear(band, clr, d, x, y, z, px, py, pz, cs, mv0)) {
                 status = 2;
 #ifdef LSRVT_DEBUG
                 atomicAdd(&g_path_dbg[10], 1ULL);
