@@ -8,13 +8,13 @@
 // moments use the closed form of the pairwise update of Chan, Golub & LeVeque (1979):
 //   mean = sum n_i mean_i / n,  M2 = sum (M2_i + n_i (mean_i - mean)^2),
 //   C_ab = sum (C_i,ab + n_i (mean_i,a - mean_a)(mean_i,b - mean_b)),
-// evaluated in FP64 by one CTA per parent with a fixed reduction tree (deterministic).
+// evaluated in FP64 with fixed reduction trees (deterministic): a warp per parent with few
+// children, a CTA per parent with many.
 #include "common.cuh"
 
 namespace lsrvt {
 namespace {
 
-constexpr int kMergeThreads = 128;
 
 struct Level {
     const int64_t *count;
@@ -49,104 +49,251 @@ __global__ void merge_init_kernel(lsrvt_stats out, const int32_t *n_parent_dev, 
         out.count[i] = 0;
 }
 
-__global__ void merge_exact_kernel(Level in, const int32_t *n_child_dev, int32_t n_child_max, const int32_t *parent,
-                                   int32_t m, int32_t B, lsrvt_stats out, unsigned *omin, unsigned *omax) {
-    int32_t nc = n_child_dev ? min(*n_child_dev, n_child_max) : n_child_max;
-    int64_t per = (int64_t)(m > 0 ? m : 1);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nc * per;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t c = (int32_t)(i / per);
-        int32_t j = (int32_t)(i - (int64_t)c * per);
-        int64_t n = in.count[c];
-        if (n == 0) continue;
-        int32_t p = parent[c];
-        if (j == 0) atomicAdd((unsigned long long *)&out.count[p], (unsigned long long)n);
-        if (m == 0) continue;
-        int64_t cj = (int64_t)c * m + j, pj = (int64_t)p * m + j;
-        atomicMin(&omin[pj], float_to_ordered(in.vmin[cj]));
-        atomicMax(&omax[pj], float_to_ordered(in.vmax[cj]));
-        if (B > 0 && in.hist)
-            for (int b = 0; b < B; ++b) {
-                uint32_t h = in.hist[cj * B + b];
-                if (h) atomicAdd(&out.hist[pj * B + b], h);
+// Exact parts (count, min, max, histogram).  Children of a parent are contiguous, so a CTA
+// takes 256 consecutive children (a thread each) and aggregates before touching memory: a warp
+// combines the lanes of one parent (match on the parent id, warp reductions) and one lane
+// issues the atomics; when the whole chunk has one parent (the upper levels, where few parents
+// own very many children) the warps combine in shared memory first, so a parent receives one
+// atomic per chunk and bin instead of one per child and bin.
+constexpr int kMX = 256;
+
+__global__ void __launch_bounds__(kMX) merge_exact_kernel(Level in, const int32_t *n_child_dev, int32_t n_child_max,
+                                                          const int32_t *parent, int32_t m, int32_t B,
+                                                          lsrvt_stats out, unsigned *omin, unsigned *omax,
+                                                          bool shared_ok) {
+    extern __shared__ unsigned msh[];  // [m * B] histogram, [m] min, [m] max, [2] count (when shared_ok)
+    unsigned *sh_hist = msh, *sh_min = msh + (size_t)m * B, *sh_max = sh_min + m;
+    unsigned long long *sh_cnt = reinterpret_cast<unsigned long long *>(sh_max + m + ((m * B + 2 * m) & 1));
+    const int32_t nc = n_child_dev ? min(*n_child_dev, n_child_max) : n_child_max;
+    const int tid = threadIdx.x;
+    for (int32_t c0 = blockIdx.x * kMX; c0 < nc; c0 += gridDim.x * kMX) {
+        const int32_t c = c0 + tid;
+        const int64_t n = c < nc ? in.count[c] : 0;
+        const int32_t p = n > 0 ? parent[c] : -1;
+        const bool one = shared_ok && parent[c0] == parent[min(c0 + kMX, nc) - 1];  // parents are sorted
+        if (one) {
+            for (int i = tid; i < m * B; i += kMX) sh_hist[i] = 0u;
+            for (int i = tid; i < m; i += kMX) {
+                sh_min[i] = float_to_ordered(__int_as_float(0x7f800000));
+                sh_max[i] = float_to_ordered(-__int_as_float(0x7f800000));
             }
+            if (tid == 0) *sh_cnt = 0ull;
+            __syncthreads();
+        }
+        const unsigned mk = __match_any_sync(0xffffffffu, p);
+        const bool lead = p >= 0 && (mk & lanemask_lt()) == 0;
+        {
+            const unsigned s = __reduce_add_sync(mk, (unsigned)n);  // N < 2^31: a warp's sum fits
+            if (lead) {
+                if (one) atomicAdd(sh_cnt, (unsigned long long)s);
+                else atomicAdd((unsigned long long *)&out.count[p], (unsigned long long)s);
+            }
+        }
+        for (int j = 0; j < m; ++j) {
+            const int64_t cj = (int64_t)c * m + j, pj = (int64_t)p * m + j;
+            const unsigned lo = __reduce_min_sync(mk, n > 0 ? float_to_ordered(in.vmin[cj]) : 0xFFFFFFFFu);
+            const unsigned hi = __reduce_max_sync(mk, n > 0 ? float_to_ordered(in.vmax[cj]) : 0u);
+            if (lead) {
+                if (one) {
+                    atomicMin(&sh_min[j], lo);
+                    atomicMax(&sh_max[j], hi);
+                } else {
+                    atomicMin(&omin[pj], lo);
+                    atomicMax(&omax[pj], hi);
+                }
+            }
+            if (B > 0 && in.hist)
+                for (int b = 0; b < B; ++b) {
+                    const unsigned h = __reduce_add_sync(mk, n > 0 ? in.hist[cj * B + b] : 0u);
+                    if (lead && h) {
+                        if (one) atomicAdd(&sh_hist[j * B + b], h);
+                        else atomicAdd(&out.hist[pj * B + b], h);
+                    }
+                }
+        }
+        if (one) {
+            __syncthreads();
+            const int32_t pp = parent[c0];
+            for (int i = tid; i < m * B; i += kMX)
+                if (sh_hist[i]) atomicAdd(&out.hist[(int64_t)pp * m * B + i], sh_hist[i]);
+            for (int i = tid; i < m; i += kMX) {
+                atomicMin(&omin[(int64_t)pp * m + i], sh_min[i]);
+                atomicMax(&omax[(int64_t)pp * m + i], sh_max[i]);
+            }
+            if (tid == 0 && *sh_cnt) atomicAdd((unsigned long long *)&out.count[pp], *sh_cnt);
+            __syncthreads();
+        }
     }
 }
 
-__device__ double block_sum_d(double v, double *red) {
+// Moments (Chan et al.): the parent's mean first, then M2 (and co-moments) around it, in FP64
+// with fixed reduction trees (deterministic).  Variables (and co-moment entries) go in groups of
+// kMG so the per-thread partial sums stay in registers.  Parents with at most kSmallKids children
+// (the cell -> component level: a component holds few cells) take a warp each, with no barriers;
+// larger parents (components -> bands, bands -> volume: few parents, very many children) take a
+// CTA each, every thread streaming whole child rows.
+constexpr int kMG = 8;
+constexpr int kSmallKids = 128;
+
+__device__ __forceinline__ double warp_allsum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
-    return s;
+    return v;
 }
 
-__device__ long long block_sum_ll(long long v, long long *red) {
+__device__ __forceinline__ long long warp_allsum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    long long s = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
-    return s;
+    return v;
 }
 
-__global__ void __launch_bounds__(kMergeThreads) merge_moments_kernel(Level in, const int32_t *off32,
-                                                                       const int64_t *off64, const int32_t *n_parent_dev,
-                                                                       int32_t n_parent_max, int32_t m, bool cov,
-                                                                       lsrvt_stats out, const unsigned *omin,
-                                                                       const unsigned *omax) {
-    __shared__ double red[kMergeThreads / 32];
-    __shared__ long long redl[kMergeThreads / 32];
-    __shared__ double mu[64];
-    int32_t np = n_parent_dev ? min(*n_parent_dev, n_parent_max) : n_parent_max;
-    int32_t T = m * (m + 1) / 2;
-    for (int32_t p = blockIdx.x; p < np; p += gridDim.x) {
-        int64_t a = off32 ? off32[p] : off64[p];
-        int64_t b = off32 ? off32[p + 1] : off64[p + 1];
-        long long nloc = 0;
-        for (int64_t c = a + threadIdx.x; c < b; c += blockDim.x) nloc += in.count[c];
-        long long n = block_sum_ll(nloc, redl);
-        for (int j = 0; j < m; ++j) {
-            double s = 0.0;
-            for (int64_t c = a + threadIdx.x; c < b; c += blockDim.x) s += (double)in.count[c] * in.mean[c * m + j];
-            s = block_sum_d(s, red);
-            double meanj = n > 0 ? s / (double)n : 0.0;
-            if (threadIdx.x == 0) mu[j] = meanj;
-            double q = 0.0;
-            for (int64_t c = a + threadIdx.x; c < b; c += blockDim.x) {
-                int64_t nc = in.count[c];
-                if (nc == 0) continue;
-                double dd = in.mean[c * m + j] - meanj;
-                q += in.m2[c * m + j] + (double)nc * dd * dd;
-            }
-            q = block_sum_d(q, red);
-            if (threadIdx.x == 0) {
-                out.mean[(int64_t)p * m + j] = meanj;
-                out.m2[(int64_t)p * m + j] = q;
-                out.vmin[(int64_t)p * m + j] = ordered_to_float(omin[(int64_t)p * m + j]);
-                out.vmax[(int64_t)p * m + j] = ordered_to_float(omax[(int64_t)p * m + j]);
-            }
+// sum over the CTA of the kMG values of every thread (fixed order: warp trees, then warps in
+// order); every thread receives the totals
+__device__ __forceinline__ void block_allsum(double *v, double (*red)[kMG], int nw) {
+#pragma unroll
+    for (int k = 0; k < kMG; ++k) v[k] = warp_allsum(v[k]);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < kMG; ++k) red[threadIdx.x >> 5][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMG; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w][k];
+        v[k] = s;
+    }
+}
+
+// The moments of one parent with children [a, b).  Lanes of a group of G threads (a warp, or a
+// whole CTA) step over the children; reduce(v) sums the kMG values over the group.
+template <typename R>
+__device__ __forceinline__ void parent_moments(const Level &in, int64_t a, int64_t b, long long n, int32_t m, bool cov,
+                                               int32_t p, lsrvt_stats &out, const unsigned *omin,
+                                               const unsigned *omax, double *mu, int gl, int G, R reduce) {
+    const int32_t T = m * (m + 1) / 2;
+    for (int j0 = 0; j0 < m; j0 += kMG) {
+        const int g = m - j0 < kMG ? m - j0 : kMG;
+        double v[kMG];
+#pragma unroll
+        for (int k = 0; k < kMG; ++k) v[k] = 0.0;
+        for (int64_t c = a + gl; c < b; c += G) {
+            const double nc = (double)in.count[c];
+#pragma unroll
+            for (int k = 0; k < kMG; ++k)
+                if (k < g) v[k] += nc * in.mean[c * m + j0 + k];
         }
-        __syncthreads();
-        if (cov && in.comom && out.comom) {
-            int t = 0;
-            for (int i = 0; i < m; ++i)
-                for (int j = i; j < m; ++j, ++t) {
-                    double q = 0.0;
-                    for (int64_t c = a + threadIdx.x; c < b; c += blockDim.x) {
-                        int64_t nc = in.count[c];
-                        if (nc == 0) continue;
-                        q += in.comom[c * T + t] + (double)nc * (in.mean[c * m + i] - mu[i]) * (in.mean[c * m + j] - mu[j]);
-                    }
-                    q = block_sum_d(q, red);
-                    if (threadIdx.x == 0) out.comom[(int64_t)p * T + t] = q;
+        reduce(v);
+#pragma unroll
+        for (int k = 0; k < kMG; ++k) v[k] = n > 0 ? v[k] / (double)n : 0.0;
+        if (gl == 0)
+#pragma unroll
+            for (int k = 0; k < kMG; ++k)
+                if (k < g) mu[j0 + k] = v[k];
+        double mj[kMG];
+#pragma unroll
+        for (int k = 0; k < kMG; ++k) { mj[k] = v[k]; v[k] = 0.0; }
+        for (int64_t c = a + gl; c < b; c += G) {
+            const int64_t nc = in.count[c];
+            if (nc == 0) continue;
+#pragma unroll
+            for (int k = 0; k < kMG; ++k)
+                if (k < g) {
+                    const double dd = in.mean[c * m + j0 + k] - mj[k];
+                    v[k] += in.m2[c * m + j0 + k] + (double)nc * dd * dd;
                 }
         }
+        reduce(v);
+        if (gl == 0)
+#pragma unroll
+            for (int k = 0; k < kMG; ++k) {
+                if (k >= g) continue;
+                const int64_t pj = (int64_t)p * m + j0 + k;
+                out.mean[pj] = mj[k];
+                out.m2[pj] = v[k];
+                out.vmin[pj] = ordered_to_float(omin[pj]);
+                out.vmax[pj] = ordered_to_float(omax[pj]);
+            }
+    }
+    if (!cov || !in.comom || !out.comom) return;
+    for (int t0 = 0; t0 < T; t0 += kMG) {
+        const int g = T - t0 < kMG ? T - t0 : kMG;
+        // the (i, j) of entry t0 + k (upper triangle, rows in order)
+        int ii[kMG], jj[kMG];
+        {
+            int t = 0, i = 0, j = 0;
+            while (t < t0) { ++t; if (++j == m) { ++i; j = i; } }
+#pragma unroll
+            for (int k = 0; k < kMG; ++k) {
+                ii[k] = i; jj[k] = j;
+                if (k < g - 1 && ++j == m) { ++i; j = i; }
+            }
+        }
+        double v[kMG];
+#pragma unroll
+        for (int k = 0; k < kMG; ++k) v[k] = 0.0;
+        for (int64_t c = a + gl; c < b; c += G) {
+            const int64_t nc = in.count[c];
+            if (nc == 0) continue;
+#pragma unroll
+            for (int k = 0; k < kMG; ++k)
+                if (k < g)
+                    v[k] += in.comom[c * T + t0 + k] +
+                            (double)nc * (in.mean[c * m + ii[k]] - mu[ii[k]]) * (in.mean[c * m + jj[k]] - mu[jj[k]]);
+        }
+        reduce(v);
+        if (gl == 0)
+#pragma unroll
+            for (int k = 0; k < kMG; ++k)
+                if (k < g) out.comom[(int64_t)p * T + t0 + k] = v[k];
+    }
+}
+
+__global__ void __launch_bounds__(256) merge_small_kernel(Level in, const int32_t *off32, const int64_t *off64,
+                                                           const int32_t *n_parent_dev, int32_t n_parent_max,
+                                                           int32_t m, bool cov, lsrvt_stats out,
+                                                           const unsigned *omin, const unsigned *omax) {
+    __shared__ double mu_s[256 / 32][64];
+    const int32_t np = n_parent_dev ? min(*n_parent_dev, n_parent_max) : n_parent_max;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double *mu = mu_s[w];
+    for (int32_t p = blockIdx.x * (blockDim.x >> 5) + w; p < np; p += gridDim.x * (blockDim.x >> 5)) {
+        const int64_t a = off32 ? off32[p] : off64[p], b = off32 ? off32[p + 1] : off64[p + 1];
+        if (b - a > kSmallKids) continue;  // warp-uniform
+        long long nl = 0;
+        for (int64_t c = a + lane; c < b; c += 32) nl += in.count[c];
+        const long long n = warp_allsum_ll(nl);
+        parent_moments(in, a, b, n, m, cov, p, out, omin, omax, mu, lane, 32, [&](double *v) {
+#pragma unroll
+            for (int k = 0; k < kMG; ++k) v[k] = warp_allsum(v[k]);
+            __syncwarp();
+        });
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) merge_large_kernel(Level in, const int32_t *off32, const int64_t *off64,
+                                                           const int32_t *n_parent_dev, int32_t n_parent_max,
+                                                           int32_t m, bool cov, lsrvt_stats out,
+                                                           const unsigned *omin, const unsigned *omax) {
+    __shared__ double red[256 / 32][kMG];
+    __shared__ double mu[64];
+    __shared__ long long redl[256 / 32];
+    const int32_t np = n_parent_dev ? min(*n_parent_dev, n_parent_max) : n_parent_max;
+    const int nw = blockDim.x >> 5;
+    for (int32_t p = blockIdx.x; p < np; p += gridDim.x) {
+        const int64_t a = off32 ? off32[p] : off64[p], b = off32 ? off32[p + 1] : off64[p + 1];
+        if (b - a <= kSmallKids) continue;  // CTA-uniform
+        long long nl = 0;
+        for (int64_t c = a + threadIdx.x; c < b; c += blockDim.x) nl += in.count[c];
+        nl = warp_allsum_ll(nl);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) redl[threadIdx.x >> 5] = nl;
+        __syncthreads();
+        long long n = 0;
+        for (int k = 0; k < nw; ++k) n += redl[k];
+        parent_moments(in, a, b, n, m, cov, p, out, omin, omax, mu, threadIdx.x, blockDim.x,
+                       [&](double *v) { block_allsum(v, red, nw); });
         __syncthreads();
     }
 }
@@ -201,10 +348,14 @@ void merge_level(lsrvt_stats child, const int32_t *n_child_dev, int32_t n_child_
                  bool cov, lsrvt_stats parent_out, MergeWs &w, cudaStream_t s) {
     parent_of_kernel<<<kSMs * 4, 128, 0, s>>>(off32, off64, n_parent_dev, n_parent_max, w.parent);
     merge_init_kernel<<<kSMs * 8, 256, 0, s>>>(parent_out, n_parent_dev, n_parent_max, m, B, w.omin, w.omax);
-    merge_exact_kernel<<<grid_for((int64_t)n_child_max * (m > 0 ? m : 1), 256, kSMs * 8), 256, 0, s>>>(
-        as_level(child), n_child_dev, n_child_max, w.parent, m, B, parent_out, w.omin, w.omax);
-    merge_moments_kernel<<<kSMs * 4, kMergeThreads, 0, s>>>(as_level(child), off32, off64, n_parent_dev, n_parent_max,
-                                                            m, cov, parent_out, w.omin, w.omax);
+    const size_t xsm = sizeof(unsigned) * ((size_t)m * B + 2 * m + 4);
+    const bool shared_ok = xsm <= 48 * 1024;
+    merge_exact_kernel<<<grid_for(n_child_max, kMX, kSMs * 8), kMX, shared_ok ? xsm : 0, s>>>(
+        as_level(child), n_child_dev, n_child_max, w.parent, m, B, parent_out, w.omin, w.omax, shared_ok);
+    merge_small_kernel<<<grid_for((int64_t)n_parent_max * 32, 256, kSMs * 8), 256, 0, s>>>(
+        as_level(child), off32, off64, n_parent_dev, n_parent_max, m, cov, parent_out, w.omin, w.omax);
+    merge_large_kernel<<<kSMs * 2, 256, 0, s>>>(as_level(child), off32, off64, n_parent_dev, n_parent_max, m, cov,
+                                                parent_out, w.omin, w.omax);
 }
 
 }  // namespace
