@@ -24,17 +24,39 @@ import torch
 from . import decompose, set_stream_share, Workspace
 
 
+def request_bytes_split(n_voxels, n_aux, voxels_per_site, n_bins=32, dims=None):
+    """Estimate of the device bytes one decomposition holds, as (workspace, the rest): the
+    workspace lives in the slot and is reused by its next request; the rest (the inputs and
+    every output tensor) belongs to the request."""
+    from . import default_max_comp, workspace_bytes
+    n = int(n_voxels)
+    per_voxel = 4 + 1 + 4 + 2 + 4 + 4 + 4 * n_aux  # field, band, comp, q, cell, dist, aux
+    max_comp = default_max_comp(n)
+    rows = n // max(int(voxels_per_site), 1) + max_comp + 1024  # the seeding's site capacity
+    per_row = 8 + 4 * 4 + n_aux * (8 + 8 + 4 + 4 + 4 * n_bins)  # counts, site tables, moments, histograms
+    rest = n * per_voxel + (rows + max_comp + 64) * per_row
+    if dims is None:
+        side = max(int(round(n ** (1.0 / 3.0))), 1)
+        dims = (side, side, side)
+    ws = max(workspace_bytes(step, tuple(int(v) for v in dims), max_comp=max_comp, max_sites=rows, n_aux=n_aux)
+             for step in ("label", "seed", "cvt", "aggregate", "merge"))
+    return int(ws * 1.1) + (1 << 20), int(rest)
+
+
 def request_bytes(n_voxels, n_aux, voxels_per_site, n_bins=32):
     """Estimate of the device bytes one decomposition holds (inputs, outputs, workspaces)."""
-    per_voxel = 4 + 1 + 4 + 2 + 4 + 4 + 4 * n_aux  # field, band, comp, q, cell, dist, aux
-    work = 26 * n_voxels  # tessellation workspace (keys, parents, clearance, bit planes, bins)
-    rows = n_voxels // max(int(voxels_per_site), 1) + (n_voxels // 16) + 4096
-    stats = rows * (8 + n_aux * (8 + 8 + 4 + 4 + 4 * n_bins))
-    return n_voxels * per_voxel + work + stats
+    ws, rest = request_bytes_split(n_voxels, n_aux, voxels_per_site, n_bins)
+    return ws + rest
+
+
+def job_bytes_split(job):
+    nz, ny, nx = job["field"].shape
+    return request_bytes_split(job["field"].numel(), len(job.get("aux", ())), job["voxels_per_site"],
+                               job.get("n_bins", 32), dims=(nx, ny, nz))
 
 
 def job_bytes(job):
-    return request_bytes(job["field"].numel(), len(job.get("aux", ())), job["voxels_per_site"], job.get("n_bins", 32))
+    return sum(job_bytes_split(job))
 
 
 def default_share(n_slots):
@@ -190,12 +212,29 @@ class Server:
 
     def serve(self, requests, make_job, keep_outputs=False):
         """requests: list of dicts with 'arrival' (seconds from start); make_job(req) builds the
-        job (device tensors) when the request is admitted.  Returns one record per request."""
+        job (device tensors) when the request is admitted.  Returns one record per request.
+
+        HBM accounting: the slots' workspaces are resident (each keeps the largest it has needed),
+        so they are counted as they are; a request adds its own bytes (inputs, outputs: its
+        'bytes' less its 'ws_bytes') plus what its slot's workspace would have to grow by; kept
+        outputs stay counted after their request ends."""
         pending = sorted(range(len(requests)), key=lambda i: requests[i]["arrival"])
         records = [None] * len(requests)
         cv = threading.Condition()
-        state = dict(used=0, active=0, error=None)
+        state = dict(used=0, grow=0, active=0, error=None)
         t0 = time.perf_counter()
+
+        def ws_bytes(slot):
+            return 0 if slot.ws.buf is None else slot.ws.buf.numel()
+
+        def resident():
+            return sum(ws_bytes(sl) for sl in self.slots)
+
+        def need_on(slot, i):
+            r = requests[i]
+            total = r.get("bytes") or 0
+            ws = min(r.get("ws_bytes") or 0, total)
+            return (total - ws) + max(0, ws - ws_bytes(slot))
 
         def admit_loop(slot_id):
             slot = self.slots[slot_id]
@@ -205,11 +244,19 @@ class Server:
                         if state["error"] is not None or not pending:
                             return
                         now = time.perf_counter() - t0
-                        i = pick_next(pending, requests, now, state["used"], self.budget, state["active"], self.policy)
+                        # per-request needs on this slot, in the form pick_next reads
+                        view = {i: dict(requests[i], bytes=need_on(slot, i)) for i in pending}
+                        i = pick_next(pending, view, now, state["used"] + state["grow"] + resident(), self.budget,
+                                      state["active"], self.policy)
                         if i is not None:
                             pending.remove(i)
-                            need = requests[i].get("bytes") or 0
+                            grow = max(0, min(requests[i].get("ws_bytes") or 0, requests[i].get("bytes") or 0)
+                                       - ws_bytes(slot))
+                            need = view[i]["bytes"] - grow
                             state["used"] += need
+                            # the slot's workspace growth, reserved until the request ends (then it is
+                            # resident and counted by resident())
+                            state["grow"] += grow
                             state["active"] += 1
                             break
                         wait = requests[pending[0]]["arrival"] - now
@@ -225,6 +272,8 @@ class Server:
                     records[i] = dict(arrival=requests[i]["arrival"], admitted=admitted, finished=finished,
                                       latency=finished - requests[i]["arrival"], voxels=job["field"].numel(),
                                       iters=job["n_iters"], out=out if keep_outputs else None)
+                    # drop this thread's references before the bytes are released for admission
+                    del out, done, job
                 except Exception as e:
                     with cv:
                         state["error"] = e
@@ -232,7 +281,9 @@ class Server:
                     return
                 finally:
                     with cv:
-                        state["used"] -= need
+                        if not keep_outputs:
+                            state["used"] -= need
+                        state["grow"] -= grow
                         state["active"] -= 1
                         cv.notify_all()
 

@@ -83,8 +83,8 @@ def test_autotuner_picks_a_schedule_without_changing_results(pk):
 def test_served_requests_equal_alone(pk, policy):
     from paper_2208_06970_b300 import runtime
     jobs = _jobs(8, 24, 64, 5)
-    reqs = [dict(arrival=0.02 * i, k=i, bytes=runtime.job_bytes(j), work=j["field"].numel() * j["n_iters"])
-            for i, j in enumerate(jobs)]
+    reqs = [dict(arrival=0.02 * i, k=i, bytes=runtime.job_bytes(j), ws_bytes=runtime.job_bytes_split(j)[0],
+                 work=j["field"].numel() * j["n_iters"]) for i, j in enumerate(jobs)]
     # a budget of about two requests forces admission to wait for memory
     budget = 2 * max(r["bytes"] for r in reqs)
     srv = runtime.Server(n_slots=3, hbm_budget=budget, policy=policy)
@@ -120,3 +120,34 @@ def test_host_buffer_form_equals_device_form(pk):
         for k in ("mean", "m2"):
             assert torch.allclose(got["cells"][k], ref["cells"][k][:ns].cpu(), rtol=1e-12, atol=1e-12), k
             assert torch.allclose(got["volume"][k], ref["volume"][k].cpu(), rtol=1e-12, atol=1e-12), k
+
+
+def test_server_stays_within_its_hbm_budget(pk):
+    """Admission counts what is really held: the slots' resident workspaces (each keeps the
+    largest it has needed) and each in-flight request's own inputs and outputs.  The device
+    memory the serving adds never exceeds the budget (the inputs are made up front here, so
+    they count before).  The per-request estimate bounds what one request allocates alone."""
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(10, 24, 72, 17)
+    reqs = []
+    for i, j in enumerate(jobs):
+        ws, rest = runtime.job_bytes_split(j)
+        reqs.append(dict(arrival=0.01 * i, k=i, bytes=ws + rest, ws_bytes=ws))
+    big = max(range(len(jobs)), key=lambda i: reqs[i]["bytes"])
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    alone = runtime.Server(n_slots=1, hbm_budget=1 << 40).serve([dict(reqs[big], arrival=0.0)], lambda r: jobs[r["k"]])
+    torch.cuda.synchronize()
+    assert alone[0] is not None and torch.cuda.max_memory_allocated() - base <= reqs[big]["bytes"]
+    del alone
+    torch.cuda.empty_cache()
+    budget = int(2.5 * reqs[big]["bytes"])
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    srv = runtime.Server(n_slots=3, hbm_budget=budget, policy="fifo")
+    recs = srv.serve(reqs, lambda r: jobs[r["k"]])
+    torch.cuda.synchronize()
+    assert all(r is not None for r in recs)
+    assert torch.cuda.max_memory_allocated() - base <= budget
