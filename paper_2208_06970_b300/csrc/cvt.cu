@@ -886,9 +886,10 @@ struct UpdateOut {
 // Voxels whose key needs their own path check (no brick tube covers them), handed from the
 // candidate filter to check_paths_kernel: voxel, winning site, first move to walk.
 struct CheckList {
-    int32_t *v;
-    int32_t *s;
-    int32_t *mv;
+    int32_t *v;   // voxel
+    int32_t *s;   // winning site
+    int32_t *p;   // the site's voxel
+    int32_t *mv;  // first move to walk (the tube-covered prefix), low 24 bits; the site's clearance above
     int32_t *n;
 };
 
@@ -1074,6 +1075,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
     __shared__ uint32_t present[8];
     __shared__ short band_start[257];
     __shared__ int ncand_s, unknown_s, pcount_s, pbase_s, ccount_s, cbase_s;
+    __shared__ uint8_t csclr[kMaxCand];       // per winning candidate: the clearance at its site
     __shared__ unsigned long long vbest[RV];  // per voxel: best chamfer key
     __shared__ short vwin[RV];                // per voxel: index of the winner in cs (-1 none)
     __shared__ uint8_t wcert[kMaxCand];       // per candidate: 1 = wins a voxel, 2 = brick certificate holds
@@ -1294,6 +1296,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         for (int c2 = tid; c2 < nc && ok_list; c2 += blockDim.x) {
             if (wcert[c2] != 1) continue;
             const int4 c = cs[c2];
+            csclr[c2] = __ldg(clr + c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * (c.w & 0xFFFFFF)));
             const int cov = brick_tube_in_band(clr, d, lx, ly, lz, hx, hy, hz, c.y, c.z, c.w & 0xFFFFFF);
             const int L2 = max(abs(2 * c.y - lx - hx), max(abs(2 * c.z - ly - hy), abs(2 * (c.w & 0xFFFFFF) - lz - hz)));
             wcov[c2] = cov;
@@ -1441,9 +1444,12 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                 if ((pmask >> j) & 1u) up.plist[off + __popc(bal[j] & lanemask_lt())] = g32;
                 if ((cmask >> j) & 1u) {
                     const int at = coff + __popc(cbal[j] & lanemask_lt());
+                    const int w2 = vwin[i];
+                    const int4 cw = cs[w2];
                     chk.v[at] = g32;
-                    chk.s[at] = cs[vwin[i]].x;
-                    chk.mv[at] = cmv[j];
+                    chk.s[at] = cw.x;
+                    chk.p[at] = (int32_t)(cw.y + (int64_t)d.nx * (cw.z + (int64_t)d.ny * (cw.w & 0xFFFFFF)));
+                    chk.mv[at] = min(cmv[j], 0xFFFFFF) | ((int)csclr[w2] << 24);
                 }
                 off += __popc(bal[j]);
                 coff += __popc(cbal[j]);
@@ -1475,7 +1481,7 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
 // brick queued for the relaxation); status 2 certifies line of sight (moments added);
 // status 1 (exact key, no margin) walks Eq. 2's traversal here, and only voxels without
 // line of sight go to the pending pass (their parents need the final keys).
-__global__ void __launch_bounds__(256) check_paths_kernel(
+__global__ void __launch_bounds__(256, 3) check_paths_kernel(
     const uint8_t *__restrict__ band, const uint32_t *__restrict__ emask, const uint8_t *__restrict__ clr, Dims d,
     BrickGeom bg,
     const int32_t *__restrict__ site_pos, unsigned long long *key, uint32_t *xmask, uint8_t *hasunk, uint32_t *flags,
@@ -1488,18 +1494,17 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
         const int32_t i = bstart + threadIdx.x;
         const bool valid = i < cnt;
         int status = 2;
-        int x = 0, y = 0, z = 0;
+        int x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0;
         int32_t s = -1;
         int64_t g = -1;
         if (valid) {
             g = __ldg(chk.v + i);
             s = __ldg(chk.s + i);
-            const int mv0 = __ldg(chk.mv + i);
+            const int32_t p = __ldg(chk.p + i);
+            const int mvw = __ldg(chk.mv + i);
+            const int mv0 = mvw & 0xFFFFFF, cs = (int)((unsigned)mvw >> 24);
             decode_voxel((uint32_t)g, d, x, y, z);
-            const int32_t p = __ldg(site_pos + s);
-            int px, py, pz;
             decode_voxel((uint32_t)p, d, px, py, pz);
-            const int cs = __ldg(clr + p);
             status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, cs, mv0);
 #ifdef LSRVT_DEBUG
             atomicAdd(&g_path_dbg[mv0 > 0 ? 1 : 0], 1ULL);
@@ -1549,13 +1554,7 @@ __global__ void __launch_bounds__(256) check_paths_kernel(
         // warp-aggregated integer moment sums of the line-of-sight voxels (Eq. 2, phi(v) = v)
         const int32_t sid = los ? s : -1;
         const unsigned w = los ? (up.q ? up.q[g] : 1u) : 0u;
-        if (los) {
-            // the key of a checked voxel is its chamfer distance to the site
-            const int32_t p = __ldg(site_pos + s);
-            int px, py, pz;
-            decode_voxel((uint32_t)p, d, px, py, pz);
-            eacc.add(w, (uint32_t)chamfer(px - x, py - y, pz - z));
-        }
+        if (los) eacc.add(w, (uint32_t)chamfer(px - x, py - y, pz - z));  // the checked key: chamfer distance
         if (up.small_coords) {
             unsigned m = __match_any_sync(0xffffffffu, sid);
             unsigned sx = __reduce_add_sync(m, w * (unsigned)x);
@@ -1628,7 +1627,8 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
     const uint8_t *__restrict__ band, const uint16_t *__restrict__ q, Dims d, const unsigned long long *__restrict__ key,
     const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
     uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const int32_t *__restrict__ plist,
-    const int32_t *n_plist, bool small_coords, const int32_t *__restrict__ src, unsigned long long *energy) {
+    const int32_t *n_plist, bool small_coords, const int32_t *__restrict__ src, unsigned long long *energy,
+    const uint32_t *__restrict__ emask) {
     // plist == nullptr: every voxel (N < 2^31); src != nullptr: the path's next node is the
     // voxel's source (any-angle tessellation) instead of the chamfer parent
     const int32_t cnt = plist ? *n_plist : (int32_t)d.n();
@@ -1669,21 +1669,14 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
 #endif
                 }
                 if (!los) {
-                    // parent: first neighbour in (dz,dy,dx) order with an edge, same site and D(u)+w = D(v)
-                    uint8_t b = band[v];
+                    // parent: first neighbour in (dz,dy,dx) order with an edge (the edge mask: the
+                    // spanned box lies in the band), same site and D(u)+w = D(v)
                     int32_t parent = src ? __ldg(src + v) : -1;
+                    const uint32_t e = src ? 0u : __ldg(emask + v);
                     for (int o = 0; o < 27 && parent < 0 && !src; ++o) {
-                        if (o == 13) continue;
+                        if (o == 13 || !((e >> o) & 1u)) continue;
                         int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
-                        int ux = x + dx, uy = y + dy, uz = z + dz;
-                        if (ux < 0 || ux >= d.nx || uy < 0 || uy >= d.ny || uz < 0 || uz >= d.nz) continue;
-                        bool ok = true;
-                        for (int az = 0; az <= (dz != 0) && ok; ++az)
-                            for (int ay = 0; ay <= (dy != 0) && ok; ++ay)
-                                for (int ax = 0; ax <= (dx != 0) && ok; ++ax)
-                                    ok = band[(x + ax * dx) + (int64_t)d.nx * ((y + ay * dy) + (int64_t)d.ny * (z + az * dz))] == b;
-                        if (!ok) continue;
-                        int64_t u = ux + (int64_t)d.nx * (uy + (int64_t)d.ny * uz);
+                        int64_t u = (x + dx) + (int64_t)d.nx * ((y + dy) + (int64_t)d.ny * (z + dz));
                         unsigned long long ku = key[u];
                         if ((int32_t)(uint32_t)ku != s) continue;
                         if ((ku >> 32) + weight_of(o) == (k >> 32)) parent = (int32_t)u;
@@ -1692,10 +1685,17 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
 #ifdef LSRVT_DEBUG
                     atomicAdd(&g_phase[7], 1ULL);
 #endif
-                    int pos = atomicAdd(n_nonlos, 1);
-                    nonlos[pos] = (int32_t)v;
                 }
             }
+        }
+        {
+            // voxels without line of sight, for the phi pass: one atomic per warp
+            const bool nl = v >= 0 && s >= 0 && !los;
+            const unsigned nb2 = __ballot_sync(0xffffffffu, nl);
+            int nbase = 0;
+            if ((threadIdx.x & 31) == 0 && nb2) nbase = atomicAdd(n_nonlos, __popc(nb2));
+            nbase = __shfl_sync(0xffffffffu, nbase, 0);
+            if (nl) nonlos[nbase + __popc(nb2 & lanemask_lt())] = (int32_t)v;
         }
         {
             // one atomic per distinct bit-array word in the warp
@@ -1849,6 +1849,7 @@ struct CvtWs {
     int4 *cell_list;
     int32_t *cell_count;
     int32_t *plist;
+    int32_t *chk_p;    // path checks: the site's voxel
     int32_t *msteps;   // per site: face steps of its last move (warm start)
     GridBarrier *bar;
     void *scan;
@@ -1888,6 +1889,7 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.cell_list = c.take<int4>(ncoarse * kCellList);
     w.cell_count = c.take<int32_t>(ncoarse);
     w.plist = c.take<int32_t>(n);
+    w.chk_p = c.take<int32_t>(n);
     w.msteps = c.take<int32_t>((int64_t)max_sites + 1);
     w.bar = c.take<GridBarrier>(1);
     w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
@@ -2158,7 +2160,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     // the path-check list lives in buffers that are idle while the assignment runs: the
     // erosion planes (used once per call for the clearance, >= 4 bytes per voxel), and the
     // parent and non-LOS arrays (written only by the update pass afterwards)
-    CheckList chk{reinterpret_cast<int32_t *>(w.planes), w.par, w.nonlos, w.counters + 6};
+    CheckList chk{reinterpret_cast<int32_t *>(w.planes), w.par, w.chk_p, w.nonlos, w.counters + 6};
     cudaMemsetAsync(w.coarse_off, 0, sizeof(int64_t) * (ncoarse + 1), s);
     cudaMemsetAsync(w.fine_cur, 0, sizeof(int32_t) * nbricks, s);
     cudaMemsetAsync(w.coarse_cur, 0, sizeof(int32_t) * ncoarse, s);
@@ -2272,7 +2274,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
                                                    w.nonlos, w.counters, w.plist, w.counters + 5, small, nullptr,
-                                                   up.energy);
+                                                   up.energy, w.emask);
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev, up.energy);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
@@ -2408,7 +2410,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key[0], site_pos, w.clr, w.sums, w.los_bits, w.par,
                                                    w.nonlos, w.counters, nullptr, nullptr, small, w.src[0],
-                                                   rec ? rec + 3 : nullptr);
+                                                   rec ? rec + 3 : nullptr, w.emask);
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key[0], w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev, rec ? rec + 3 : nullptr);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
