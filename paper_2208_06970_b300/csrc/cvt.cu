@@ -126,6 +126,9 @@ __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
     return e;
 }
 
+#ifdef LSRVT_DEBUG
+__device__ unsigned long long g_relax_steps[2];  // in-brick steps, brick visits
+#endif
 // One relaxation round: the CTAs of the grid take the queued bricks one at a time.
 // Only voxels the candidate filter left unsettled can change (settled keys are exact), so
 // their exact bits (xmask, brick order) switch the others off, and only bricks holding
@@ -238,6 +241,12 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
             }
             __syncthreads();
         }
+#ifdef LSRVT_DEBUG
+        if (tid == 0) {
+            atomicAdd(&g_relax_steps[0], (unsigned long long)step);
+            atomicAdd(&g_relax_steps[1], 1ULL);
+        }
+#endif
         // ---- write back and collect the neighbour bricks to requeue
         uint32_t my_touch = step >= kMaxSteps ? (1u << 13) : 0u;
 #pragma unroll
@@ -2224,7 +2233,11 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
         cudaStreamSynchronize(s);
         cudaMemcpyFromSymbol(rd, g_relax_dbg, sizeof(rd));
         cudaMemcpyToSymbol(g_relax_dbg, z, sizeof(z));
-        fprintf(stderr, " | relax rounds %llu brick visits %llu\n", rd[0], rd[1]);
+        unsigned long long rs[2], rz[2] = {0, 0};
+        cudaMemcpyFromSymbol(rs, g_relax_steps, sizeof(rs));
+        cudaMemcpyToSymbol(g_relax_steps, rz, sizeof(rz));
+        fprintf(stderr, " | relax rounds %llu brick visits %llu steps/visit %.1f\n", rd[0], rd[1],
+                rs[1] ? (double)rs[0] / rs[1] : 0.0);
     }
 #endif
     return launch_status();
