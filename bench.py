@@ -908,8 +908,9 @@ def main():
                                                            N_AUX, N_BINS),
                         voxels=n, sites=r["n_sites"], components=r["n_comp"], parallelism="replicas" if world > 1
                         else "single", l2="inputs larger than L2 (field 512 MiB + aux 8 GiB), no flush"),
-            roofline=dict(kernel="one Lloyd iteration: site bins + cell lists + cfi_kernel + relax_persistent_kernel + "
-                                 "update_voxels_kernel + update_nonlos_kernel + move_sites_kernel",
+            roofline=dict(kernel="one Lloyd iteration: site bins + cell lists + cfi_kernel + check_paths_kernel + "
+                                 "relax_persistent_kernel + update_voxels_kernel + update_nonlos_kernel + "
+                                 "move_sites_kernel",
                           # the roofline axis is HBM (algorithmic bytes against the measured copy rate);
                           # the measured limiter is issue and latency (dependent loads in the path and
                           # line-of-sight walks, barriers between the filter's per-brick phases)
