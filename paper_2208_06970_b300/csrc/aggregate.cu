@@ -4,25 +4,31 @@
 // Per cell s and variable j: count, mean, M2 (population variance M2/n), exact min and
 // max, an n_bins histogram, and optionally co-moments (tensor cores, below).
 //
-// B300 design (statistics sweep).  The volume is cut into 32x8x4 bricks (1024 voxels).  A
-// CTA of 16 consumer warps and one producer warp walks its bricks; the producer streams
-// each brick's cell labels and up to 16 variables (one 4 KB tile each) into shared memory
-// with TMA tile loads, double buffered on mbarriers, so HBM reads of the next brick overlap
-// the arithmetic on the current one.  Per brick the consumers group the voxels by cell
-// with a counting sort (shared hash of the brick's cells -> dense slots -> per-slot runs of
-// local indices).  The sorted runs are cut into 32-position chunks shared out to the warps
-// in order.  Inside a warp, lane (j, h) owns variable j and every second position of the
-// chunk (h = 0, 1), so one cell's 16 variables are reduced in parallel and only the two
-// halves of the warp have to be combined when a cell ends.  A lane accumulates x - c and
-// (x - c)^2 (c = the variable at the cell's site voxel, a shift common to all bricks of the
-// cell) in float-float (TwoSum / FMA error-free transforms) over at most 51 elements, then
-// folds them into a normalised float-float sum by accurate double-word additions (FP64 only
-// once per cell and warp, for the atomics); min / max are exact; the histogram goes to lane-private 16-bit
-// counters in shared memory (no bank conflicts, no atomics).  One FP64 atomic
-// per (brick, cell, variable) and moment combines the bricks; a finalize pass forms
-// mean = c + S1/n and M2 = S2 - S1^2/n in FP64.  HBM traffic is the algorithmic 4 B (cell)
-// + 4 m B (variables) per voxel.  Volumes whose row pitch is not a multiple of 16 bytes
-// (TMA cannot describe them) take the same kernel with tiles staged by plain loads.
+// B300 design (statistics sweep), two kernels.  The volume is cut into 32x4x4 bricks (512
+// voxels, rows of 128 bytes).  (1) A grouping pass orders each brick's valid voxels by cell (a
+// counting sort: shared hash of the brick's cell ids -> dense slots -> runs), counts every
+// cell's voxels, and writes the order (512 local indices, 1 KB) and a 128-byte record of the
+// run starts per brick.  It keeps little shared state, so many bricks are in flight per SM and
+// the sort's barriers overlap.  (2) The sweep: a producer warp streams each brick's cell
+// labels, its order and record, and up to 16 variables (one 2 KB tile each) into a ring of
+// shared-memory tiles with TMA (tensor tile loads and bulk copies, mbarrier completion), so HBM
+// reads of the next brick overlap the arithmetic on the current one.  The consumer warps split
+// the brick's valid positions evenly and walk them in chunks of at most 32 positions inside one
+// run; they never wait for each other, only for the tile's mbarrier.  Inside a warp, lane (j, h)
+// owns variable j and every second position of the chunk (h = 0, 1), so one cell's 16
+// variables are reduced in parallel and only the two halves of the warp have to be combined
+// when the warp's segment of a cell ends.  A lane accumulates x - s and (x - s)^2 (s = the
+// variable at the first position of the segment) in float-float (TwoSum / FMA error-free
+// transforms) over at most 51 elements, then folds them into a normalised float-float sum by
+// accurate double-word additions; at the segment's end the sums move, in FP64, to the cell's
+// common shift c (the variable at its site voxel) and go out with one FP64 atomic per moment.
+// min / max are exact; the histogram goes to lane-private 16-bit counters in shared memory (no
+// bank conflicts, no contention), and a flush visits only the words the segment touched.  A
+// finalize pass forms mean = c + S1/n and M2 = S2 - S1^2/n in FP64.  HBM traffic is the
+// algorithmic 4 B (cell) + 4 m B (variables) per voxel, plus 4 B (labels) and 2.25 B (order)
+// per voxel for the grouping pass and 2.25 B per voxel of order read back.  Volumes whose row
+// pitch is not a multiple of 16 bytes (TMA cannot describe them) take the same kernel with
+// tiles staged by plain loads.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -75,13 +81,15 @@ constexpr int kG = 16;                   // variables per tile: one per lane of 
 constexpr int kCW = 8;                   // consumer warps per CTA (two CTAs per SM)
 constexpr int kCT = kCW * 32;            // consumer threads
 constexpr int kAggBlock = kCT + 32;      // + the producer warp
-constexpr int kVPT = GV / kCT;           // voxels per consumer thread in the sort
+constexpr int kStages = 2;               // tiles in flight per CTA
 constexpr int kChunk = 32;               // sorted positions per work chunk
 constexpr int kHashN = 2 * GV;           // twice the brick's voxels: the table never fills
 constexpr int kLaneBins = 32;            // lane-private histograms up to 32 bins
-constexpr int kShiftSlots = 64;          // slots per brick whose shifts are staged in shared memory
 constexpr int kStackBox = 4;             // stacked variables per 4-D tensor box (8 KB)
 constexpr int kRun = 16;                 // consecutive bricks (along x) a CTA takes at a time
+constexpr int kRecRuns = 8;              // runs whose shifts the brick record carries
+constexpr int kRecHead = 32;             // record head: run-start mask (16 words), valid voxels, runs
+constexpr int kRecWords = kRecHead + kRecRuns * kG;  // + the shifts of the first runs' cells
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 
 struct AggMaps {
@@ -93,23 +101,226 @@ struct AggMaps {
 // how the tiles reach shared memory
 enum AggLoad { kLoadPlain = 0, kLoadTma = 1, kLoadTmaStack = 2 };
 
+// The brick grouping: for every brick, its valid voxels ordered by cell (local indices, one
+// run per cell) and a record of the run starts.  Written by group_bricks_kernel, read by the
+// sweep with bulk copies.
+struct BrickOrder {
+    uint16_t *perm;  // [nbricks][GV]
+    uint32_t *rec;   // [nbricks][kRecWords]: words 0..15 run-start bits, 16 valid voxels, 17 runs, then
+                     // the shift (variable at the site voxel) of run r's cell for variable j at 32 + 16 r + j
+};
+
+// ---- grouping pass: one CTA per brick at a time, many CTAs per SM (small shared state), so
+// the barriers of one brick overlap the others.
+constexpr int kGrpThreads = 256;
+constexpr int kGrpWarps = kGrpThreads / 32;
+constexpr int kGrpVPT = GV / kGrpThreads;
+
+struct GrpSmem {
+    int32_t tab[kHashN];     // hash of the brick's cell ids (-1 empty)
+    int16_t tslot[kHashN];   // table position -> dense slot
+    int16_t vt[GV];          // voxel -> table position (-1 none)
+    int32_t off[GV + 1];     // counts, then run offsets per slot
+    int32_t cur[GV];         // scatter cursors
+    int32_t cellOf[GV];      // slot -> cell id
+    uint16_t sorted[GV];     // local voxel indices grouped by slot
+    uint32_t mask[16];       // run starts
+    int32_t wsum[2][kGrpWarps];
+    int32_t nslots, nvalid;
+};
+
+// exclusive scan of one int over the CTA; `buf` alternates between calls so one barrier suffices
+__device__ __forceinline__ int grp_scan(GrpSmem &S, int buf, int a, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ia = a;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, ia, o);
+        if (lane >= o) ia += u;
+    }
+    if (lane == 31) S.wsum[buf][w] = ia;
+    __syncthreads();
+    int pre = 0;
+    total = 0;
+#pragma unroll
+    for (int q = 0; q < kGrpWarps; ++q) {
+        const int v = S.wsum[buf][q];
+        if (q < w) pre += v;
+        total += v;
+    }
+    return pre + ia - a;
+}
+
+// Groups every brick's voxels by cell (a counting sort: shared hash of the brick's cell ids ->
+// dense slots -> run offsets -> scatter), counts each cell's voxels, and writes the order and
+// the run starts.  The order of the runs and of the voxels inside a run is whatever the atomics
+// give; every consumer of the order sums, so only rounding depends on it.
+__global__ void __launch_bounds__(kGrpThreads, 8) group_bricks_kernel(const int32_t *__restrict__ cell, Dims d,
+                                                                   int32_t max_sites, unsigned long long *cnt,
+                                                                   const float *__restrict__ shift_tab, int32_t m,
+                                                                   BrickOrder ord) {
+    __shared__ GrpSmem S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nbx = (d.nx + GX - 1) / GX, nby = (d.ny + GY - 1) / GY, nbz = (d.nz + GZ - 1) / GZ;
+    const int64_t nbricks = (int64_t)nbx * nby * nbz;
+    for (int i = tid; i < kHashN; i += kGrpThreads) S.tab[i] = -1;
+    __syncthreads();
+    for (int64_t brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+        const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
+                  oz = (int)(brick / ((int64_t)nbx * nby)) * GZ;
+        bool val[kGrpVPT];
+        int32_t cv[kGrpVPT];
+        const int32_t c00 = __ldg(cell + ox + (int64_t)d.nx * (oy + (int64_t)d.ny * oz));  // the brick's first voxel
+#pragma unroll
+        for (int r = 0; r < kGrpVPT; ++r) {
+            const int v = tid + r * kGrpThreads;
+            const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
+            const bool inb = gx < d.nx && gy < d.ny && gz < d.nz;
+            cv[r] = inb ? __ldg(cell + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)) : -1;
+        }
+        bool same = true;
+#pragma unroll
+        for (int r = 0; r < kGrpVPT; ++r) {
+            val[r] = cv[r] >= 0 && cv[r] < max_sites;
+            same = same && val[r] && cv[r] == c00;
+        }
+        // the shift of the first cell for variable tid - kRecHead (used if the brick is one cell)
+        const float sh0 = tid >= kRecHead && tid < kRecHead + kG && tid - kRecHead < m && c00 >= 0 && c00 < max_sites
+                              ? __ldg(shift_tab + (int64_t)c00 * m + (tid - kRecHead)) : 0.0f;
+        if (__syncthreads_and(same)) {
+            // the whole brick is one cell (the common case inside large cells): the identity order
+            reinterpret_cast<uint32_t *>(ord.perm + brick * GV)[tid] = (uint32_t)(2 * tid) | ((uint32_t)(2 * tid + 1) << 16);
+            if (tid < kRecHead)
+                ord.rec[brick * kRecWords + tid] = tid == 0 ? 1u : tid == 16 ? (uint32_t)GV : tid == 17 ? 1u : 0u;
+            else if (tid < kRecWords)
+                ord.rec[brick * kRecWords + tid] = tid < kRecHead + kG ? __float_as_uint(sh0) : 0u;
+            if (tid == 0) atomicAdd(&cnt[c00], (unsigned long long)GV);
+            continue;
+        }
+#pragma unroll
+        for (int r = 0; r < kGrpVPT; ++r) {
+            const int v = tid + r * kGrpThreads;
+            const int32_t c = cv[r];
+            const bool valid = val[r];
+            const unsigned mm = __match_any_sync(0xffffffffu, valid ? c : -1);
+            const int leader = __ffs(mm) - 1;
+            int h = 0;
+            if (valid && lane == leader) {
+                h = (int)(((uint32_t)c * 2654435761u) >> (32 - 10));
+                for (int probe = 0; probe < kHashN; ++probe) {
+                    const int old = atomicCAS(&S.tab[h], -1, c);
+                    if (old == -1 || old == c) break;
+                    h = (h + 1) & (kHashN - 1);
+                }
+            }
+            h = __shfl_sync(0xffffffffu, h, leader);
+            S.vt[v] = valid ? (int16_t)h : (int16_t)-1;
+            val[r] = valid;
+        }
+        if (tid < 16) S.mask[tid] = 0u;
+        __syncthreads();
+        {
+            // occupied table entries -> dense slots; clear the per-slot counts on the way
+            constexpr int E = kHashN / kGrpThreads;
+            int f = 0;
+#pragma unroll
+            for (int q = 0; q < E; ++q) f += S.tab[tid * E + q] != -1;
+            for (int i = tid; i <= GV; i += kGrpThreads) S.off[i] = 0;
+            int total;
+            int e0 = grp_scan(S, 0, f, total);
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int h = tid * E + q;
+                const int c = S.tab[h];
+                if (c != -1) {
+                    S.tslot[h] = (int16_t)e0;
+                    S.cellOf[e0] = c;
+                    ++e0;
+                }
+            }
+            if (tid == 0) S.nslots = total;
+        }
+        __syncthreads();
+        // the shifts of the first runs' cells (runs are in slot order), loaded now and stored at the
+        // end so the loads overlap the counting and the scatter
+        float shr = 0.0f;
+        {
+            const int r = (tid - kRecHead) / kG, jj = (tid - kRecHead) % kG;
+            if (tid >= kRecHead && tid < kRecWords && r < S.nslots && jj < m)
+                shr = __ldg(shift_tab + (int64_t)S.cellOf[r] * m + jj);
+        }
+        int sl[kGrpVPT];
+#pragma unroll
+        for (int r = 0; r < kGrpVPT; ++r) {
+            const int v = tid + r * kGrpThreads;
+            const int s = val[r] ? (int)S.tslot[S.vt[v]] : -1;
+            sl[r] = s;
+            const unsigned mm = __match_any_sync(0xffffffffu, s);
+            if (s >= 0 && lane == __ffs(mm) - 1) atomicAdd(&S.off[s], __popc(mm));
+        }
+        for (int i = tid; i < kHashN; i += kGrpThreads) S.tab[i] = -1;  // empty again for the next brick
+        __syncthreads();
+        {
+            const int ns = S.nslots;
+            int a[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) a[r] = 2 * tid + r < ns ? S.off[2 * tid + r] : 0;
+            int total;
+            int ea = grp_scan(S, 1, a[0] + a[1], total);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int i = 2 * tid + r;
+                if (i < ns) {
+                    S.off[i] = ea;
+                    S.cur[i] = ea;
+                    atomicAdd(&cnt[S.cellOf[i]], (unsigned long long)a[r]);
+                    atomicOr(&S.mask[ea >> 5], 1u << (ea & 31));
+                }
+                ea += a[r];
+            }
+            if (tid == 0) S.nvalid = total;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kGrpVPT; ++r) {
+            const int v = tid + r * kGrpThreads;
+            const int s = sl[r];
+            const unsigned mm = __match_any_sync(0xffffffffu, s);
+            const int leader = __ffs(mm) - 1;
+            int base = 0;
+            if (s >= 0 && lane == leader) base = atomicAdd(&S.cur[s], __popc(mm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (s >= 0) S.sorted[base + __popc(mm & lanemask_lt())] = (uint16_t)v;
+        }
+        __syncthreads();
+        // positions at and beyond the valid count are never read; they are written anyway so the
+        // record is one full 1 KB line
+        reinterpret_cast<uint32_t *>(ord.perm + brick * GV)[tid] = reinterpret_cast<const uint32_t *>(S.sorted)[tid];
+        if (tid < kRecHead) {
+            ord.rec[brick * kRecWords + tid] = tid < 16 ? S.mask[tid] : tid == 16 ? (uint32_t)S.nvalid
+                                                                      : tid == 17 ? (uint32_t)S.nslots : 0u;
+        } else if (tid < kRecWords) {
+            ord.rec[brick * kRecWords + tid] = __float_as_uint(shr);
+        }
+        __syncthreads();  // the next brick reuses the shared state
+    }
+}
+
+// ---- the sweep
+struct AggTile {
+    float vars[kG][GV];          // TMA tiles (128-byte rows)
+    int32_t cells[GV];
+    uint16_t perm[GV];           // the brick's valid voxels grouped by cell
+    uint32_t rec[kRecWords];
+};
+static_assert(sizeof(AggTile) % 128 == 0, "tiles stay 128-byte aligned");
+
 struct AggSmem {
-    float vars[2][kG][GV];                     // TMA tiles (128-byte rows)
-    int32_t cells[2][GV];
-    // per warp and lane, 16 words: word w holds bin w (low half) and bin w + 16 (high half)
-    uint32_t hist[kCW][16][32];
-    int32_t tab[kHashN];                       // hash of the brick's cell ids (-1 empty)
-    int16_t tslot[kHashN];                     // table position -> dense slot
-    int16_t vt[GV];                            // voxel -> table position, then slot (-1 none)
-    uint16_t sorted[GV];                       // local voxel indices grouped by slot
-    int32_t off[GV + 1];                       // counts, then run offsets per slot
-    int32_t cho[GV + 1];                       // first chunk of each slot
-    int32_t cur[GV];                           // scatter cursors
-    int32_t cellOf[GV];                        // slot -> cell id
-    float shift[kShiftSlots][kG];              // per slot and variable of the tile: x at the site voxel
-    uint64_t full[2], empty[2];
-    int32_t wsa[2][kCW], wsb[2][kCW];
-    int32_t nslots, nchunks;
+    AggTile tile[kStages];
+    // per warp and lane, 16 words: word w holds bin w (low half) and bin w + 16 (high half); rows
+    // padded to 33 words so a flush can read one word of 16 lanes without bank conflicts
+    uint32_t hist[kCW][16][33];
+    uint64_t full[kStages], empty[kStages];
 };
 constexpr size_t kAggSmem = sizeof(AggSmem) + 1024;
 static_assert(2 * (kAggSmem + 1024) <= 228 * 1024, "two statistics CTAs must fit one SM");
@@ -129,161 +340,6 @@ struct RunMap {
     __device__ int64_t brick(int64_t bi) const { return (blockIdx.x + (bi / kRun) * (int64_t)gridDim.x) * kRun + bi % kRun; }
 };
 
-// exclusive scan of two ints over the consumer threads; totals in ta, tb.  `buf` alternates
-// between calls so one barrier suffices.
-__device__ __forceinline__ void consumer_scan2(AggSmem &S, int buf, int a, int b, int &ea, int &eb, int &ta,
-                                               int &tb) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int ia = a, ib = b;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) { ia += ua; ib += ub; }
-    }
-    if (lane == 31) { S.wsa[buf][w] = ia; S.wsb[buf][w] = ib; }
-    named_bar_sync(1, kCT);
-    int pa = 0, pb = 0;
-    ta = 0; tb = 0;
-#pragma unroll
-    for (int q = 0; q < kCW; ++q) {
-        const int va = S.wsa[buf][q], vb = S.wsb[buf][q];
-        if (q < w) { pa += va; pb += vb; }
-        ta += va; tb += vb;
-    }
-    ea = pa + ia - a;
-    eb = pb + ib - b;
-}
-
-// Groups the brick's voxels by cell: slots (dense, in hash-table order), run offsets, the
-// sorted local indices, chunk offsets, and the per-cell voxel counts.  On entry the hash
-// table is empty (cleared by the previous brick's sort, or at kernel start).
-__device__ void sort_brick(AggSmem &S, const int32_t *cells_tile, Dims d, int ox, int oy, int oz, int32_t max_sites,
-                           AggAcc acc, const float *__restrict__ shift_tab, int m, int j0, int G) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    bool val[kVPT];
-#pragma unroll
-    for (int r = 0; r < kVPT; ++r) {
-        const int v = tid + r * kCT;
-        const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
-        const int32_t c = cells_tile[v];
-        const bool valid = gx < d.nx && gy < d.ny && gz < d.nz && c >= 0 && c < max_sites;
-        const unsigned mm = __match_any_sync(0xffffffffu, valid ? c : -1);
-        const int leader = __ffs(mm) - 1;
-        int h = 0;
-        if (valid && lane == leader) {
-            h = (int)(((uint32_t)c * 2654435761u) >> (32 - 10));
-            for (int probe = 0; probe < kHashN; ++probe) {
-                const int old = atomicCAS(&S.tab[h], -1, c);
-                if (old == -1 || old == c) break;
-                h = (h + 1) & (kHashN - 1);
-            }
-        }
-        h = __shfl_sync(0xffffffffu, h, leader);
-        S.vt[v] = valid ? (int16_t)h : (int16_t)-1;
-        val[r] = valid;
-    }
-    named_bar_sync(1, kCT);
-    {
-        // occupied table entries -> dense slots (kHashN / kCT entries per thread); clear the
-        // per-slot counts on the way
-        constexpr int E = kHashN / kCT;
-        int f = 0;
-#pragma unroll
-        for (int q = 0; q < E; ++q) f += S.tab[tid * E + q] != -1;
-        for (int i = tid; i <= GV; i += kCT) S.off[i] = 0;
-        int e0, e1, t0, t1;
-        consumer_scan2(S, 0, f, 0, e0, e1, t0, t1);
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            const int h = tid * E + q;
-            const int c = S.tab[h];
-            if (c != -1) {
-                S.tslot[h] = (int16_t)e0;
-                S.cellOf[e0] = c;
-                ++e0;
-            }
-        }
-        if (tid == 0) S.nslots = t0;
-    }
-    named_bar_sync(1, kCT);
-    // the tile's shifts (site values of its cells): loads issued now, stored after the scatter,
-    // so their latency hides behind the remaining phases
-    constexpr int kShPT = kShiftSlots * kG / kCT;
-    float shv[kShPT];
-    {
-        const int nsh = S.nslots < kShiftSlots ? S.nslots : kShiftSlots;
-#pragma unroll
-        for (int r = 0; r < kShPT; ++r) {
-            const int i = tid + r * kCT, sl2 = i / kG, jj = i % kG;
-            shv[r] = (sl2 < nsh && jj < G) ? __ldg(shift_tab + (int64_t)S.cellOf[sl2] * m + j0 + jj) : 0.0f;
-        }
-    }
-    int sl[kVPT];
-#pragma unroll
-    for (int r = 0; r < kVPT; ++r) {
-        const int v = tid + r * kCT;
-        const int s = val[r] ? (int)S.tslot[S.vt[v]] : -1;
-        sl[r] = s;
-        const unsigned mm = __match_any_sync(0xffffffffu, s);
-        if (s >= 0 && lane == __ffs(mm) - 1) atomicAdd(&S.off[s], __popc(mm));
-    }
-    for (int i = tid; i < kHashN; i += kCT) S.tab[i] = -1;  // empty again for the next brick
-    named_bar_sync(1, kCT);
-    {
-        const int ns = S.nslots;
-        int a[2], c[2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int i = 2 * tid + r;
-            a[r] = i < ns ? S.off[i] : 0;
-            c[r] = (a[r] + kChunk - 1) / kChunk;
-        }
-        int ea, ec, ta, tc;
-        consumer_scan2(S, 1, a[0] + a[1], c[0] + c[1], ea, ec, ta, tc);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int i = 2 * tid + r;
-            if (i < ns) {
-                S.off[i] = ea; S.cur[i] = ea; S.cho[i] = ec;
-                atomicAdd(&acc.cnt[S.cellOf[i]], (unsigned long long)a[r]);
-            }
-            ea += a[r];
-            ec += c[r];
-        }
-        if (tid == 0) {
-            S.off[ns] = ta;
-            S.cho[ns] = tc;
-            S.nchunks = tc;
-        }
-    }
-    named_bar_sync(1, kCT);
-#pragma unroll
-    for (int r = 0; r < kVPT; ++r) {
-        const int v = tid + r * kCT;
-        const int s = sl[r];
-        const unsigned mm = __match_any_sync(0xffffffffu, s);
-        const int leader = __ffs(mm) - 1;
-        int base = 0;
-        if (s >= 0 && lane == leader) base = atomicAdd(&S.cur[s], __popc(mm));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (s >= 0) S.sorted[base + __popc(mm & lanemask_lt())] = (uint16_t)v;
-    }
-#pragma unroll
-    for (int r = 0; r < kShPT; ++r) (&S.shift[0][0])[tid + r * kCT] = shv[r];
-    named_bar_sync(1, kCT);
-}
-
-// the shifts of a later pass over the same brick (the sort ran on its first pass)
-__device__ void load_shifts(AggSmem &S, const float *__restrict__ shift_tab, int m, int j0, int G) {
-    const int tid = threadIdx.x;
-    const int nsh = S.nslots < kShiftSlots ? S.nslots : kShiftSlots;
-    for (int i = tid; i < kShiftSlots * kG; i += kCT) {
-        const int sl2 = i / kG, jj = i % kG;
-        (&S.shift[0][0])[i] = (sl2 < nsh && jj < G) ? __ldg(shift_tab + (int64_t)S.cellOf[sl2] * m + j0 + jj) : 0.0f;
-    }
-    named_bar_sync(1, kCT);
-}
-
 // shift of every (site, variable): the variable at the site voxel
 __global__ void shift_table_kernel(const __grid_constant__ AggParams p, const int32_t *__restrict__ site_pos,
                                    const int32_t *n_sites_dev, int32_t max_sites, float *shift) {
@@ -296,21 +352,33 @@ __global__ void shift_table_kernel(const __grid_constant__ AggParams p, const in
     }
 }
 
-template <int kLoad>
+// The sweep.  A producer warp streams each brick's cell labels, its order (from the grouping
+// pass) and up to 16 variables into a ring of shared-memory tiles; the consumer warps share
+// each brick's valid positions out evenly (no barrier between them: each waits for the tile's
+// mbarrier and releases it when done).  A warp walks its positions in chunks of at most 32
+// inside one run (one cell).  Lane (j, h) owns variable j and the chunk positions of parity h;
+// it accumulates x - c and (x - c)^2, c = the variable at the first position of the warp's
+// current segment of the cell, in float-float (TwoSum / FMA error-free transforms), folded
+// every <= 51 steps into a normalised float-float sum by accurate double-word additions.  At
+// the end of a segment the two halves of the warp are combined and the sums are moved, in FP64,
+// to the cell's common shift (the variable at its site voxel) before one FP64 atomic per moment;
+// only the histogram words the segment touched are flushed.
+enum AggHist { kHistNone = 0, kHistLane = 1, kHistGlobal = 2 };
+
+template <int kLoad, int kHist>
 __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *__restrict__ cell, Dims d,
                                                                  const __grid_constant__ AggParams p,
                                                                  const __grid_constant__ AggMaps maps,
+                                                                 BrickOrder ord,
                                                                  const float *__restrict__ lo,
                                                                  const float *__restrict__ scale,
                                                                  const float *__restrict__ shift_tab,
-                                                                 int32_t max_sites, AggAcc acc, uint32_t *hist,
-                                                                 int32_t *status) {
+                                                                 AggAcc acc, uint32_t *hist, int32_t *status) {
     extern __shared__ __align__(16) unsigned char agg_smem_raw[];
     // align in the shared address space (pointer arithmetic keeps the accesses shared-memory
     // instructions; a round trip through an integer would turn them into generic ones)
     const uint32_t raw_addr = smem_u32(agg_smem_raw);
     AggSmem &S = *reinterpret_cast<AggSmem *>(agg_smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr));
-    constexpr bool kTma = kLoad != kLoadPlain;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nbx = (d.nx + GX - 1) / GX, nby = (d.ny + GY - 1) / GY, nbz = (d.nz + GZ - 1) / GZ;
     const int64_t nbricks = (int64_t)nbx * nby * nbz;
@@ -319,73 +387,88 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
     const RunMap runs(nbricks);
     const int64_t ntiles = runs.my_bricks() * npass;
     if (tid == 0) {
-        mbar_init(&S.full[0], 1);
-        mbar_init(&S.full[1], 1);
-        mbar_init(&S.empty[0], kCW);
-        mbar_init(&S.empty[1], kCW);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(&S.full[st], 1);
+            mbar_init(&S.empty[st], kCW);
+        }
         fence_mbar_init();
     }
-    for (int i = tid; i < kCW * 16 * 32; i += blockDim.x) (&S.hist[0][0][0])[i] = 0u;
-    for (int i = tid; i < kHashN; i += blockDim.x) S.tab[i] = -1;
+    for (int i = tid; i < kCW * 16 * 33; i += blockDim.x) (&S.hist[0][0][0])[i] = 0u;
     __syncthreads();
 
     if (warp == kCW) {
         // ---------------- producer warp.  A thread keeps about one tensor copy in flight at a
-        // time, so the boxes of a tile are spread over lanes: lane 0 arms the stage's barrier with
-        // the tile's bytes, then one lane per box issues it (stage 1 starts at lane 16, so the two
-        // stages' copies are in flight together).  Stacked variables go four per 4-D box.
-        if (kTma) {
-            constexpr int kVarsPerBox = kLoad == kLoadTmaStack ? kStackBox : 1;
-            int64_t t = 0;
-            bool alive = true;
-            for (; t < ntiles; ++t) {
-                const int st = (int)(t & 1);
-                const uint32_t ph = (uint32_t)(t >> 1) & 1u;
-                int ok = 1;
-                if (lane == 0) ok = mbar_wait(&S.empty[st], ph ^ 1u, kWaitNs) ? 1 : 0;
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) {
-                    if (lane == 0) set_status(status, LSRVT_ERR_TIMEOUT);
-                    alive = false;
-                    break;
-                }
-                const int64_t brick = runs.brick(t / npass);
-                const int pass = (int)(t % npass);
-                const int j0 = pass * kG, G = m - j0 < kG ? m - j0 : kG;
-                const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
-                          oz = (int)(brick / ((int64_t)nbx * nby)) * GZ;
+        // time, so the copies of a tile are spread over lanes: lane 0 arms the stage's barrier
+        // with the tile's bytes, then one lane per copy issues it (odd stages start at lane 16).
+        constexpr int kVarsPerBox = kLoad == kLoadTmaStack ? kStackBox : 1;
+        int64_t t = 0;
+        for (; t < ntiles; ++t) {
+            const int st = (int)(t % kStages);
+            const uint32_t ph = (uint32_t)(t / kStages) & 1u;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&S.empty[st], ph ^ 1u, kWaitNs) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) set_status(status, LSRVT_ERR_TIMEOUT);
+                break;
+            }
+            const int64_t brick = runs.brick(t / npass);
+            const int pass = (int)(t % npass);
+            const int j0 = pass * kG, G = m - j0 < kG ? m - j0 : kG;
+            const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
+                      oz = (int)(brick / ((int64_t)nbx * nby)) * GZ;
+            AggTile &T = S.tile[st];
+            if (kLoad != kLoadPlain) {
                 const int nvbox = G > 0 ? (G + kVarsPerBox - 1) / kVarsPerBox : 0;
-                const uint32_t bytes = (uint32_t)nvbox * kVarsPerBox * GV * 4u + (pass == 0 ? GV * 4u : 0u);
+                const uint32_t bytes = (uint32_t)nvbox * kVarsPerBox * GV * 4u + GV * 4u + GV * 2u + kRecWords * 4u;
+                static_assert(kRecWords * 4 % 16 == 0, "bulk copies move multiples of 16 bytes");
                 if (lane == 0) mbar_arrive_expect_tx(&S.full[st], bytes);
                 __syncwarp();
-                const int li = (lane - 16 * st) & 31;  // this lane's box of the tile: 0 = cells, 1..16 = variables
-                if (li == 0 && pass == 0) tma_load_3d(S.cells[st], &maps.cell, ox, oy, oz, &S.full[st]);
-                if (li >= 1 && li <= nvbox) {
-                    const int jj = (li - 1) * kVarsPerBox;
-                    if (kLoad == kLoadTmaStack) tma_load_4d(S.vars[st][jj], &maps.stack, ox, oy, oz, j0 + jj, &S.full[st]);
-                    else tma_load_3d(S.vars[st][jj], &maps.var[j0 + jj], ox, oy, oz, &S.full[st]);
+                const int li = (lane - 16 * (st & 1)) & 31;  // 0 = cells, 1 = order, 2 = record, 3.. = variables
+                if (li == 0) tma_load_3d(T.cells, &maps.cell, ox, oy, oz, &S.full[st]);
+                if (li == 1) bulk_load(T.perm, ord.perm + brick * GV, GV * 2u, &S.full[st]);
+                if (li == 2) bulk_load(T.rec, ord.rec + brick * kRecWords, kRecWords * 4u, &S.full[st]);
+                if (li >= 3 && li < 3 + nvbox) {
+                    const int jj = (li - 3) * kVarsPerBox;
+                    if (kLoad == kLoadTmaStack) tma_load_4d(T.vars[jj], &maps.stack, ox, oy, oz, j0 + jj, &S.full[st]);
+                    else tma_load_3d(T.vars[jj], &maps.var[j0 + jj], ox, oy, oz, &S.full[st]);
                 }
+            } else {
+                // plain loads (arrays TMA cannot describe); the order and record with them
+                for (int i = lane; i < GV * (1 + G); i += 32) {
+                    const int k = i & (GV - 1), jj = i / GV - 1;
+                    const int gx = ox + (k & (GX - 1)), gy = oy + ((k / GX) & (GY - 1)), gz = oz + k / (GX * GY);
+                    const bool inb = gx < d.nx && gy < d.ny && gz < d.nz;
+                    const int64_t g = gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz);
+                    if (jj < 0) T.cells[k] = inb ? __ldcs(cell + g) : -1;
+                    else T.vars[jj][k] = inb ? __ldcs(p.aux[j0 + jj] + g) : 0.0f;
+                }
+                for (int i = lane; i < GV / 2; i += 32)
+                    reinterpret_cast<uint32_t *>(T.perm)[i] = reinterpret_cast<const uint32_t *>(ord.perm + brick * GV)[i];
+                for (int i = lane; i < kRecWords; i += 32) T.rec[i] = ord.rec[brick * kRecWords + i];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.full[st]);
             }
-            (void)alive;
-            // never leave with copies in flight: wait (bounded) for the last tile of each stage
-            if (lane == 0)
-                for (int64_t u = t - 2 < 0 ? 0 : t - 2; u < t; ++u)
-                    mbar_wait(&S.full[u & 1], (uint32_t)(u >> 1) & 1u, kWaitNs);
         }
+        // never leave with copies in flight: wait (bounded) for the last tile of each stage
+        if (lane == 0)
+            for (int64_t u = t - kStages < 0 ? 0 : t - kStages; u < t; ++u)
+                mbar_wait(&S.full[u % kStages], (uint32_t)(u / kStages) & 1u, kWaitNs);
         return;
     }
 
     // ---------------- consumers
     const int j = lane & 15, hh = lane >> 4;
-    uint32_t *hw = &S.hist[warp][0][lane];  // this lane's 16 words, stride 32
-    const bool lane_hist = B > 0 && B <= kLaneBins;
+    uint32_t *hw = &S.hist[warp][0][lane];  // this lane's 16 words, stride 33
     const float Bm1 = (float)(B > 0 ? B - 1 : 0);
     // Accumulator state, carried from brick to brick of a run while this warp stays in the same
     // cell (one variable tile per brick): a cell that spans many bricks is flushed once per run.
     int cur_cell = -1, kacc = 0;
+    int tj0 = 0, tG = 0;               // the current tile's first variable and variable count
     bool act = false;
     int jv = 0;
-    float nsh = 0.0f;
+    float nsh = 0.0f;                  // minus the cell's shift
+    uint32_t tmask = 0u;               // histogram words this lane touched in the segment
     // two independent float-float accumulator sets (even / odd steps) for instruction-level
     // parallelism
     float h1[2] = {0.0f, 0.0f}, l1[2] = {0.0f, 0.0f}, h2[2] = {0.0f, 0.0f}, l2[2] = {0.0f, 0.0f};
@@ -420,17 +503,21 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
             atomicMax(&acc.vmax[cj], float_to_ordered(mx));
             if (!isfinite(D1) || !isfinite(D2)) set_status(status, LSRVT_ERR_NONFINITE);
         }
-        if (lane_hist) {
-            const int words = B < 16 ? B : 16;
-            for (int w2 = 0; w2 < words; ++w2) {
-                const uint32_t own = hw[w2 * 32];
-                const uint32_t tot = own + __shfl_down_sync(0xffffffffu, own, 16);
-                hw[w2 * 32] = 0u;
-                if (hh == 0 && act) {
-                    const uint32_t c0 = tot & 0xFFFFu, c1 = tot >> 16;
-                    if (c0) atomicAdd(&hist[cj * B + w2], c0);
-                    if (c1) atomicAdd(&hist[cj * B + w2 + 16], c1);
+        if (kHist == kHistLane) {
+            if (__reduce_or_sync(0xffffffffu, tmask)) {
+                // transposed: per variable, lane q takes bin q (word q & 15, half q & 16 of the
+                // variable's two lanes) and the warp adds one coalesced row of bins
+                __syncwarp();
+                const uint32_t *col = &S.hist[warp][lane & 15][0];
+                const int shq = lane & 16;
+                for (int jj = 0; jj < tG; ++jj) {
+                    const uint32_t n_q = ((col[jj] >> shq) & 0xFFFFu) + ((col[jj + 16] >> shq) & 0xFFFFu);
+                    if (n_q && lane < B) atomicAdd(&hist[((int64_t)cur_cell * m + tj0 + jj) * B + lane], n_q);
                 }
+                __syncwarp();
+#pragma unroll
+                for (int w2 = 0; w2 < 16; ++w2) hw[w2 * 33] = 0u;
+                tmask = 0u;
             }
         }
         H1 = L1 = H2 = L2 = 0.0f;
@@ -439,11 +526,13 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
         cur_cell = -1;
     };
     float loj = 0.0f, scj = 0.0f;
-    auto acc_one = [&](const float x, int u) {
+    // one step of lane (j, h); inc = 0 makes it neutral (x is then the segment's shift, which adds
+    // nothing to the sums and is inside the segment's min / max)
+    auto acc_one = [&](const float x, int u, uint32_t inc) {
         mn = fminf(mn, x);
         mx = fmaxf(mx, x);
         float dh, dl, s_, e_;
-        two_sum(x, nsh, dh, dl);  // x - c = dh + dl exactly
+        two_sum(x, nsh, dh, dl);  // x - s = dh + dl exactly
         two_sum(h1[u], dh, s_, e_);
         h1[u] = s_;
         l1[u] = __fadd_rn(l1[u], __fadd_rn(e_, dl));
@@ -452,99 +541,109 @@ __global__ void __launch_bounds__(kAggBlock, 2) aggregate_kernel(const int32_t *
         two_sum(h2[u], pp, s_, e_);
         h2[u] = s_;
         l2[u] = __fadd_rn(l2[u], __fadd_rn(e_, corr));
-        if (B) {
+        if (kHist != kHistNone) {
             float tt = __fmul_rn(__fsub_rn(x, loj), scj);
             tt = fminf(fmaxf(tt, 0.0f), Bm1);  // NaN and t <= 0 -> bin 0, t >= B -> B - 1
             // x + 2^23 rounded toward zero is 2^23 + floor(x) for 0 <= x < 2^23: its low
             // mantissa bits are the bin
             const uint32_t bits = __float_as_uint(__fadd_rz(tt, 8388608.0f));
-            // the lane's own words: a reduction with no result keeps the steps independent
-            if (lane_hist) atomicAdd(hw + ((bits & 15u) << 5), 1u << (bits & 16u));
-            else atomicAdd(&hist[cj * B + (bits - 0x4B000000u)], 1u);
+            if (kHist == kHistLane) {
+                // the lane's own words: a reduction with no result keeps the steps independent
+                atomicAdd(hw + (bits & 15u) * 33u, inc << (bits & 16u));
+                tmask |= inc << (bits & 15u);
+            } else if (inc) {
+                atomicAdd(&hist[cj * B + (bits - 0x4B000000u)], 1u);
+            }
         }
     };
     for (int64_t t = 0; t < ntiles; ++t) {
-        const int st = kTma ? (int)(t & 1) : 0;
+        const int st = (int)(t % kStages);
         const int64_t bi = t / npass;
-        const int64_t brick = runs.brick(bi);
         const int pass = (int)(t % npass);
         const int j0 = pass * kG, G = m - j0 < kG ? m - j0 : kG;
-        const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
-                  oz = (int)(brick / ((int64_t)nbx * nby)) * GZ;
         act = j < G;
         jv = j0 + (act ? j : 0);
+        tj0 = j0;
+        tG = G;
         loj = (B && act) ? lo[jv] : 0.0f;  // issued before the wait
         scj = (B && act) ? scale[jv] : 0.0f;
-        bool ok = true;
-        if (kTma) {
-            ok = mbar_wait(&S.full[st], (uint32_t)(t >> 1) & 1u, kWaitNs);
-            if (!ok && lane == 0) set_status(status, LSRVT_ERR_TIMEOUT);
-        } else {
-            named_bar_sync(1, kCT);  // every warp is done with the previous tile
-            const int nload = (pass == 0 ? GV : 0) + G * GV;
-            for (int i = tid; i < nload; i += kCT) {
-                const bool is_cell = pass == 0 && i < GV;
-                const int k = is_cell ? i : i - (pass == 0 ? GV : 0);
-                const int v = k & (GV - 1), jj = k / GV;
-                const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
-                const bool inb = gx < d.nx && gy < d.ny && gz < d.nz;
-                const int64_t g = gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz);
-                if (is_cell) S.cells[0][v] = inb ? __ldcs(cell + g) : -1;
-                else S.vars[0][jj][v] = inb ? __ldcs(p.aux[j0 + jj] + g) : 0.0f;
-            }
+        if (!mbar_wait(&S.full[st], (uint32_t)(t / kStages) & 1u, kWaitNs)) {
+            if (lane == 0) set_status(status, LSRVT_ERR_TIMEOUT);
+            break;
         }
-        // a timed-out wait anywhere ends every consumer warp at the same point; the barrier also
-        // orders this tile's sort after the previous tile's reads of the sort data
-        if (named_bar_or(1, kCT, !ok)) break;
-        if (pass == 0) sort_brick(S, S.cells[st], d, ox, oy, oz, max_sites, acc, shift_tab, m, j0, G);
-        else load_shifts(S, shift_tab, m, j0, G);
-        // ---- this warp's share of the chunks, in order
-        const int ns = S.nslots, T = S.nchunks;
-        const int q0 = (int)((int64_t)warp * T / kCW), q1 = (int)((int64_t)(warp + 1) * T / kCW);
-        const float *xt = S.vars[st][j];
-        int s = 0;
-        for (int q = q0; q < q1; ++q) {
-            while (s + 1 < ns && S.cho[s + 1] <= q) ++s;  // slot of chunk q (chunks are in slot order)
-            const int c = S.cellOf[s];
+        const AggTile &T = S.tile[st];
+        const float *xt = T.vars[j];
+        const int nv = (int)T.rec[16];
+        const uint32_t mw = lane < 16 ? T.rec[lane] : 0u;  // run-start bits, word per lane
+        // this warp's share of the brick's valid positions
+        const int pe = (int)(((warp + 1) * nv) / kCW);
+        int pos = (int)((warp * nv) / kCW);
+        while (pos < pe) {
+            // end of the run that holds pos: the next run start after it
+            int re = nv;
+            {
+                const int q = pos + 1;
+                const int qw = q >> 5;
+                const uint32_t mine = lane < qw ? 0u : (lane == qw ? (mw & (0xffffffffu << (q & 31))) : mw);
+                const unsigned nz = __ballot_sync(0xffffffffu, mine != 0u);
+                if (nz) {
+                    const int wl = __ffs(nz) - 1;
+                    const uint32_t word = __shfl_sync(0xffffffffu, mine, wl);
+                    re = min(nv, wl * 32 + __ffs(word) - 1);
+                }
+            }
+            const int ce = min(min(pe, re), pos + kChunk);
+            const int c = T.cells[T.perm[pos]];
             if (c != cur_cell) {
                 if (cur_cell >= 0) flush();
                 cur_cell = c;
                 cj = (int64_t)c * m + jv;
-                nsh = !act ? 0.0f : (s < kShiftSlots ? -S.shift[s][j] : -__ldg(shift_tab + cj));
+                // the cell's shift: from the brick record for its first runs (the run index is the
+                // number of run starts at or before pos, less one), else from the table
+                const int pw = pos >> 5;
+                const uint32_t upto = lane < pw ? mw : lane == pw ? (mw & ((2u << (pos & 31)) - 1u)) : 0u;
+                const int r = __reduce_add_sync(0xffffffffu, (unsigned)__popc(upto)) - 1;
+                nsh = !act ? 0.0f
+                           : -(r < kRecRuns && pass == 0 ? __uint_as_float(T.rec[kRecHead + r * kG + j])
+                                                         : __ldg(shift_tab + cj));
             }
-            const int p0 = S.off[s] + (q - S.cho[s]) * kChunk;
-            const int pe = S.off[s + 1] < p0 + kChunk ? S.off[s + 1] : p0 + kChunk;
-            const int L = pe - p0, Le = L & ~1;
-            if (act && Le) {
-                // lane (j, h) takes the chunk positions of parity h, starting at 2j + h (mod the
-                // even length), so the 32 lanes read 32 different banks; every lane makes Le / 2
-                // steps, so the warp stays converged
-                int o = 2 * j + hh;
-                while (o >= Le) o -= Le;
-                const uint16_t *sp = S.sorted + p0;
-                const int n2 = Le >> 1;
+            const int L = ce - pos;
+            if (act) {
+                // lane (j, h) takes the positions of parity h, starting at index (j * n_h) / 16 of
+                // its n_h positions and wrapping, so the 32 lanes read 32 different banks; every
+                // lane makes ceil(L / 2) steps, the odd lanes' last one neutral when L is odd
+                const int n0 = (L + 1) >> 1, nh = hh ? (L >> 1) : n0;
+                const uint16_t *sp = T.perm + pos + hh;
+                const float sx = -nsh;
+                int i = (j * nh) >> 4;
                 int k = 0;
-                for (; k + 1 < n2; k += 2) {
-                    int ob = o + 2;
-                    ob = ob >= Le ? ob - Le : ob;
-                    const float xa = xt[sp[o]], xb = xt[sp[ob]];
-                    acc_one(xa, 0);
-                    acc_one(xb, 1);
-                    o = ob + 2;
-                    o = o >= Le ? o - Le : o;
+                for (; k + 1 < n0; k += 2) {
+                    int ib = i + 1;
+                    ib = ib == nh ? 0 : ib;
+                    const bool vb = k + 1 < nh;
+                    const float xa = xt[sp[2 * i]];
+                    const float xb = xt[sp[2 * (vb ? ib : i)]];
+                    acc_one(xa, 0, 1u);
+                    acc_one(vb ? xb : sx, 1, vb ? 1u : 0u);
+                    i = ib + 1;
+                    i = i >= nh ? i - nh : i;
                 }
-                if (k < n2) acc_one(xt[sp[o]], 0);
+                if (k < n0) {
+                    const bool va = k < nh;
+                    const float xa = xt[va ? sp[2 * i] : T.perm[pos]];
+                    acc_one(va ? xa : sx, 0, va ? 1u : 0u);
+                }
             }
-            if (act && (L & 1) && hh == 0) acc_one(xt[S.sorted[pe - 1]], 1);
-            kacc += (Le >> 1) + 1;
+            kacc += (L + 1) >> 1;
             if (kacc > 34) fold();  // at most 51 float-float additions before a fold
+            pos = ce;
         }
         // flush at the end of a run, and after every tile when the variables come in several
         // tiles per brick (the next tile holds other variables)
         const bool run_end = npass > 1 || bi % kRun == kRun - 1 || t + 1 == ntiles;
         if (run_end && cur_cell >= 0) flush();
         __syncwarp();
-        if (kTma && lane == 0) mbar_arrive(&S.empty[st]);
+        if (lane == 0) mbar_arrive(&S.empty[st]);
     }
 }
 
@@ -910,6 +1009,7 @@ struct AggWs {
     AggAcc acc;
     float *shift;     // [max_sites][m]: the variable at each site voxel
     int32_t *perm;    // [N]: voxels ordered by cell (co-moments)
+    BrickOrder ord;   // the sweep's per-brick order (same memory as perm)
     int64_t *off;     // [max_sites + 1]: first position of each cell in perm
     int32_t *cur;     // [max_sites]: scatter cursors
     int32_t *work;    // co-moment work counter
@@ -926,7 +1026,12 @@ AggWs carve_agg(void *ws, size_t bytes, Dims d, int32_t max_sites, int32_t m, si
     w.acc.vmax = c.take<unsigned>(sm);
     w.acc.cnt = c.take<unsigned long long>(max_sites > 0 ? max_sites : 1);
     w.shift = c.take<float>(sm);
-    w.perm = c.take<int32_t>(d.n());
+    // the brick order of the sweep and the co-moments' voxel order are never live together
+    const int64_t nbricks = (int64_t)((d.nx + GX - 1) / GX) * ((d.ny + GY - 1) / GY) * ((d.nz + GZ - 1) / GZ);
+    const int64_t order_bytes = nbricks * (GV * 2 + kRecWords * 4);
+    w.perm = (int32_t *)c.take<char>(d.n() * 4 > order_bytes ? d.n() * 4 : order_bytes);
+    w.ord.perm = (uint16_t *)w.perm;
+    w.ord.rec = (uint32_t *)((char *)w.perm + nbricks * GV * 2);
     w.off = c.take<int64_t>((int64_t)max_sites + 1);
     w.cur = c.take<int32_t>(max_sites > 0 ? max_sites : 1);
     w.work = c.take<int32_t>(1);
@@ -1033,9 +1138,11 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
         if (n_aux > 0)
             shift_table_kernel<<<grid_for((int64_t)max_sites * n_aux, 256, kSMs * 4), 256, 0, s>>>(
                 p, site_pos, n_sites_dev, max_sites, w.shift);
+        // every brick's voxels grouped by cell (and the cells' voxel counts), many bricks per SM
+        group_bricks_kernel<<<(int)(nbricks < (int64_t)nsm * 8 ? nbricks : (int64_t)nsm * 8), kGrpThreads, 0, s>>>(
+            cell, d, max_sites, w.acc.cnt, w.shift, n_aux, w.ord);
         auto launch = [&](auto kern) {
-            // two CTAs per SM: one CTA's sort and barriers overlap the other's arithmetic, which
-            // needs the largest shared-memory carveout
+            // two CTAs per SM, which needs the largest shared-memory carveout
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAggSmem);
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             int occ = 0;
@@ -1043,12 +1150,24 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
             if (occ < 1) occ = 1;
             const int64_t nruns = (nbricks + kRun - 1) / kRun;
             const int grid = (int)(nruns < (int64_t)nsm * occ ? nruns : (int64_t)nsm * occ);
-            kern<<<grid, kAggBlock, kAggSmem, s>>>(cell, d, p, maps, lo_dev, scale_dev, w.shift, max_sites, w.acc,
+            kern<<<grid, kAggBlock, kAggSmem, s>>>(cell, d, p, maps, w.ord, lo_dev, scale_dev, w.shift, w.acc,
                                                    out.hist, status_dev);
         };
-        if (mode == kLoadTmaStack) launch(aggregate_kernel<kLoadTmaStack>);
-        else if (mode == kLoadTma) launch(aggregate_kernel<kLoadTma>);
-        else launch(aggregate_kernel<kLoadPlain>);
+        const int hm = p.n_bins == 0 ? kHistNone : p.n_bins <= kLaneBins ? kHistLane : kHistGlobal;
+        auto launch_h = [&](auto k0, auto k1, auto k2) {
+            if (hm == kHistNone) launch(k0);
+            else if (hm == kHistLane) launch(k1);
+            else launch(k2);
+        };
+        if (mode == kLoadTmaStack)
+            launch_h(aggregate_kernel<kLoadTmaStack, kHistNone>, aggregate_kernel<kLoadTmaStack, kHistLane>,
+                     aggregate_kernel<kLoadTmaStack, kHistGlobal>);
+        else if (mode == kLoadTma)
+            launch_h(aggregate_kernel<kLoadTma, kHistNone>, aggregate_kernel<kLoadTma, kHistLane>,
+                     aggregate_kernel<kLoadTma, kHistGlobal>);
+        else
+            launch_h(aggregate_kernel<kLoadPlain, kHistNone>, aggregate_kernel<kLoadPlain, kHistLane>,
+                     aggregate_kernel<kLoadPlain, kHistGlobal>);
     }
     aggregate_finalize_kernel<<<kSMs * 8, 256, 0, s>>>(
         w.acc, n_sites_dev, max_sites, n_aux, p, site_pos, out);
