@@ -83,7 +83,6 @@ constexpr int kCT = kCW * 32;            // consumer threads
 constexpr int kAggBlock = kCT + 32;      // + the producer warp
 constexpr int kStages = 2;               // tiles in flight per CTA
 constexpr int kChunk = 32;               // sorted positions per work chunk
-constexpr int kHashN = 2 * GV;           // twice the brick's voxels: the table never fills
 constexpr int kLaneBins = 32;            // lane-private histograms up to 32 bins
 constexpr int kStackBox = 4;             // stacked variables per 4-D tensor box (8 KB)
 constexpr int kRun = 16;                 // consecutive bricks (along x) a CTA takes at a time
@@ -110,199 +109,85 @@ struct BrickOrder {
                      // the shift (variable at the site voxel) of run r's cell for variable j at 32 + 16 r + j
 };
 
-// ---- grouping pass: one CTA per brick at a time, many CTAs per SM (small shared state), so
-// the barriers of one brick overlap the others.
-constexpr int kGrpThreads = 256;
-constexpr int kGrpWarps = kGrpThreads / 32;
-constexpr int kGrpVPT = GV / kGrpThreads;
+// ---- grouping pass: one warp per brick, no block barriers.  Lane l holds the brick's voxels
+// l + 32 r (row r = y + 4 z).  The runs are found one at a time: the cell of the first voxel
+// (in index order) not yet placed leads, and every voxel of that cell is placed after the
+// previous runs, in index order (a ballot per row and prefix counts).  The work per brick grows
+// with its number of cells (about three on average in the flame volumes, 40 % of the bricks a
+// single cell), not with the size of a hash table.
+constexpr int kGrpWarps = 8;
+constexpr int kGrpThreads = kGrpWarps * 32;
+constexpr int kRows = GV / 32;
 
-struct GrpSmem {
-    int32_t tab[kHashN];     // hash of the brick's cell ids (-1 empty)
-    int16_t tslot[kHashN];   // table position -> dense slot
-    int16_t vt[GV];          // voxel -> table position (-1 none)
-    int32_t off[GV + 1];     // counts, then run offsets per slot
-    int32_t cur[GV];         // scatter cursors
-    int32_t cellOf[GV];      // slot -> cell id
-    uint16_t sorted[GV];     // local voxel indices grouped by slot
-    uint32_t mask[16];       // run starts
-    int32_t wsum[2][kGrpWarps];
-    int32_t nslots, nvalid;
-};
-
-// exclusive scan of one int over the CTA; `buf` alternates between calls so one barrier suffices
-__device__ __forceinline__ int grp_scan(GrpSmem &S, int buf, int a, int &total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int ia = a;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, ia, o);
-        if (lane >= o) ia += u;
-    }
-    if (lane == 31) S.wsum[buf][w] = ia;
-    __syncthreads();
-    int pre = 0;
-    total = 0;
-#pragma unroll
-    for (int q = 0; q < kGrpWarps; ++q) {
-        const int v = S.wsum[buf][q];
-        if (q < w) pre += v;
-        total += v;
-    }
-    return pre + ia - a;
-}
-
-// Groups every brick's voxels by cell (a counting sort: shared hash of the brick's cell ids ->
-// dense slots -> run offsets -> scatter), counts each cell's voxels, and writes the order and
-// the run starts.  The order of the runs and of the voxels inside a run is whatever the atomics
-// give; every consumer of the order sums, so only rounding depends on it.
-__global__ void __launch_bounds__(kGrpThreads, 8) group_bricks_kernel(const int32_t *__restrict__ cell, Dims d,
+__global__ void __launch_bounds__(kGrpThreads, 6) group_bricks_kernel(const int32_t *__restrict__ cell, Dims d,
                                                                    int32_t max_sites, unsigned long long *cnt,
                                                                    const float *__restrict__ shift_tab, int32_t m,
                                                                    BrickOrder ord) {
-    __shared__ GrpSmem S;
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ __align__(16) uint16_t sorted_s[kGrpWarps][GV];
+    __shared__ __align__(16) uint32_t rec_s[kGrpWarps][kRecWords];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    uint16_t *sorted = sorted_s[wl];
+    uint32_t *rec = rec_s[wl];
     const int nbx = (d.nx + GX - 1) / GX, nby = (d.ny + GY - 1) / GY, nbz = (d.nz + GZ - 1) / GZ;
     const int64_t nbricks = (int64_t)nbx * nby * nbz;
-    for (int i = tid; i < kHashN; i += kGrpThreads) S.tab[i] = -1;
-    __syncthreads();
-    for (int64_t brick = blockIdx.x; brick < nbricks; brick += gridDim.x) {
+    const int64_t wstride = (int64_t)gridDim.x * kGrpWarps;
+    for (int64_t brick = (int64_t)blockIdx.x * kGrpWarps + wl; brick < nbricks; brick += wstride) {
         const int ox = (int)(brick % nbx) * GX, oy = (int)((brick / nbx) % nby) * GY,
                   oz = (int)(brick / ((int64_t)nbx * nby)) * GZ;
-        bool val[kGrpVPT];
-        int32_t cv[kGrpVPT];
-        const int32_t c00 = __ldg(cell + ox + (int64_t)d.nx * (oy + (int64_t)d.ny * oz));  // the brick's first voxel
+        int32_t cv[kRows];
+        uint32_t pend = 0u;  // bit r: voxel (lane, r) valid and not yet placed
 #pragma unroll
-        for (int r = 0; r < kGrpVPT; ++r) {
-            const int v = tid + r * kGrpThreads;
-            const int gx = ox + (v & (GX - 1)), gy = oy + ((v / GX) & (GY - 1)), gz = oz + v / (GX * GY);
+        for (int r = 0; r < kRows; ++r) {
+            const int gx = ox + lane, gy = oy + (r & (GY - 1)), gz = oz + r / GY;
             const bool inb = gx < d.nx && gy < d.ny && gz < d.nz;
             cv[r] = inb ? __ldg(cell + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)) : -1;
+            pend |= (uint32_t)(cv[r] >= 0 && cv[r] < max_sites) << r;
         }
-        bool same = true;
+        for (int i = lane; i < kRecWords; i += 32) rec[i] = 0u;
+        __syncwarp();
+        int base = 0, nruns = 0;
+        uint32_t mword = 0u;  // lane w < 16: run-start bits of positions 32 w .. 32 w + 31
+        while (true) {
+            // the first pending voxel in index order: lowest row with one, then lowest lane
+            const unsigned rows = __reduce_or_sync(0xffffffffu, pend);
+            if (!rows) break;
+            const int rs = __ffs(rows) - 1;
+            const int ls = __ffs(__ballot_sync(0xffffffffu, (pend >> rs) & 1u)) - 1;
+            int cr = cv[0];
 #pragma unroll
-        for (int r = 0; r < kGrpVPT; ++r) {
-            val[r] = cv[r] >= 0 && cv[r] < max_sites;
-            same = same && val[r] && cv[r] == c00;
-        }
-        // the shift of the first cell for variable tid - kRecHead (used if the brick is one cell)
-        const float sh0 = tid >= kRecHead && tid < kRecHead + kG && tid - kRecHead < m && c00 >= 0 && c00 < max_sites
-                              ? __ldg(shift_tab + (int64_t)c00 * m + (tid - kRecHead)) : 0.0f;
-        if (__syncthreads_and(same)) {
-            // the whole brick is one cell (the common case inside large cells): the identity order
-            reinterpret_cast<uint32_t *>(ord.perm + brick * GV)[tid] = (uint32_t)(2 * tid) | ((uint32_t)(2 * tid + 1) << 16);
-            if (tid < kRecHead)
-                ord.rec[brick * kRecWords + tid] = tid == 0 ? 1u : tid == 16 ? (uint32_t)GV : tid == 17 ? 1u : 0u;
-            else if (tid < kRecWords)
-                ord.rec[brick * kRecWords + tid] = tid < kRecHead + kG ? __float_as_uint(sh0) : 0u;
-            if (tid == 0) atomicAdd(&cnt[c00], (unsigned long long)GV);
-            continue;
-        }
+            for (int r = 1; r < kRows; ++r) cr = r == rs ? cv[r] : cr;
+            const int32_t cur = __shfl_sync(0xffffffffu, cr, ls);
+            int pos = base;
+            uint32_t hit = 0u;
 #pragma unroll
-        for (int r = 0; r < kGrpVPT; ++r) {
-            const int v = tid + r * kGrpThreads;
-            const int32_t c = cv[r];
-            const bool valid = val[r];
-            const unsigned mm = __match_any_sync(0xffffffffu, valid ? c : -1);
-            const int leader = __ffs(mm) - 1;
-            int h = 0;
-            if (valid && lane == leader) {
-                h = (int)(((uint32_t)c * 2654435761u) >> (32 - 10));
-                for (int probe = 0; probe < kHashN; ++probe) {
-                    const int old = atomicCAS(&S.tab[h], -1, c);
-                    if (old == -1 || old == c) break;
-                    h = (h + 1) & (kHashN - 1);
-                }
+            for (int r = 0; r < kRows; ++r) {
+                const bool e = ((pend >> r) & 1u) && cv[r] == cur;
+                const unsigned bm = __ballot_sync(0xffffffffu, e);
+                if (e) sorted[pos + __popc(bm & lanemask_lt())] = (uint16_t)(lane + 32 * r);
+                pos += __popc(bm);
+                hit |= (uint32_t)e << r;
             }
-            h = __shfl_sync(0xffffffffu, h, leader);
-            S.vt[v] = valid ? (int16_t)h : (int16_t)-1;
-            val[r] = valid;
+            pend &= ~hit;
+            if (lane == (base >> 5)) mword |= 1u << (base & 31);
+            if (lane == 0) atomicAdd(&cnt[cur], (unsigned long long)(pos - base));
+            if (nruns < kRecRuns && lane < kG && lane < m)
+                rec[kRecHead + nruns * kG + lane] = __float_as_uint(__ldg(shift_tab + (int64_t)cur * m + lane));
+            base = pos;
+            ++nruns;
         }
-        if (tid < 16) S.mask[tid] = 0u;
-        __syncthreads();
-        {
-            // occupied table entries -> dense slots; clear the per-slot counts on the way
-            constexpr int E = kHashN / kGrpThreads;
-            int f = 0;
-#pragma unroll
-            for (int q = 0; q < E; ++q) f += S.tab[tid * E + q] != -1;
-            for (int i = tid; i <= GV; i += kGrpThreads) S.off[i] = 0;
-            int total;
-            int e0 = grp_scan(S, 0, f, total);
-#pragma unroll
-            for (int q = 0; q < E; ++q) {
-                const int h = tid * E + q;
-                const int c = S.tab[h];
-                if (c != -1) {
-                    S.tslot[h] = (int16_t)e0;
-                    S.cellOf[e0] = c;
-                    ++e0;
-                }
-            }
-            if (tid == 0) S.nslots = total;
+        if (lane < 16) rec[lane] = mword;
+        if (lane == 0) {
+            rec[16] = (uint32_t)base;
+            rec[17] = (uint32_t)nruns;
         }
-        __syncthreads();
-        // the shifts of the first runs' cells (runs are in slot order), loaded now and stored at the
-        // end so the loads overlap the counting and the scatter
-        float shr = 0.0f;
-        {
-            const int r = (tid - kRecHead) / kG, jj = (tid - kRecHead) % kG;
-            if (tid >= kRecHead && tid < kRecWords && r < S.nslots && jj < m)
-                shr = __ldg(shift_tab + (int64_t)S.cellOf[r] * m + jj);
-        }
-        int sl[kGrpVPT];
-#pragma unroll
-        for (int r = 0; r < kGrpVPT; ++r) {
-            const int v = tid + r * kGrpThreads;
-            const int s = val[r] ? (int)S.tslot[S.vt[v]] : -1;
-            sl[r] = s;
-            const unsigned mm = __match_any_sync(0xffffffffu, s);
-            if (s >= 0 && lane == __ffs(mm) - 1) atomicAdd(&S.off[s], __popc(mm));
-        }
-        for (int i = tid; i < kHashN; i += kGrpThreads) S.tab[i] = -1;  // empty again for the next brick
-        __syncthreads();
-        {
-            const int ns = S.nslots;
-            int a[2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) a[r] = 2 * tid + r < ns ? S.off[2 * tid + r] : 0;
-            int total;
-            int ea = grp_scan(S, 1, a[0] + a[1], total);
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int i = 2 * tid + r;
-                if (i < ns) {
-                    S.off[i] = ea;
-                    S.cur[i] = ea;
-                    atomicAdd(&cnt[S.cellOf[i]], (unsigned long long)a[r]);
-                    atomicOr(&S.mask[ea >> 5], 1u << (ea & 31));
-                }
-                ea += a[r];
-            }
-            if (tid == 0) S.nvalid = total;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kGrpVPT; ++r) {
-            const int v = tid + r * kGrpThreads;
-            const int s = sl[r];
-            const unsigned mm = __match_any_sync(0xffffffffu, s);
-            const int leader = __ffs(mm) - 1;
-            int base = 0;
-            if (s >= 0 && lane == leader) base = atomicAdd(&S.cur[s], __popc(mm));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (s >= 0) S.sorted[base + __popc(mm & lanemask_lt())] = (uint16_t)v;
-        }
-        __syncthreads();
-        // positions at and beyond the valid count are never read; they are written anyway so the
-        // record is one full 1 KB line
-        reinterpret_cast<uint32_t *>(ord.perm + brick * GV)[tid] = reinterpret_cast<const uint32_t *>(S.sorted)[tid];
-        if (tid < kRecHead) {
-            ord.rec[brick * kRecWords + tid] = tid < 16 ? S.mask[tid] : tid == 16 ? (uint32_t)S.nvalid
-                                                                      : tid == 17 ? (uint32_t)S.nslots : 0u;
-        } else if (tid < kRecWords) {
-            ord.rec[brick * kRecWords + tid] = __float_as_uint(shr);
-        }
-        __syncthreads();  // the next brick reuses the shared state
+        __syncwarp();
+        // positions at and beyond the valid count are never read; the whole 1 KB line is written
+        const uint4 *src = reinterpret_cast<const uint4 *>(sorted);
+        uint4 *dst = reinterpret_cast<uint4 *>(ord.perm + brick * GV);
+        dst[lane] = src[lane];
+        dst[lane + 32] = src[lane + 32];
+        for (int i = lane; i < kRecWords; i += 32) ord.rec[brick * kRecWords + i] = rec[i];
+        __syncwarp();  // the staging is reused by the next brick
     }
 }
 
@@ -1138,8 +1023,9 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
         if (n_aux > 0)
             shift_table_kernel<<<grid_for((int64_t)max_sites * n_aux, 256, kSMs * 4), 256, 0, s>>>(
                 p, site_pos, n_sites_dev, max_sites, w.shift);
-        // every brick's voxels grouped by cell (and the cells' voxel counts), many bricks per SM
-        group_bricks_kernel<<<(int)(nbricks < (int64_t)nsm * 8 ? nbricks : (int64_t)nsm * 8), kGrpThreads, 0, s>>>(
+        // every brick's voxels grouped by cell (and the cells' voxel counts), a warp per brick
+        const int64_t gblocks = (nbricks + kGrpWarps - 1) / kGrpWarps;  // six CTAs per SM are resident
+        group_bricks_kernel<<<(int)(gblocks < (int64_t)nsm * 6 ? gblocks : (int64_t)nsm * 6), kGrpThreads, 0, s>>>(
             cell, d, max_sites, w.acc.cnt, w.shift, n_aux, w.ord);
         auto launch = [&](auto kern) {
             // two CTAs per SM, which needs the largest shared-memory carveout
