@@ -611,7 +611,9 @@ constexpr uint32_t kCoIdesc = umma_idesc_bf16_f32(128, 32);
 struct CoSmem {
     unsigned char a[kCoChunks * kCoChunkBytes + kCoSlack];  // tensor-core operands (first)
     float mean_f[kCoGroup][kCovVars];
-    float tr[2][32][33];                     // lo.hi^T blocks for the transposition
+    float dmean[kCoGroup][kCovVars];         // mean - float(mean): the centring offset, exactly
+    float tr[2][32][33];                     // one cell's hi.hi^T and lo.hi^T, read from TMEM
+    uint16_t tri[kCovVars * (kCovVars + 1) / 2];  // (row << 8 | column) of each upper-triangle entry
     int64_t start[kCoGroup];                 // first sorted position of each cell of the group
     int32_t count[kCoGroup];
     int32_t chunk0[kCoGroup + 1];            // first chunk of each cell of the group
@@ -679,6 +681,11 @@ __global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t
         fence_mbar_init();
     }
     if (warp == 0) tmem_alloc(&S.tmem_base, kCoTmemCols);
+    // the upper triangle in its stored (row-major) order
+    for (int i = tid; i < m; i += kCoThreads) {
+        const int row0 = i * m - i * (i - 1) / 2;
+        for (int jj = i; jj < m; ++jj) S.tri[row0 + jj - i] = (uint16_t)(i << 8 | jj);
+    }
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
@@ -699,7 +706,9 @@ __global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t
         }
         for (int i = tid; i < nk * kCovVars; i += kCoThreads) {
             const int k = i / kCovVars, j = i % kCovVars;
-            S.mean_f[k][j] = j < m ? (float)mean[(int64_t)(g0 + k) * m + j] : 0.0f;
+            const double mu = j < m ? mean[(int64_t)(g0 + k) * m + j] : 0.0;
+            S.mean_f[k][j] = (float)mu;
+            S.dmean[k][j] = (float)(mu - (double)(float)mu);
         }
         __syncthreads();
         if (tid == 0) {
@@ -762,41 +771,30 @@ __global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t
             tc_fence_after_sync();
         }
         if (failed) break;
-        // epilogue: warps 0 / 4 read hi.hi^T (lanes 0..31), warps 1 / 5 lo.hi^T (lanes 32..63);
-        // the two warp pairs take alternate cells; each co-moment is written once
-        const int pair = warp >> 2, wq = warp & 3;
-        if (wq < 2) {
-            for (int k = pair; k < nk; k += 2) {
-                const int64_t c = g0 + k;
-                const int64_t n = S.count[k];
+        // epilogue, one cell at a time: warp 0 reads hi.hi^T (TMEM lanes 0..31) and warp 1 lo.hi^T
+        // (lanes 32..63) into shared memory; then every thread writes entries of the upper
+        // triangle in their stored order (coalesced), C_ij = hi.hi^T + lo.hi^T + (lo.hi^T)^T
+        // - n d_i d_j in FP32 (d = the centring offset), the diagonal from the moments' M2
+        for (int k = 0; k < nk; ++k) {
+            const int64_t c = g0 + k;
+            const int32_t n = S.count[k];
+            if (warp < 2 && n > 0) {
                 float v[32];
-                if (n > 0) tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)k * 32, v);
-                if (wq == 1 && n > 0) {
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)k * 32, v);
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) S.tr[pair][lane][jj] = v[jj];
-                }
-                if (pair == 0) named_bar_sync(2, 64); else named_bar_sync(3, 64);
-                if (wq == 0 && lane < m) {
-                    const int i = lane;
-                    const int64_t base = c * T + (int64_t)i * m - (int64_t)i * (i - 1) / 2 - i;
-                    const double mi = mean[c * m + i], di = mi - (double)(float)mi;
-#pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        if (jj < i || jj >= m) continue;
-                        double val = 0.0;
-                        if (n > 0) {
-                            if (jj == i) {
-                                val = m2[c * m + i];
-                            } else {
-                                const double mj = mean[c * m + jj], dj = mj - (double)(float)mj;
-                                val = (double)(v[jj] + S.tr[pair][i][jj] + S.tr[pair][jj][i]) - (double)n * di * dj;
-                            }
-                        }
-                        comom[base + jj] = val;
-                    }
-                }
-                if (pair == 0) named_bar_sync(2, 64); else named_bar_sync(3, 64);
+                for (int jj = 0; jj < 32; ++jj) S.tr[warp][lane][jj] = v[jj];
             }
+            __syncthreads();
+            for (int t = tid; t < T; t += kCoThreads) {
+                const int i = S.tri[t] >> 8, jj = S.tri[t] & 255;
+                double val = 0.0;
+                if (n > 0)
+                    val = i == jj ? m2[c * m + i]
+                                  : (double)(S.tr[0][i][jj] + S.tr[1][i][jj] + S.tr[1][jj][i] -
+                                             (float)n * S.dmean[k][i] * S.dmean[k][jj]);
+                comom[c * T + t] = val;
+            }
+            __syncthreads();
         }
         tc_fence_before_sync();
         __syncthreads();
