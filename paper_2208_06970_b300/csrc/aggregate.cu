@@ -583,7 +583,9 @@ __global__ void aggregate_finalize_kernel(AggAcc acc, const int32_t *n_sites_dev
 // C_ij = sum over the cell (x_i - mean_i)(x_j - mean_j), a grouped contraction X_c^T X_c over
 // the cells.  The voxels are first ordered by cell (a counting sort with the counts of the
 // moments pass), so each cell is contracted by exactly one CTA and its co-moments are written
-// once, with no atomics.  A CTA takes groups of kCoGroup consecutive cells from a work counter;
+// once, with no atomics.  A CTA takes groups of kCoGroup cells from a work counter, the cells in
+// the raster order of their site voxels, so cells that share cache lines (neighbours along x) are
+// gathered at about the same time and the lines are read from DRAM once;
 // each cell's voxels are gathered in 16-voxel chunks (the last one zero-padded), centred by
 // c = float(mean) of the cell, split d = hi + lo into two BF16 numbers (lo = the float remainder
 // rounded to BF16), and staged in the K-major canonical layout of the tensor core: a chunk holds
@@ -615,6 +617,7 @@ struct CoSmem {
     float tr[2][32][33];                     // one cell's hi.hi^T and lo.hi^T, read from TMEM
     uint16_t tri[kCovVars * (kCovVars + 1) / 2];  // (row << 8 | column) of each upper-triangle entry
     int64_t start[kCoGroup];                 // first sorted position of each cell of the group
+    int32_t cellid[kCoGroup];                // the group's cells
     int32_t count[kCoGroup];
     int32_t chunk0[kCoGroup + 1];            // first chunk of each cell of the group
     uint64_t mma_bar;
@@ -626,6 +629,16 @@ static_assert(3 * (kCoSmem + 1024) <= 228 * 1024, "three co-moment CTAs must fit
 
 __device__ __forceinline__ unsigned short bf16_bits(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// (site voxel, cell) pairs of the live cells, to be sorted into the co-moments' cell order
+__global__ void cell_order_keys_kernel(const int32_t *__restrict__ site_pos, const int32_t *n_sites_dev,
+                                       int32_t max_sites, uint32_t *key, uint32_t *val) {
+    const int32_t ns = min(*n_sites_dev, max_sites);
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ns; c += (int64_t)gridDim.x * blockDim.x) {
+        key[c] = (uint32_t)site_pos[c];
+        val[c] = (uint32_t)c;
+    }
 }
 
 // cell offsets of the voxel order: off[c] = counts of the cells before c (counts of rows
@@ -669,7 +682,8 @@ __global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t
                                                                    const double *__restrict__ mean,
                                                                    const double *__restrict__ m2,
                                                                    const int32_t *n_sites_dev, int32_t max_sites,
-                                                                   int32_t *work, double *comom, int32_t *status) {
+                                                                   const uint32_t *__restrict__ order, int32_t *work,
+                                                                   double *comom, int32_t *status) {
     extern __shared__ __align__(16) unsigned char co_smem_raw[];
     const uint32_t raw_addr = smem_u32(co_smem_raw);
     CoSmem &S = *reinterpret_cast<CoSmem *>(co_smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr));
@@ -700,13 +714,14 @@ __global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t
         if (g0 >= ns) break;
         const int nk = ns - g0 < kCoGroup ? ns - g0 : kCoGroup;
         if (tid < nk) {
-            const int32_t c = g0 + tid;
+            const int32_t c = (int32_t)order[g0 + tid];
+            S.cellid[tid] = c;
             S.start[tid] = off[c];
             S.count[tid] = (int32_t)count[c];
         }
         for (int i = tid; i < nk * kCovVars; i += kCoThreads) {
             const int k = i / kCovVars, j = i % kCovVars;
-            const double mu = j < m ? mean[(int64_t)(g0 + k) * m + j] : 0.0;
+            const double mu = j < m ? mean[(int64_t)order[g0 + k] * m + j] : 0.0;
             S.mean_f[k][j] = (float)mu;
             S.dmean[k][j] = (float)(mu - (double)(float)mu);
         }
@@ -776,7 +791,7 @@ __global__ void __launch_bounds__(kCoThreads, 3) covariance_kernel(const int32_t
         // triangle in their stored order (coalesced), C_ij = hi.hi^T + lo.hi^T + (lo.hi^T)^T
         // - n d_i d_j in FP32 (d = the centring offset), the diagonal from the moments' M2
         for (int k = 0; k < nk; ++k) {
-            const int64_t c = g0 + k;
+            const int64_t c = S.cellid[k];
             const int32_t n = S.count[k];
             if (warp < 2 && n > 0) {
                 float v[32];
@@ -896,6 +911,8 @@ struct AggWs {
     int64_t *off;     // [max_sites + 1]: first position of each cell in perm
     int32_t *cur;     // [max_sites]: scatter cursors
     int32_t *work;    // co-moment work counter
+    uint32_t *okey, *oval;  // cells by the raster position of their site voxel (co-moment order)
+    void *rtemp;      // radix sort temporaries
     void *scan;       // scan temporaries
 };
 
@@ -918,6 +935,9 @@ AggWs carve_agg(void *ws, size_t bytes, Dims d, int32_t max_sites, int32_t m, si
     w.off = c.take<int64_t>((int64_t)max_sites + 1);
     w.cur = c.take<int32_t>(max_sites > 0 ? max_sites : 1);
     w.work = c.take<int32_t>(1);
+    w.okey = c.take<uint32_t>(max_sites > 0 ? max_sites : 1);
+    w.oval = c.take<uint32_t>(max_sites > 0 ? max_sites : 1);
+    w.rtemp = c.take<char>(radix_temp_bytes(max_sites > 0 ? max_sites : 1));
     w.scan = c.take<char>(scan_temp_bytes((int64_t)max_sites + 1));
     *need = c.used;
     return w;
@@ -1073,8 +1093,13 @@ extern "C" lsrvt_status lsrvt_aggregate(const int32_t *cell, const float *const 
         // starts later.
         const int occ = 3;
         const int nsm2 = stream_sms(s);
+        cell_order_keys_kernel<<<grid_for(max_sites, 256, kSMs * 4), 256, 0, s>>>(site_pos, n_sites_dev, max_sites,
+                                                                                   w.okey, w.oval);
+        int bits = 1;
+        while (bits < 32 && (int64_t(1) << bits) < n) ++bits;
+        radix_sort_pairs(w.okey, w.oval, max_sites, n_sites_dev, bits, w.rtemp, s);
         covariance_kernel<<<nsm2 * occ, kCoThreads, kCoSmem, s>>>(w.perm, w.off, p, out.count, out.mean, out.m2,
-                                                                   n_sites_dev, max_sites, w.work, out.comom,
+                                                                   n_sites_dev, max_sites, w.oval, w.work, out.comom,
                                                                    status_dev);
     }
     return launch_status();
