@@ -684,6 +684,53 @@ def forms_arm(args, dev):
     return out
 
 
+def serve_config5(args, dev):
+    """The served form on the request stream as specified: args.requests Poisson requests at
+    50/s, sides U{64..512} per axis, 2-10 isovalues, 0-16 aux variables, 10-30 Lloyd iterations,
+    512 voxels per site.  Each request's field and variables are cut from resident 512^3 blob
+    volumes when it is admitted (on the slot's stream, so every arm pays for it).  Arms: the
+    plain form (one request at a time, FIFO), the served form (args.slots slots, FIFO) and
+    shortest-work-first; each arm runs args.repeats times.  Prints one JSON line."""
+    import paper_2208_06970_b300 as pkg
+    import workloads
+    from paper_2208_06970_b300 import runtime
+    pool = workloads.CropPool(side=512, n_aux=16, seed=7, device=dev)
+    reqs = workloads.request_stream(n_requests=args.requests, rate=50.0, seed=5, lo=64, hi=512)
+
+    def make_job(r):
+        f, aux = pool.request_data(r)
+        return dict(field=f, iso=r["iso"], voxels_per_site=r["voxels_per_site"], n_iters=r["n_iters"], aux=aux,
+                    gamma=0, strat_block=16, rng_seed=r["seed"], n_bins=32)
+
+    for k, r in enumerate(reqs):
+        r["k"] = k
+        n = int(np.prod(r["dims"]))
+        r["ws_bytes"], rest = runtime.request_bytes_split(n, r["n_aux"], 512, 32, dims=tuple(r["dims"]))
+        r["bytes"] = r["ws_bytes"] + rest
+        r["work"] = n * r["n_iters"]
+    arms = (("plain", 1, "fifo"), ("served", args.slots, "fifo"), ("served_sjf", args.slots, "sjf"))
+    runs = {name: [] for name, _, _ in arms}
+    for rep in range(args.repeats):
+        for name, slots, policy in arms:
+            srv = runtime.Server(n_slots=slots, hbm_budget=args.hbm_budget << 30, device=dev, policy=policy)
+            srv.serve([dict(reqs[0], arrival=0.0)], make_job)  # warm-up
+            torch.cuda.synchronize()
+            runs[name].append(runtime.latency_summary(srv.serve(reqs, make_job)))
+            del srv
+            torch.cuda.empty_cache()
+    summ = {}
+    for name, rs in runs.items():
+        thr = [r["throughput_req_s"] for r in rs]
+        summ[name] = dict(throughput_req_s=thr, mean_throughput=sum(thr) / len(thr), spread=max(thr) - min(thr),
+                          p50_ms=[r["p50_ms"] for r in rs], p99_ms=[r["p99_ms"] for r in rs],
+                          gvoxel_iters_s=[r["gvoxel_iters_s"] for r in rs])
+    vox_it = sum(r["work"] for r in reqs)
+    print(json.dumps(dict(form="served", requests=len(reqs), rate_per_s=50.0, sides="64..512", isovalues="2..10",
+                          aux="0..16", iters="10..30", slots=args.slots, hbm_budget_gib=args.hbm_budget,
+                          repeats=args.repeats, gvoxel_iters=vox_it / 1e9, data="synthetic: crops of 512^3 blob volumes",
+                          arms=summ)))
+
+
 def precision_setup(pkg, side, dev, m=32):
     """The precision form's inputs and labels: blob field (seed 4), 32 correlated variables,
     classify -> components -> seeds (512 voxels per site) -> 10 Lloyd iterations."""
@@ -852,6 +899,9 @@ def main():
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-hi", type=int, default=384)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-config5", action="store_true",
+                    help="only the served form on the specified request stream (sides 64..512), --repeats times")
+    ap.add_argument("--repeats", type=int, default=3)
     ap.add_argument("--hbm-budget", type=int, default=96, help="GiB admitted at once by the server")
     ap.add_argument("--prec-side", type=int, default=640, help="side of the precision-form workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
@@ -877,6 +927,11 @@ def main():
         return
     if args.profile_layout:
         profile_layout(args)
+        return
+    if args.serve_config5:
+        from paper_2208_06970_b300 import build
+        build.build()
+        serve_config5(args, torch.device("cuda", local_rank))
         return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))

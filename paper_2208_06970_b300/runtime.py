@@ -263,7 +263,9 @@ class Server:
                         cv.wait(timeout=max(min(wait, 0.05), 0.0005) if wait > 0 else 0.01)
                 try:
                     admitted = time.perf_counter() - t0
-                    job = make_job(requests[i])
+                    # the job's inputs are built on the slot's stream, ahead of its kernels
+                    with torch.cuda.stream(slot.stream):
+                        job = make_job(requests[i])
                     out, done = _run(slot, job)
                     done.synchronize()
                     finished = time.perf_counter() - t0

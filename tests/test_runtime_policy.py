@@ -1,6 +1,7 @@
 """Admission choice of the continuous-batching server (host logic, no GPU): arrival, HBM
 budget and the FIFO / shortest-job-first policies."""
 import pytest
+import torch
 
 from paper_2208_06970_b300.runtime import pick_next
 
@@ -44,3 +45,23 @@ def test_an_idle_server_admits_an_oversized_request():
 def test_unknown_policy():
     with pytest.raises(ValueError):
         pick_next([0], _reqs(), 1.0, 0, 100, 0, "lifo")
+
+
+def test_crop_pool_cuts_each_request_inside_the_masters():
+    """The served stream's inputs are sub-volumes of resident masters: every request gets its
+    own dims and number of variables, at a seeded offset that keeps the cut inside the masters,
+    and the same request always gets the same data."""
+    import workloads
+    pool = workloads.CropPool(side=24, n_aux=16, seed=7, device="cpu")
+    reqs = workloads.request_stream(n_requests=30, rate=50.0, seed=5, lo=4, hi=24)
+    for r in reqs:
+        f, aux = pool.request_data(r)
+        nx, ny, nz = r["dims"]
+        assert f.shape == (nz, ny, nx) and f.is_contiguous()
+        assert len(aux) == r["n_aux"] and all(a.shape == f.shape for a in aux)
+        f2, _ = pool.request_data(r)
+        assert torch.equal(f, f2)
+        # the cut is a window of the master: find it by its first voxel's row
+        assert any(torch.equal(f, pool.field[z:z + nz, y:y + ny, x:x + nx])
+                   for z in range(24 - nz + 1) for y in range(24 - ny + 1) for x in range(24 - nx + 1)
+                   if pool.field[z, y, x] == f[0, 0, 0])

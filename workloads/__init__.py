@@ -187,6 +187,26 @@ def block_batch(n_blocks=64, seed=3, lo=32, hi=256, device="cpu"):
     return out
 
 
+class CropPool:
+    """Resident master volumes a request stream is cut from: one blob field and `n_aux` blob
+    variables of side `side` (the served requests are blocks of one large simulation, each a
+    sub-volume at a seeded offset).  `request_data(req)` copies a request's field and variables
+    out of the masters on the current stream (a few device copies, no host work), so a server
+    can build a request's inputs when it admits it."""
+
+    def __init__(self, side=512, n_aux=16, seed=7, device="cpu"):
+        self.side = side
+        self.field = blob_field((side, side, side), seed, device)
+        self.aux = [blob_field((side, side, side), seed + 1 + j, device, n_blobs=8, noise=0.1) for j in range(n_aux)]
+
+    def request_data(self, req):
+        nx, ny, nz = req["dims"]
+        rng = np.random.default_rng(req["seed"])
+        x0, y0, z0 = (int(rng.integers(0, self.side - n + 1)) for n in (nx, ny, nz))
+        cut = lambda v: v[z0:z0 + nz, y0:y0 + ny, x0:x0 + nx].contiguous()
+        return cut(self.field), [cut(self.aux[j]) for j in range(req["n_aux"])]
+
+
 def request_stream(n_requests=1000, rate=50.0, seed=5, lo=64, hi=512):
     """Poisson arrivals (exponential gaps, mean rate per second) of decomposition requests.
     Returns descriptors only (fields are generated by the caller with blob_field)."""
