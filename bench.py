@@ -708,11 +708,17 @@ def serve_config5(args, dev):
         r["ws_bytes"], rest = runtime.request_bytes_split(n, r["n_aux"], 512, 32, dims=tuple(r["dims"]))
         r["bytes"] = r["ws_bytes"] + rest
         r["work"] = n * r["n_iters"]
-    arms = (("plain", 1, "fifo"), ("served", args.slots, "fifo"), ("served_sjf", args.slots, "sjf"))
+    # size-aware filling: requests up to the stream's lower quartile of work may run beside the
+    # large ones, on a slot with a fifth of the SMs
+    fill_work = sorted(r["work"] for r in reqs)[len(reqs) // 4]
+    all_arms = {"plain": (1, "fifo"), "served": (args.slots, "fifo"), "served_sjf": (args.slots, "sjf"),
+                "served_fill": (args.slots, "fill")}
+    arms = [(a, all_arms[a][0], all_arms[a][1]) for a in args.arms.split(",")]
     runs = {name: [] for name, _, _ in arms}
     for rep in range(args.repeats):
         for name, slots, policy in arms:
-            srv = runtime.Server(n_slots=slots, hbm_budget=args.hbm_budget << 30, device=dev, policy=policy)
+            srv = runtime.Server(n_slots=slots, hbm_budget=args.hbm_budget << 30, device=dev, policy=policy,
+                                 fill_work=fill_work, fill_share=20)
             srv.serve([dict(reqs[0], arrival=0.0)], make_job)  # warm-up
             torch.cuda.synchronize()
             runs[name].append(runtime.latency_summary(srv.serve(reqs, make_job)))
@@ -728,6 +734,7 @@ def serve_config5(args, dev):
     print(json.dumps(dict(form="served", requests=len(reqs), rate_per_s=50.0, sides="64..512", isovalues="2..10",
                           aux="0..16", iters="10..30", slots=args.slots, hbm_budget_gib=args.hbm_budget,
                           repeats=args.repeats, gvoxel_iters=vox_it / 1e9, data="synthetic: crops of 512^3 blob volumes",
+                          fill_work=fill_work,
                           arms=summ)))
 
 
@@ -902,6 +909,8 @@ def main():
     ap.add_argument("--serve-config5", action="store_true",
                     help="only the served form on the specified request stream (sides 64..512), --repeats times")
     ap.add_argument("--repeats", type=int, default=3)
+    ap.add_argument("--arms", default="plain,served,served_sjf,served_fill",
+                    help="arms of --serve-config5 (plain, served, served_sjf, served_fill)")
     ap.add_argument("--hbm-budget", type=int, default=96, help="GiB admitted at once by the server")
     ap.add_argument("--prec-side", type=int, default=640, help="side of the precision-form workload")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision form")

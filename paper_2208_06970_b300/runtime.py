@@ -173,17 +173,21 @@ class GraphBatch:
             check_status(out["status"], "block %d" % k)
 
 
-def pick_next(pending, requests, now, used, budget, active, policy="fifo"):
+def pick_next(pending, requests, now, used, budget, active, policy="fifo", max_work=None):
     """Admission choice of the server.  pending: indices not yet admitted, in arrival order.
     A request is eligible once it has arrived and its estimated device bytes fit in the budget
     left (any request fits when nothing runs, so the server always progresses).  'fifo' admits
     the earliest arrival and waits for it when it does not fit yet; 'sjf' admits the eligible
     request with the least work (requests[i]['work'], else its bytes), earliest arrival first on
-    ties.  Returns the chosen index or None."""
+    ties.  With max_work, only requests whose work is at most max_work are considered (the
+    earliest of them for 'fifo': small requests may overtake large ones).  Returns the chosen
+    index or None."""
     def fits(i):
         return used + (requests[i].get("bytes") or 0) <= budget or active == 0
 
     arrived = [i for i in pending if requests[i]["arrival"] <= now]
+    if max_work is not None:
+        arrived = [i for i in arrived if requests[i].get("work", requests[i].get("bytes") or 0) <= max_work]
     if not arrived:
         return None
     if policy == "fifo":
@@ -200,14 +204,23 @@ class Server:
     """Continuous batching: requests are admitted whenever a slot is free and their estimated
     device bytes fit in the remaining HBM budget -- in arrival order ('fifo') or smallest work
     first among those that have arrived ('sjf'); admitted requests run concurrently on the
-    slots' streams.  Latency = completion - arrival (host clock)."""
+    slots' streams.  'fill' is size-aware: slot 0 takes every request in arrival order with all
+    the SMs, the other slots take only small requests (work <= fill_work voxel-iterations, the
+    earliest first) with a small SM share (fill_share percent), so they run in the gaps of the
+    large ones.  Latency = completion - arrival (host clock)."""
 
-    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda", share=None, policy="fifo"):
-        share = default_share(n_slots) if share is None else share
-        self.slots = [Slot(device, share) for _ in range(n_slots)]
-        self.budget = int(hbm_budget)
-        if policy not in ("fifo", "sjf"):
+    def __init__(self, n_slots=4, hbm_budget=64 << 30, device="cuda", share=None, policy="fifo", fill_work=None,
+                 fill_share=20):
+        if policy not in ("fifo", "sjf", "fill"):
             raise ValueError("unknown admission policy %r" % (policy,))
+        if policy == "fill":
+            shares = [100] + [fill_share] * (n_slots - 1)
+            self.max_work = [None] + [fill_work] * (n_slots - 1)
+        else:
+            shares = [default_share(n_slots) if share is None else share] * n_slots
+            self.max_work = [None] * n_slots
+        self.slots = [Slot(device, sh) for sh in shares]
+        self.budget = int(hbm_budget)
         self.policy = policy
 
     def serve(self, requests, make_job, keep_outputs=False):
@@ -247,7 +260,8 @@ class Server:
                         # per-request needs on this slot, in the form pick_next reads
                         view = {i: dict(requests[i], bytes=need_on(slot, i)) for i in pending}
                         i = pick_next(pending, view, now, state["used"] + state["grow"] + resident(), self.budget,
-                                      state["active"], self.policy)
+                                      state["active"], "sjf" if self.policy == "sjf" else "fifo",
+                                      self.max_work[slot_id])
                         if i is not None:
                             pending.remove(i)
                             grow = max(0, min(requests[i].get("ws_bytes") or 0, requests[i].get("bytes") or 0)

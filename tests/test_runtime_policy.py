@@ -65,3 +65,14 @@ def test_crop_pool_cuts_each_request_inside_the_masters():
         assert any(torch.equal(f, pool.field[z:z + nz, y:y + ny, x:x + nx])
                    for z in range(24 - nz + 1) for y in range(24 - ny + 1) for x in range(24 - nx + 1)
                    if pool.field[z, y, x] == f[0, 0, 0])
+
+
+def test_fill_slots_take_only_small_requests_and_may_overtake():
+    r = _reqs()  # work 800, 100, 50, 1
+    # a fill slot (max_work 100) skips the large head and takes the earliest small request
+    assert pick_next([0, 1, 2, 3], r, 1.0, 0, 100, 1, "fifo", max_work=100) == 1
+    assert pick_next([0, 2, 3], r, 1.0, 0, 100, 1, "fifo", max_work=100) == 2
+    # nothing small has arrived yet
+    assert pick_next([0, 3], r, 1.0, 0, 100, 1, "fifo", max_work=100) is None
+    # the main slot keeps arrival order
+    assert pick_next([0, 1, 2, 3], r, 1.0, 0, 100, 1, "fifo") == 0
