@@ -542,6 +542,22 @@ __device__ __forceinline__ unsigned long long chamfer(int dx, int dy, int dz) {
            (unsigned long long)c * kWCorner;
 }
 
+// The same distance in 32-bit arithmetic, for differences below 2048 per axis (the whole sum
+// stays below 2^28): |d| sorted by three compare-exchanges, then a W1 + b (W2 - W1) + c (W3 - W2)
+// for a >= b >= c.
+__device__ __forceinline__ unsigned long long chamfer_small(int dx, int dy, int dz) {
+    const unsigned a = abs(dx), b = abs(dy), c = abs(dz);
+    const unsigned hi = max(a, b), lo = min(a, b);
+    const unsigned mid = max(lo, c), low = min(lo, c);
+    const unsigned top = max(hi, mid), mid2 = min(hi, mid);
+    return top * kWFace + mid2 * (kWEdge - kWFace) + low * (kWCorner - kWEdge);
+}
+
+template <bool kSmall>
+__device__ __forceinline__ unsigned long long chamfer_t(int dx, int dy, int dz) {
+    return kSmall ? chamfer_small(dx, dy, dz) : chamfer(dx, dy, dz);
+}
+
 // unsigned division, 32-bit when both operands fit (the common case for volumes <= 2048^3)
 __device__ __forceinline__ unsigned long long udiv(unsigned long long a, unsigned long long b) {
     if (((a | b) >> 32) == 0) return (unsigned)a / (unsigned)b;
@@ -1068,6 +1084,7 @@ __global__ void __launch_bounds__(kCellThreads) cell_list_kernel(Dims d, CoarseG
 // centre), and every voxel scans its band's segment until C(centre, s) - R exceeds its
 // best (triangle inequality; R = the brick's chamfer radius).  Keys are exact where one
 // shortest chamfer path to the winner stays in band; elsewhere +inf and the brick is queued.
+template <bool kSmall>
 __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__restrict__ band,
                                                             const uint8_t *__restrict__ clr,
                                                             const uint32_t *__restrict__ emask, Dims d, BrickGeom bg,
@@ -1252,8 +1269,8 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
 #pragma unroll
                     for (int j = 0; j < kVPT; ++j) {
                         if (!act[j]) continue;
-                        const unsigned long long cd = chamfer(c.y - xv[j], c.z - yv[j], cz - zv[j]);
-                        if (cd >= kInf32) continue;
+                        const unsigned long long cd = chamfer_t<kSmall>(c.y - xv[j], c.z - yv[j], cz - zv[j]);
+                        if (!kSmall && cd >= kInf32) continue;
                         const unsigned long long k2 = (cd << 32) | (unsigned)c.x;
                         if (k2 < bestv[j]) { bestv[j] = k2; bidxv[j] = (int)(e & 0xFFF); }
                     }
@@ -1270,8 +1287,9 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
                         atomicAdd(&g_phase[11], 1ULL);
 #endif
                         const int4 c = cs[(unsigned)(e & 0xFFF)];
-                        const unsigned long long cd = chamfer(c.y - xv[j], c.z - yv[j], (c.w & 0xFFFFFF) - zv[j]);
-                        if (cd >= kInf32) continue;
+                        const unsigned long long cd =
+                            chamfer_t<kSmall>(c.y - xv[j], c.z - yv[j], (c.w & 0xFFFFFF) - zv[j]);
+                        if (!kSmall && cd >= kInf32) continue;
                         const unsigned long long k2 = (cd << 32) | (unsigned)c.x;
                         if (k2 < bestv[j]) { bestv[j] = k2; bidxv[j] = (int)(e & 0xFFF); }
                     }
@@ -2190,12 +2208,20 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     }
     ++tag;
     int nb_cfi = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cfi, cfi_kernel, kRelaxThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cfi, cfi_kernel<true>, kRelaxThreads, 0);
     if (nb_cfi < 1) nb_cfi = 1;
     int cgrid = (int)(nbricks < (int64_t)sms * nb_cfi ? nbricks : (int64_t)sms * nb_cfi);
-    cfi_kernel<<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count, w.fine_off,
-                                               w.fine_cand, w.key, w.list[0], w.counters + 1, w.flags, w.xmask,
-                                               w.hasunk, tag, up, chk, WarmStart{warm, w.msteps});
+    // differences of coordinates below 2048 per axis: the scan's distances in 32-bit arithmetic
+    if (d.nx <= 2048 && d.ny <= 2048 && d.nz <= 2048)
+        cfi_kernel<true><<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count,
+                                                         w.fine_off, w.fine_cand, w.key, w.list[0], w.counters + 1,
+                                                         w.flags, w.xmask, w.hasunk, tag, up, chk,
+                                                         WarmStart{warm, w.msteps});
+    else
+        cfi_kernel<false><<<cgrid, kRelaxThreads, 0, s>>>(band, w.clr, w.emask, d, bg, cg, w.cell_list, w.cell_count,
+                                                          w.fine_off, w.fine_cand, w.key, w.list[0], w.counters + 1,
+                                                          w.flags, w.xmask, w.hasunk, tag, up, chk,
+                                                          WarmStart{warm, w.msteps});
     check_paths_kernel<<<sms * 16, 256, 0, s>>>(band, w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
                                                  tag, w.list[0], w.counters + 1, chk, up);
 #ifdef LSRVT_DEBUG
