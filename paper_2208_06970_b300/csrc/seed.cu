@@ -62,6 +62,25 @@ __device__ int load_sort_block(const int32_t *__restrict__ comp, Dims d, BlockGe
     return npow2;
 }
 
+// The component of block b if every voxel of it lies inside the volume and in that one component
+// (the common case away from band boundaries), else -1.  Such a block is one stratum whose
+// voxels in (component, index) order are the block's own linear order, so the callers skip the
+// sort.  All threads of the CTA call it (it ends with a barrier).
+__device__ int32_t uniform_block(const int32_t *__restrict__ comp, Dims d, BlockGeom g, int64_t b) {
+    const int sb = g.sb;
+    const int bx = (int)(b % g.nbx), by = (int)((b / g.nbx) % g.nby), bz = (int)(b / ((int64_t)g.nbx * g.nby));
+    const int x0 = bx * sb, y0 = by * sb, z0 = bz * sb;
+    const bool inside = x0 + sb <= d.nx && y0 + sb <= d.ny && z0 + sb <= d.nz;
+    const int32_t c0 = inside ? __ldg(comp + x0 + (int64_t)d.nx * (y0 + (int64_t)d.ny * z0)) : -1;
+    bool same = inside && c0 >= 0;
+    const int nvox = sb * sb * sb;
+    for (int i = threadIdx.x; i < nvox && same; i += blockDim.x) {
+        const int lx = i % sb, ly = (i / sb) % sb, lz = i / (sb * sb);
+        same = __ldg(comp + (x0 + lx) + (int64_t)d.nx * ((y0 + ly) + (int64_t)d.ny * (z0 + lz))) == c0;
+    }
+    return __syncthreads_and(same) ? c0 : -1;
+}
+
 __device__ __forceinline__ int64_t local_to_global(int li, Dims d, BlockGeom g, int64_t b) {
     int sb = g.sb;
     int bx = (int)(b % g.nbx), by = (int)((b / g.nbx) % g.nby), bz = (int)(b / ((int64_t)g.nbx * g.nby));
@@ -81,6 +100,10 @@ __global__ void __launch_bounds__(kSeedThreads) seed_block_count_kernel(const in
     __shared__ int cnt;
     int64_t nblocks = (int64_t)g.nbx * g.nby * g.nbz;
     for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        if (uniform_block(comp, d, g, b) >= 0) {
+            if (threadIdx.x == 0) blk_cnt[b] = 1;
+            continue;
+        }
         if (threadIdx.x == 0) cnt = 0;
         int npow2 = load_sort_block(comp, d, g, b, keys);
         int c = 0;
@@ -120,6 +143,40 @@ __global__ void __launch_bounds__(kSeedThreads) seed_block_emit_kernel(const int
     int64_t nblocks = (int64_t)g.nbx * g.nby * g.nbz;
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const int32_t cu = uniform_block(comp, d, g, b);
+        if (cu >= 0) {
+            // one stratum: all sb^3 voxels, mass = the sum of their weights
+            const int nvox = g.sb * g.sb * g.sb;
+            unsigned long long qs = 0;
+            if (q)
+                for (int i = threadIdx.x; i < nvox; i += blockDim.x) qs += q[local_to_global(i, d, g, b)];
+            else
+                for (int i = threadIdx.x; i < nvox; i += blockDim.x) qs += 1;
+            qs = __reduce_add_sync(0xffffffffu, (unsigned)qs);  // at most 4096 x 65535 < 2^32
+            if (lane == 0) warp_q[w] = (uint32_t)qs;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint64_t mm = 0;
+                for (int k2 = 0; k2 < nw; ++k2) mm += warp_q[k2];
+                const int64_t pos = blk_off[b];
+                if (pos < max_rec) {
+                    rec.comp[pos] = (uint32_t)cu;
+                    rec.idx[pos] = (uint32_t)pos;
+                    rec.block[pos] = (int32_t)b;
+                    rec.k[pos] = nvox;
+                    rec.m[pos] = mm;
+                }
+                if (cu < max_comp) {
+                    atomicAdd((unsigned long long *)&comp_mass[cu], (unsigned long long)mm);
+                    atomicAdd((unsigned long long *)&comp_cnt[cu], (unsigned long long)nvox);
+                    atomicAdd((unsigned long long *)&comp_nstr[cu], 1ULL);
+                }
+                atomicAdd(&totals[0], (unsigned long long)nvox);
+                atomicAdd(&totals[1], (unsigned long long)mm);
+            }
+            __syncthreads();
+            continue;
+        }
         int npow2 = load_sort_block(comp, d, g, b, keys);
         // block scan over sorted positions: prefix of q and numbering of run heads
         uint32_t qcarry = 0;
@@ -344,9 +401,32 @@ __global__ void __launch_bounds__(kSeedThreads) seed_place_kernel(const int32_t 
     __shared__ unsigned long long keys[kMaxBlockVox];
     int64_t nblocks = (int64_t)g.nbx * g.nby * g.nbz;
     for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
-        int npow2 = load_sort_block(comp, d, g, b, keys);
         int64_t off = blk_off[b];
         uint64_t hb = seed ^ splitmix64((uint64_t)b);
+        const int32_t cu = uniform_block(comp, d, g, b);
+        if (cu >= 0) {
+            // one stratum in the block's linear order: the voxel of rank r is local index r
+            const int64_t r = off;
+            if (r < max_rec) {
+                const int64_t k = rec_k[r];
+                const uint32_t pos = inv[r];
+                const int64_t n_b = nb[pos], so = site_off[pos];
+                for (int64_t j = threadIdx.x; j < n_b; j += blockDim.x) {
+                    uint64_t lo = (uint64_t)j * (uint64_t)k / (uint64_t)n_b;
+                    uint64_t hi = (uint64_t)(j + 1) * (uint64_t)k / (uint64_t)n_b;
+                    uint64_t h2 = splitmix64(hb + (uint64_t)j);
+                    uint64_t rank = lo + h2 % (hi - lo);
+                    int64_t sid = so + j;
+                    if (sid < max_sites) {
+                        site_pos[sid] = (int32_t)local_to_global((int)rank, d, g, b);
+                        site_comp[sid] = cu;
+                    }
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        int npow2 = load_sort_block(comp, d, g, b, keys);
         // one warp per run head found by scanning positions
         int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         // runs: enumerate heads in order; count heads before each head with a running scan
