@@ -114,35 +114,54 @@ __device__ void gunion(int32_t *L, int32_t a, int32_t b, int32_t *status) {
     set_status(status, LSRVT_ERR_TIMEOUT);
 }
 
-// Unions across brick faces.  Two neighbouring one-band bricks of the same band are each one
-// component, so one voxel pair of their face (the face's first) joins them and the others skip.
+// Unions across the brick faces normal to one axis (0: x, 1: y, 2: z); grid rows take face
+// planes, threads the voxels of a plane.  Two neighbouring one-band bricks of the same band are
+// each one component, so one voxel pair of their face (the face's first) joins them and the
+// others skip -- decided from the brick summaries before any band byte is read.  Every index
+// fits 32 bits (volumes below 2^31 voxels).
+template <int kAxis>
 __global__ void ccl_face_kernel(const uint8_t *__restrict__ band, Dims d, const uint8_t *__restrict__ ub, int32_t *L,
                                 int32_t *status) {
-    int64_t n = d.n();
     const int nbx = (d.nx + BX - 1) / BX, nby = (d.ny + BY - 1) / BY;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t x = (int32_t)(v % d.nx);
-        int64_t r = v / d.nx;
-        int32_t y = (int32_t)(r % d.ny), z = (int32_t)(r / d.ny);
-        bool fx = x > 0 && (x % BX) == 0, fy = y > 0 && (y % BY) == 0, fz = z > 0 && (z % BZ) == 0;
-        if (!(fx || fy || fz)) continue;
-        uint8_t b = band[v];
-        if (b == kInvalidBand) continue;
-        const int bx = x / BX, by = y / BY, bz = z / BZ;
-        const uint8_t u0 = __ldg(ub + bx + (int64_t)nbx * (by + (int64_t)nby * bz));
-        // same one-band brick on the other side: only the face's first voxel pair unites them
-        auto skip = [&](int ox, int oy, int oz, bool first) {
-            if (u0 == kMixedBrick) return false;
-            const uint8_t u1 = __ldg(ub + (bx - ox) + (int64_t)nbx * ((by - oy) + (int64_t)nby * (bz - oz)));
-            return u1 == u0 && !first;
-        };
-        if (fx && band[v - 1] == b && !skip(1, 0, 0, (y % BY) == 0 && (z % BZ) == 0))
-            gunion(L, (int32_t)v, (int32_t)(v - 1), status);
-        if (fy && band[v - d.nx] == b && !skip(0, 1, 0, (x % BX) == 0 && (z % BZ) == 0))
-            gunion(L, (int32_t)v, (int32_t)(v - d.nx), status);
-        if (fz && band[v - (int64_t)d.nx * d.ny] == b && !skip(0, 0, 1, (x % BX) == 0 && (y % BY) == 0))
-            gunion(L, (int32_t)v, (int32_t)(v - (int64_t)d.nx * d.ny), status);
+    constexpr int bw = kAxis == 0 ? BX : (kAxis == 1 ? BY : BZ);
+    const int na = kAxis == 0 ? d.nx : (kAxis == 1 ? d.ny : d.nz);
+    const int nplanes = (na - 1) / bw;  // faces at bw, 2 bw, ... below na
+    const int nu = kAxis == 0 ? d.ny : d.nx;  // in-plane extents (u fastest)
+    const int nw = kAxis == 2 ? d.ny : d.nz;
+    const int psize = nu * nw;
+    const int32_t sa = kAxis == 0 ? 1 : (kAxis == 1 ? d.nx : d.nx * d.ny);  // stride along the axis
+    for (int pl = blockIdx.y; pl < nplanes; pl += gridDim.y) {
+        const int a = (pl + 1) * bw;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < psize; i += gridDim.x * blockDim.x) {
+            const int u = i % nu, w = i / nu;
+            const int x = kAxis == 0 ? a : u, y = kAxis == 1 ? a : (kAxis == 0 ? u : w), z = kAxis == 2 ? a : w;
+            const int bx = x / BX, by = y / BY, bz = z / BZ;
+            const uint8_t u0 = __ldg(ub + bx + nbx * (by + nby * bz));
+            const bool first = kAxis == 0 ? (y % BY == 0 && z % BZ == 0)
+                                          : (kAxis == 1 ? (x % BX == 0 && z % BZ == 0) : (x % BX == 0 && y % BY == 0));
+            if (u0 != kMixedBrick && !first) {
+                const int ob = (bx - (kAxis == 0)) + nbx * ((by - (kAxis == 1)) + nby * (bz - (kAxis == 2)));
+                if (__ldg(ub + ob) == u0) continue;
+            }
+            const int32_t v = x + d.nx * (y + d.ny * z);
+            const uint8_t b = band[v];
+            if (b == kInvalidBand || band[v - sa] != b) continue;
+            gunion(L, v, v - sa, status);
+        }
     }
+}
+
+void ccl_faces(const uint8_t *band, Dims d, const uint8_t *ub, int32_t *L, int32_t *status, cudaStream_t s) {
+    auto launch = [&](auto kern, int na, int bw, int64_t psize) {
+        const int nplanes = (na - 1) / bw;
+        if (nplanes <= 0) return;
+        const int gx = (int)((psize + 255) / 256 < 4096 ? (psize + 255) / 256 : 4096);
+        const int gy = nplanes < 65535 ? nplanes : 65535;
+        kern<<<dim3(gx, gy), 256, 0, s>>>(band, d, ub, L, status);
+    };
+    launch(ccl_face_kernel<0>, d.nx, BX, (int64_t)d.ny * d.nz);
+    launch(ccl_face_kernel<1>, d.ny, BY, (int64_t)d.nx * d.nz);
+    launch(ccl_face_kernel<2>, d.nz, BZ, (int64_t)d.nx * d.ny);
 }
 
 __global__ void ccl_compress_kernel(int32_t *L, int64_t n) {
@@ -311,7 +330,7 @@ extern "C" lsrvt_status lsrvt_label_components(const uint8_t *band, lsrvt_dims d
     int64_t nchunks = (n + kChunk - 1) / kChunk;
     dim3 bgrid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
     ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L, w.ub);
-    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.ub, w.L, status_dev);
+    ccl_faces(band, d, w.ub, w.L, status_dev, s);
     ccl_compress_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.L, n);
     int warps = 8;
     int cgrid = (int)((nchunks + warps - 1) / warps);
@@ -392,7 +411,7 @@ extern "C" lsrvt_status lsrvt_label_components_static(const uint8_t *band, lsrvt
     int64_t nchunks = (n + kChunk - 1) / kChunk;
     dim3 bgrid((d.nx + BX - 1) / BX, (d.ny + BY - 1) / BY, (d.nz + BZ - 1) / BZ);
     ccl_brick_kernel<<<bgrid, BV, 0, s>>>(band, d, w.L, w.ub);
-    ccl_face_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(band, d, w.ub, w.L, status_dev);
+    ccl_faces(band, d, w.ub, w.L, status_dev, s);
     ccl_compress_kernel<<<grid_for(n, 256, kSMs * 16), 256, 0, s>>>(w.L, n);
     int warps = 8;
     int cgrid = (int)((nchunks + warps - 1) / warps);
