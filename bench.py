@@ -973,7 +973,7 @@ def main():
                         voxels=n, sites=r["n_sites"], components=r["n_comp"], parallelism="replicas" if world > 1
                         else "single", l2="inputs larger than L2 (field 512 MiB + aux 8 GiB), no flush"),
             roofline=dict(kernel="one Lloyd iteration: site bins + cell lists + cfi_kernel + check_paths_kernel + "
-                                 "relax_persistent_kernel + update_voxels_kernel + update_nonlos_kernel + "
+                                 "relax_async_kernel + update_voxels_kernel + update_nonlos_kernel + "
                                  "move_sites_kernel",
                           # the roofline axis is HBM (algorithmic bytes against the measured copy rate);
                           # the measured limiter is issue and latency (dependent loads in the path and

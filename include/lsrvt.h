@@ -18,7 +18,7 @@
  *    the legacy default stream).  Argument errors (bad dims, NULL pointers, isovalues
  *    not strictly increasing, too small a workspace) return synchronously and launch
  *    nothing.  Errors that depend on the data (capacity exceeded, distance overflow,
- *    non-finite statistics input, relaxation round limit) are written to the caller's
+ *    non-finite statistics input, a bounded wait or loop that ran out) are written to the caller's
  *    device status word `status_dev` (int32, first error wins; 0 = OK); the caller
  *    clears it and reads it after synchronising.  LSRVT_ERR_CUDA reports a failed
  *    kernel launch (cudaGetLastError) on return.
@@ -221,7 +221,8 @@ lsrvt_status lsrvt_seed(const int32_t *comp, const uint16_t *q, lsrvt_dims d, co
  *     unsigned 128-bit integer: [3] its low 64 bits, [4] its high 64 bits.  Recorded
  *     only: E is not guaranteed to fall (the geodesic update of Eq. 2 is not Lloyd's
  *     centroid step), and nothing depends on it.
- * OVERFLOW if a distance reaches 2^32; TIMEOUT if the relaxation exceeds its round limit. */
+ * OVERFLOW if a distance reaches 2^32; TIMEOUT if a bounded wait of the relaxation's work queue
+ * runs out (about a second without progress) or a parent chain of the update is broken. */
 lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q, lsrvt_dims d, int32_t *site_pos,
                                const int32_t *n_sites_dev, int32_t max_sites, int32_t n_iters, int32_t *cell,
                                uint32_t *dist, int64_t *iter_trace, void *ws, size_t ws_bytes,

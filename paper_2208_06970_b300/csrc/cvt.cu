@@ -12,8 +12,8 @@
 // spans is in one band), and relaxes in place (pull updates from the 26 neighbours)
 // only where a neighbour changed in the previous step (row bitmasks dilated each step),
 // until nothing changes.  Improved keys are written back; bricks whose boundary layer
-// changed queue their neighbours for the next round (deduplicated by a per-brick tag).
-// Rounds run until the queue is empty.
+// changed queue their neighbours (at most once at a time: a per-brick flag) on one
+// asynchronous work queue that runs until no queued or running brick is left.
 //
 // Update (Eq. 2).  One pass over the voxels: a voxel at distance 0 is its site; other
 // voxels walk the 6-connected traversal toward their site (line of sight); LOS voxels add
@@ -129,30 +129,29 @@ __device__ __forceinline__ uint32_t edges_from_same(uint32_t S) {
 #ifdef LSRVT_DEBUG
 __device__ unsigned long long g_relax_steps[2];  // in-brick steps, brick visits
 #endif
-// One relaxation round: the CTAs of the grid take the queued bricks one at a time.
+// The relaxation: the CTAs of the grid take queued bricks one at a time.
 // Only voxels the candidate filter left unsettled can change (settled keys are exact), so
 // their exact bits (xmask, brick order) switch the others off, and only bricks holding
 // unsettled voxels (hasunk) are ever queued.
-__device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, const uint32_t *__restrict__ xmask,
+// One visit of a brick: load its keys with a one-voxel halo, relax in place until stable, write
+// back what changed, and hand every neighbour brick whose shared boundary improved to `queue`
+// (called by one thread per neighbour, after the block's writes).  All threads of the CTA call it.
+// kMinStore: two visits of the brick may overlap (the asynchronous queue), so a key is written
+// with a 64-bit atomic minimum -- keys only decrease, and an older visit must not overwrite what
+// a newer one found.
+template <bool kMinStore, class Queue>
+__device__ __forceinline__ void relax_brick(const uint32_t *__restrict__ emask, const uint32_t *__restrict__ xmask,
                                             const uint8_t *__restrict__ hasunk, Dims d, BrickGeom bg,
-                                            unsigned long long *key, const int32_t *list_in, const int nin,
-                                            int32_t *list_out, int32_t *n_out, uint32_t *flags, uint32_t tag,
-                                            int32_t *work, int32_t *status) {
+                                            unsigned long long *key, const int brick, int32_t *status,
+                                            Queue &&queue) {
     // packed keys: one aligned 64-bit access per read/write, so a reader never pairs the
     // distance of one update with the site of another
     __shared__ unsigned long long sk[HV];
     __shared__ uint32_t changed[2][kRows];  // double buffered: written in one step, cleared in the next
     __shared__ uint32_t dirty[kRows];
     __shared__ uint32_t touch;
-    __shared__ int item;
     const int tid = threadIdx.x;
-    while (true) {
-        if (tid == 0) item = atomicAdd(work, 1);
-        __syncthreads();
-        const int it = item;
-        __syncthreads();  // every thread has read `item` before thread 0 may overwrite it
-        if (it >= nin) break;
-        const int brick = __ldcg(list_in + it);
+    {
         const int bx = brick % bg.nbx, by = (brick / bg.nbx) % bg.nby, bz = brick / (bg.nbx * bg.nby);
         const int ox = bx * RX, oy = by * RY, oz = bz * RZ;
         // ---- load halo
@@ -257,7 +256,8 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
             unsigned long long nk = sk[h];
             if (nk == orig[j]) continue;
             int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-            key[gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)] = nk;
+            if (kMinStore) atomicMin(key + gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz), nk);
+            else key[gx + (int64_t)d.nx * (gy + (int64_t)d.ny * gz)] = nk;
             int xs0 = lx == 0 ? -1 : 0, xs1 = lx == RX - 1 ? 1 : 0;
             int ys0 = ly == 0 ? -1 : 0, ys1 = ly == RY - 1 ? 1 : 0;
             int zs0 = lz == 0 ? -1 : 0, zs1 = lz == RZ - 1 ? 1 : 0;
@@ -272,101 +272,97 @@ __device__ __forceinline__ void relax_items(const uint32_t *__restrict__ emask, 
             int nx2 = bx + tid % 3 - 1, ny2 = by + (tid / 3) % 3 - 1, nz2 = bz + tid / 9 - 1;
             if (nx2 >= 0 && nx2 < bg.nbx && ny2 >= 0 && ny2 < bg.nby && nz2 >= 0 && nz2 < bg.nbz) {
                 int nb = nx2 + bg.nbx * (ny2 + bg.nby * nz2);
-                if (__ldcg(hasunk + nb) && atomicExch(&flags[nb], tag) != tag) {
-                    int pos = atomicAdd(n_out, 1);
-                    list_out[pos] = nb;
-                }
+                if (__ldcg(hasunk + nb)) queue(nb);
             }
         }
         __syncthreads();
     }
 }
 
-#ifdef LSRVT_DEBUG
-__device__ unsigned long long g_relax_dbg[2];  // rounds, brick visits
-__device__ unsigned long long g_relax_rt[3][32];  // per round index: ns, bricks, launches
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-#endif
-
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The last CTA to arrive
-// clears the queue that was just consumed, so the next round can append to it, then releases
-// the others.  Waits are bounded: past the limit the status word gets TIMEOUT and every CTA
-// leaves the loop at the next barrier (abort flag), so the kernel always ends.
-struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
-    int abort;
+// The relaxation as one asynchronous work queue (one launch, no rounds).  A ticket counter
+// hands out work: tickets below the filter's count read its brick list, later ones a ring of
+// bricks queued during the relaxation (capacity = the number of bricks: a brick is in the queue
+// at most once at a time -- its flag holds `tag` from the push until the pop).  A CTA pops a
+// brick, relaxes it, and pushes every neighbour whose shared boundary improved; `outstanding`
+// counts the bricks pushed and not yet finished, so a CTA whose ticket finds nothing leaves once
+// it reaches zero.  A brick pushed again while a visit of it is still running can be visited
+// twice at once, so keys are written back with an atomic minimum.  Keys only decrease and the
+// fixed point is unique, so the result does not depend on the order.  Every wait is bounded: past the limit the status gets TIMEOUT and the
+// abort flag empties the queue.
+struct RelaxQueue {
+    int32_t head;         // next ticket
+    int32_t pushed;       // bricks pushed to the ring so far
+    int32_t outstanding;  // pushed (or listed) and not yet finished
+    int32_t abort;
 };
 
-__device__ bool grid_barrier(GridBarrier *bar, int32_t *reset_n, int32_t *reset_work, int32_t *status) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &bar->gen;
-        const unsigned int g = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            bar->count = 0;
-            *reset_n = 0;
-            *reset_work = 0;
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == g) {
-                __nanosleep(64);
-                if (++spins > (1LL << 26) || *(volatile int *)&bar->abort) {
-                    set_status(status, LSRVT_ERR_TIMEOUT);
-                    atomicExch(&bar->abort, 1);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        if (*(volatile int *)&bar->abort) ok = 0;
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
+__global__ void relax_queue_init_kernel(RelaxQueue *q, const int32_t *n_list) {
+    q->head = 0;
+    q->pushed = 0;
+    q->outstanding = *n_list;
+    q->abort = 0;
 }
 
-// All relaxation rounds in one cooperative launch: round r consumes queue r & 1 and fills
-// the other; the loop ends when a round starts with an empty queue.  No host round trips.
-__global__ void __launch_bounds__(kRelaxThreads) relax_persistent_kernel(
+__global__ void __launch_bounds__(kRelaxThreads) relax_async_kernel(
     const uint32_t *__restrict__ emask, const uint32_t *__restrict__ xmask, const uint8_t *__restrict__ hasunk, Dims d,
-    BrickGeom bg, unsigned long long *key, int32_t *list0, int32_t *list1, int32_t *counts, int32_t *works,
-    uint32_t *flags, uint32_t tag0, int32_t max_rounds, GridBarrier *bar, int32_t *status) {
-    int r = 0;
-    for (; r < max_rounds; ++r) {
-        const int cur = r & 1;
-        const int nin = __ldcg(counts + cur);
-        if (nin == 0) break;
-#ifdef LSRVT_DEBUG
-        unsigned long long t_round = gtimer();
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            atomicAdd(&g_relax_dbg[0], 1ULL);
-            atomicAdd(&g_relax_dbg[1], (unsigned long long)nin);
-            if (r < 32) {
-                atomicAdd(&g_relax_rt[1][r], (unsigned long long)nin);
-                atomicAdd(&g_relax_rt[2][r], 1ULL);
+    BrickGeom bg, unsigned long long *key, const int32_t *list0, const int32_t *n_list, int32_t *ring, int32_t cap,
+    RelaxQueue *q, uint32_t *flags, uint32_t tag, int32_t max_tickets, int32_t *status) {
+    __shared__ int item;
+    const int n0 = __ldcg(n_list);
+    while (true) {
+        if (threadIdx.x == 0) {
+            int b = -1;
+            if (!*(volatile int32_t *)&q->abort) {
+                const int t = atomicAdd(&q->head, 1);
+                if (t >= max_tickets) {
+                    set_status(status, LSRVT_ERR_TIMEOUT);
+                    atomicExch(&q->abort, 1);
+                } else if (t < n0) {
+                    b = __ldcg(list0 + t);
+                } else {
+                    int32_t *slot = ring + (t - n0) % cap;
+                    for (long long spin = 0;; ++spin) {
+                        const int v = atomicExch(slot, 0);
+                        if (v) {
+                            b = v - 1;
+                            break;
+                        }
+                        if (*(volatile int32_t *)&q->outstanding == 0 || *(volatile int32_t *)&q->abort) break;
+                        if (spin > (1LL << 24)) {
+                            set_status(status, LSRVT_ERR_TIMEOUT);
+                            atomicExch(&q->abort, 1);
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+                if (b >= 0) {
+                    // the pop: pushes from now on queue the brick again; the fence orders the
+                    // neighbours' key writes seen through the flag and the ring before our loads
+                    atomicExch(&flags[b], 0u);
+                    __threadfence();
+                }
             }
+            item = b;
         }
-#endif
-        relax_items(emask, xmask, hasunk, d, bg, key, cur ? list1 : list0, nin, cur ? list0 : list1, counts + (1 - cur), flags,
-                    tag0 + (uint32_t)r + 1u, works + cur, status);
-        if (!grid_barrier(bar, counts + cur, works + cur, status)) return;
-#ifdef LSRVT_DEBUG
-        if (blockIdx.x == 0 && threadIdx.x == 0 && r < 32) atomicAdd(&g_relax_rt[0][r], gtimer() - t_round);
-#endif
+        __syncthreads();
+        const int b = item;
+        __syncthreads();  // every thread has read `item` before thread 0 may overwrite it
+        if (b < 0) break;
+        relax_brick<true>(emask, xmask, hasunk, d, bg, key, b, status, [&](int nb) {
+            __threadfence();  // the block's key writes (ordered by the barrier) before the push
+            if (atomicExch(&flags[nb], tag) != tag) {
+                atomicAdd(&q->outstanding, 1);
+                const int pidx = atomicAdd(&q->pushed, 1);
+                atomicExch(ring + pidx % cap, nb + 1);
+            }
+        });
+        // relax_brick ends with a barrier: the pushes above are done
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicSub(&q->outstanding, 1);
+        }
     }
-    if (r == max_rounds && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, LSRVT_ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------- clearance field
@@ -1863,6 +1859,7 @@ struct CvtWs {
     unsigned long long *sums;
     uint32_t *flags;
     int32_t *list[2];
+    RelaxQueue *rq;
     int64_t *fine_off, *coarse_off;
     int32_t *fine_cur, *coarse_cur;
     int4 *fine_cand, *coarse_cand;
@@ -1878,7 +1875,6 @@ struct CvtWs {
     int32_t *plist;
     int32_t *chk_p;    // path checks: the site's voxel
     int32_t *msteps;   // per site: face steps of its last move (warm start)
-    GridBarrier *bar;
     void *scan;
 };
 
@@ -1918,7 +1914,7 @@ CvtWs carve_cvt(void *ws, size_t bytes, Dims d, int32_t max_sites, size_t *need)
     w.plist = c.take<int32_t>(n);
     w.chk_p = c.take<int32_t>(n);
     w.msteps = c.take<int32_t>((int64_t)max_sites + 1);
-    w.bar = c.take<GridBarrier>(1);
+    w.rq = c.take<RelaxQueue>(1);
     w.scan = c.take<char>(scan_temp_bytes((nbricks > ncoarse ? nbricks : ncoarse) + 1));
     *need = c.used;
     return w;
@@ -2105,8 +2101,6 @@ __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict
     if (__syncthreads_or(any) && threadIdx.x == 0) flags[round] = 1u;
 }
 
-constexpr int kMaxRounds = 1 << 16;
-
 }  // namespace
 
 size_t cvt_workspace(Dims d, int32_t max_sites) {
@@ -2233,36 +2227,27 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
     }
 #endif
     int nb_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, relax_persistent_kernel, kRelaxThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_per_sm, relax_async_kernel, kRelaxThreads, 0);
     if (nb_per_sm < 1) nb_per_sm = 1;
     const int nsm = sms;
     // at most one CTA per brick: small volumes leave the rest of the GPU to concurrent work
     int grid = (int)((int64_t)nsm * nb_per_sm < nbricks ? (int64_t)nsm * nb_per_sm : nbricks);
-    cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), s);
-    uint32_t tag_round0 = tag;
-    int32_t max_rounds = kMaxRounds;
-    int32_t *list0 = w.list[0], *list1 = w.list[1], *counts = w.counters + 1, *works = w.counters + 3;
-    GridBarrier *bar = w.bar;
-    const uint32_t *emask = w.emask;
-    const uint32_t *xmask = w.xmask;
-    const uint8_t *hasunk = w.hasunk;
-    void *args[] = {(void *)&emask, (void *)&xmask, (void *)&hasunk, (void *)&d, (void *)&bg, (void *)&w.key, (void *)&list0, (void *)&list1,
-                    (void *)&counts, (void *)&works, (void *)&w.flags, (void *)&tag_round0, (void *)&max_rounds,
-                    (void *)&bar, (void *)&status};
-    if (cudaLaunchCooperativeKernel((const void *)relax_persistent_kernel, grid, kRelaxThreads, args, 0, s) !=
-        cudaSuccess)
-        return LSRVT_ERR_CUDA;
-    tag += (uint32_t)kMaxRounds + 1u;
+    relax_queue_init_kernel<<<1, 1, 0, s>>>(w.rq, w.counters + 1);
+    cudaMemsetAsync(w.list[1], 0, sizeof(int32_t) * (size_t)nbricks, s);
+    const int32_t max_tickets = (int32_t)(int64_t(1) << 30);
+    relax_async_kernel<<<grid, kRelaxThreads, 0, s>>>(w.emask, w.xmask, w.hasunk, d, bg, w.key, w.list[0],
+                                                      w.counters + 1, w.list[1], (int32_t)nbricks, w.rq, w.flags,
+                                                      tag, max_tickets, status);
+    tag += 1u;
 #ifdef LSRVT_DEBUG
     {
-        unsigned long long rd[2], z[2] = {0, 0};
+        RelaxQueue hq;
         cudaStreamSynchronize(s);
-        cudaMemcpyFromSymbol(rd, g_relax_dbg, sizeof(rd));
-        cudaMemcpyToSymbol(g_relax_dbg, z, sizeof(z));
+        cudaMemcpy(&hq, w.rq, sizeof(hq), cudaMemcpyDeviceToHost);
         unsigned long long rs[2], rz[2] = {0, 0};
         cudaMemcpyFromSymbol(rs, g_relax_steps, sizeof(rs));
         cudaMemcpyToSymbol(g_relax_steps, rz, sizeof(rz));
-        fprintf(stderr, " | relax rounds %llu brick visits %llu steps/visit %.1f\n", rd[0], rd[1],
+        fprintf(stderr, " | relax brick visits %llu (pushed %d) steps/visit %.1f\n", rs[1], hq.pushed,
                 rs[1] ? (double)rs[0] / rs[1] : 0.0);
     }
 #endif
@@ -2328,15 +2313,6 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         unsigned long long ph[12];
         cudaMemcpyFromSymbol(ph, g_phase, sizeof(ph));
         fprintf(stderr, "cfi tube-certified voxels %llu own path checks %llu\n", ph[5], ph[8]);
-        {
-            unsigned long long rt[3][32], rz[3][32] = {{0}};
-            cudaMemcpyFromSymbol(rt, g_relax_rt, sizeof(rt));
-            cudaMemcpyToSymbol(g_relax_rt, rz, sizeof(rz));
-            fprintf(stderr, "relax per round index (launches, bricks total, us total):");
-            for (int r = 0; r < 32 && rt[2][r]; ++r)
-                fprintf(stderr, " [%d: %llu, %llu, %.0f]", r, rt[2][r], rt[1][r], rt[0][r] / 1e3);
-            fprintf(stderr, "\n");
-        }
         unsigned long long pd[12], pz[12] = {0};
         cudaMemcpyFromSymbol(pd, g_path_dbg, sizeof(pd));
         cudaMemcpyToSymbol(g_path_dbg, pz, sizeof(pz));
