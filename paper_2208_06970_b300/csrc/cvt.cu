@@ -1113,6 +1113,13 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         const int hx = min(ox + RX, d.nx) - 1, hy = min(oy + RY, d.ny) - 1, hz = min(oz + RZ, d.nz) - 1;
         const int64_t cell = (ox >> kCoarseShift) + (int64_t)cg.ncx * ((oy >> kCoarseShift) + (int64_t)cg.ncy * (oz >> kCoarseShift));
         PHASE_T0();
+        // the coarse cell's list (when complete): this thread's first entry is loaded now, so its
+        // latency overlaps the initialisation and the band loads
+        const int nl = cell_count[cell];
+        const int4 *L = cell_list + cell * kCellList;
+        const bool has_reg = tid < nl;
+        int4 c_reg = make_int4(0, 0, 0, 0);
+        if (has_reg) c_reg = L[tid];
         if (tid < 8) present[tid] = 0;
         for (int b = tid; b < 256; b += blockDim.x) Ub[b] = ~0ULL;
         for (int c2 = tid; c2 < kMaxCand / 4; c2 += blockDim.x) reinterpret_cast<uint32_t *>(wcert)[c2] = 0u;
@@ -1128,38 +1135,45 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             vb[j] = b;
             if (b != kInvalidBand) atomicOr(&present[b >> 5], 1u << (b & 31));
         }
-        __syncthreads();
-        const int nl = cell_count[cell];
         // complete = the coarse cell's list is usable (it holds every site that can win);
         // otherwise (dense regions overflow it) the brick takes the sites of the bricks within
         // +-1 (x) / +-2 (y, z) bricks and settles a voxel only when its best is closer than
         // any site outside that box can be
         const bool complete = nl >= 0;
         constexpr int FX = 1, FY = 2, FZ = 2, NFX = 2 * FX + 1, NFY = 2 * FY + 1, NFZ = 2 * FZ + 1;
-        // brick-level bounds, then the survivors (two passes over the same candidates)
-        for (int pass = 0; pass < 2; ++pass) {
-            auto visit = [&](const int4 &c) {
-                int b = c.w >> 24;
-                if (!((present[b >> 5] >> (b & 31)) & 1u)) return;
-                if (pass == 0) {
-                    atomicMin(&Ub[b], chamfer_box_max(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz));
-                } else if (chamfer_box_min(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz) <= Ub[b]) {
-                    int at = atomicAdd(&ncand_s, 1);
-                    if (at < kMaxCand) cs[at] = c;
-                }
-            };
-            if (complete) {
-                const int4 *L = cell_list + cell * kCellList;
-                for (int i = tid; i < nl; i += blockDim.x) visit(L[i]);
-            } else {
+        // brick-level bounds Ub (every band, present or not: a bound of an absent band is never
+        // read), then the survivors of the present bands
+        auto bound = [&](const int4 &c) {
+            atomicMin(&Ub[c.w >> 24], chamfer_box_max(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz));
+        };
+        auto keep = [&](const int4 &c) {
+            int b = c.w >> 24;
+            if (!((present[b >> 5] >> (b & 31)) & 1u)) return;
+            if (chamfer_box_min(c.y, c.z, c.w & 0xFFFFFF, lx, ly, lz, hx, hy, hz) <= Ub[b]) {
+                int at = atomicAdd(&ncand_s, 1);
+                if (at < kMaxCand) cs[at] = c;
+            }
+        };
+        if (complete) {
+            if (has_reg) bound(c_reg);
+            for (int i = tid + blockDim.x; i < nl; i += blockDim.x) bound(L[i]);
+            __syncthreads();
+            if (has_reg) keep(c_reg);
+            for (int i = tid + blockDim.x; i < nl; i += blockDim.x) keep(L[i]);
+            __syncthreads();
+        } else {
+            for (int pass = 0; pass < 2; ++pass) {
                 for (int qb = tid; qb < NFX * NFY * NFZ; qb += blockDim.x) {
                     int cx = bx + qb % NFX - FX, cy = by + (qb / NFX) % NFY - FY, cz = bz + qb / (NFX * NFY) - FZ;
                     if (cx < 0 || cx >= bg.nbx || cy < 0 || cy >= bg.nby || cz < 0 || cz >= bg.nbz) continue;
                     int64_t bb = cx + (int64_t)bg.nbx * (cy + (int64_t)bg.nby * cz);
-                    for (int64_t r = fine_off[bb]; r < fine_off[bb + 1]; ++r) visit(fine_cand[r]);
+                    for (int64_t r = fine_off[bb]; r < fine_off[bb + 1]; ++r) {
+                        if (pass == 0) bound(fine_cand[r]);
+                        else keep(fine_cand[r]);
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
         PHASE_ADD(0);
         const int nc = ncand_s;
