@@ -167,6 +167,13 @@ def test_cvt_parity_weighted_ragged(pk):
     _cvt_compare(pk, f, np.array([0.2, 0.45, 0.7], np.float32), 150, 1, 2, rs=3)
 
 
+def test_cvt_parity_tall_volume(pk):
+    """A volume taller than 1024 voxels along z: the path-check list keeps linear voxel indices
+    (its packed coordinates hold z below 1024 only)."""
+    f = workloads.blob_field((12, 10, 1100), 13, "cpu", n_blobs=40).numpy()
+    _cvt_compare(pk, f, np.array([0.25, 0.5, 0.75], np.float32), 120, 0, 2, rs=5)
+
+
 def test_cvt_parity_flame(pk):
     f, u = workloads.flame_field((40, 36, 32), 2, "cpu")
     _cvt_compare(pk, f.numpy(), (np.arange(1, 9, dtype=np.float32) / np.float32(9)), 300, 1, 2)
