@@ -689,6 +689,8 @@ __device__ int chamfer_path_in_band(const uint32_t *__restrict__ emask, const ui
 // voxels of band b, so all of them lie in band b.  Exact integer arithmetic in doubled
 // coordinates: k counts half voxels along the dominant axis of s - C (length L2).
 // Returns the covered extent: the tube is certified for t <= k / L2 (k >= L2: all of it).
+// The sequential walk below serves the debug counters; the kernels run the warp form after it.
+#ifdef LSRVT_DEBUG
 __device__ int brick_tube_in_band(const uint8_t *__restrict__ clr, Dims d, int lx, int ly, int lz, int hx, int hy,
                                   int hz, int sx, int sy, int sz) {
     const int cx2 = lx + hx, cy2 = ly + hy, cz2 = lz + hz;  // doubled centre
@@ -715,6 +717,49 @@ __device__ int brick_tube_in_band(const uint8_t *__restrict__ clr, Dims d, int l
         k += delta;
     }
     return k;
+}
+#endif
+
+// The same walk by a group of G lanes (G a power of two, at most 32, groups aligned within the
+// warp): the lanes load the clearance of G consecutive tube points at once, then the group
+// follows the sequential walk's jumps through that window with shuffles, so the result is the
+// sequential one, with one dependent load per G positions instead of one per jump.  All lanes
+// of a group call it with the same arguments.
+__device__ int brick_tube_in_band_group(const uint8_t *__restrict__ clr, Dims d, int lx, int ly, int lz, int hx,
+                                        int hy, int hz, int sx, int sy, int sz, int G) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const unsigned mask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(G - 1));
+    const int cx2 = lx + hx, cy2 = ly + hy, cz2 = lz + hz;
+    const int dx2 = 2 * sx - cx2, dy2 = 2 * sy - cy2, dz2 = 2 * sz - cz2;
+    const int L2 = max(abs(dx2), max(abs(dy2), abs(dz2)));
+    const int R2 = max(hx - lx, max(hy - ly, hz - lz));
+    if (L2 == 0) {
+        int c = __ldg(clr + (cx2 >> 1) + (int64_t)d.nx * ((cy2 >> 1) + (int64_t)d.ny * (cz2 >> 1)));
+        return 2 * c - 1 - (R2 + 4) >= 1 ? 1 : 0;
+    }
+    const unsigned den = 2u * (unsigned)L2;
+    int f = 0;  // the walk's position: every tube point before it is covered
+    for (int round = 0; round < 4 * 4096; ++round) {
+        const int k = f + gl;
+        int delta = 0;
+        if (k < L2) {
+            const int ux = (int)((unsigned)(cx2 * L2 + dx2 * k + L2) / den);
+            const int uy = (int)((unsigned)(cy2 * L2 + dy2 * k + L2) / den);
+            const int uz = (int)((unsigned)(cz2 * L2 + dz2 * k + L2) / den);
+            const int c = __ldg(clr + ux + (int64_t)d.nx * (uy + (int64_t)d.ny * uz));
+            const int two_rho = (int)(((unsigned)R2 * (unsigned)(L2 - k) + (unsigned)L2 - 1u) / (unsigned)L2) + 4;
+            delta = 2 * c - 1 - two_rho;
+        }
+        int cur = f;
+        while (cur - f < G) {  // every jump is at least 1: at most G turns
+            const int dd = __shfl_sync(mask, delta, cur - f, G);
+            if (dd < 1) return cur;
+            if (cur + dd >= L2) return L2;
+            cur += dd;
+        }
+        f = cur;
+    }
+    return f;
 }
 
 // site bins: one pass counts, a scan gives offsets, a second pass fills entries
@@ -1329,16 +1374,25 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
         }
         __syncthreads();
         PHASE_ADD(2);
-        // (2) one tube certificate per (brick, winning site)
-        for (int c2 = tid; c2 < nc && ok_list; c2 += blockDim.x) {
-            if (wcert[c2] != 1) continue;
-            const int4 c = cs[c2];
-            csclr[c2] = __ldg(clr + c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * (c.w & 0xFFFFFF)));
-            const int cov = brick_tube_in_band(clr, d, lx, ly, lz, hx, hy, hz, c.y, c.z, c.w & 0xFFFFFF);
-            const int L2 = max(abs(2 * c.y - lx - hx), max(abs(2 * c.z - ly - hy), abs(2 * (c.w & 0xFFFFFF) - lz - hz)));
-            wcov[c2] = cov;
-            // L2 = 0 (a clipped edge brick centred on the site): the walk returns its answer, 0 or 1
-            if (cov >= max(L2, 1)) wcert[c2] = 2;
+        // (2) one tube certificate per (brick, winning site), a group of G lanes per candidate
+        // that wins: whole warps for at most 8 candidates, narrower groups for more, so that
+        // the block's threads cover the candidates in one pass
+        if (ok_list) {
+            int G = 32;
+            while (G > 1 && nc * G > kRelaxThreads) G >>= 1;
+            for (int c2 = tid / G; c2 < nc; c2 += kRelaxThreads / G) {
+                if (wcert[c2] != 1) continue;  // uniform over the group
+                const int4 c = cs[c2];
+                const int cz = c.w & 0xFFFFFF;
+                const int cov = brick_tube_in_band_group(clr, d, lx, ly, lz, hx, hy, hz, c.y, c.z, cz, G);
+                if ((tid & (G - 1)) == 0) {
+                    csclr[c2] = __ldg(clr + c.y + (int64_t)d.nx * (c.z + (int64_t)d.ny * cz));
+                    const int L2 = max(abs(2 * c.y - lx - hx), max(abs(2 * c.z - ly - hy), abs(2 * cz - lz - hz)));
+                    wcov[c2] = cov;
+                    // L2 = 0 (a clipped edge brick centred on the site): the walk returns its answer, 0 or 1
+                    if (cov >= max(L2, 1)) wcert[c2] = 2;
+                }
+            }
         }
         __syncthreads();
         PHASE_ADD(4);
