@@ -43,7 +43,7 @@ ALG_BYTES_PER_VOXEL_ITER = 11
 # DRAM bytes one Lloyd iteration moves per voxel, summed over its kernels, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 256^3 flame case and scaled by the
 # voxel count (the traffic grows in proportion to it)
-NCU_BYTES_PER_VOXEL_ITER = 71.4
+NCU_BYTES_PER_VOXEL_ITER = 71.7
 
 
 def peaks():
