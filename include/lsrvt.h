@@ -380,6 +380,52 @@ lsrvt_status lsrvt_site_geodesics(const int64_t *adj_off, const int32_t *adj, co
                                   float *ratio, float c_far, void *ws, size_t ws_bytes, int32_t *status_dev,
                                   void *stream);
 
+/* Packed batches of independent blocks (Discussion "Block Based Distributed Parallelism":
+ * the blocks of a volume are decomposed independently, their boundaries acting as
+ * restrictions).  Many blocks are placed in one packed volume, each at its own origin, apart
+ * from each other by at least one voxel of band 0xFF (a voxel that is no graph node), so that
+ * one lsrvt_cvt_iterate over the packed volume runs every launch of the Lloyd loop over the
+ * bricks of all blocks at once.  No restricted geodesic, voxel traversal or site walk can
+ * cross the gap, every block's sites keep their order, and the update's rounding
+ * (round-half-up of sum q x / sum q) commutes with translation by the block's origin, so each
+ * block's cells, distances and sites are the ones lsrvt_cvt_iterate gives for the block alone;
+ * only the iteration trace is summed over the blocks.
+ *   Blocks are given as a host array of descriptors whose pointers are device memory of the
+ *   block's own arrays (the layout lsrvt_cvt_iterate takes for the block alone). */
+#define LSRVT_MAX_PACK_BLOCKS 128
+
+typedef struct {
+    lsrvt_dims d;            /* the block's extent */
+    int32_t x0, y0, z0;      /* the block's origin in the packed volume */
+    const uint8_t *band;     /* [N_b] isoband indices (pack: in) */
+    const uint16_t *q;       /* [N_b] weights (pack: in, read only when the packed q is given) */
+    int32_t *site_pos;       /* [n_sites_b] linear voxel indices within the block (pack: in; unpack: out) */
+    const int32_t *n_sites;  /* the block's site count, device int32 (pack: in) */
+    int32_t *cell;           /* [N_b] the block's cells, its own site ids, -1 for NaN (unpack: out) or NULL */
+    uint32_t *dist;          /* [N_b] 16.16 geodesic distances (unpack: out) or NULL */
+} lsrvt_block;
+
+/* Pack n_blocks (1..LSRVT_MAX_PACK_BLOCKS) blocks into one volume of extent `packed`:
+ *   band [N] (out): 0xFF everywhere, each block's bands at its origin;
+ *   q [N] (out, optional): 0 everywhere, each block's weights at its origin (NULL: uniform);
+ *   site_pos [max_sites] (out): block b's site i at packed id site_base[b] + i, as a packed
+ *     linear index; n_sites_dev (out): the total; site_base [n_blocks + 1] (out, device
+ *     int32): the exclusive prefix sums of the blocks' counts.
+ * INVALID_ARG (synchronously) for a block outside the packed volume or two blocks whose boxes,
+ * each widened by one voxel, overlap (their voxels would touch); CAPACITY (status_dev) if the
+ * total count exceeds max_sites (then nothing is packed for the sites). */
+lsrvt_status lsrvt_pack_blocks(const lsrvt_block *blocks_host, int32_t n_blocks, lsrvt_dims packed, uint8_t *band,
+                               uint16_t *q, int32_t *site_pos, int32_t max_sites, int32_t *n_sites_dev,
+                               int32_t *site_base, int32_t *status_dev, void *stream);
+
+/* The inverse for the results of lsrvt_cvt_iterate over a packed volume: per block, its cells
+ * (packed site ids less site_base[b]; -1 stays -1), its distances, and its sites as linear
+ * indices within the block.  cell and dist [N] are the packed results (dist may be NULL, then
+ * the blocks' dist are not written); site_pos the packed sites; site_base from the packing. */
+lsrvt_status lsrvt_unpack_blocks(const lsrvt_block *blocks_host, int32_t n_blocks, lsrvt_dims packed,
+                                 const int32_t *cell, const uint32_t *dist, const int32_t *site_pos,
+                                 const int32_t *site_base, void *stream);
+
 /* Execution resources (the execution forms of Sec. 3.2 "Parallel Algorithm": independent
  * blocks processed side by side).  Kernels launched on `stream` size their grids to `percent`
  * of the GPU's SMs (1..100; 100 restores the whole GPU), so decompositions running

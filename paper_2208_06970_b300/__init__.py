@@ -53,6 +53,14 @@ class Stats(C.Structure):
                 ("vmax", C.c_void_p), ("hist", C.c_void_p), ("comom", C.c_void_p)]
 
 
+class Block(C.Structure):
+    _fields_ = [("d", Dims), ("x0", C.c_int32), ("y0", C.c_int32), ("z0", C.c_int32), ("band", C.c_void_p),
+                ("q", C.c_void_p), ("site_pos", C.c_void_p), ("n_sites", C.c_void_p), ("cell", C.c_void_p),
+                ("dist", C.c_void_p)]
+
+
+MAX_PACK_BLOCKS = 128
+
 _lib = None
 
 
@@ -92,11 +100,14 @@ def lib():
         L.lsrvt_merge_joint_hierarchy.argtypes = [Joint, P, i32, i32, P, P, P, i32, i32, Joint, Joint, Joint, P, sz, P]
         L.lsrvt_site_graph.argtypes = [P, P, Dims, P, P, i32, P, P, P, i64, P, P, sz, P, P]
         L.lsrvt_site_geodesics.argtypes = [P, P, P, P, Dims, i32, i32, P, P, C.c_float, P, sz, P, P]
+        L.lsrvt_pack_blocks.argtypes = [P, i32, Dims, P, P, P, i32, P, P, P, P]
+        L.lsrvt_unpack_blocks.argtypes = [P, i32, Dims, P, P, P, P, P]
         for name in ("lsrvt_classify", "lsrvt_label_components", "lsrvt_label_components_static",
                      "lsrvt_saliency_grad", "lsrvt_seed",
                      "lsrvt_cvt_iterate", "lsrvt_cvt_iterate_anyangle", "lsrvt_aux_range", "lsrvt_aggregate",
                      "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout", "lsrvt_joint_moments",
-                     "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics"):
+                     "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics",
+                     "lsrvt_pack_blocks", "lsrvt_unpack_blocks"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -106,7 +117,8 @@ def exported_symbols():
     return ["lsrvt_status_string", "lsrvt_version", "lsrvt_workspace_bytes", "lsrvt_classify",
             "lsrvt_label_components", "lsrvt_label_components_static", "lsrvt_saliency_grad", "lsrvt_seed", "lsrvt_cvt_iterate", "lsrvt_cvt_iterate_anyangle", "lsrvt_aux_range",
             "lsrvt_aggregate", "lsrvt_merge_hierarchy", "lsrvt_set_stream_share", "lsrvt_structured_layout",
-            "lsrvt_joint_moments", "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics"]
+            "lsrvt_joint_moments", "lsrvt_merge_joint_hierarchy", "lsrvt_site_graph", "lsrvt_site_geodesics",
+            "lsrvt_pack_blocks", "lsrvt_unpack_blocks"]
 
 
 def set_stream_share(percent, stream=None):
@@ -288,6 +300,45 @@ def cvt_iterate(band, q, site_pos, n_sites_dev, n_iters, want_dist=True, want_tr
                                    _ptr(trace), _ptr(buf), buf.numel(), _ptr(status), _stream()),
            "lsrvt_cvt_iterate")
     return cell, (dist if want_dist else None), (trace[:n_iters] if want_trace else None)
+
+
+def _block_table(blocks):
+    tab = (Block * len(blocks))()
+    for i, b in enumerate(blocks):
+        nx, ny, nz = b["dims"]
+        x0, y0, z0 = b["origin"]
+        tab[i] = Block(Dims(int(nx), int(ny), int(nz)), int(x0), int(y0), int(z0), _ptr(b.get("band")),
+                       _ptr(b.get("q")), _ptr(b.get("site_pos")), _ptr(b.get("n_sites")), _ptr(b.get("cell")),
+                       _ptr(b.get("dist")))
+    return tab
+
+
+def pack_blocks(blocks, packed, max_sites, want_q=False, status=None):
+    """lsrvt_pack_blocks: independent blocks into one packed volume of extent packed = (nx, ny, nz).
+    blocks: dicts with dims (nx, ny, nz), origin (x0, y0, z0), band, q (when want_q), site_pos and
+    n_sites (device) of the block.  Returns (band, q or None, site_pos, n_sites, site_base)."""
+    dev = blocks[0]["band"].device
+    nx, ny, nz = (int(v) for v in packed)
+    band = torch.empty((nz, ny, nx), dtype=torch.uint8, device=dev)
+    q = torch.empty((nz, ny, nx), dtype=torch.int16, device=dev) if want_q else None
+    sp = torch.empty(max(int(max_sites), 1), dtype=torch.int32, device=dev)
+    ns = torch.empty(1, dtype=torch.int32, device=dev)
+    base = torch.empty(len(blocks) + 1, dtype=torch.int32, device=dev)
+    status = new_status(dev) if status is None else status
+    tab = _block_table(blocks)
+    _check(lib().lsrvt_pack_blocks(C.cast(tab, C.c_void_p), len(blocks), Dims(nx, ny, nz), _ptr(band), _ptr(q),
+                                   _ptr(sp), int(max_sites), _ptr(ns), _ptr(base), _ptr(status), _stream()),
+           "lsrvt_pack_blocks")
+    return band, q, sp, ns, base
+
+
+def unpack_blocks(blocks, packed, cell, dist, site_pos, site_base):
+    """lsrvt_unpack_blocks: each block's cells (its own site ids), distances (when both the block's
+    `dist` and the packed dist are given) and sites, from the packed results."""
+    nx, ny, nz = (int(v) for v in packed)
+    tab = _block_table(blocks)
+    _check(lib().lsrvt_unpack_blocks(C.cast(tab, C.c_void_p), len(blocks), Dims(nx, ny, nz), _ptr(cell), _ptr(dist),
+                                     _ptr(site_pos), _ptr(site_base), _stream()), "lsrvt_unpack_blocks")
 
 
 def trace_summary(trace, n_sites):

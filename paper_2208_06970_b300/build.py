@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblsrvt.so")
 SOURCES = ["api.cu", "scan.cu", "classify.cu", "ccl.cu", "saliency.cu", "seed.cu", "cvt.cu", "aggregate.cu",
-           "merge.cu", "layout.cu", "joint.cu", "graph.cu"]
+           "merge.cu", "layout.cu", "joint.cu", "graph.cu", "pack.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-O3", "--expt-relaxed-constexpr"]
 

@@ -1221,6 +1221,21 @@ __global__ void __launch_bounds__(kRelaxThreads, 3) cfi_kernel(const uint8_t *__
             }
         }
         PHASE_ADD(0);
+        // a brick without a voxel of any band (NaN regions, the gaps between the blocks of a
+        // packed batch): every voxel keeps +inf and counts as exact; nothing else to do
+        if (!(present[0] | present[1] | present[2] | present[3] | present[4] | present[5] | present[6] |
+              present[7])) {
+#pragma unroll
+            for (int j = 0; j < kVPT; ++j) {
+                const int i = tid + kRelaxThreads * j;
+                const int x = ox + (i & (RX - 1)), y = oy + ((i >> 4) & (RY - 1)), z = oz + (i >> 7);
+                if (x < d.nx && y < d.ny && z < d.nz) key[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)] = kInfKey;
+                if ((tid & 31) == 0) xmask[brick * 32 + (tid >> 5) + (kRelaxThreads / 32) * j] = 0xFFFFFFFFu;
+            }
+            if (tid == 0) hasunk[brick] = 0;
+            __syncthreads();
+            continue;
+        }
         const int nc = ncand_s;
         const bool ok_list = nc <= kMaxCand;
 #ifdef LSRVT_DEBUG
@@ -1893,6 +1908,14 @@ __global__ void move_sites_kernel(const uint8_t *__restrict__ band, Dims d, int3
     }
 }
 
+// the moment sums of the live sites (4 words each) and the 4 words after them, cleared before
+// each update: the count is read on the device, so the work follows the sites, not the capacity
+__global__ void zero_sums_kernel(unsigned long long *sums, const int32_t *__restrict__ n_sites_dev, int32_t max_sites) {
+    const int64_t words = 4 * (int64_t)min(max(*n_sites_dev, 0), max_sites) + 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+        sums[i] = 0ull;
+}
+
 __global__ void emit_kernel(const unsigned long long *__restrict__ key, int64_t n, int32_t *cell, uint32_t *dist) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long k = key[v];
@@ -2357,7 +2380,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
     for (int32_t it = 0; it < n_iters; ++it) {
         unsigned long long *rec = iter_trace ? (unsigned long long *)(iter_trace + (int64_t)LSRVT_TRACE * it) : nullptr;
         up.energy = rec ? rec + 3 : nullptr;
-        cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
+        zero_sums_kernel<<<sms * 2, 256, 0, s>>>(w.sums, n_sites_dev, max_sites);
         cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
         cudaMemsetAsync(w.counters + 5, 0, sizeof(int32_t), s);
@@ -2488,7 +2511,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
         if (st == LSRVT_ERR_TIMEOUT) return stop_at_limit();
         if (st != LSRVT_OK) return st;
         unsigned long long *rec = iter_trace ? (unsigned long long *)(iter_trace + (int64_t)LSRVT_TRACE * it) : nullptr;
-        cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * ((size_t)max_sites * 4 + 4), s);
+        zero_sums_kernel<<<sms * 2, 256, 0, s>>>(w.sums, n_sites_dev, max_sites);
         cudaMemsetAsync(w.los_bits, 0, sizeof(uint32_t) * nwords, s);
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key[0], site_pos, w.clr, w.sums, w.los_bits, w.par,

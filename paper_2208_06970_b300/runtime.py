@@ -11,6 +11,9 @@ Parallelism"); here independent blocks / requests share one GPU instead.
   GraphBatch(jobs, n_slots).replay() -> results in job order, the batch replayed as one CUDA graph
   Server(n_slots, hbm_budget).serve(requests, make_job) -> per-request records
   tune_batch(sample_jobs) -> the fastest (slots, share) schedule, checked to leave results unchanged
+  PackedBatch(jobs).run()            -> results in job order, one Lloyd loop over all blocks packed
+                                        into one volume (PackedBatch.capture(): as one CUDA graph)
+  tune_packed(jobs)                  -> the fastest packing schedule, checked to leave results unchanged
 
 A job is a dict: field (CUDA float32 (nz, ny, nx)), iso, voxels_per_site, n_iters, aux (list
 of CUDA tensors), gamma, strat_block, rng_seed, n_bins.
@@ -19,6 +22,7 @@ import queue
 import threading
 import time
 
+import numpy as np
 import torch
 
 from . import decompose, set_stream_share, Workspace
@@ -349,3 +353,212 @@ def latency_summary(records):
     vox_it = sum(r["voxels"] * r["iters"] for r in records)
     return dict(n=n, p50_ms=pct(50), p99_ms=pct(99), mean_ms=1e3 * sum(lat) / n,
                 throughput_req_s=n / span, gvoxel_iters_s=vox_it / span / 1e9, span_s=span)
+
+
+# --------------------------------------------------------------------------- packed batches
+def pack_layout(dims, gap=1, footprint=None, res=8, max_side=2048):
+    """Origins of independent blocks in one packed volume: blocks of extents dims[i] =
+    (nx, ny, nz), at least `gap` (>= 1) voxels apart, placed on a height map over a
+    (width, depth) footprint kept at a resolution of `res` voxels -- the tallest block first,
+    each at the lowest height its footprint (widened by the gap) allows, then the smallest y,
+    then x.  footprint None: of a few candidate footprints, the one whose packed volume is the
+    smallest with every side at most max_side.  Returns (origins [(x0, y0, z0)], (NX, NY, NZ))."""
+    from numpy.lib.stride_tricks import sliding_window_view as windows
+    dims = [tuple(int(v) for v in d) for d in dims]
+    if gap < 1:
+        raise ValueError("blocks must be at least one voxel apart")
+    order = sorted(range(len(dims)), key=lambda i: (-dims[i][2], -dims[i][0] * dims[i][1], i))
+
+    def place(W, D):
+        wc, dc = -(-W // res), -(-D // res)
+        height = np.zeros((dc, wc), np.int64)
+        org = [None] * len(dims)
+        for i in order:
+            nx, ny, nz = dims[i]
+            fx, fy = -(-(nx + gap) // res), -(-(ny + gap) // res)
+            if fx > wc or fy > dc:
+                return None
+            top = windows(height, fx, axis=1).max(axis=2)
+            top = windows(top, fy, axis=0).max(axis=2)
+            z = top.min()
+            ys, xs = np.nonzero(top == z)
+            k = np.lexsort((xs, ys))[0]
+            y, x = int(ys[k]), int(xs[k])
+            org[i] = (x * res, y * res, int(z))
+            height[y:y + fy, x:x + fx] = z + nz + gap
+        ext = tuple(max(org[i][a] + dims[i][a] for i in range(len(dims))) for a in range(3))
+        return org, ext
+
+    if footprint is not None:
+        res_ = place(*footprint)
+        if res_ is None:
+            raise ValueError("a block does not fit the footprint %r" % (footprint,))
+        return res_
+    wmin = max(d[0] for d in dims) + gap
+    dmin = max(d[1] for d in dims) + gap
+    best = None
+    for W in range(-(-wmin // 128) * 128, max_side + 1, 128):
+        for ratio in (0.75, 1.0, 1.33):
+            D = max(dmin, int(round(W * ratio / res)) * res)
+            if D > max_side:
+                continue
+            r = place(W, D)
+            if r is None or max(r[1]) > max_side:
+                continue
+            vol = r[1][0] * r[1][1] * r[1][2]
+            if best is None or vol < best[0]:
+                best = (vol, r)
+    if best is None:
+        raise ValueError("the blocks do not fit a packed volume of side %d" % max_side)
+    return best[1]
+
+
+class PackedBatch:
+    """Independent blocks (Sec. 3.2 "Parallel Algorithm", Discussion "Block Based Distributed
+    Parallelism": blocks are decomposed independently, their boundaries acting as restrictions)
+    decomposed with ONE Lloyd loop over all of them.  Per block, on the slots' streams:
+    classification, labelling, [saliency,] seeding.  Then the blocks' bands, weights and sites
+    are packed into one volume (pack_layout; the blocks at least `gap` voxels of band 0xFF
+    apart), lsrvt_cvt_iterate runs once over it -- every launch of the loop a grid, or the
+    relaxation's work queue, over the bricks of all blocks -- and each block gets its cells
+    and sites back.  Then per block again: statistics and the hierarchy merge.
+
+    Cells, sites and statistics equal decompose() of each block alone (tests/test_gpu_forms.py);
+    the Lloyd trace is the batch's sum (`self.trace`).  All jobs share n_iters and whether they
+    are weighted (gamma > 0).  capture() records the whole batch as one CUDA graph."""
+
+    def __init__(self, jobs, gap=1, footprint=None, n_slots=4, device="cuda", share=None, want_dist=False):
+        from . import MAX_PACK_BLOCKS
+        if not jobs or len(jobs) > MAX_PACK_BLOCKS:
+            raise ValueError("a packed batch holds 1..%d blocks" % MAX_PACK_BLOCKS)
+        if len({int(j["n_iters"]) for j in jobs}) != 1 or len({bool(j.get("gamma", 0)) for j in jobs}) != 1:
+            raise ValueError("the blocks of a packed batch share n_iters and weighting")
+        self.jobs = jobs
+        self.device = torch.device(device)
+        self.dims = [(int(j["field"].shape[2]), int(j["field"].shape[1]), int(j["field"].shape[0])) for j in jobs]
+        self.origins, self.packed = pack_layout(self.dims, gap, footprint)
+        share = default_share(n_slots) if share is None else share
+        self.slots = [Slot(self.device, share) for _ in range(n_slots)]
+        self.main = torch.cuda.Stream(device=self.device)
+        self.ws = Workspace(self.device)
+        self.want_dist = want_dist
+        self.graph = None
+        self.trace = None
+
+    def fill(self):
+        """Voxels of the blocks over voxels of the packed volume."""
+        nx, ny, nz = self.packed
+        return sum(a * b * c for a, b, c in self.dims) / float(nx * ny * nz)
+
+    def run(self):
+        from . import (aggregate, classify, cvt_iterate, default_max_comp, label_components, merge_hierarchy,
+                       new_status, pack_blocks, saliency_grad, seed, unpack_blocks)
+        dev = self.device
+        cur = torch.cuda.current_stream(dev)
+        status = new_status(dev)
+        for sl in self.slots:
+            sl.stream.wait_stream(cur)
+        outs = []
+        # per block: classification, labelling, weights, seeding
+        for k, job in enumerate(self.jobs):
+            sl = self.slots[k % len(self.slots)]
+            with torch.cuda.stream(sl.stream):
+                field = job["field"]
+                n = field.numel()
+                max_comp = default_max_comp(n)
+                band = classify(field, job["iso"])
+                comp, cb, cs, cf, nc = label_components(band, max_comp, sl.ws, status)
+                g = job.get("gamma", 0)
+                q = saliency_grad(field, g, sl.ws) if g else None
+                sp, sc, off, ns = seed(comp, q, nc, max_comp, job["voxels_per_site"], job.get("strat_block", 16),
+                                       job.get("rng_seed", 0), ws=sl.ws, status=status)
+                outs.append(dict(band=band, comp=comp, comp_band=cb, comp_size=cs, comp_first=cf, n_comp=nc, q=q,
+                                 site_pos=sp, site_comp=sc, comp_site_off=off, n_sites=ns, max_comp=max_comp,
+                                 status=status))
+        for sl in self.slots:
+            self.main.wait_stream(sl.stream)
+        # one Lloyd loop over the packed volume
+        with torch.cuda.stream(self.main):
+            blocks = []
+            for k, o in enumerate(outs):
+                nz, ny, nx = o["band"].shape
+                o["cell"] = torch.empty((nz, ny, nx), dtype=torch.int32, device=dev)
+                o["dist"] = torch.empty((nz, ny, nx), dtype=torch.int32, device=dev) if self.want_dist else None
+                blocks.append(dict(dims=self.dims[k], origin=self.origins[k], band=o["band"], q=o["q"],
+                                   site_pos=o["site_pos"], n_sites=o["n_sites"], cell=o["cell"], dist=o["dist"]))
+            max_sites = sum(int(o["site_pos"].numel()) for o in outs)
+            pband, pq, psp, pns, base = pack_blocks(blocks, self.packed, max_sites, want_q=outs[0]["q"] is not None,
+                                                    status=status)
+            pcell, pdist, trace = cvt_iterate(pband, pq, psp, pns, int(self.jobs[0]["n_iters"]),
+                                              want_dist=self.want_dist, ws=self.ws, status=status)
+            unpack_blocks(blocks, self.packed, pcell, pdist, psp, base)
+            self.trace = trace
+            self.n_sites_packed = pns
+        for sl in self.slots:
+            sl.stream.wait_stream(self.main)
+        # per block: statistics and the hierarchy merge
+        for k, (job, o) in enumerate(zip(self.jobs, outs)):
+            sl = self.slots[k % len(self.slots)]
+            aux = job.get("aux", ())
+            if len(aux):
+                with torch.cuda.stream(sl.stream):
+                    cells = aggregate(o["cell"], list(aux), o["site_pos"], o["n_sites"], n_bins=job.get("n_bins", 32),
+                                      ws=sl.ws, status=status)
+                    comps, bands, vol = merge_hierarchy(cells, o["n_sites"], o["comp_site_off"], o["comp_band"],
+                                                        o["n_comp"], o["max_comp"], len(job["iso"]) + 1,
+                                                        job.get("n_bins", 32), False, sl.ws)
+                    o.update(cells=cells, comps=comps, bands=bands, volume=vol)
+        for sl in self.slots:
+            cur.wait_stream(sl.stream)
+        cur.wait_stream(self.main)
+        self.outputs = outs
+        return outs
+
+    def capture(self):
+        """Record the whole batch (per-block stages, packing, the packed Lloyd loop, unpacking,
+        statistics) as one CUDA graph after an eager run that sizes every workspace; replay()
+        then runs it with one launch.  Inputs are read at replay time."""
+        self.run()
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=self.device)
+        cap.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.graph(self.graph, stream=cap):
+            self.run()
+        torch.cuda.synchronize(self.device)
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.outputs
+
+    def check(self):
+        from . import check_status
+        check_status(self.outputs[0]["status"], "packed batch")
+
+
+def tune_packed(jobs, candidates=((1, 4), (1, 2), (4, 4)), device="cuda", reps=1):
+    """Autotuner of the packing schedule: (gap, slots for the per-block stages) candidates,
+    each run on the sample `jobs`; every candidate must reproduce the first one's cells and
+    sites bit for bit (the schedule must not change results).  Returns (best candidate,
+    {candidate: seconds}, {candidate: packed fill})."""
+    times, fills, ref = {}, {}, None
+    for gap, slots in candidates:
+        pb = PackedBatch(jobs, gap=gap, n_slots=slots, device=device)
+        pb.run()  # sizes the workspaces
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            outs = pb.run()
+        torch.cuda.synchronize(device)
+        pb.check()
+        times[(gap, slots)] = (time.perf_counter() - t0) / reps
+        fills[(gap, slots)] = pb.fill()
+        if ref is None:
+            ref = [(o["cell"].clone(), o["site_pos"].clone()) for o in outs]
+        else:
+            for (c0, s0), o in zip(ref, outs):
+                if not (torch.equal(c0, o["cell"]) and torch.equal(s0, o["site_pos"])):
+                    raise RuntimeError("packing schedule %r changed the results" % ((gap, slots),))
+    best = min(times, key=times.get)
+    return best, times, fills

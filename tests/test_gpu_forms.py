@@ -151,3 +151,76 @@ def test_server_stays_within_its_hbm_budget(pk):
     torch.cuda.synchronize()
     assert all(r is not None for r in recs)
     assert torch.cuda.max_memory_allocated() - base <= budget
+
+
+def _energy(t):
+    return ((int(t[4]) & (2 ** 64 - 1)) << 64) | (int(t[3]) & (2 ** 64 - 1))
+
+
+def test_packed_batch_equals_alone(pk):
+    # one Lloyd loop over blocks packed one voxel apart (ragged sides, some thinner than a brick)
+    # gives each block the cells, distances, sites and statistics it gets alone; the packed
+    # trace is the sum of the blocks' traces (moves, d_s and the exact 128-bit energy)
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(7, 12, 70, 21)
+    pb = runtime.PackedBatch(jobs, gap=1, n_slots=3, want_dist=True)
+    got = pb.run()
+    torch.cuda.synchronize()
+    pb.check()
+    tr = pb.trace.cpu().numpy()
+    sums = np.zeros((tr.shape[0], 3), dtype=np.int64)
+    energy = [0] * tr.shape[0]
+    for j, g in zip(jobs, got):
+        a = pk.decompose(j["field"], j["iso"], j["voxels_per_site"], j["n_iters"], aux=j["aux"],
+                         rng_seed=j["rng_seed"])
+        _same(pk, a, g)
+        t = a["trace"].cpu().numpy()
+        sums += t[:, :3]
+        for it in range(t.shape[0]):
+            energy[it] += _energy(t[it])
+    assert np.array_equal(sums, tr[:, :3])
+    assert energy == [_energy(tr[it]) for it in range(tr.shape[0])]
+
+
+def test_packed_batch_weighted_and_wide_gap(pk):
+    # saliency weights packed with the bands; a wider gap leaves the results unchanged
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(4, 16, 48, 5)
+    for j in jobs:
+        j["gamma"] = 1
+        j["aux"] = j["aux"][:1]
+    for gap in (1, 5):
+        got = runtime.PackedBatch(jobs, gap=gap, n_slots=2, want_dist=True).run()
+        torch.cuda.synchronize()
+        for j, g in zip(jobs, got):
+            a = pk.decompose(j["field"], j["iso"], j["voxels_per_site"], j["n_iters"], aux=j["aux"], gamma=1,
+                             rng_seed=j["rng_seed"])
+            _same(pk, a, g)
+
+
+def test_packed_graph_replay_equals_alone(pk):
+    # the packed batch captured as one CUDA graph; new data in the input tensors between replays
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(5, 20, 56, 17)
+    pb = runtime.PackedBatch(jobs, n_slots=2).capture()
+    for step in range(2):
+        if step == 1:
+            for k, j in enumerate(jobs):
+                j["field"].copy_(workloads.blob_field(tuple(j["field"].shape[::-1]), 300 + k, "cuda"))
+        got = pb.replay()
+        torch.cuda.synchronize()
+        pb.check()
+        for j, g in zip(jobs, got):
+            a = pk.decompose(j["field"], j["iso"], j["voxels_per_site"], j["n_iters"], aux=j["aux"],
+                             rng_seed=j["rng_seed"])
+            for k in ("band", "comp", "cell"):
+                assert torch.equal(a[k], g[k]), k
+            ns = int(a["n_sites"].item())
+            assert torch.equal(a["site_pos"][:ns], g["site_pos"][:ns])
+
+
+def test_packing_tuner_keeps_results(pk):
+    from paper_2208_06970_b300 import runtime
+    jobs = _jobs(4, 24, 56, 13)
+    best, times, fills = runtime.tune_packed(jobs, candidates=((1, 2), (3, 2)))
+    assert best in times and len(times) == 2 and all(0 < f <= 1 for f in fills.values())
