@@ -439,7 +439,11 @@ class PackedBatch:
         self.origins, self.packed = pack_layout(self.dims, gap, footprint)
         share = default_share(n_slots) if share is None else share
         self.slots = [Slot(self.device, share) for _ in range(n_slots)]
+        # the packed loop takes the whole GPU; the share is set explicitly because a share belongs
+        # to a stream handle and torch hands out recycled handles (an earlier slot's share would
+        # otherwise stay with this stream)
         self.main = torch.cuda.Stream(device=self.device)
+        set_stream_share(100, self.main)
         self.ws = Workspace(self.device)
         self.want_dist = want_dist
         self.graph = None
