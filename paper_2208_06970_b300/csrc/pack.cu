@@ -10,7 +10,15 @@
 // table travels as a kernel parameter, so a packed batch captures into a CUDA graph without
 // host memory behind it, and the sites' offsets are prefix sums taken on the device from the
 // blocks' device counts.
+#include <cstddef>
+
 #include "common.cuh"
+
+// the descriptor layout the Python binding mirrors (LP64): dims and origin, then six pointers
+static_assert(sizeof(lsrvt_block) == 72, "lsrvt_block layout");
+static_assert(offsetof(lsrvt_block, x0) == 12 && offsetof(lsrvt_block, band) == 24 &&
+                  offsetof(lsrvt_block, n_sites) == 48 && offsetof(lsrvt_block, dist) == 64,
+              "lsrvt_block layout");
 
 namespace lsrvt {
 namespace {

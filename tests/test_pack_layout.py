@@ -85,3 +85,16 @@ def test_pack_abi_rejects_bad_tables():
                                None) == 1
     # unpacking checks the same table
     assert L.lsrvt_unpack_blocks(C.cast(touching, C.c_void_p), 2, P, fake, None, fake, fake, None) == 1
+
+
+def test_block_descriptor_matches_the_header():
+    # the ctypes mirror has the C layout the library asserts at compile time (72 bytes; x0 at 12,
+    # band at 24, n_sites at 48, dist at 64), and the table size agrees with the header
+    import os
+    import re
+    import paper_2208_06970_b300 as pkg
+    B = pkg.Block
+    assert C.sizeof(B) == 72
+    assert (B.x0.offset, B.band.offset, B.n_sites.offset, B.dist.offset) == (12, 24, 48, 64)
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lsrvt.h")).read()
+    assert int(re.search(r"#define LSRVT_MAX_PACK_BLOCKS (\d+)", hdr).group(1)) == pkg.MAX_PACK_BLOCKS
