@@ -71,6 +71,43 @@ __device__ __forceinline__ void decode_voxel(uint32_t v, Dims d, int &x, int &y,
     y = (int)(r - (uint32_t)z * (uint32_t)d.ny);
 }
 
+// Division by a divisor fixed for a launch (Granlund & Montgomery 1994, "Division by invariant
+// integers using multiplication", the method for unsigned run-time invariant divisors): for
+// 1 <= d < 2^31 let l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, which fits in 32
+// bits; then floor(n / d) = (t + ((n - t) >> s1)) >> s2 for every 32-bit n, with t the high word
+// of m n, s1 = min(l, 1) and s2 = max(l - 1, 0).
+struct InvDiv {
+    uint32_t m;
+    int s1, s2;
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        const uint32_t t = __umulhi(m, n);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+};
+
+inline InvDiv make_invdiv(uint32_t d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    InvDiv r;
+    r.m = (uint32_t)(((((1ull << l) - d) << 32) / d) + 1);
+    r.s1 = l < 1 ? l : 1;
+    r.s2 = l > 1 ? l - 1 : 0;
+    return r;
+}
+
+// decode_voxel with the two divisions by the volume's extents done by InvDiv
+struct VoxelCoder {
+    InvDiv by_nx, by_ny;
+    __device__ __forceinline__ void decode(uint32_t v, Dims d, int &x, int &y, int &z) const {
+        const uint32_t r = by_nx.div(v);
+        x = (int)(v - r * (uint32_t)d.nx);
+        z = (int)by_ny.div(r);
+        y = (int)(r - (uint32_t)z * (uint32_t)d.ny);
+    }
+};
+
+inline VoxelCoder make_coder(Dims d) { return VoxelCoder{make_invdiv((uint32_t)d.nx), make_invdiv((uint32_t)d.ny)}; }
+
 // CVT energy sum of m_v D(v)^2 (16.16 distances), exact in 128 bits: each thread keeps its
 // own sum, a warp folds its lanes' sums at the end of the kernel and adds them to the two
 // 64-bit words of the iteration's trace record (low word first, the carry detected from the
@@ -1591,7 +1628,7 @@ __global__ void __launch_bounds__(256, 3) check_paths_kernel(
     const uint8_t *__restrict__ band, const uint32_t *__restrict__ emask, const uint8_t *__restrict__ clr, Dims d,
     BrickGeom bg,
     const int32_t *__restrict__ site_pos, unsigned long long *key, uint32_t *xmask, uint8_t *hasunk, uint32_t *flags,
-    uint32_t tag, int32_t *list_out, int32_t *n_out, CheckList chk, UpdateOut up) {
+    uint32_t tag, int32_t *list_out, int32_t *n_out, CheckList chk, UpdateOut up, VoxelCoder vc) {
     const int32_t cnt = *chk.n;
     const int lane = threadIdx.x & 31;
     EnergyAcc eacc;
@@ -1609,8 +1646,8 @@ __global__ void __launch_bounds__(256, 3) check_paths_kernel(
             const int32_t p = __ldg(chk.p + i);
             const int mvw = __ldg(chk.mv + i);
             const int mv0 = mvw & 0xFFFFFF, cs = (int)((unsigned)mvw >> 24);
-            decode_voxel((uint32_t)g, d, x, y, z);
-            decode_voxel((uint32_t)p, d, px, py, pz);
+            vc.decode((uint32_t)g, d, x, y, z);
+            vc.decode((uint32_t)p, d, px, py, pz);
             status = chamfer_path_in_band(emask, clr, d, x, y, z, px, py, pz, cs, mv0);
 #ifdef LSRVT_DEBUG
             atomicAdd(&g_path_dbg[mv0 > 0 ? 1 : 0], 1ULL);
@@ -1734,7 +1771,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
     const int32_t *__restrict__ site_pos, const uint8_t *__restrict__ clr, unsigned long long *sums,
     uint32_t *los_bits, int32_t *par, int32_t *nonlos, int32_t *n_nonlos, const int32_t *__restrict__ plist,
     const int32_t *n_plist, bool small_coords, const int32_t *__restrict__ src, unsigned long long *energy,
-    const uint32_t *__restrict__ emask) {
+    const uint32_t *__restrict__ emask, VoxelCoder vc) {
     // plist == nullptr: every voxel (N < 2^31); src != nullptr: the path's next node is the
     // voxel's source (any-angle tessellation) instead of the chamfer parent
     const int32_t cnt = plist ? *n_plist : (int32_t)d.n();
@@ -1758,7 +1795,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
             if (k != kInfKey) {
                 s = (int32_t)(uint32_t)k;
                 uint32_t dist = (uint32_t)(k >> 32);
-                decode_voxel((uint32_t)v, d, x, y, z);
+                vc.decode((uint32_t)v, d, x, y, z);
                 if (dist == 0) {
                     los = true;
                 } else {
@@ -1767,7 +1804,7 @@ __global__ void __launch_bounds__(256) update_voxels_kernel(
 #endif
                     int32_t p = site_pos[s];
                     int px, py, pz;
-                    decode_voxel((uint32_t)p, d, px, py, pz);
+                    vc.decode((uint32_t)p, d, px, py, pz);
                     los = los_clear(band, clr, d, x, y, z, px, py, pz, __ldg(clr + p));
 #ifdef LSRVT_DEBUG
                     atomicAdd(&g_phase[6], (unsigned long long)(clock64() - _u0));
@@ -2077,7 +2114,8 @@ __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict
                                                        const unsigned long long *__restrict__ k0,
                                                        const int32_t *__restrict__ p0, unsigned long long *k1,
                                                        int32_t *p1, const uint32_t *__restrict__ c0, uint32_t *c1,
-                                                       uint32_t *flags, int32_t round, int32_t *status) {
+                                                       uint32_t *flags, int32_t round, int32_t *status,
+                                                       VoxelCoder vc) {
     if (round > 0 && __ldcg(flags + round - 1) == 0) return;
     const int64_t n = d.n();
     const int64_t nwords = (n + 31) >> 5;
@@ -2107,7 +2145,7 @@ __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict
             }
             if (active) {
                 int x, y, z;
-                decode_voxel((uint32_t)v, d, x, y, z);
+                vc.decode((uint32_t)v, d, x, y, z);
                 const unsigned long long kv = k0[v];
                 unsigned long long bk = kInfKey;
                 uint32_t bdp = kInf32;
@@ -2117,7 +2155,7 @@ __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict
                     const unsigned long long kt = k0[t];
                     if (kt == kInfKey) return false;
                     int tx, ty, tz;
-                    decode_voxel((uint32_t)t, d, tx, ty, tz);
+                    vc.decode((uint32_t)t, d, tx, ty, tz);
                     const long long dx = x - tx, dy = y - ty, dz = z - tz;
                     const unsigned long long D = (unsigned long long)(dx * dx + dy * dy + dz * dz);
                     if (D >= (1ull << 32)) return false;
@@ -2167,7 +2205,7 @@ __global__ void __launch_bounds__(256) aa_round_kernel(const uint8_t *__restrict
                     uint32_t cdp;
                     if (!through(t, ck, cdp) || !aa_less(ck, cdp, t, bk, bdp, bp)) continue;  // cannot win: no ray
                     int tx, ty, tz;
-                    decode_voxel((uint32_t)t, d, tx, ty, tz);
+                    vc.decode((uint32_t)t, d, tx, ty, tz);
                     const int cs = band[t] == b ? __ldg(clr + t) : 0;
                     if (los_clear(band, clr, d, x, y, z, tx, ty, tz, cs)) {
                         bk = ck;
@@ -2308,7 +2346,7 @@ lsrvt_status run_assignment(const uint8_t *band, Dims d, const int32_t *site_pos
                                                           w.flags, w.xmask, w.hasunk, tag, up, chk,
                                                           WarmStart{warm, w.msteps});
     check_paths_kernel<<<sms * 16, 256, 0, s>>>(band, w.emask, w.clr, d, bg, site_pos, w.key, w.xmask, w.hasunk, w.flags,
-                                                 tag, w.list[0], w.counters + 1, chk, up);
+                                                 tag, w.list[0], w.counters + 1, chk, up, make_coder(d));
 #ifdef LSRVT_DEBUG
     {
         int32_t q0 = 0;
@@ -2389,7 +2427,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate(const uint8_t *band, const uint16_t *q
         if (st != LSRVT_OK) return st;
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key, site_pos, w.clr, w.sums, w.los_bits, w.par,
                                                    w.nonlos, w.counters, w.plist, w.counters + 5, small, nullptr,
-                                                   up.energy, w.emask);
+                                                   up.energy, w.emask, make_coder(d));
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key, w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev, up.energy);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
@@ -2455,7 +2493,7 @@ lsrvt_status aa_assignment(const uint8_t *band, Dims d, const int32_t *site_pos,
         for (; r < r1; ++r)
             aa_round_kernel<<<grid, 256, 0, s>>>(band, w.clr, w.emask, d, w.key[r & 1], w.src[r & 1],
                                                  w.key[(r + 1) & 1], w.src[(r + 1) & 1], w.chg[r & 1],
-                                                 w.chg[(r + 1) & 1], w.flags, r, status);
+                                                 w.chg[(r + 1) & 1], w.flags, r, status, make_coder(d));
         if (cudaMemcpyAsync(h, w.flags + r0, sizeof(uint32_t) * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
@@ -2516,7 +2554,7 @@ extern "C" lsrvt_status lsrvt_cvt_iterate_anyangle(const uint8_t *band, const ui
         cudaMemsetAsync(w.counters, 0, sizeof(int32_t), s);
         update_voxels_kernel<<<vgrid, 256, 0, s>>>(band, q, d, w.key[0], site_pos, w.clr, w.sums, w.los_bits, w.par,
                                                    w.nonlos, w.counters, nullptr, nullptr, small, w.src[0],
-                                                   rec ? rec + 3 : nullptr, w.emask);
+                                                   rec ? rec + 3 : nullptr, w.emask, make_coder(d));
         update_nonlos_kernel<<<sms * 8, 256, 0, s>>>(q, d, w.key[0], w.los_bits, w.par, w.nonlos, w.counters, w.sums,
                                                       status_dev, rec ? rec + 3 : nullptr);
         move_sites_kernel<<<grid_for(max_sites, 256, kSMs * 8), 256, 0, s>>>(band, d, site_pos, n_sites_dev,
