@@ -71,43 +71,6 @@ __device__ __forceinline__ void decode_voxel(uint32_t v, Dims d, int &x, int &y,
     y = (int)(r - (uint32_t)z * (uint32_t)d.ny);
 }
 
-// Division by a divisor fixed for a launch (Granlund & Montgomery 1994, "Division by invariant
-// integers using multiplication", the method for unsigned run-time invariant divisors): for
-// 1 <= d < 2^31 let l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, which fits in 32
-// bits; then floor(n / d) = (t + ((n - t) >> s1)) >> s2 for every 32-bit n, with t the high word
-// of m n, s1 = min(l, 1) and s2 = max(l - 1, 0).
-struct InvDiv {
-    uint32_t m;
-    int s1, s2;
-    __device__ __forceinline__ uint32_t div(uint32_t n) const {
-        const uint32_t t = __umulhi(m, n);
-        return (t + ((n - t) >> s1)) >> s2;
-    }
-};
-
-inline InvDiv make_invdiv(uint32_t d) {
-    int l = 0;
-    while ((1ull << l) < d) ++l;
-    InvDiv r;
-    r.m = (uint32_t)(((((1ull << l) - d) << 32) / d) + 1);
-    r.s1 = l < 1 ? l : 1;
-    r.s2 = l > 1 ? l - 1 : 0;
-    return r;
-}
-
-// decode_voxel with the two divisions by the volume's extents done by InvDiv
-struct VoxelCoder {
-    InvDiv by_nx, by_ny;
-    __device__ __forceinline__ void decode(uint32_t v, Dims d, int &x, int &y, int &z) const {
-        const uint32_t r = by_nx.div(v);
-        x = (int)(v - r * (uint32_t)d.nx);
-        z = (int)by_ny.div(r);
-        y = (int)(r - (uint32_t)z * (uint32_t)d.ny);
-    }
-};
-
-inline VoxelCoder make_coder(Dims d) { return VoxelCoder{make_invdiv((uint32_t)d.nx), make_invdiv((uint32_t)d.ny)}; }
-
 // CVT energy sum of m_v D(v)^2 (16.16 distances), exact in 128 bits: each thread keeps its
 // own sum, a warp folds its lanes' sums at the end of the kernel and adds them to the two
 // 64-bit words of the iteration's trace record (low word first, the carry detected from the

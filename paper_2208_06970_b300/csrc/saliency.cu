@@ -36,13 +36,13 @@ __device__ __forceinline__ float grad_pow(const float *__restrict__ f, Dims d, i
 }
 
 __global__ void __launch_bounds__(256) saliency_max_kernel(const float *__restrict__ f, Dims d, int gamma,
-                                                           unsigned *gmax_bits) {
+                                                           unsigned *gmax_bits, VoxelCoder vc) {
     int64_t n = d.n();
     float best = 0.0f;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t x = (int32_t)(v % d.nx);
-        int64_t r = v / d.nx;
-        float p = grad_pow(f, d, x, (int32_t)(r % d.ny), (int32_t)(r / d.ny), gamma);
+        int x, y, z;
+        vc.decode((uint32_t)v, d, x, y, z);
+        float p = grad_pow(f, d, x, y, z, gamma);
         if (isfinite(p) && p > best) best = p;
     }
 #pragma unroll
@@ -51,14 +51,15 @@ __global__ void __launch_bounds__(256) saliency_max_kernel(const float *__restri
 }
 
 __global__ void __launch_bounds__(256) saliency_q_kernel(const float *__restrict__ f, Dims d, int gamma,
-                                                         const unsigned *gmax_bits, uint16_t *__restrict__ q) {
+                                                         const unsigned *gmax_bits, uint16_t *__restrict__ q,
+                                                         VoxelCoder vc) {
     float gmax = __uint_as_float(*gmax_bits);
     float scale = gmax > 0.0f ? __fdiv_rn(65535.0f, gmax) : 0.0f;
     int64_t n = d.n();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t x = (int32_t)(v % d.nx);
-        int64_t r = v / d.nx;
-        float p = grad_pow(f, d, x, (int32_t)(r % d.ny), (int32_t)(r / d.ny), gamma);
+        int x, y, z;
+        vc.decode((uint32_t)v, d, x, y, z);
+        float p = grad_pow(f, d, x, y, z, gamma);
         float t = __fmul_rn(p, scale);
         uint16_t w = 1;
         if (isfinite(p) && t >= 0.5f) {
@@ -99,7 +100,8 @@ extern "C" lsrvt_status lsrvt_saliency_grad(const float *field, lsrvt_dims dd, i
     }
     unsigned *gmax = (unsigned *)ws;
     cudaMemsetAsync(gmax, 0, sizeof(unsigned), s);
-    saliency_max_kernel<<<grid, 256, 0, s>>>(field, d, gamma, gmax);
-    saliency_q_kernel<<<grid, 256, 0, s>>>(field, d, gamma, gmax, q);
+    const VoxelCoder vc = make_coder(d);
+    saliency_max_kernel<<<grid, 256, 0, s>>>(field, d, gamma, gmax, vc);
+    saliency_q_kernel<<<grid, 256, 0, s>>>(field, d, gamma, gmax, q, vc);
     return launch_status();
 }
