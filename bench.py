@@ -212,10 +212,10 @@ def gpu_arm(args, rank, world, local_rank):
                                  recipe=args.flame_recipe)
     field, aux, iso = w["field"], w["aux"], w["iso"]
     n = field.numel()
-    # the survey recipe shatters the isobands into more components than the default capacity:
+    # the sharp recipe shatters the isobands into more components than the default capacity:
     # count them once and size the component (and so the site and statistics) capacity to fit
     max_comp = None
-    if args.flame_recipe == "survey":
+    if args.flame_recipe == "sharp":
         b0 = pkg.classify(field, iso)
         nc0 = pkg.label_components(b0, max_comp=n // 4)[4]
         max_comp = int(nc0.item()) + 1024
@@ -923,8 +923,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lsrvt")
     ap.add_argument("--side", type=int, default=512)
-    ap.add_argument("--flame-recipe", default="resolved", choices=("resolved", "survey"),
-                    help="flame field: resolved front (default) or the survey's eta = 0, 4-voxel front")
+    ap.add_argument("--flame-recipe", default="resolved", choices=("resolved", "sharp"),
+                    help="flame field: resolved front (default) or the sharp one: eta = 0, 4-voxel front")
     ap.add_argument("--ref-side", type=int, default=96)
     ap.add_argument("--ref-iters", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -996,7 +996,7 @@ def main():
             dtype="int32/u64 labels, f32 float-float + f64 stats", data="synthetic",
             config=dict(workload="flame %d^3%s, 8 isovalues, |grad| weight, 1 site/4096 voxels, %d Lloyd iters, "
                                  "%d aux vars, %d bins" % (args.side, "" if args.flame_recipe == "resolved"
-                                                           else " (survey recipe: eta 0, front width 4)", N_ITERS,
+                                                           else " (sharp recipe: eta 0, front width 4)", N_ITERS,
                                                            N_AUX, N_BINS),
                         voxels=n, sites=r["n_sites"], components=r["n_comp"], parallelism="replicas" if world > 1
                         else "single", l2="inputs larger than L2 (field 512 MiB + aux 8 GiB), no flush"),

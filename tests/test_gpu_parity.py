@@ -385,11 +385,11 @@ def test_degenerate_volumes_end_to_end(pk, case):
         _moment_ok(cpu(got["mean"])[:ns], cpu(got["m2"])[:ns], stats["mean"], stats["m2"], stats["count"])
 
 
-def test_cvt_parity_survey_flame_recipe(pk):
-    """The survey's flame recipe (no dissipation cutoff, 4-voxel front) at 128^3 shatters the
+def test_cvt_parity_sharp_flame_recipe(pk):
+    """The sharp flame recipe (no dissipation cutoff, 4-voxel front) at 128^3 shatters the
     thin isobands into ~10^5 components, most of a few voxels: labels, seeds (at least one per
     component), two Lloyd iterations with |grad f| weights and the final cells, bit for bit."""
-    w = workloads.flame_workload(side=128, seed=2, n_aux=0, recipe="survey")
+    w = workloads.flame_workload(side=128, seed=2, n_aux=0, recipe="sharp")
     f = w["field"].numpy()
     band = oracle.classify(f, w["iso"])
     comp, cb, cs, cf = oracle.label_components(band)

@@ -14,7 +14,7 @@ Recipes (the five workloads):
   flame   : u = isotropic spectral field with amplitude ~ |k|^(-11/6) (E(k) ~ k^(-5/3))
             and a dissipation-range cutoff exp(-2.6 k eta), eta = 2 voxels, random phases,
             unit std; f = (1 + tanh((x - nx/2 + 24 u) / 8)) / 2, a progress-variable-like
-            front about 16 voxels thick.  Recipe "survey": eta = 0 (no cutoff) and tanh
+            front about 16 voxels thick.  Recipe "sharp": eta = 0 (no cutoff) and tanh
             width 4, which shatters the thin isobands into very many components.
   corr    : m correlated Gaussian variables x = mu + L z, L L^T = A A^T / m + 0.1 I.
 """
@@ -98,9 +98,9 @@ def spectral_field(dims, seed, device="cpu", slope=-11.0 / 6.0, eta=2.0):
 FLAME_RECIPES = {
     # a resolved front: dissipation-range cutoff (eta = 2 voxels), tanh width 8
     "resolved": dict(eta=2.0, width=8.0),
-    # the survey's recipe as written: pure k^-5/3 amplitudes to the grid scale, tanh width 4;
+    # a sharp front: pure k^-5/3 amplitudes to the grid scale, tanh width 4;
     # it breaks the thin isobands into very many small components
-    "survey": dict(eta=0.0, width=4.0),
+    "sharp": dict(eta=0.0, width=4.0),
 }
 
 
@@ -154,7 +154,7 @@ def blobs_workload(side=64, seed=1, device="cpu", n_aux=3):
 def flame_workload(side=512, seed=2, device="cpu", n_aux=16, n_iters=30, recipe="resolved"):
     """512^3 spectral-turbulence flame; 8 isovalues i/9; weight |grad f| (gamma 1);
     4096 voxels per site; 30 Lloyd iterations; 16 aux = (f, u, 14 spectral fields).
-    recipe: "resolved" (default) or "survey" (see FLAME_RECIPES)."""
+    recipe: "resolved" (default) or "sharp" (see FLAME_RECIPES)."""
     dims = (side, side, side) if np.isscalar(side) else tuple(side)
     f, u = flame_field(dims, seed, device, **FLAME_RECIPES[recipe])
     aux = torch.empty((n_aux,) + f.shape, dtype=torch.float32, device=device)
