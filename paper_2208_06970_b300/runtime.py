@@ -362,7 +362,8 @@ def pack_layout(dims, gap=1, footprint=None, res=8, max_side=2048):
     (width, depth) footprint kept at a resolution of `res` voxels -- the tallest block first,
     each at the lowest height its footprint (widened by the gap) allows, then the smallest y,
     then x.  footprint None: of a few candidate footprints, the one whose packed volume is the
-    smallest with every side at most max_side.  Returns (origins [(x0, y0, z0)], (NX, NY, NZ))."""
+    smallest with every side at most max_side and fewer than 2^31 voxels (the library's limit on a
+    volume).  Returns (origins [(x0, y0, z0)], (NX, NY, NZ))."""
     from numpy.lib.stride_tricks import sliding_window_view as windows
     dims = [tuple(int(v) for v in d) for d in dims]
     if gap < 1:
@@ -393,6 +394,8 @@ def pack_layout(dims, gap=1, footprint=None, res=8, max_side=2048):
         res_ = place(*footprint)
         if res_ is None:
             raise ValueError("a block does not fit the footprint %r" % (footprint,))
+        if res_[1][0] * res_[1][1] * res_[1][2] >= 1 << 31:
+            raise ValueError("the packed volume would hold 2^31 voxels or more")
         return res_
     wmin = max(d[0] for d in dims) + gap
     dmin = max(d[1] for d in dims) + gap
@@ -406,6 +409,8 @@ def pack_layout(dims, gap=1, footprint=None, res=8, max_side=2048):
             if r is None or max(r[1]) > max_side:
                 continue
             vol = r[1][0] * r[1][1] * r[1][2]
+            if vol >= 1 << 31:
+                continue
             if best is None or vol < best[0]:
                 best = (vol, r)
     if best is None:
@@ -490,7 +495,9 @@ class PackedBatch:
                 o["dist"] = torch.empty((nz, ny, nx), dtype=torch.int32, device=dev) if self.want_dist else None
                 blocks.append(dict(dims=self.dims[k], origin=self.origins[k], band=o["band"], q=o["q"],
                                    site_pos=o["site_pos"], n_sites=o["n_sites"], cell=o["cell"], dist=o["dist"]))
-            max_sites = sum(int(o["site_pos"].numel()) for o in outs)
+            # every block's site capacity, at most one site per voxel of the packed volume
+            nxp, nyp, nzp = self.packed
+            max_sites = min(sum(int(o["site_pos"].numel()) for o in outs), nxp * nyp * nzp)
             pband, pq, psp, pns, base = pack_blocks(blocks, self.packed, max_sites, want_q=outs[0]["q"] is not None,
                                                     status=status)
             pcell, pdist, trace = cvt_iterate(pband, pq, psp, pns, int(self.jobs[0]["n_iters"]),

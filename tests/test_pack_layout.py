@@ -98,3 +98,11 @@ def test_block_descriptor_matches_the_header():
     assert (B.x0.offset, B.band.offset, B.n_sites.offset, B.dist.offset) == (12, 24, 48, 64)
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lsrvt.h")).read()
     assert int(re.search(r"#define LSRVT_MAX_PACK_BLOCKS (\d+)", hdr).group(1)) == pkg.MAX_PACK_BLOCKS
+
+
+def test_layout_stays_below_the_volume_limit():
+    # eight 1024^3 blocks cannot share a volume of fewer than 2^31 voxels
+    with pytest.raises(ValueError):
+        runtime.pack_layout([(1024, 1024, 1024)] * 8, gap=1)
+    with pytest.raises(ValueError):
+        runtime.pack_layout([(1024, 1024, 1024)] * 2, gap=1, footprint=(2048, 1024))
